@@ -1,0 +1,312 @@
+"""Throughput of batched forward + adjoint rollouts on one GPU.
+
+One step = one forward rollout of T steps with a checkpoint every step, plus the
+adjoint rollout (recompute + hand-derived adjoint) that returns gradients with
+respect to the initial state, every joint torque and every link mass, for a
+batch of B independent articulated systems.  Default workload: 4096 serial
+7-DOF revolute chains, dt 1e-3, T = 1000, FP32.
+
+Prints one JSON line.  `--impl reference` times the CPU FP64 oracle on a bounded
+sample of the same workload instead.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "env-steps/s fwd+adjoint"
+
+# Algorithmic FLOPs per system-step of the kernels' formulation, from the
+# counting build of the step functions (paper_2109_07719_gb300/flopcount.cpp):
+# per revolute link with a parent / revolute root / free root, for the forward
+# step (kinematics + three passes + integration) and for the adjoint step.
+FLOPS = None  # filled by _flop_table()
+
+
+def _flop_table():
+    path = os.path.join(ROOT, "paper_2109_07719_gb300", "flops.json")
+    with open(path) as f:
+        return json.load(f)
+
+
+def flops_per_system_step(model, kind):
+    """kind: 'fwd' (forward step) or 'adj' (adjoint step without its recompute)."""
+    import numpy as np
+    tab = _flop_table()[kind]
+    jt = np.asarray(model.joint_type)
+    par = np.asarray(model.parent)
+    n_free = int((jt == 1).sum())
+    n_rev_root = int(((jt == 0) & (par < 0)).sum())
+    n_rev = int(((jt == 0) & (par >= 0)).sum())
+    return (tab["rev"] * n_rev + tab["rev_root"] * n_rev_root + tab["free_root"] * n_free) / model.n_systems
+
+
+def _clock_sampler(stop, out):
+    cmd = ["nvidia-smi", "--query-gpu=clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+           "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+           "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap",
+           "--format=csv,noheader,nounits", "-i", os.environ.get("CUDA_VISIBLE_DEVICES", "0").split(",")[0]]
+    while not stop.is_set():
+        try:
+            r = subprocess.run(cmd, capture_output=True, text=True, timeout=5)
+            if r.returncode == 0 and r.stdout.strip():
+                out.append([x.strip() for x in r.stdout.strip().split(",")])
+        except Exception:
+            pass
+        stop.wait(0.2)
+
+
+def _clocks_summary(samples):
+    if not samples:
+        return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
+    import statistics
+    sm = [float(s[0]) for s in samples if s[0].replace(".", "").isdigit()]
+    mx = [float(s[1]) for s in samples if s[1].replace(".", "").isdigit()]
+    names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+    reasons = sorted({names[i] for s in samples for i in range(4) if len(s) > 4 + i and s[4 + i] == "Active"})
+    return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+            "reasons": reasons, "samples": len(samples)}
+
+
+def _dist():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    return ws, rank
+
+
+def workload(cfg: int, precision: str, B=None, T=None):
+    import workloads as wl
+    kw = {}
+    if B:
+        kw["B"] = B
+    if T:
+        kw["T"] = T
+    if cfg != 1:
+        kw["precision"] = precision
+    return wl.config(cfg, **kw)
+
+
+def run_ours(args):
+    import numpy as np
+    import torch
+    import torch.distributed as dist
+    from paper_2109_07719_gb300 import Simulator
+
+    ws, rank = _dist()
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    if ws > 1:
+        dist.init_process_group("nccl")
+    work = workload(args.config, args.precision, args.batch, args.horizon)
+    m = work.model
+    T, k = work.T, args.k
+    sim = Simulator(m, precision=args.precision)
+    if args.block:
+        sim.set_block(args.block)
+    dev, dt = sim.device, sim.dtype
+    B = sim.B
+    q0 = torch.tensor(work.q0, dtype=dt, device=dev)
+    qd0 = torch.tensor(work.qd0, dtype=dt, device=dev)
+    tau = work.tau(device=dev, dtype=dt)
+    # output and scratch buffers, allocated once (the calls allocate nothing)
+    qT, qdT = sim.empty(sim.nq_max, B), sim.empty(sim.nv_max, B)
+    ck = sim.empty((T + k - 1) // k, sim.nx, B)
+    gq0, gqd0 = sim.empty(sim.nq_max, B), sim.empty(sim.nv_max, B)
+    gtau = sim.empty(T, sim.nv_max, B)
+    gm = sim.empty(sim.n_links)
+    wb = sim.work_bytes(k)
+    work_buf = torch.empty(max(wb, 1), dtype=torch.uint8, device=dev)
+    gqT = torch.ones_like(qT)
+    gqdT = torch.zeros_like(qdT)
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+    stream = torch.cuda.current_stream()
+
+    def step(evs=None):
+        if evs:
+            evs[0].record(stream)
+        sim.rollout(q0, qd0, tau, k=k, out=(qT, qdT, ck, None))
+        if evs:
+            evs[1].record(stream)
+        sim.backward(ck, tau, gqT, gqdT, k=k, work=work_buf, out=(gq0, gqd0, gtau, gm))
+        if evs:
+            evs[2].record(stream)
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    stop = threading.Event()
+    samples = []
+    th = threading.Thread(target=_clock_sampler, args=(stop, samples), daemon=True)
+    th.start()
+    time.sleep(0.3)
+    events = [[torch.cuda.Event(enable_timing=True) for _ in range(3)] for _ in range(args.steps)]
+    if ws > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    for i in range(args.steps):
+        flush.fill_(float(i))            # evict L2 between timed steps (not timed)
+        step(events[i])
+    torch.cuda.synchronize()
+    if ws > 1:
+        dist.barrier()
+    stop.set()
+    th.join()
+    fwd_ms = [e[0].elapsed_time(e[1]) for e in events]
+    adj_ms = [e[1].elapsed_time(e[2]) for e in events]
+    step_ms = float(np.sum(fwd_ms) + np.sum(adj_ms)) / args.steps
+    t = torch.tensor([step_ms], device=dev)
+    if ws > 1:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    step_ms = float(t.item())
+    flags = sim.status()
+    units = B * T * ws
+    value = units / (step_ms / 1e3)
+    # end to end through the public API with host buffers
+    e2e = run_e2e(sim, work, k, args.steps, tau.cpu().pin_memory(), q0.cpu().pin_memory(),
+                  qd0.cpu().pin_memory())
+    if rank != 0:
+        return None
+    f_fwd = flops_per_system_step(m, "fwd")
+    f_adj = flops_per_system_step(m, "adj")
+    adj_flops = B * T * (f_fwd + f_adj)
+    adj_s = float(np.mean(adj_ms)) / 1e3
+    clocks = _clocks_summary(samples)
+    peak = fp_peak(args.precision)
+    achieved = adj_flops / adj_s / 1e12
+    line = {
+        "metric": METRIC, "value": value, "unit": "env-steps/s", "n_gpus": ws, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": step_ms, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": {"fp64": "f64", "fp32": "f32", "fp32_d64": "f32+f64"}[args.precision],
+        "data": "synthetic",
+        "config": {"workload": m.name, "n_systems": B, "horizon": T, "dt": m.dt, "checkpoint_interval": k,
+                   "precision": args.precision, "l2": "flushed between steps (256 MB write)",
+                   "parallelism": f"replicas x{ws}" if ws > 1 else "single GPU", "block": sim_block(args)},
+        "fwd_env_steps_per_s": B * T / (float(np.mean(fwd_ms)) / 1e3),
+        "ms_fwd": float(np.mean(fwd_ms)), "ms_adj": float(np.mean(adj_ms)),
+        "roofline": {"bound": "alu", "kernel": "k_backward", "achieved": achieved, "peak": peak["tflops"],
+                     "unit": "TFLOP/s", "frac": achieved / peak["tflops"], "traffic": None,
+                     "flops_per_system_step": {"fwd": f_fwd, "adj": f_adj}, "peak_note": peak["note"]},
+        "e2e": e2e,
+        "gpu_launches": args.steps * 3,
+        "clocks": clocks,
+        "nonfinite_systems": int((flags != 0).sum()),
+    }
+    if args.cpu_baseline:
+        line["cpu_baseline"] = cpu_baseline(args)
+    return line
+
+
+def sim_block(args):
+    return args.block or 32
+
+
+def fp_peak(precision):
+    """Plain-ALU peak from unit counts and the maximum SM clock: 152 SMs x 128 FP32
+    lanes x 2 FLOP per FMA x 2.07 GHz (FP64: the nominal 1.25 TFLOP/s)."""
+    if precision == "fp64":
+        return {"tflops": 1.25, "note": "nominal FP64 vector rate of GB300 (1.25 TFLOP/s)"}
+    return {"tflops": 152 * 128 * 2 * 2.07e9 / 1e12, "note": "152 SM x 128 FP32 lanes x 2 x 2.07 GHz"}
+
+
+def run_e2e(sim, work, k, steps, tau_h, q0_h, qd0_h):
+    """Same metric through the public API with host inputs: the step's H2D copy of
+    (q0, qd0, tau) and D2H read of the gradients inside the timed region."""
+    import torch
+    from paper_2109_07719_gb300 import Rollout
+    dev = sim.device
+    gq_h = torch.empty(q0_h.shape, dtype=q0_h.dtype).pin_memory()
+    gtau_h = torch.empty(tau_h.shape, dtype=tau_h.dtype).pin_memory()
+    times = []
+    for i in range(steps + 1):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        q0 = q0_h.to(dev, non_blocking=True).requires_grad_(True)
+        qd0 = qd0_h.to(dev, non_blocking=True).requires_grad_(True)
+        tau = tau_h.to(dev, non_blocking=True).requires_grad_(True)
+        qT, qdT = Rollout.apply(sim, q0, qd0, tau, None, k)
+        qT.sum().backward()
+        gq_h.copy_(q0.grad, non_blocking=True)
+        gtau_h.copy_(tau.grad, non_blocking=True)
+        torch.cuda.synchronize()
+        if i:
+            times.append(time.perf_counter() - t0)
+    s = sum(times) / len(times)
+    es = tau_h.element_size()
+    return {"value": sim.B * work.T / s, "unit": "env-steps/s",
+            "h2d_bytes_per_step": (q0_h.numel() + qd0_h.numel() + tau_h.numel()) * es,
+            "d2h_bytes_per_step": (gq_h.numel() + gtau_h.numel()) * es}
+
+
+def cpu_baseline(args, budget_s: float = 15.0):
+    """The FP64 oracle (forward + adjoint, one-step recompute) on a bounded sample:
+    a few systems of the workload over a short horizon, scaled to env-steps/s."""
+    import numpy as np
+    import torch
+    from oracle.dynamics import OracleModel
+    from oracle.rollout import rollout_backward
+    threads = torch.get_num_threads()
+    work = workload(args.config, args.precision, 16, 20)
+    m = work.model
+    sys_ = list(range(min(16, m.n_systems)))
+    done = 0
+    t0 = time.perf_counter()
+    T = 20
+    tau = work.tau(T=T)
+    while time.perf_counter() - t0 < budget_s:
+        om = OracleModel(m, sys_)
+        q0 = torch.tensor(work.q0[:om.nq, sys_].T)
+        qd0 = torch.tensor(work.qd0[:om.nv, sys_].T)
+        ot = tau[:, :om.nv, sys_].permute(0, 2, 1).contiguous()
+        rollout_backward(om, q0, qd0, ot, torch.ones_like(q0), torch.zeros_like(qd0))
+        done += len(sys_) * T
+    el = time.perf_counter() - t0
+    return {"value": done / el, "unit": "env-steps/s", "cores": threads, "kind": "oracle",
+            "sample": f"{len(sys_)} systems x {T} steps of the same workload, repeated for {el:.1f} s "
+                      f"(FP64 CRBA+RNEA forward, per-step recompute + reverse-mode step adjoint)"}
+
+
+def run_reference(args):
+    ws, rank = _dist()
+    if rank != 0:
+        return None
+    cb = cpu_baseline(args, budget_s=max(5.0, 10.0 * args.steps / max(args.steps, 1)))
+    line = {"impl": "reference", "metric": METRIC, "value": cb["value"], "unit": "env-steps/s",
+            "n_gpus": ws, "steps": args.steps, "warmup": args.warmup, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": workload(args.config, args.precision, 4, 1).model.name,
+                       "note": "CPU FP64 oracle, bounded sample"},
+            "cpu_baseline": cb,
+            "e2e": {"value": cb["value"], "unit": "env-steps/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    return line
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--config", type=int, default=2)
+    ap.add_argument("--precision", default="fp32", choices=["fp64", "fp32", "fp32_d64"])
+    ap.add_argument("--batch", type=int, default=None)
+    ap.add_argument("--horizon", type=int, default=None)
+    ap.add_argument("--k", type=int, default=1)
+    ap.add_argument("--block", type=int, default=0)
+    ap.add_argument("--no-cpu-baseline", dest="cpu_baseline", action="store_false")
+    args = ap.parse_args()
+    args.warmup = max(args.warmup, 3)
+    line = run_reference(args) if args.impl == "reference" else run_ours(args)
+    if line is not None:
+        print(json.dumps(line))
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,155 @@
+/*
+ * abasim: batched, differentiable articulated-body simulation on one GPU (C ABI).
+ *
+ * Computes, for many independent articulated systems at once, time-stepped
+ * forward dynamics with Featherstone's Articulated Body Algorithm plus an Euler
+ * integrator, and the reverse-mode adjoint of that rollout with only the
+ * per-step initial states checkpointed and the intermediates recomputed during
+ * backprop (Qiao et al., "Efficient Differentiable Simulation of Articulated
+ * Bodies", ICML 2021: problem statement Sec. 2; step modules and adjoint Sec. 3.1,
+ * Eq. 3-6; checkpointing Sec. 3.2, Eq. 7; checkpoint interval supplement Sec. B).
+ *
+ * Layouts.  Every per-system array is structure-of-arrays with the system index
+ * fastest and the coordinate index zero-padded to the batch maximum:
+ *   q    [nq_max][B]        generalized positions (revolute angle; free joint:
+ *                           world position p then unit quaternion x y z w)
+ *   qd   [nv_max][B]        generalized velocities (free joint: body-frame
+ *                           angular then linear velocity)
+ *   tau  [T][nv_max][B]     joint forces; tau^t acts over step t -> t+1
+ *   ckpt [ceil(T/k)][nq_max+nv_max][B]   x^t = (q^t, qd^t) for t = 0, k, 2k, ...
+ *   traj [T+1][nq_max+nv_max][B]         x^0 .. x^T (optional)
+ * Scalars are double for SIM_FP64 and float for SIM_FP32 / SIM_FP32_D64.
+ * Per-link arrays (gmass, set_masses) follow the link order of the model
+ * description (CSR by system).
+ *
+ * Ownership.  Every array argument of the step / rollout / backward calls is
+ * DEVICE memory owned by the caller, on the device that was current at
+ * sim_create.  Those calls allocate nothing; they enqueue kernels on `stream`
+ * (a cudaStream_t, NULL = legacy default stream) and return without waiting.
+ * Model constants, the per-step tape and the status words are owned by the
+ * handle.
+ *
+ * Errors.  Every call returns SIM_OK (0) or a negative SIM_E* code and stores a
+ * message readable with sim_last_error(handle) (sim_last_error(NULL) for a
+ * failed sim_create).  Non-finite results are reported per system through
+ * sim_status, never by a trap.
+ */
+#ifndef ABASIM_H
+#define ABASIM_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define SIM_OK 0
+#define SIM_EINVAL (-1)      /* bad model, size or pointer */
+#define SIM_ECUDA (-2)       /* a CUDA runtime call failed */
+#define SIM_ENOMEM (-3)      /* device allocation or caller workspace too small */
+#define SIM_ENONFINITE (-4)  /* sim_status: some system produced NaN/Inf */
+#define SIM_EUNSUPPORTED (-6)
+
+enum sim_precision { SIM_FP64 = 0, SIM_FP32 = 1, SIM_FP32_D64 = 2 };
+enum sim_integrator { SIM_SEMI_IMPLICIT_EULER = 0, SIM_EXPLICIT_EULER = 1 };
+enum sim_joint { SIM_REVOLUTE = 0, SIM_FREE = 1 };
+
+/* Model description, host memory, copied by sim_create.
+ * Links are stored CSR by system (sys_link_offset[n_systems+1]); within a system
+ * they are in topological order: parent[l] is the parent's index inside the
+ * same system and must be < l, or -1 for the world.  A SIM_FREE joint is allowed
+ * only on a system's first link (the floating base).  Per link:
+ *   axis[3]     unit rotation axis in the link frame (revolute)
+ *   X_tree[12]  parent frame -> joint frame: rotation E (row major, 9) then the
+ *               joint origin r in parent coordinates (3); motion vectors map as
+ *               [E w; E (v - r x w)] (the supplement's st_apply)
+ *   mass, com[3], I_com[6]  rigid-body inertia: mass, centre of mass in the link
+ *               frame, rotational inertia about the COM (xx yy zz xy xz yz)
+ * gravity[3] is the world-frame gravitational acceleration (e.g. 0 0 -9.81).  */
+typedef struct sim_model_desc {
+  int32_t n_systems;
+  int32_t precision;   /* enum sim_precision */
+  int32_t integrator;  /* enum sim_integrator */
+  int32_t reserved;
+  double dt;
+  double gravity[3];
+  const int32_t* sys_link_offset;
+  const int32_t* parent;
+  const int32_t* joint_type;
+  const double* axis;
+  const double* X_tree;
+  const double* mass;
+  const double* com;
+  const double* I_com;
+} sim_model_desc;
+
+typedef struct sim_handle sim_handle;
+
+/* Validate and pack a model (Sec. 2: state x = [q, qd], control u = tau), upload
+ * its constants to the current device and allocate the per-step tape.
+ * Returns SIM_EINVAL with a message for an invalid tree, joint, axis, rotation or
+ * inertia; SIM_ENOMEM / SIM_ECUDA for device failures.  *out is NULL on error. */
+int sim_create(const sim_model_desc* desc, sim_handle** out);
+
+/* Free every device and host resource of the handle.  NULL is ignored. */
+void sim_destroy(sim_handle* h);
+
+/* Batch dimensions: number of systems, padded coordinate counts, links. */
+int sim_dims(const sim_handle* h, int32_t* n_systems, int32_t* nq_max, int32_t* nv_max,
+             int32_t* n_links_total);
+
+/* Bytes of the checkpoint buffer for a T-step rollout with interval k >= 1:
+ * ceil(T/k) states (Sec. 3.2; the supplement's memory model n/k * m_ckpt). */
+size_t sim_ckpt_bytes(const sim_handle* h, int64_t T, int32_t k);
+
+/* Bytes of caller workspace sim_backward_rollout needs for interval k (the k
+ * replayed states of one segment); 0 for k == 1. */
+size_t sim_work_bytes(const sim_handle* h, int32_t k);
+
+/* Replace every link mass from a device array [n_links_total] of the handle's
+ * scalar type, COM and rotational inertia held fixed.  Stream ordered. */
+int sim_set_masses(sim_handle* h, const void* mass, void* stream);
+
+/* One step x -> x' for every system (Sec. 3.1: kinematics, the three ABA passes,
+ * integration).  q, qd may alias q_out, qd_out. */
+int sim_step_batch(sim_handle* h, const void* q, const void* qd, const void* tau, void* q_out,
+                   void* qd_out, void* stream);
+
+/* T steps from (q0, qd0) under tau [T][nv_max][B].  Writes x^T to (qT, qdT),
+ * the checkpoints x^0, x^k, ... to ckpt (if non-NULL; sim_ckpt_bytes(T, k)
+ * bytes) and every state to traj (if non-NULL).  T == 0 copies the input. */
+int sim_rollout(sim_handle* h, const void* q0, const void* qd0, const void* tau, int64_t T,
+                int32_t k, void* ckpt, void* qT, void* qdT, void* traj, void* stream);
+
+/* Adjoint of sim_rollout (Sec. 3.1 Eq. 3-4: R^k = xbar^k pulled back step by step;
+ * Sec. 3.2 Eq. 7: each step recomputed from its checkpoint; for k > 1 each
+ * segment is replayed forward once into `work` and then differentiated).
+ * Seeds: gqT, gqdT = dPhi/dx^T; g_traj (optional, traj layout) adds dPhi/dx^t
+ * for t = 0..T.  Outputs (overwritten): gq0, gqd0 = dPhi/dx^0, gtau
+ * [T][nv_max][B] = dPhi/dtau, gmass [n_links_total] = dPhi/dm (optional; COM and
+ * rotational inertia held fixed).  Padded coordinates come back as 0. */
+int sim_backward_rollout(sim_handle* h, const void* ckpt, const void* tau, int64_t T, int32_t k,
+                         const void* gqT, const void* gqdT, const void* g_traj, void* gq0,
+                         void* gqd0, void* gtau, void* gmass, void* work, size_t work_bytes,
+                         void* stream);
+
+/* Copy the per-system status words to host memory flags[n_systems] (bit 0:
+ * a non-finite state or gradient was produced since the last sim_clear_status)
+ * after synchronizing the device.  Returns SIM_ENONFINITE if any bit is set. */
+int sim_status(sim_handle* h, int32_t* flags);
+int sim_clear_status(sim_handle* h, void* stream);
+
+/* Select the threads per block of the batched kernels (a multiple of 32, at
+ * most 1024); 0 restores the default.  The autotuner drives this. */
+int sim_set_block(sim_handle* h, int32_t threads);
+
+/* Message of the last failed call on h (or of the last failed sim_create when h
+ * is NULL).  Owned by the library, valid until the next call on h. */
+const char* sim_last_error(const sim_handle* h);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* ABASIM_H */

@@ -1,0 +1,524 @@
+// One simulation step of one articulated system and its reverse-mode adjoint.
+//
+// Forward (Sec. 3.1, Fig. 1): joint transforms, then the Articulated Body
+// Algorithm's three tree passes (root->leaves kinematics/velocities, leaves->root
+// articulated inertias and bias forces, root->leaves accelerations), then time
+// integration.  Adjoint: the same modules in reverse order (Sec. 3.1), each
+// spatial operator replaced by its adjoint (Eq. 6 and the supplement's rules,
+// re-derived in the standard dPhi/dE convention).  The adjoint step is run after
+// a recompute of the forward intermediates from the step's initial state
+// (Sec. 3.2, Eq. 7): the per-link intermediates Z^k live in a per-step tape that
+// is overwritten every step, never kept across steps.
+//
+// Joint models: revolute about a unit axis a (S = [a; 0], E_J = R(a, q)^T) and a
+// free root joint (q = world position p and unit quaternion (x, y, z, w),
+// qd = body-frame spatial velocity, S = 1_6, E_J = R(quat)^T, r_J = p).
+// Integrator: semi-implicit Euler (qd' = qd + dt qdd, q' = q + dt qd') or
+// explicit Euler (q' = q + dt qd); the free joint integrates p' = p + dt R v and
+// quat' = normalize(quat + dt/2 quat (x) (w, 0)).
+#pragma once
+
+#include "spatial.cuh"
+
+namespace abasim {
+
+enum JointType : int { J_REVOLUTE = 0, J_FREE = 1 };
+enum Integrator : int { I_SEMI_IMPLICIT = 0, I_EXPLICIT = 1 };
+
+// per-link model parameters, [link][field][system]
+enum : int { P_E = 0, P_R = 9, P_AX = 12, P_M = 15, P_C = 16, P_IC = 19, NPRM = 25 };
+// per-link forward tape
+enum : int {
+  T_E = 0, T_R = 9, T_V = 12, T_C = 18, T_H = 24, T_IA = 30, T_PA = 51, T_U = 57, T_D = 63,
+  T_DI = 64, T_u = 65, T_Ia = 71, T_pa = 92, T_AP = 98, T_A = 104, T_QDD = 110, T_SC = 116, NTAPE = 118
+};
+// per-link adjoint accumulators
+enum : int {
+  G_A = 0, G_C = 6, G_E = 12, G_R = 21, G_U = 24, G_D = 30, G_u = 31, G_IA = 37, G_PA = 58,
+  G_V = 64, G_QDD = 70, NADJ = 76
+};
+
+// meta word per link: parent+1 (8 bits) | joint type (2) | q offset (11) | v offset (11)
+SD int meta_parent(int m) { return (m & 0xff) - 1; }
+SD int meta_jtype(int m) { return (m >> 8) & 0x3; }
+SD int meta_qoff(int m) { return (m >> 10) & 0x7ff; }
+SD int meta_voff(int m) { return (m >> 21) & 0x7ff; }
+SD int make_meta(int parent, int jt, int qo, int vo) {
+  return (parent + 1) | (jt << 8) | (qo << 10) | (vo << 21);
+}
+
+template <class T> SD void sincos_t(T x, T* s, T* c);
+template <> SD void sincos_t<float>(float x, float* s, float* c) {
+#ifdef __CUDA_ARCH__
+  sincosf(x, s, c);
+#else
+  *s = sinf(x); *c = cosf(x);
+#endif
+}
+template <> SD void sincos_t<double>(double x, double* s, double* c) {
+#ifdef __CUDA_ARCH__
+  sincos(x, s, c);
+#else
+  *s = sin(x); *c = cos(x);
+#endif
+}
+template <class T> SD T sqrt_t(T x) { return sqrt(x); }
+
+// Strided column of one system: element d lives at p[d * B].
+template <class T> struct Col {
+  T* p;
+  long long B;
+  SD T& operator[](int d) const { return p[(long long)d * B]; }
+};
+
+// The per-system view used by the step functions.
+template <class T> struct Sys {
+  const T* prm;   // [maxL][NPRM][B] + slot
+  const int* meta;  // [maxL][B] + slot
+  T* tape;        // [maxL][NTAPE][B] + slot
+  T* adj;         // [maxL][NADJ][B] + slot
+  long long B;
+  int nl;
+  SD T P(int l, int f) const { return prm[((long long)l * NPRM + f) * B]; }
+  SD int M(int l) const { return meta[(long long)l * B]; }
+  SD T& tp(int l, int f) const { return tape[((long long)l * NTAPE + f) * B]; }
+  SD T& ad(int l, int f) const { return adj[((long long)l * NADJ + f) * B]; }
+
+  // ---- field helpers
+  SD V3<T> pv3(int l, int f) const { return {P(l, f), P(l, f + 1), P(l, f + 2)}; }
+  SD M3<T> pm3(int l, int f) const { M3<T> m; for (int i = 0; i < 9; ++i) m.a[i] = P(l, f + i); return m; }
+  SD S3<T> ps3(int l, int f) const { return {P(l, f), P(l, f + 1), P(l, f + 2), P(l, f + 3), P(l, f + 4), P(l, f + 5)}; }
+};
+
+#define ABASIM_FIELD_IO(NAME, ACC)                                                                   \
+  template <class T> SD V3<T> NAME##_v3(const Sys<T>& s, int l, int f) {                              \
+    return {s.ACC(l, f), s.ACC(l, f + 1), s.ACC(l, f + 2)};                                           \
+  }                                                                                                  \
+  template <class T> SD void NAME##_v3(const Sys<T>& s, int l, int f, V3<T> v) {                      \
+    s.ACC(l, f) = v.x; s.ACC(l, f + 1) = v.y; s.ACC(l, f + 2) = v.z;                                  \
+  }                                                                                                  \
+  template <class T> SD SV<T> NAME##_sv(const Sys<T>& s, int l, int f) {                              \
+    return {NAME##_v3(s, l, f), NAME##_v3(s, l, f + 3)};                                              \
+  }                                                                                                  \
+  template <class T> SD void NAME##_sv(const Sys<T>& s, int l, int f, SV<T> v) {                      \
+    NAME##_v3(s, l, f, v.w); NAME##_v3(s, l, f + 3, v.v);                                             \
+  }                                                                                                  \
+  template <class T> SD M3<T> NAME##_m3(const Sys<T>& s, int l, int f) {                              \
+    M3<T> m; for (int i = 0; i < 9; ++i) m.a[i] = s.ACC(l, f + i); return m;                          \
+  }                                                                                                  \
+  template <class T> SD void NAME##_m3(const Sys<T>& s, int l, int f, const M3<T>& m) {               \
+    for (int i = 0; i < 9; ++i) s.ACC(l, f + i) = m.a[i];                                             \
+  }                                                                                                  \
+  template <class T> SD S3<T> NAME##_s3(const Sys<T>& s, int l, int f) {                              \
+    return {s.ACC(l, f), s.ACC(l, f + 1), s.ACC(l, f + 2), s.ACC(l, f + 3), s.ACC(l, f + 4), s.ACC(l, f + 5)}; \
+  }                                                                                                  \
+  template <class T> SD void NAME##_s3(const Sys<T>& s, int l, int f, const S3<T>& v) {               \
+    s.ACC(l, f) = v.xx; s.ACC(l, f + 1) = v.yy; s.ACC(l, f + 2) = v.zz;                               \
+    s.ACC(l, f + 3) = v.xy; s.ACC(l, f + 4) = v.xz; s.ACC(l, f + 5) = v.yz;                           \
+  }                                                                                                  \
+  template <class T> SD SI<T> NAME##_si(const Sys<T>& s, int l, int f) {                              \
+    return {NAME##_s3(s, l, f), NAME##_m3(s, l, f + 6), NAME##_s3(s, l, f + 15)};                     \
+  }                                                                                                  \
+  template <class T> SD void NAME##_si(const Sys<T>& s, int l, int f, const SI<T>& v) {               \
+    NAME##_s3(s, l, f, v.A); NAME##_m3(s, l, f + 6, v.B); NAME##_s3(s, l, f + 15, v.C);               \
+  }                                                                                                  \
+  template <class T> SD XF<T> NAME##_xf(const Sys<T>& s, int l, int f) {                              \
+    return {NAME##_m3(s, l, f), NAME##_v3(s, l, f + 9)};                                              \
+  }                                                                                                  \
+  template <class T> SD void NAME##_xf(const Sys<T>& s, int l, int f, const XF<T>& v) {               \
+    NAME##_m3(s, l, f, v.E); NAME##_v3(s, l, f + 9, v.r);                                             \
+  }
+
+ABASIM_FIELD_IO(tp, tp)
+ABASIM_FIELD_IO(ad, ad)
+#undef ABASIM_FIELD_IO
+
+// ------------------------------------------------------------------ 6x6 SPD solve
+// Cholesky of a symmetric 6x6 given in block form; L stored row-major lower
+// triangle (21 numbers).  Used for the free root's D = S^T I^A S = I^A.
+template <class T> SD void si_full(const SI<T>& I, T* F) {  // 36, row major
+  M3<T> A = full(I.A), C = full(I.C);
+  for (int i = 0; i < 3; ++i)
+    for (int j = 0; j < 3; ++j) {
+      F[i * 6 + j] = A.a[3 * i + j];
+      F[i * 6 + 3 + j] = I.B.a[3 * i + j];
+      F[(3 + i) * 6 + j] = I.B.a[3 * j + i];
+      F[(3 + i) * 6 + 3 + j] = C.a[3 * i + j];
+    }
+}
+template <class T> SD void chol6(const SI<T>& I, T* L) {
+  T F[36];
+  si_full(I, F);
+  for (int i = 0; i < 6; ++i) {
+    for (int j = 0; j <= i; ++j) {
+      T s = F[i * 6 + j];
+      for (int k = 0; k < j; ++k) s -= L[i * (i + 1) / 2 + k] * L[j * (j + 1) / 2 + k];
+      if (i == j) L[i * (i + 1) / 2 + i] = sqrt_t(s);
+      else L[i * (i + 1) / 2 + j] = s / L[j * (j + 1) / 2 + j];
+    }
+  }
+}
+template <class T> SD SV<T> chol6_solve(const T* L, SV<T> b) {
+  T x[6] = {b.w.x, b.w.y, b.w.z, b.v.x, b.v.y, b.v.z};
+  for (int i = 0; i < 6; ++i) {
+    T s = x[i];
+    for (int k = 0; k < i; ++k) s -= L[i * (i + 1) / 2 + k] * x[k];
+    x[i] = s / L[i * (i + 1) / 2 + i];
+  }
+  for (int i = 5; i >= 0; --i) {
+    T s = x[i];
+    for (int k = i + 1; k < 6; ++k) s -= L[k * (k + 1) / 2 + i] * x[k];
+    x[i] = s / L[i * (i + 1) / 2 + i];
+  }
+  return {{x[0], x[1], x[2]}, {x[3], x[4], x[5]}};
+}
+
+// ------------------------------------------------------------------ forward
+// Runs jcalc and the three ABA passes for the state (q, qd) and joint force tau,
+// leaving every intermediate on the tape (qdd included).
+template <class T>
+SD void aba_forward(const Sys<T>& s, Col<const T> q, Col<const T> qd, Col<const T> tau, V3<T> grav) {
+  const int nl = s.nl;
+  // jcalc + pass 1 (root -> leaves)
+  for (int l = 0; l < nl; ++l) {
+    const int m = s.M(l);
+    const int par = meta_parent(m), jt = meta_jtype(m), qo = meta_qoff(m), vo = meta_voff(m);
+    M3<T> Et = s.pm3(l, P_E);
+    V3<T> rt = s.pv3(l, P_R);
+    XF<T> X;
+    SV<T> vJ;
+    if (jt == J_REVOLUTE) {
+      V3<T> a = s.pv3(l, P_AX);
+      T sn, cs;
+      sincos_t(q[qo], &sn, &cs);
+      s.tp(l, T_SC) = sn;
+      s.tp(l, T_SC + 1) = cs;
+      X = XF<T>{mm(rot_axis_T(a, sn, cs), Et), rt};
+      vJ = SV<T>{qd[vo] * a, zero3<T>()};
+    } else {
+      V3<T> p{q[qo], q[qo + 1], q[qo + 2]};
+      M3<T> EJ = transpose(quat_R(q[qo + 3], q[qo + 4], q[qo + 5], q[qo + 6]));
+      X = compose(EJ, p, Et, rt);
+      vJ = SV<T>{{qd[vo], qd[vo + 1], qd[vo + 2]}, {qd[vo + 3], qd[vo + 4], qd[vo + 5]}};
+    }
+    SV<T> v = vJ;
+    if (par >= 0) v += apply(X, tp_sv(s, par, T_V));
+    SV<T> c = crossm(v, vJ);
+    SI<T> I = rbi(s.P(l, P_M), s.pv3(l, P_C), s.ps3(l, P_IC));
+    SV<T> h = mul(I, v);
+    tp_xf(s, l, T_E, X);
+    tp_sv(s, l, T_V, v);
+    tp_sv(s, l, T_C, c);
+    tp_sv(s, l, T_H, h);
+    tp_si(s, l, T_IA, I);
+    tp_sv(s, l, T_PA, crossf(v, h));
+  }
+  // pass 2 (leaves -> root)
+  for (int l = nl - 1; l >= 0; --l) {
+    const int m = s.M(l);
+    const int par = meta_parent(m), jt = meta_jtype(m), vo = meta_voff(m);
+    SI<T> IA = tp_si(s, l, T_IA);
+    SV<T> pA = tp_sv(s, l, T_PA);
+    if (jt == J_REVOLUTE) {
+      V3<T> a = s.pv3(l, P_AX);
+      SV<T> U{mul(IA.A, a), mulT(IA.B, a)};
+      T D = dot(a, U.w);
+      T Di = T(1) / D;
+      T u = tau[vo] - dot(a, pA.w);
+      tp_sv(s, l, T_U, U);
+      s.tp(l, T_D) = D;
+      s.tp(l, T_DI) = Di;
+      s.tp(l, T_u) = u;
+      if (par >= 0) {
+        SI<T> Ia = IA - scale(Di, sym_outer(U, U));
+        SV<T> pa = pA + mul(Ia, tp_sv(s, l, T_C)) + (u * Di) * U;
+        tp_si(s, l, T_Ia, Ia);
+        tp_sv(s, l, T_pa, pa);
+        XF<T> X = tp_xf(s, l, T_E);
+        tp_si(s, par, T_IA, tp_si(s, par, T_IA) + congruence(X, Ia));
+        tp_sv(s, par, T_PA, tp_sv(s, par, T_PA) + applyT(X, pa));
+      }
+    } else {  // free root: D = I^A, u = tau - p^A
+      SV<T> u{{tau[vo], tau[vo + 1], tau[vo + 2]}, {tau[vo + 3], tau[vo + 4], tau[vo + 5]}};
+      u -= pA;
+      T L[21];
+      chol6(IA, L);
+      for (int i = 0; i < 21; ++i) s.tp(l, T_Ia + i) = L[i];
+      tp_sv(s, l, T_u, u);
+    }
+  }
+  // pass 3 (root -> leaves)
+  const SV<T> a0{zero3<T>(), -grav};
+  for (int l = 0; l < nl; ++l) {
+    const int m = s.M(l);
+    const int par = meta_parent(m), jt = meta_jtype(m);
+    XF<T> X = tp_xf(s, l, T_E);
+    SV<T> ap = apply(X, par >= 0 ? tp_sv(s, par, T_A) : a0) + tp_sv(s, l, T_C);
+    SV<T> a;
+    if (jt == J_REVOLUTE) {
+      V3<T> ax = s.pv3(l, P_AX);
+      T qdd = (s.tp(l, T_u) - dot(tp_sv(s, l, T_U), ap)) * s.tp(l, T_DI);
+      s.tp(l, T_QDD) = qdd;
+      a = ap;
+      a.w += qdd * ax;
+    } else {
+      T L[21];
+      for (int i = 0; i < 21; ++i) L[i] = s.tp(l, T_Ia + i);
+      a = chol6_solve(L, tp_sv(s, l, T_u));
+      tp_sv(s, l, T_QDD, a - ap);
+    }
+    tp_sv(s, l, T_AP, ap);
+    tp_sv(s, l, T_A, a);
+  }
+}
+
+// Integrates x -> x' in place from the qdd on the tape.
+template <class T>
+SD void integrate(const Sys<T>& s, Col<T> q, Col<T> qd, T dt, int integ) {
+  for (int l = 0; l < s.nl; ++l) {
+    const int m = s.M(l);
+    const int jt = meta_jtype(m), qo = meta_qoff(m), vo = meta_voff(m);
+    if (jt == J_REVOLUTE) {
+      T v0 = qd[vo];
+      T v1 = v0 + dt * s.tp(l, T_QDD);
+      qd[vo] = v1;
+      q[qo] = q[qo] + dt * (integ == I_SEMI_IMPLICIT ? v1 : v0);
+    } else {
+      T nu[6];
+      for (int i = 0; i < 6; ++i) {
+        T v0 = qd[vo + i];
+        T v1 = v0 + dt * s.tp(l, T_QDD + i);
+        qd[vo + i] = v1;
+        nu[i] = integ == I_SEMI_IMPLICIT ? v1 : v0;
+      }
+      T qt[4] = {q[qo + 3], q[qo + 4], q[qo + 5], q[qo + 6]};
+      V3<T> dp = mul(quat_R(qt[0], qt[1], qt[2], qt[3]), V3<T>{nu[3], nu[4], nu[5]});
+      q[qo] = q[qo] + dt * dp.x;
+      q[qo + 1] = q[qo + 1] + dt * dp.y;
+      q[qo + 2] = q[qo + 2] + dt * dp.z;
+      T wq[4] = {nu[0], nu[1], nu[2], T(0)};
+      T r[4];
+      quat_mul(qt, wq, r);
+      T raw[4];
+      for (int i = 0; i < 4; ++i) raw[i] = qt[i] + T(0.5) * dt * r[i];
+      T n = sqrt_t(raw[0] * raw[0] + raw[1] * raw[1] + raw[2] * raw[2] + raw[3] * raw[3]);
+      for (int i = 0; i < 4; ++i) q[qo + 3 + i] = raw[i] / n;
+    }
+  }
+}
+
+// ------------------------------------------------------------------ adjoint
+// Requires aba_forward(q, qd, tau) to have filled the tape.  On entry gq, gqd hold
+// the adjoint of x^{k+1}; on exit they hold the adjoint of x^k.  Writes the
+// adjoint of tau into gtau and adds dPhi/dm of every link into gm[l * B].
+template <class T>
+SD void step_adjoint(const Sys<T>& s, Col<const T> q, Col<const T> qd, Col<T> gq, Col<T> gqd,
+                     Col<T> gtau, Col<T> gm, V3<T> grav, T dt, int integ) {
+  const int nl = s.nl;
+  const T half = T(0.5);
+  // integrator adjoint; zero the per-link accumulators
+  for (int l = 0; l < nl; ++l) {
+    const int m = s.M(l);
+    const int jt = meta_jtype(m), qo = meta_qoff(m), vo = meta_voff(m);
+    for (int f = 0; f < NADJ; ++f) s.ad(l, f) = T(0);
+    if (jt == J_REVOLUTE) {
+      T qb = gq[qo], vb = gqd[vo];
+      if (integ == I_SEMI_IMPLICIT) {
+        T vt = vb + dt * qb;
+        gqd[vo] = vt;
+        s.ad(l, G_QDD) = dt * vt;
+      } else {
+        gqd[vo] = vb + dt * qb;
+        s.ad(l, G_QDD) = dt * vb;
+      }
+    } else {
+      T nu[6], nub[6];
+      for (int i = 0; i < 6; ++i) {
+        T v0 = qd[vo + i];
+        nu[i] = integ == I_SEMI_IMPLICIT ? v0 + dt * s.tp(l, T_QDD + i) : v0;
+        nub[i] = gqd[vo + i];
+      }
+      T qt[4] = {q[qo + 3], q[qo + 4], q[qo + 5], q[qo + 6]};
+      T wq[4] = {nu[0], nu[1], nu[2], T(0)};
+      T r[4], raw[4];
+      quat_mul(qt, wq, r);
+      for (int i = 0; i < 4; ++i) raw[i] = qt[i] + half * dt * r[i];
+      T n = sqrt_t(raw[0] * raw[0] + raw[1] * raw[1] + raw[2] * raw[2] + raw[3] * raw[3]);
+      T qn[4], qnb[4], rawb[4];
+      T d = 0;
+      for (int i = 0; i < 4; ++i) { qn[i] = raw[i] / n; qnb[i] = gq[qo + 3 + i]; d += qn[i] * qnb[i]; }
+      for (int i = 0; i < 4; ++i) rawb[i] = (qnb[i] - qn[i] * d) / n;
+      // raw = quat + dt/2 quat (x) (w, 0)
+      T qb[4] = {rawb[0], rawb[1], rawb[2], rawb[3]};
+      T wconj[4] = {-nu[0], -nu[1], -nu[2], T(0)};
+      T t1[4];
+      quat_mul(rawb, wconj, t1);
+      for (int i = 0; i < 4; ++i) qb[i] += half * dt * t1[i];
+      T qconj[4] = {-qt[0], -qt[1], -qt[2], qt[3]};
+      T t2[4];
+      quat_mul(qconj, rawb, t2);
+      T velb[6] = {half * dt * t2[0], half * dt * t2[1], half * dt * t2[2], 0, 0, 0};
+      // p' = p + dt R(quat) v
+      V3<T> pb{gq[qo], gq[qo + 1], gq[qo + 2]};
+      M3<T> R = quat_R(qt[0], qt[1], qt[2], qt[3]);
+      V3<T> vvb = dt * mulT(R, pb);
+      velb[3] = vvb.x; velb[4] = vvb.y; velb[5] = vvb.z;
+      quat_R_adj(qt[0], qt[1], qt[2], qt[3], scale(dt, outer(pb, V3<T>{nu[3], nu[4], nu[5]})), qb);
+      for (int i = 0; i < 4; ++i) gq[qo + 3 + i] = qb[i];
+      for (int i = 0; i < 6; ++i) {
+        if (integ == I_SEMI_IMPLICIT) {
+          T tot = nub[i] + velb[i];
+          gqd[vo + i] = tot;
+          s.ad(l, G_QDD + i) = dt * tot;
+        } else {
+          gqd[vo + i] = nub[i] + velb[i];
+          s.ad(l, G_QDD + i) = dt * nub[i];
+        }
+      }
+    }
+  }
+  const SV<T> a0{zero3<T>(), -grav};
+  // pass 3 adjoint (leaves -> root)
+  for (int l = nl - 1; l >= 0; --l) {
+    const int m = s.M(l);
+    const int par = meta_parent(m), jt = meta_jtype(m);
+    XF<T> X = tp_xf(s, l, T_E);
+    SV<T> ab = ad_sv(s, l, G_A);
+    SV<T> apb;
+    if (jt == J_REVOLUTE) {
+      V3<T> ax = s.pv3(l, P_AX);
+      T qddb = s.ad(l, G_QDD) + dot(ax, ab.w);
+      apb = ab;
+      T wb = qddb * s.tp(l, T_DI);
+      s.ad(l, G_D) += -wb * s.tp(l, T_QDD);
+      s.ad(l, G_u) += wb;
+      SV<T> U = tp_sv(s, l, T_U);
+      ad_sv(s, l, G_U, ad_sv(s, l, G_U) - wb * tp_sv(s, l, T_AP));
+      apb -= wb * U;
+    } else {
+      SV<T> qddb = ad_sv(s, l, G_QDD);
+      SV<T> gb = ab + qddb;
+      apb = zeroSV<T>() - qddb;
+      T L[21];
+      for (int i = 0; i < 21; ++i) L[i] = s.tp(l, T_Ia + i);
+      SV<T> ub = chol6_solve(L, gb);
+      ad_sv(s, l, G_u, ub);
+      SI<T> IAb = ad_si(s, l, G_IA);
+      IAb += scale(T(-1), sym_outer(ub, tp_sv(s, l, T_A)));
+      ad_si(s, l, G_IA, IAb);
+    }
+    ad_sv(s, l, G_C, ad_sv(s, l, G_C) + apb);
+    M3<T> Eb = ad_m3(s, l, G_E);
+    V3<T> rb = ad_v3(s, l, G_R);
+    if (par >= 0) {
+      SV<T> apar_b = ad_sv(s, par, G_A);
+      apply_adj(X, tp_sv(s, par, T_A), apb, Eb, rb, &apar_b);
+      ad_sv(s, par, G_A, apar_b);
+    } else {
+      apply_adj(X, a0, apb, Eb, rb, (SV<T>*)nullptr);
+    }
+    ad_m3(s, l, G_E, Eb);
+    ad_v3(s, l, G_R, rb);
+  }
+  // pass 2 adjoint (root -> leaves)
+  for (int l = 0; l < nl; ++l) {
+    const int m = s.M(l);
+    const int par = meta_parent(m), jt = meta_jtype(m), vo = meta_voff(m);
+    SI<T> IAb = ad_si(s, l, G_IA);
+    SV<T> pAb = ad_sv(s, l, G_PA);
+    if (jt == J_REVOLUTE) {
+      V3<T> ax = s.pv3(l, P_AX);
+      SV<T> Ub = ad_sv(s, l, G_U);
+      T Db = s.ad(l, G_D);
+      T ub = s.ad(l, G_u);
+      const T Di = s.tp(l, T_DI);
+      const T u = s.tp(l, T_u);
+      SV<T> U = tp_sv(s, l, T_U);
+      if (par >= 0) {
+        XF<T> X = tp_xf(s, l, T_E);
+        M3<T> Eb = ad_m3(s, l, G_E);
+        V3<T> rb = ad_v3(s, l, G_R);
+        SV<T> pab = zeroSV<T>();
+        SI<T> Iab = zeroSI<T>();
+        SI<T> Ia = tp_si(s, l, T_Ia);
+        applyT_adj(X, tp_sv(s, l, T_pa), ad_sv(s, par, G_PA), Eb, rb, &pab);
+        congruence_adj(X, Ia, ad_si(s, par, G_IA), Iab, Eb, rb);
+        ad_m3(s, l, G_E, Eb);
+        ad_v3(s, l, G_R, rb);
+        // pa = pA + Ia c + U (u / D)
+        SV<T> c = tp_sv(s, l, T_C);
+        pAb += pab;
+        Iab += sym_outer(pab, c);
+        ad_sv(s, l, G_C, ad_sv(s, l, G_C) + mul(Ia, pab));
+        Ub += (u * Di) * pab;
+        T gb = dot(U, pab);
+        ub += gb * Di;
+        Db -= gb * u * Di * Di;
+        // Ia = IA - U U^T / D
+        IAb += Iab;
+        SV<T> IbU = mul(Iab, U);
+        Ub -= (T(2) * Di) * IbU;
+        Db += Di * Di * dot(U, IbU);
+      }
+      // u = tau - S^T pA,  D = S^T U,  U = IA S
+      gtau[vo] = ub;
+      pAb.w -= ub * ax;
+      Ub.w += Db * ax;
+      IAb.A += sym_outer(Ub.w, ax);
+      IAb.B += scale(half, outer(ax, Ub.v));
+    } else {
+      SV<T> ub = ad_sv(s, l, G_u);
+      gtau[vo] = ub.w.x; gtau[vo + 1] = ub.w.y; gtau[vo + 2] = ub.w.z;
+      gtau[vo + 3] = ub.v.x; gtau[vo + 4] = ub.v.y; gtau[vo + 5] = ub.v.z;
+      pAb -= ub;
+    }
+    ad_si(s, l, G_IA, IAb);
+    ad_sv(s, l, G_PA, pAb);
+    gm[l] += rbi_dmass(IAb, s.pv3(l, P_C));
+  }
+  // pass 1 adjoint + jcalc adjoint (leaves -> root)
+  for (int l = nl - 1; l >= 0; --l) {
+    const int m = s.M(l);
+    const int par = meta_parent(m), jt = meta_jtype(m), qo = meta_qoff(m), vo = meta_voff(m);
+    SV<T> v = tp_sv(s, l, T_V);
+    SV<T> h = tp_sv(s, l, T_H);
+    SV<T> vb = ad_sv(s, l, G_V);
+    SV<T> hb = zeroSV<T>();
+    crossf_adj(v, h, ad_sv(s, l, G_PA), vb, hb);
+    V3<T> com = s.pv3(l, P_C);
+    SI<T> I = rbi(s.P(l, P_M), com, s.ps3(l, P_IC));
+    gm[l] += rbi_dmass_bilinear(hb, v, com);
+    vb += mul(I, hb);
+    SV<T> vJ;
+    if (jt == J_REVOLUTE) vJ = SV<T>{qd[vo] * s.pv3(l, P_AX), zero3<T>()};
+    else vJ = SV<T>{{qd[vo], qd[vo + 1], qd[vo + 2]}, {qd[vo + 3], qd[vo + 4], qd[vo + 5]}};
+    SV<T> vJb = zeroSV<T>();
+    crossm_adj(v, vJ, ad_sv(s, l, G_C), vb, vJb);
+    vJb += vb;
+    XF<T> X = tp_xf(s, l, T_E);
+    M3<T> Eb = ad_m3(s, l, G_E);
+    V3<T> rb = ad_v3(s, l, G_R);
+    if (par >= 0) {
+      SV<T> vpb = ad_sv(s, par, G_V);
+      apply_adj(X, tp_sv(s, par, T_V), vb, Eb, rb, &vpb);
+      ad_sv(s, par, G_V, vpb);
+    }
+    M3<T> Et = s.pm3(l, P_E);
+    M3<T> EJb = mmT(Eb, Et);  // E = E_J E_t
+    if (jt == J_REVOLUTE) {
+      V3<T> ax = s.pv3(l, P_AX);
+      gqd[vo] += dot(ax, vJb.w);
+      gq[qo] += rot_axis_T_dq(ax, s.tp(l, T_SC), s.tp(l, T_SC + 1), EJb);
+    } else {
+      T vv[6] = {vJb.w.x, vJb.w.y, vJb.w.z, vJb.v.x, vJb.v.y, vJb.v.z};
+      for (int i = 0; i < 6; ++i) gqd[vo + i] += vv[i];
+      V3<T> pb = mul(Et, rb);  // r = r_t + E_t^T p
+      gq[qo] += pb.x; gq[qo + 1] += pb.y; gq[qo + 2] += pb.z;
+      T qb[4] = {0, 0, 0, 0};
+      quat_R_adj(q[qo + 3], q[qo + 4], q[qo + 5], q[qo + 6], transpose(EJb), qb);
+      for (int i = 0; i < 4; ++i) gq[qo + 3 + i] += qb[i];
+    }
+  }
+}
+
+}  // namespace abasim

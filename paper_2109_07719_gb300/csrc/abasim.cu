@@ -1,0 +1,531 @@
+// C-ABI implementation: model validation and packing (host), and the batched
+// rollout / adjoint kernels (one thread per system, per-link tape in a
+// handle-owned scratch laid out [link][field][system] so that neighbouring
+// threads touch neighbouring words).
+#include <cuda_runtime.h>
+
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "../../include/abasim.h"
+#include "aba_step.cuh"
+
+using namespace abasim;
+
+namespace {
+
+constexpr int kMaxLinks = 255;
+constexpr int kMaxCoords = 2047;
+constexpr int kDefaultBlock = 32;
+
+thread_local std::string g_create_error;
+
+}  // namespace
+
+struct sim_handle {
+  int B = 0, maxL = 0, nq_max = 0, nv_max = 0, L_total = 0;
+  int precision = SIM_FP64, integrator = SIM_SEMI_IMPLICIT_EULER;
+  int block = kDefaultBlock;
+  int device = 0;
+  double dt = 0, g[3] = {0, 0, 0};
+  size_t scalar = 8;
+  void* prm = nullptr;       // [maxL][NPRM][B] scalar
+  int* meta = nullptr;       // [maxL][B]
+  int* nl = nullptr;         // [B]
+  int* nqv = nullptr;        // [B]  nq | nv << 16
+  void* tape = nullptr;      // [maxL][NTAPE][B] scalar
+  void* adj = nullptr;       // [maxL][NADJ][B] scalar
+  void* gm_acc = nullptr;    // [maxL][B] scalar
+  int* link_slot = nullptr;  // [L_total] -> l * B + b
+  int* status = nullptr;     // [B]
+  std::string err;
+};
+
+namespace {
+
+int fail(sim_handle* h, int code, const std::string& msg) {
+  if (h) h->err = msg;
+  else g_create_error = msg;
+  return code;
+}
+
+int cuda_fail(sim_handle* h, cudaError_t e, const char* what) {
+  return fail(h, e == cudaErrorMemoryAllocation ? SIM_ENOMEM : SIM_ECUDA,
+              std::string(what) + ": " + cudaGetErrorString(e));
+}
+
+template <class T> struct DevModel {
+  const T* prm;
+  const int* meta;
+  const int* nl;
+  const int* nqv;
+  T* tape;
+  T* adj;
+  int* status;
+  long long B;
+  int nq_max, nv_max;
+  T dt;
+  T g0, g1, g2;
+  int integ;
+};
+
+template <class T> DevModel<T> dev_model(const sim_handle* h) {
+  return DevModel<T>{(const T*)h->prm, h->meta, h->nl, h->nqv, (T*)h->tape, (T*)h->adj, h->status,
+                     (long long)h->B, h->nq_max, h->nv_max, (T)h->dt,
+                     (T)h->g[0], (T)h->g[1], (T)h->g[2], h->integrator};
+}
+
+template <class T> __device__ __forceinline__ Sys<T> sys_of(const DevModel<T>& m, int b) {
+  return Sys<T>{m.prm + b, m.meta + b, m.tape + b, m.adj + b, m.B, m.nl[b]};
+}
+
+template <class T> __device__ __forceinline__ bool finite_t(T x) { return isfinite(x); }
+
+// ------------------------------------------------------------------ kernels
+
+// T steps of the whole batch; system b is thread b.  The working state lives in
+// (qT, qdT); checkpoints every k steps; optional full trajectory.
+template <class T>
+__global__ void k_rollout(DevModel<T> m, const T* __restrict__ q0, const T* __restrict__ qd0,
+                          const T* __restrict__ tau, long long Tn, int k, T* ckpt, T* qT, T* qdT,
+                          T* traj) {
+  const int b = blockIdx.x * blockDim.x + threadIdx.x;
+  if (b >= m.B) return;
+  const long long B = m.B;
+  const int nqm = m.nq_max, nvm = m.nv_max, NX = nqm + nvm;
+  const V3<T> g{m.g0, m.g1, m.g2};
+  Sys<T> s = sys_of(m, b);
+  Col<T> q{qT + b, B}, qd{qdT + b, B};
+  for (int d = 0; d < nqm; ++d) q[d] = q0[d * B + b];
+  for (int d = 0; d < nvm; ++d) qd[d] = qd0[d * B + b];
+  if (traj) {
+    for (int d = 0; d < nqm; ++d) traj[d * B + b] = q[d];
+    for (int d = 0; d < nvm; ++d) traj[(nqm + d) * B + b] = qd[d];
+  }
+  for (long long t = 0; t < Tn; ++t) {
+    if (ckpt && t % k == 0) {
+      T* c = ckpt + (t / k) * NX * B + b;
+      for (int d = 0; d < nqm; ++d) c[d * B] = q[d];
+      for (int d = 0; d < nvm; ++d) c[(nqm + d) * B] = qd[d];
+    }
+    aba_forward<T>(s, Col<const T>{qT + b, B}, Col<const T>{qdT + b, B},
+                   Col<const T>{tau + t * nvm * B + b, B}, g);
+    integrate<T>(s, q, qd, m.dt, m.integ);
+    if (traj) {
+      T* c = traj + (t + 1) * NX * B + b;
+      for (int d = 0; d < nqm; ++d) c[d * B] = q[d];
+      for (int d = 0; d < nvm; ++d) c[(nqm + d) * B] = qd[d];
+    }
+  }
+  bool ok = true;
+  for (int d = 0; d < nqm; ++d) ok &= finite_t(q[d]);
+  for (int d = 0; d < nvm; ++d) ok &= finite_t(qd[d]);
+  if (!ok) m.status[b] |= 1;
+}
+
+// Adjoint of k_rollout.  (gq0, gqd0) carry the running state adjoint R^t = xbar^t.
+template <class T>
+__global__ void k_backward(DevModel<T> m, const T* __restrict__ ckpt, const T* __restrict__ tau,
+                           long long Tn, int k, const T* __restrict__ gqT, const T* __restrict__ gqdT,
+                           const T* __restrict__ gtraj, T* gq0, T* gqd0, T* gtau, T* gm_acc,
+                           T* ring) {
+  const int b = blockIdx.x * blockDim.x + threadIdx.x;
+  if (b >= m.B) return;
+  const long long B = m.B;
+  const int nqm = m.nq_max, nvm = m.nv_max, NX = nqm + nvm;
+  const int nq = m.nqv[b] & 0xffff, nv = m.nqv[b] >> 16;
+  const V3<T> g{m.g0, m.g1, m.g2};
+  Sys<T> s = sys_of(m, b);
+  Col<T> gq{gq0 + b, B}, gqd{gqd0 + b, B};
+  for (int d = 0; d < nqm; ++d) {
+    T v = d < nq ? gqT[d * B + b] : T(0);
+    if (gtraj && d < nq) v += gtraj[(Tn * NX + d) * B + b];
+    gq[d] = v;
+  }
+  for (int d = 0; d < nvm; ++d) {
+    T v = d < nv ? gqdT[d * B + b] : T(0);
+    if (gtraj && d < nv) v += gtraj[(Tn * NX + nqm + d) * B + b];
+    gqd[d] = v;
+  }
+  for (int l = 0; l < s.nl; ++l) gm_acc[l * B + b] = T(0);
+  Col<T> gm{gm_acc + b, B};
+  const long long nseg = (Tn + k - 1) / k;
+  for (long long seg = nseg - 1; seg >= 0; --seg) {
+    const long long t0 = seg * k;
+    const long long t1 = (t0 + k < Tn) ? t0 + k : Tn;
+    const T* xs = ckpt + seg * NX * B + b;
+    if (k > 1) {  // replay the segment once, keeping its states
+      T* r0 = ring + b;
+      for (int d = 0; d < NX; ++d) r0[d * B] = xs[d * B];
+      for (long long j = 1; j < t1 - t0; ++j) {
+        const T* prev = ring + (j - 1) * NX * B + b;
+        T* cur = ring + j * NX * B + b;
+        for (int d = 0; d < NX; ++d) cur[d * B] = prev[d * B];
+        aba_forward<T>(s, Col<const T>{cur, B}, Col<const T>{cur + nqm * B, B},
+                       Col<const T>{tau + (t0 + j - 1) * nvm * B + b, B}, g);
+        integrate<T>(s, Col<T>{cur, B}, Col<T>{cur + nqm * B, B}, m.dt, m.integ);
+      }
+    }
+    for (long long t = t1 - 1; t >= t0; --t) {
+      const T* x = (k > 1) ? ring + (t - t0) * NX * B + b : xs;
+      Col<const T> q{x, B}, qd{x + nqm * B, B};
+      aba_forward<T>(s, q, qd, Col<const T>{tau + t * nvm * B + b, B}, g);
+      T* gt = gtau + t * nvm * B + b;
+      step_adjoint<T>(s, q, qd, gq, gqd, Col<T>{gt, B}, gm, g, m.dt, m.integ);
+      for (int d = nv; d < nvm; ++d) gt[d * B] = T(0);
+      if (gtraj) {
+        const T* gx = gtraj + t * NX * B + b;
+        for (int d = 0; d < nq; ++d) gq[d] += gx[d * B];
+        for (int d = 0; d < nv; ++d) gqd[d] += gx[(nqm + d) * B];
+      }
+    }
+  }
+  bool ok = true;
+  for (int d = 0; d < nq; ++d) ok &= finite_t(gq[d]);
+  for (int d = 0; d < nv; ++d) ok &= finite_t(gqd[d]);
+  for (int l = 0; l < s.nl; ++l) ok &= finite_t(gm[l]);
+  if (!ok) m.status[b] |= 1;
+}
+
+template <class T>
+__global__ void k_gather_mass_grad(const T* __restrict__ gm_acc, const int* __restrict__ link_slot,
+                                   int L, T* gmass) {
+  const int j = blockIdx.x * blockDim.x + threadIdx.x;
+  if (j < L) gmass[j] = gm_acc[link_slot[j]];
+}
+
+template <class T>
+__global__ void k_set_masses(T* prm, const int* __restrict__ link_slot, int L, long long B,
+                             const T* __restrict__ mass) {
+  const int j = blockIdx.x * blockDim.x + threadIdx.x;
+  if (j >= L) return;
+  const int ls = link_slot[j];
+  const long long l = ls / B, b = ls % B;
+  prm[(l * NPRM + P_M) * B + b] = mass[j];
+}
+
+// ------------------------------------------------------------------ launches
+
+inline cudaStream_t S(void* s) { return (cudaStream_t)s; }
+
+template <class T>
+int launch_rollout(sim_handle* h, const void* q0, const void* qd0, const void* tau, int64_t T_,
+                   int k, void* ckpt, void* qT, void* qdT, void* traj, void* stream) {
+  const int grid = (h->B + h->block - 1) / h->block;
+  k_rollout<T><<<grid, h->block, 0, S(stream)>>>(dev_model<T>(h), (const T*)q0, (const T*)qd0,
+                                                  (const T*)tau, (long long)T_, k, (T*)ckpt,
+                                                  (T*)qT, (T*)qdT, (T*)traj);
+  cudaError_t e = cudaGetLastError();
+  return e == cudaSuccess ? SIM_OK : cuda_fail(h, e, "rollout launch");
+}
+
+template <class T>
+int launch_backward(sim_handle* h, const void* ckpt, const void* tau, int64_t T_, int k,
+                    const void* gqT, const void* gqdT, const void* gtraj, void* gq0, void* gqd0,
+                    void* gtau, void* gmass, void* work, void* stream) {
+  const int grid = (h->B + h->block - 1) / h->block;
+  k_backward<T><<<grid, h->block, 0, S(stream)>>>(
+      dev_model<T>(h), (const T*)ckpt, (const T*)tau, (long long)T_, k, (const T*)gqT,
+      (const T*)gqdT, (const T*)gtraj, (T*)gq0, (T*)gqd0, (T*)gtau, (T*)h->gm_acc, (T*)work);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return cuda_fail(h, e, "backward launch");
+  if (gmass) {
+    k_gather_mass_grad<T><<<(h->L_total + 255) / 256, 256, 0, S(stream)>>>(
+        (const T*)h->gm_acc, h->link_slot, h->L_total, (T*)gmass);
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return cuda_fail(h, e, "mass-gradient launch");
+  }
+  return SIM_OK;
+}
+
+bool is_fp64(const sim_handle* h) { return h->precision == SIM_FP64; }
+
+// ------------------------------------------------------------------ validation
+
+bool near(double a, double b, double tol) { return std::fabs(a - b) <= tol; }
+
+int validate(const sim_model_desc* d, std::string& why) {
+  auto bad = [&](const std::string& s) { why = s; return SIM_EINVAL; };
+  if (!d) return bad("null model description");
+  if (d->n_systems < 1) return bad("n_systems must be >= 1");
+  if (d->precision < SIM_FP64 || d->precision > SIM_FP32_D64) return bad("unknown precision");
+  if (d->integrator != SIM_SEMI_IMPLICIT_EULER && d->integrator != SIM_EXPLICIT_EULER)
+    return bad("unknown integrator");
+  if (!(d->dt > 0) || !std::isfinite(d->dt)) return bad("dt must be finite and > 0");
+  for (int i = 0; i < 3; ++i)
+    if (!std::isfinite(d->gravity[i])) return bad("gravity must be finite");
+  if (!d->sys_link_offset || !d->parent || !d->joint_type || !d->axis || !d->X_tree || !d->mass ||
+      !d->com || !d->I_com)
+    return bad("null model array");
+  if (d->sys_link_offset[0] != 0) return bad("sys_link_offset[0] must be 0");
+  for (int b = 0; b < d->n_systems; ++b) {
+    const int o0 = d->sys_link_offset[b], o1 = d->sys_link_offset[b + 1];
+    const int n = o1 - o0;
+    char buf[160];
+    if (n < 1 || n > kMaxLinks) {
+      snprintf(buf, sizeof buf, "system %d has %d links (1..%d allowed)", b, n, kMaxLinks);
+      return bad(buf);
+    }
+    int nq = 0, nv = 0;
+    for (int l = 0; l < n; ++l) {
+      const int i = o0 + l;
+      const int p = d->parent[i], jt = d->joint_type[i];
+      if (p < -1 || p >= l) {
+        snprintf(buf, sizeof buf, "system %d link %d: parent %d not in [-1, %d)", b, l, p, l);
+        return bad(buf);
+      }
+      if (jt == SIM_FREE) {
+        if (l != 0 || p != -1) {
+          snprintf(buf, sizeof buf, "system %d link %d: a free joint must be the first link", b, l);
+          return bad(buf);
+        }
+        nq += 7; nv += 6;
+      } else if (jt == SIM_REVOLUTE) {
+        const double* a = d->axis + 3 * i;
+        const double nn = a[0] * a[0] + a[1] * a[1] + a[2] * a[2];
+        if (!near(nn, 1.0, 1e-6)) {
+          snprintf(buf, sizeof buf, "system %d link %d: axis is not unit length", b, l);
+          return bad(buf);
+        }
+        nq += 1; nv += 1;
+      } else {
+        snprintf(buf, sizeof buf, "system %d link %d: unknown joint type %d", b, l, jt);
+        return bad(buf);
+      }
+      const double* E = d->X_tree + 12 * i;
+      for (int r = 0; r < 3; ++r)
+        for (int c = 0; c < 3; ++c) {
+          double s = 0;
+          for (int x = 0; x < 3; ++x) s += E[3 * x + r] * E[3 * x + c];
+          if (!near(s, r == c ? 1.0 : 0.0, 1e-6)) {
+            snprintf(buf, sizeof buf, "system %d link %d: X_tree rotation is not orthonormal", b, l);
+            return bad(buf);
+          }
+        }
+      for (int x = 0; x < 12; ++x)
+        if (!std::isfinite(E[x])) return bad("non-finite X_tree");
+      const double m = d->mass[i];
+      if (!(m > 0) || !std::isfinite(m)) {
+        snprintf(buf, sizeof buf, "system %d link %d: mass must be finite and > 0", b, l);
+        return bad(buf);
+      }
+      const double* Ic = d->I_com + 6 * i;
+      for (int x = 0; x < 6; ++x)
+        if (!std::isfinite(Ic[x]) || !std::isfinite(d->com[3 * i + x % 3]))
+          return bad("non-finite inertia or COM");
+      if (Ic[0] < 0 || Ic[1] < 0 || Ic[2] < 0) {
+        snprintf(buf, sizeof buf, "system %d link %d: negative principal inertia", b, l);
+        return bad(buf);
+      }
+    }
+    if (nq > kMaxCoords || nv > kMaxCoords) return bad("too many coordinates in one system");
+  }
+  return SIM_OK;
+}
+
+template <class T> int upload(sim_handle* h, const std::vector<double>& prm_h) {
+  std::vector<T> v(prm_h.begin(), prm_h.end());
+  cudaError_t e = cudaMalloc(&h->prm, v.size() * sizeof(T));
+  if (e != cudaSuccess) return cuda_fail(h, e, "model upload");
+  e = cudaMemcpy(h->prm, v.data(), v.size() * sizeof(T), cudaMemcpyHostToDevice);
+  if (e != cudaSuccess) return cuda_fail(h, e, "model upload");
+  return SIM_OK;
+}
+
+int check_handle(const sim_handle* h) { return h ? SIM_OK : SIM_EINVAL; }
+
+}  // namespace
+
+// ====================================================================== C ABI
+
+extern "C" {
+
+int sim_create(const sim_model_desc* d, sim_handle** out) {
+  if (!out) return fail(nullptr, SIM_EINVAL, "null output pointer");
+  *out = nullptr;
+  std::string why;
+  if (validate(d, why) != SIM_OK) return fail(nullptr, SIM_EINVAL, why);
+  sim_handle* h = new sim_handle();
+  h->B = d->n_systems;
+  h->precision = d->precision;
+  h->integrator = d->integrator;
+  h->dt = d->dt;
+  for (int i = 0; i < 3; ++i) h->g[i] = d->gravity[i];
+  h->scalar = h->precision == SIM_FP64 ? 8 : 4;
+  h->L_total = d->sys_link_offset[h->B];
+  cudaGetDevice(&h->device);
+  const int B = h->B;
+  std::vector<int> nl(B), nqv(B);
+  for (int b = 0; b < B; ++b) {
+    nl[b] = d->sys_link_offset[b + 1] - d->sys_link_offset[b];
+    h->maxL = std::max(h->maxL, nl[b]);
+  }
+  const int maxL = h->maxL;
+  std::vector<double> prm((size_t)maxL * NPRM * B, 0.0);
+  std::vector<int> meta((size_t)maxL * B, 0), slot(h->L_total);
+  for (int b = 0; b < B; ++b) {
+    int qo = 0, vo = 0;
+    for (int l = 0; l < nl[b]; ++l) {
+      const int i = d->sys_link_offset[b] + l;
+      const int jt = d->joint_type[i];
+      auto P = [&](int f) -> double& { return prm[((size_t)l * NPRM + f) * B + b]; };
+      for (int x = 0; x < 12; ++x) P(P_E + x) = d->X_tree[12 * i + x];
+      for (int x = 0; x < 3; ++x) {
+        P(P_AX + x) = jt == SIM_REVOLUTE ? d->axis[3 * i + x] : 0.0;
+        P(P_C + x) = d->com[3 * i + x];
+      }
+      P(P_M) = d->mass[i];
+      for (int x = 0; x < 6; ++x) P(P_IC + x) = d->I_com[6 * i + x];
+      meta[(size_t)l * B + b] = make_meta(d->parent[i], jt, qo, vo);
+      slot[i] = l * B + b;
+      qo += jt == SIM_FREE ? 7 : 1;
+      vo += jt == SIM_FREE ? 6 : 1;
+    }
+    nqv[b] = qo | (vo << 16);
+    h->nq_max = std::max(h->nq_max, qo);
+    h->nv_max = std::max(h->nv_max, vo);
+  }
+  int rc = h->precision == SIM_FP64 ? upload<double>(h, prm) : upload<float>(h, prm);
+  auto alloc = [&](void** p, size_t bytes, const char* what) -> int {
+    cudaError_t e = cudaMalloc(p, bytes);
+    return e == cudaSuccess ? SIM_OK : cuda_fail(h, e, what);
+  };
+  auto put = [&](void* dst, const void* src, size_t bytes) -> int {
+    cudaError_t e = cudaMemcpy(dst, src, bytes, cudaMemcpyHostToDevice);
+    return e == cudaSuccess ? SIM_OK : cuda_fail(h, e, "model upload");
+  };
+  if (rc == SIM_OK) rc = alloc((void**)&h->meta, meta.size() * sizeof(int), "meta");
+  if (rc == SIM_OK) rc = put(h->meta, meta.data(), meta.size() * sizeof(int));
+  if (rc == SIM_OK) rc = alloc((void**)&h->nl, B * sizeof(int), "nl");
+  if (rc == SIM_OK) rc = put(h->nl, nl.data(), B * sizeof(int));
+  if (rc == SIM_OK) rc = alloc((void**)&h->nqv, B * sizeof(int), "nqv");
+  if (rc == SIM_OK) rc = put(h->nqv, nqv.data(), B * sizeof(int));
+  if (rc == SIM_OK) rc = alloc((void**)&h->link_slot, slot.size() * sizeof(int), "link map");
+  if (rc == SIM_OK) rc = put(h->link_slot, slot.data(), slot.size() * sizeof(int));
+  if (rc == SIM_OK) rc = alloc(&h->tape, (size_t)maxL * NTAPE * B * h->scalar, "tape");
+  if (rc == SIM_OK) rc = alloc(&h->adj, (size_t)maxL * NADJ * B * h->scalar, "adjoint tape");
+  if (rc == SIM_OK) rc = alloc(&h->gm_acc, (size_t)maxL * B * h->scalar, "mass-gradient buffer");
+  if (rc == SIM_OK) rc = alloc((void**)&h->status, B * sizeof(int), "status");
+  if (rc == SIM_OK) {
+    cudaError_t e = cudaMemset(h->status, 0, B * sizeof(int));
+    if (e != cudaSuccess) rc = cuda_fail(h, e, "status init");
+  }
+  if (rc != SIM_OK) {
+    g_create_error = h->err;
+    sim_destroy(h);
+    return rc;
+  }
+  *out = h;
+  return SIM_OK;
+}
+
+void sim_destroy(sim_handle* h) {
+  if (!h) return;
+  void* ptrs[] = {h->prm, h->meta, h->nl, h->nqv, h->tape, h->adj, h->gm_acc, h->link_slot, h->status};
+  for (void* p : ptrs)
+    if (p) cudaFree(p);
+  delete h;
+}
+
+int sim_dims(const sim_handle* h, int32_t* n_systems, int32_t* nq_max, int32_t* nv_max,
+             int32_t* n_links_total) {
+  if (!h) return SIM_EINVAL;
+  if (n_systems) *n_systems = h->B;
+  if (nq_max) *nq_max = h->nq_max;
+  if (nv_max) *nv_max = h->nv_max;
+  if (n_links_total) *n_links_total = h->L_total;
+  return SIM_OK;
+}
+
+size_t sim_ckpt_bytes(const sim_handle* h, int64_t T, int32_t k) {
+  if (!h || T < 0 || k < 1) return 0;
+  const int64_t n = (T + k - 1) / k;
+  return (size_t)n * (h->nq_max + h->nv_max) * h->B * h->scalar;
+}
+
+size_t sim_work_bytes(const sim_handle* h, int32_t k) {
+  if (!h || k <= 1) return 0;
+  return (size_t)k * (h->nq_max + h->nv_max) * h->B * h->scalar;
+}
+
+int sim_set_masses(sim_handle* h, const void* mass, void* stream) {
+  if (!h) return SIM_EINVAL;
+  if (!mass) return fail(h, SIM_EINVAL, "null mass array");
+  const int grid = (h->L_total + 255) / 256;
+  if (is_fp64(h))
+    k_set_masses<double><<<grid, 256, 0, S(stream)>>>((double*)h->prm, h->link_slot, h->L_total,
+                                                      h->B, (const double*)mass);
+  else
+    k_set_masses<float><<<grid, 256, 0, S(stream)>>>((float*)h->prm, h->link_slot, h->L_total,
+                                                     h->B, (const float*)mass);
+  cudaError_t e = cudaGetLastError();
+  return e == cudaSuccess ? SIM_OK : cuda_fail(h, e, "set_masses launch");
+}
+
+int sim_rollout(sim_handle* h, const void* q0, const void* qd0, const void* tau, int64_t T,
+                int32_t k, void* ckpt, void* qT, void* qdT, void* traj, void* stream) {
+  if (!h) return SIM_EINVAL;
+  if (T < 0 || k < 1) return fail(h, SIM_EINVAL, "need T >= 0 and k >= 1");
+  if (!q0 || !qd0 || !qT || !qdT || (T > 0 && !tau))
+    return fail(h, SIM_EINVAL, "null state or torque pointer");
+  return is_fp64(h) ? launch_rollout<double>(h, q0, qd0, tau, T, k, ckpt, qT, qdT, traj, stream)
+                    : launch_rollout<float>(h, q0, qd0, tau, T, k, ckpt, qT, qdT, traj, stream);
+}
+
+int sim_step_batch(sim_handle* h, const void* q, const void* qd, const void* tau, void* q_out,
+                   void* qd_out, void* stream) {
+  if (!h) return SIM_EINVAL;
+  if (!tau) return fail(h, SIM_EINVAL, "null torque pointer");
+  return sim_rollout(h, q, qd, tau, 1, 1, nullptr, q_out, qd_out, nullptr, stream);
+}
+
+int sim_backward_rollout(sim_handle* h, const void* ckpt, const void* tau, int64_t T, int32_t k,
+                         const void* gqT, const void* gqdT, const void* g_traj, void* gq0,
+                         void* gqd0, void* gtau, void* gmass, void* work, size_t work_bytes,
+                         void* stream) {
+  if (!h) return SIM_EINVAL;
+  if (T < 0 || k < 1) return fail(h, SIM_EINVAL, "need T >= 0 and k >= 1");
+  if (!gqT || !gqdT || !gq0 || !gqd0 || (T > 0 && (!ckpt || !tau || !gtau)))
+    return fail(h, SIM_EINVAL, "null pointer argument");
+  if (k > 1 && T > 0 && (!work || work_bytes < sim_work_bytes(h, k)))
+    return fail(h, SIM_ENOMEM, "workspace smaller than sim_work_bytes(k)");
+  return is_fp64(h)
+             ? launch_backward<double>(h, ckpt, tau, T, k, gqT, gqdT, g_traj, gq0, gqd0, gtau, gmass, work, stream)
+             : launch_backward<float>(h, ckpt, tau, T, k, gqT, gqdT, g_traj, gq0, gqd0, gtau, gmass, work, stream);
+}
+
+int sim_status(sim_handle* h, int32_t* flags) {
+  if (!h) return SIM_EINVAL;
+  std::vector<int32_t> tmp(h->B);
+  cudaError_t e = cudaDeviceSynchronize();
+  if (e == cudaSuccess) e = cudaMemcpy(tmp.data(), h->status, h->B * sizeof(int), cudaMemcpyDeviceToHost);
+  if (e != cudaSuccess) return cuda_fail(h, e, "status read");
+  bool any = false;
+  for (int b = 0; b < h->B; ++b) any |= tmp[b] != 0;
+  if (flags) memcpy(flags, tmp.data(), h->B * sizeof(int32_t));
+  return any ? SIM_ENONFINITE : SIM_OK;
+}
+
+int sim_clear_status(sim_handle* h, void* stream) {
+  if (!h) return SIM_EINVAL;
+  cudaError_t e = cudaMemsetAsync(h->status, 0, h->B * sizeof(int), S(stream));
+  return e == cudaSuccess ? SIM_OK : cuda_fail(h, e, "status clear");
+}
+
+int sim_set_block(sim_handle* h, int32_t threads) {
+  if (!h) return SIM_EINVAL;
+  if (threads == 0) { h->block = kDefaultBlock; return SIM_OK; }
+  if (threads < 32 || threads > 1024 || threads % 32)
+    return fail(h, SIM_EINVAL, "block size must be a multiple of 32 in [32, 1024]");
+  h->block = threads;
+  return SIM_OK;
+}
+
+const char* sim_last_error(const sim_handle* h) {
+  return h ? h->err.c_str() : g_create_error.c_str();
+}
+
+}  // extern "C"
