@@ -117,8 +117,9 @@ def test_explicit_euler_fp64(cfg):
 
 @pytest.mark.parametrize("cfg,k", [(2, 7), (2, 10), (3, 10), (4, 4), (5, 16)])
 def test_checkpoint_interval_gives_same_gradients(cfg, k):
-    """Segment replay from every k-th state reproduces the k = 1 gradients
-    (identical arithmetic, so to round-off), with T not a multiple of k."""
+    """Segment replay from every k-th state reproduces the k = 1 gradients to
+    round-off (the replay runs the same formulas inside another kernel, where the
+    compiler may contract multiply-adds differently), with T not a multiple of k."""
     B, T = 41, 53
     work = _work(cfg, B, T)
     sim = _sim(work)
@@ -131,8 +132,8 @@ def test_checkpoint_interval_gives_same_gradients(cfg, k):
     gqT, gqdT = torch.ones_like(qT), -torch.ones_like(qdT)
     a = sim.backward(ck1, tau, gqT, gqdT, k=1)
     b = sim.backward(ckk, tau, gqT, gqdT, k=k)
-    for x, y in zip(a, b):
-        assert torch.equal(x, y)
+    for name, x, y in zip(("gq0", "gqd0", "gtau", "gmass"), a, b):
+        check(name, y.cpu().numpy(), x.cpu().numpy(), 1e-10)
 
 
 def test_per_step_objective_terms():
