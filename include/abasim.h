@@ -116,6 +116,27 @@ int sim_set_masses(sim_handle* h, const void* mass, void* stream);
 int sim_step_batch(sim_handle* h, const void* q, const void* qd, const void* tau, void* q_out,
                    void* qd_out, void* stream);
 
+/* Size of the library's static step scratch used by sim_step_batch_static. */
+#define SIM_STATIC_SCRATCH_BYTES (16u << 20)
+
+/* One step x -> x' like sim_step_batch, for callers that must not allocate
+ * device memory: code running while a stream is captured in global mode (where
+ * cudaMalloc is refused), or a component inside a host application that owns
+ * every device allocation and hands it only a handle and state buffers.  The
+ * paper has no counterpart; this is a deployment convenience.
+ * Allocates nothing: the per-link tape is a file-scope device array of
+ * SIM_STATIC_SCRATCH_BYTES (16 MiB) that every GPU loading the library holds
+ * until exit; batches whose tape (links x 118 scalars x systems) exceeds it are
+ * rejected with SIM_ENOMEM.  The first call on each device looks up the array's
+ * device address with that device current; make that first call before any
+ * stream capture.  The array is shared by all calls and keeps the last call's
+ * contents (every word a step reads is written earlier in the same step, so
+ * nothing needs clearing); calls whose kernels overlap on the GPU race on it,
+ * so serialize them (one stream, or events).  Same layouts, ownership and
+ * error codes as sim_step_batch. */
+int sim_step_batch_static(sim_handle* h, const void* q, const void* qd, const void* tau,
+                          void* q_out, void* qd_out, void* stream);
+
 /* T steps from (q0, qd0) under tau [T][nv_max][B].  Writes x^T to (qT, qdT),
  * the checkpoints x^0, x^k, ... to ckpt (if non-NULL; sim_ckpt_bytes(T, k)
  * bytes) and every state to traj (if non-NULL).  T == 0 copies the input. */

@@ -53,6 +53,7 @@ _SIGS = {
     "sim_work_bytes": (ctypes.c_size_t, [_P, ctypes.c_int32]),
     "sim_set_masses": (ctypes.c_int, [_P, _P, _P]),
     "sim_step_batch": (ctypes.c_int, [_P] * 7),
+    "sim_step_batch_static": (ctypes.c_int, [_P] * 7),
     "sim_rollout": (ctypes.c_int, [_P, _P, _P, _P, ctypes.c_int64, ctypes.c_int32, _P, _P, _P, _P, _P]),
     "sim_backward_rollout": (ctypes.c_int, [_P, _P, _P, ctypes.c_int64, ctypes.c_int32, _P, _P, _P,
                                             _P, _P, _P, _P, _P, ctypes.c_size_t, _P]),
@@ -183,6 +184,19 @@ class Simulator:
         qd_out = self.empty(self.nv_max, B) if qd_out is None else qd_out
         self._check(lib.sim_step_batch(self._h, _ptr(q), _ptr(qd), _ptr(tau), _ptr(q_out),
                                        _ptr(qd_out), _stream()), "sim_step_batch")
+        return q_out, qd_out
+
+    def step_static(self, q, qd, tau, q_out=None, qd_out=None):
+        """One step through sim_step_batch_static: no allocation by the library;
+        its scratch is a fixed-size static device array (SIM_STATIC_SCRATCH_BYTES)."""
+        B = self.B
+        self._arg(q, (self.nq_max, B), "q")
+        self._arg(qd, (self.nv_max, B), "qd")
+        self._arg(tau, (self.nv_max, B), "tau")
+        q_out = self.empty(self.nq_max, B) if q_out is None else q_out
+        qd_out = self.empty(self.nv_max, B) if qd_out is None else qd_out
+        self._check(lib.sim_step_batch_static(self._h, _ptr(q), _ptr(qd), _ptr(tau), _ptr(q_out),
+                                              _ptr(qd_out), _stream()), "sim_step_batch_static")
         return q_out, qd_out
 
     def rollout(self, q0, qd0, tau, k=1, ckpt=True, traj=False, out=None):

@@ -7,6 +7,7 @@
 #include <cmath>
 #include <cstdio>
 #include <cstring>
+#include <mutex>
 #include <string>
 #include <vector>
 
@@ -337,6 +338,49 @@ template <class T> int upload(sim_handle* h, const std::vector<double>& prm_h) {
 
 int check_handle(const sim_handle* h) { return h ? SIM_OK : SIM_EINVAL; }
 
+// ------------------------------------------------------------------ static scratch
+// Per-link tape for sim_step_batch_static: a file-scope device array, so that
+// entry point needs no allocation at all.  Every GPU that loads this library
+// holds it until the process exits.
+static __device__ __align__(256) unsigned char g_static_tape[SIM_STATIC_SCRATCH_BYTES];
+
+constexpr int kMaxDevices = 64;
+std::mutex g_static_mu;
+void* g_static_ptr[kMaxDevices] = {};
+
+// Device address of g_static_tape on the current device, looked up once per
+// device (the symbol's name in host code is only a host-side stand-in).
+int static_tape(sim_handle* h, void** out) {
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return cuda_fail(h, e, "static scratch: cudaGetDevice");
+  if (dev < 0 || dev >= kMaxDevices) return fail(h, SIM_EUNSUPPORTED, "static scratch: device index too large");
+  std::lock_guard<std::mutex> lock(g_static_mu);
+  if (!g_static_ptr[dev]) {
+    void* p = nullptr;
+    e = cudaGetSymbolAddress(&p, g_static_tape);
+    if (e != cudaSuccess) return cuda_fail(h, e, "static scratch: cudaGetSymbolAddress");
+    g_static_ptr[dev] = p;
+  }
+  *out = g_static_ptr[dev];
+  return SIM_OK;
+}
+
+template <class T>
+int launch_step_static(sim_handle* h, const void* q, const void* qd, const void* tau, void* q_out,
+                       void* qd_out, void* stream) {
+  void* tape = nullptr;
+  int rc = static_tape(h, &tape);
+  if (rc != SIM_OK) return rc;
+  DevModel<T> m = dev_model<T>(h);
+  m.tape = (T*)tape;
+  const int grid = (h->B + h->block - 1) / h->block;
+  k_rollout<T><<<grid, h->block, 0, S(stream)>>>(m, (const T*)q, (const T*)qd, (const T*)tau, 1LL, 1,
+                                                  (T*)nullptr, (T*)q_out, (T*)qd_out, (T*)nullptr);
+  cudaError_t e = cudaGetLastError();
+  return e == cudaSuccess ? SIM_OK : cuda_fail(h, e, "static step launch");
+}
+
 }  // namespace
 
 // ====================================================================== C ABI
@@ -480,6 +524,21 @@ int sim_step_batch(sim_handle* h, const void* q, const void* qd, const void* tau
   if (!h) return SIM_EINVAL;
   if (!tau) return fail(h, SIM_EINVAL, "null torque pointer");
   return sim_rollout(h, q, qd, tau, 1, 1, nullptr, q_out, qd_out, nullptr, stream);
+}
+
+int sim_step_batch_static(sim_handle* h, const void* q, const void* qd, const void* tau,
+                          void* q_out, void* qd_out, void* stream) {
+  if (!h) return SIM_EINVAL;
+  if (!q || !qd || !tau || !q_out || !qd_out) return fail(h, SIM_EINVAL, "null state or torque pointer");
+  const size_t need = (size_t)h->maxL * NTAPE * h->B * h->scalar;
+  if (need > (size_t)SIM_STATIC_SCRATCH_BYTES) {
+    char buf[200];
+    snprintf(buf, sizeof buf, "batch needs %zu bytes of step scratch; the static array holds %zu",
+             need, (size_t)SIM_STATIC_SCRATCH_BYTES);
+    return fail(h, SIM_ENOMEM, buf);
+  }
+  return is_fp64(h) ? launch_step_static<double>(h, q, qd, tau, q_out, qd_out, stream)
+                    : launch_step_static<float>(h, q, qd, tau, q_out, qd_out, stream);
 }
 
 int sim_backward_rollout(sim_handle* h, const void* ckpt, const void* tau, int64_t T, int32_t k,
