@@ -142,6 +142,15 @@ def run_ours(args):
     for _ in range(args.warmup):
         step()
     torch.cuda.synchronize()
+    graph = None
+    if args.graph:
+        # the whole step (forward rollout, adjoint rollout, mass-gradient gather) as one
+        # CUDA graph: the calls allocate nothing, so they capture as plain kernel nodes
+        graph = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(graph):
+            step()
+        graph.replay()
+        torch.cuda.synchronize()
     stop = threading.Event()
     samples = []
     th = threading.Thread(target=_clock_sampler, args=(stop, samples), daemon=True)
@@ -161,6 +170,16 @@ def run_ours(args):
     th.join()
     fwd_ms = [e[0].elapsed_time(e[1]) for e in events]
     adj_ms = [e[1].elapsed_time(e[2]) for e in events]
+    graph_ms = None
+    if graph is not None:   # the same step replayed as one CUDA graph
+        gev = [[torch.cuda.Event(enable_timing=True) for _ in range(2)] for _ in range(args.steps)]
+        for i in range(args.steps):
+            flush.fill_(float(i))
+            gev[i][0].record(stream)
+            graph.replay()
+            gev[i][1].record(stream)
+        torch.cuda.synchronize()
+        graph_ms = float(np.mean([a.elapsed_time(b) for a, b in gev]))
     step_ms = float(np.sum(fwd_ms) + np.sum(adj_ms)) / args.steps
     t = torch.tensor([step_ms], device=dev)
     if ws > 1:
@@ -188,9 +207,11 @@ def run_ours(args):
         "data": "synthetic",
         "config": {"workload": m.name, "n_systems": B, "horizon": T, "dt": m.dt, "checkpoint_interval": k,
                    "precision": args.precision, "l2": "flushed between steps (256 MB write)",
-                   "parallelism": f"replicas x{ws}" if ws > 1 else "single GPU", "block": sim_block(args)},
+                   "parallelism": f"replicas x{ws}" if ws > 1 else "single GPU", "block": sim_block(args),
+                   "cuda_graph": bool(args.graph)},
         "fwd_env_steps_per_s": B * T / (float(np.mean(fwd_ms)) / 1e3),
         "ms_fwd": float(np.mean(fwd_ms)), "ms_adj": float(np.mean(adj_ms)),
+        "ms_per_step_cuda_graph": graph_ms,
         "roofline": {"bound": "alu", "kernel": "k_backward", "achieved": achieved, "peak": peak["tflops"],
                      "unit": "TFLOP/s", "frac": achieved / peak["tflops"], "traffic": None,
                      "flops_per_system_step": {"fwd": f_fwd, "adj": f_adj}, "peak_note": peak["note"]},
@@ -199,9 +220,53 @@ def run_ours(args):
         "clocks": clocks,
         "nonfinite_systems": int((flags != 0).sum()),
     }
+    if args.plain:
+        pl = plain_per_system(work, args, k)
+        line["plain_per_system"] = pl
+        line["vs_plain_per_system"] = value / pl["value"]
     if args.cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(args)
     return line
+
+
+def plain_per_system(work, args, k, n_sys=64):
+    """The same kernels with one system per launch (a 1-system handle each), systems
+    run one after another: the per-system GPU version the batched path is compared
+    with.  n_sys systems are timed and the rate is per env-step (extrapolation to the
+    whole batch is linear: the launches are serial)."""
+    import numpy as np
+    import torch
+    from paper_2109_07719_gb300 import Simulator
+    m = work.model
+    T = work.T
+    sims, bufs = [], []
+    for b in range(min(n_sys, m.n_systems)):
+        sim = Simulator(m.subset([b]), precision=args.precision)
+        dev, dt = sim.device, sim.dtype
+        q0 = torch.tensor(work.q0[:, b:b + 1], dtype=dt, device=dev).contiguous()
+        qd0 = torch.tensor(work.qd0[:, b:b + 1], dtype=dt, device=dev).contiguous()
+        sims.append(sim)
+        bufs.append((q0, qd0))
+    tau_all = work.tau(device=sims[0].device, dtype=sims[0].dtype)
+    taus = [tau_all[:, :, b:b + 1].contiguous() for b in range(len(sims))]
+    del tau_all
+
+    def run_all():
+        for sim, (q0, qd0), tau in zip(sims, bufs, taus):
+            qT, qdT, ck, _ = sim.rollout(q0, qd0, tau, k=k)
+            sim.backward(ck, tau, torch.ones_like(qT), torch.zeros_like(qdT), k=k)
+
+    run_all()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    run_all()
+    e1.record()
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1)
+    return {"value": len(sims) * T / (ms / 1e3), "unit": "env-steps/s", "systems_timed": len(sims),
+            "ms": ms, "note": "one system per launch (rollout + adjoint), systems serial; "
+                              "rate per env-step from the timed systems"}
 
 
 def sim_block(args):
@@ -301,6 +366,8 @@ def main():
     ap.add_argument("--k", type=int, default=1)
     ap.add_argument("--block", type=int, default=0)
     ap.add_argument("--no-cpu-baseline", dest="cpu_baseline", action="store_false")
+    ap.add_argument("--no-plain", dest="plain", action="store_false")
+    ap.add_argument("--graph", action="store_true", help="replay the step as one CUDA graph")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
     line = run_reference(args) if args.impl == "reference" else run_ours(args)

@@ -35,16 +35,19 @@ enum : int {
 // per-link adjoint accumulators
 enum : int {
   G_A = 0, G_C = 6, G_E = 12, G_R = 21, G_U = 24, G_D = 30, G_u = 31, G_IA = 37, G_PA = 58,
-  G_V = 64, G_QDD = 70, NADJ = 76
+  G_V = 64, G_M = 70, NADJ = 71
 };
 
-// meta word per link: parent+1 (8 bits) | joint type (2) | q offset (11) | v offset (11)
+// meta word per link: parent+1 (8 bits) | joint type (1) | "has a child other than
+// link l+1" (1) | q offset (10) | v offset (10).  Chains never set the flag: their
+// parent/child values are carried in registers from one loop iteration to the next.
 SD int meta_parent(int m) { return (m & 0xff) - 1; }
-SD int meta_jtype(int m) { return (m >> 8) & 0x3; }
-SD int meta_qoff(int m) { return (m >> 10) & 0x7ff; }
-SD int meta_voff(int m) { return (m >> 21) & 0x7ff; }
-SD int make_meta(int parent, int jt, int qo, int vo) {
-  return (parent + 1) | (jt << 8) | (qo << 10) | (vo << 21);
+SD int meta_jtype(int m) { return (m >> 8) & 0x1; }
+SD bool meta_treechild(int m) { return (m >> 9) & 0x1; }
+SD int meta_qoff(int m) { return (m >> 10) & 0x3ff; }
+SD int meta_voff(int m) { return (m >> 20) & 0x3ff; }
+SD int make_meta(int parent, int jt, bool treechild, int qo, int vo) {
+  return (parent + 1) | (jt << 8) | ((treechild ? 1 : 0) << 9) | (qo << 10) | (vo << 20);
 }
 
 template <class T> SD void sincos_t(T x, T* s, T* c);
@@ -175,68 +178,103 @@ template <class T> SD SV<T> chol6_solve(const T* L, SV<T> b) {
 
 // ------------------------------------------------------------------ forward
 // Runs jcalc and the three ABA passes for the state (q, qd) and joint force tau,
-// leaving every intermediate on the tape (qdd included).
+// leaving every intermediate on the tape (qdd included).  Values passed between a
+// link and its parent ride in registers when the parent is the previous link (the
+// whole of a serial chain); other parents go through the tape.  Each iteration
+// loads what it needs before it stores anything, so the loads overlap.
 template <class T>
 SD void aba_forward(const Sys<T>& s, Col<const T> q, Col<const T> qd, Col<const T> tau, V3<T> grav) {
   const int nl = s.nl;
   // jcalc + pass 1 (root -> leaves)
+  SV<T> v_prev = zeroSV<T>();
   for (int l = 0; l < nl; ++l) {
     const int m = s.M(l);
     const int par = meta_parent(m), jt = meta_jtype(m), qo = meta_qoff(m), vo = meta_voff(m);
-    M3<T> Et = s.pm3(l, P_E);
-    V3<T> rt = s.pv3(l, P_R);
+    const M3<T> Et = s.pm3(l, P_E);
+    const V3<T> rt = s.pv3(l, P_R);
+    const T mass = s.P(l, P_M);
+    const V3<T> com = s.pv3(l, P_C);
+    const S3<T> Ic = s.ps3(l, P_IC);
+    SV<T> vpar = zeroSV<T>();
+    if (par >= 0) vpar = (par == l - 1) ? v_prev : tp_sv(s, par, T_V);
     XF<T> X;
     SV<T> vJ;
+    T sn = 0, cs = 1;
     if (jt == J_REVOLUTE) {
-      V3<T> a = s.pv3(l, P_AX);
-      T sn, cs;
-      sincos_t(q[qo], &sn, &cs);
-      s.tp(l, T_SC) = sn;
-      s.tp(l, T_SC + 1) = cs;
+      const V3<T> a = s.pv3(l, P_AX);
+      const T ql = q[qo], vl = qd[vo];
+      sincos_t(ql, &sn, &cs);
       X = XF<T>{mm(rot_axis_T(a, sn, cs), Et), rt};
-      vJ = SV<T>{qd[vo] * a, zero3<T>()};
+      vJ = SV<T>{vl * a, zero3<T>()};
     } else {
-      V3<T> p{q[qo], q[qo + 1], q[qo + 2]};
-      M3<T> EJ = transpose(quat_R(q[qo + 3], q[qo + 4], q[qo + 5], q[qo + 6]));
+      const V3<T> p{q[qo], q[qo + 1], q[qo + 2]};
+      const M3<T> EJ = transpose(quat_R(q[qo + 3], q[qo + 4], q[qo + 5], q[qo + 6]));
       X = compose(EJ, p, Et, rt);
       vJ = SV<T>{{qd[vo], qd[vo + 1], qd[vo + 2]}, {qd[vo + 3], qd[vo + 4], qd[vo + 5]}};
     }
     SV<T> v = vJ;
-    if (par >= 0) v += apply(X, tp_sv(s, par, T_V));
-    SV<T> c = crossm(v, vJ);
-    SI<T> I = rbi(s.P(l, P_M), s.pv3(l, P_C), s.ps3(l, P_IC));
-    SV<T> h = mul(I, v);
+    if (par >= 0) v += apply(X, vpar);
+    const SV<T> c = crossm(v, vJ);
+    const SI<T> I = rbi(mass, com, Ic);
+    const SV<T> h = mul(I, v);
     tp_xf(s, l, T_E, X);
     tp_sv(s, l, T_V, v);
     tp_sv(s, l, T_C, c);
     tp_sv(s, l, T_H, h);
     tp_si(s, l, T_IA, I);
     tp_sv(s, l, T_PA, crossf(v, h));
+    if (jt == J_REVOLUTE) {
+      s.tp(l, T_SC) = sn;
+      s.tp(l, T_SC + 1) = cs;
+    }
+    v_prev = v;
   }
   // pass 2 (leaves -> root)
+  SI<T> cI = zeroSI<T>();
+  SV<T> cp = zeroSV<T>();
+  bool carry = false;
   for (int l = nl - 1; l >= 0; --l) {
     const int m = s.M(l);
     const int par = meta_parent(m), jt = meta_jtype(m), vo = meta_voff(m);
     SI<T> IA = tp_si(s, l, T_IA);
     SV<T> pA = tp_sv(s, l, T_PA);
+    if (carry) {
+      IA += cI;
+      pA += cp;
+    }
+    carry = false;
     if (jt == J_REVOLUTE) {
-      V3<T> a = s.pv3(l, P_AX);
-      SV<T> U{mul(IA.A, a), mulT(IA.B, a)};
-      T D = dot(a, U.w);
-      T Di = T(1) / D;
-      T u = tau[vo] - dot(a, pA.w);
+      const V3<T> a = s.pv3(l, P_AX);
+      const T tl = tau[vo];
+      SV<T> c = zeroSV<T>();
+      XF<T> X;
+      if (par >= 0) {
+        c = tp_sv(s, l, T_C);
+        X = tp_xf(s, l, T_E);
+      }
+      const SV<T> U{mul(IA.A, a), mulT(IA.B, a)};
+      const T D = dot(a, U.w);
+      const T Di = T(1) / D;
+      const T u = tl - dot(a, pA.w);
       tp_sv(s, l, T_U, U);
       s.tp(l, T_D) = D;
       s.tp(l, T_DI) = Di;
       s.tp(l, T_u) = u;
       if (par >= 0) {
-        SI<T> Ia = IA - scale(Di, sym_outer(U, U));
-        SV<T> pa = pA + mul(Ia, tp_sv(s, l, T_C)) + (u * Di) * U;
+        const SI<T> Ia = IA - scale(Di, sym_outer(U, U));
+        const SV<T> pa = pA + mul(Ia, c) + (u * Di) * U;
         tp_si(s, l, T_Ia, Ia);
         tp_sv(s, l, T_pa, pa);
-        XF<T> X = tp_xf(s, l, T_E);
-        tp_si(s, par, T_IA, tp_si(s, par, T_IA) + congruence(X, Ia));
-        tp_sv(s, par, T_PA, tp_sv(s, par, T_PA) + applyT(X, pa));
+        const SI<T> Cn = congruence(X, Ia);
+        const SV<T> pn = applyT(X, pa);
+        if (par == l - 1) {
+          cI = Cn;
+          cp = pn;
+          carry = true;
+        } else {
+          tp_si(s, par, T_IA, tp_si(s, par, T_IA) + Cn);
+          tp_sv(s, par, T_PA, tp_sv(s, par, T_PA) + pn);
+        }
       }
     } else {  // free root: D = I^A, u = tau - p^A
       SV<T> u{{tau[vo], tau[vo + 1], tau[vo + 2]}, {tau[vo + 3], tau[vo + 4], tau[vo + 5]}};
@@ -249,26 +287,36 @@ SD void aba_forward(const Sys<T>& s, Col<const T> q, Col<const T> qd, Col<const 
   }
   // pass 3 (root -> leaves)
   const SV<T> a0{zero3<T>(), -grav};
+  SV<T> a_prev = a0;
   for (int l = 0; l < nl; ++l) {
     const int m = s.M(l);
     const int par = meta_parent(m), jt = meta_jtype(m);
-    XF<T> X = tp_xf(s, l, T_E);
-    SV<T> ap = apply(X, par >= 0 ? tp_sv(s, par, T_A) : a0) + tp_sv(s, l, T_C);
+    const XF<T> X = tp_xf(s, l, T_E);
+    const SV<T> c = tp_sv(s, l, T_C);
+    SV<T> apar = a0;
+    if (par >= 0) apar = (par == l - 1) ? a_prev : tp_sv(s, par, T_A);
     SV<T> a;
     if (jt == J_REVOLUTE) {
-      V3<T> ax = s.pv3(l, P_AX);
-      T qdd = (s.tp(l, T_u) - dot(tp_sv(s, l, T_U), ap)) * s.tp(l, T_DI);
+      const V3<T> ax = s.pv3(l, P_AX);
+      const SV<T> U = tp_sv(s, l, T_U);
+      const T u = s.tp(l, T_u), Di = s.tp(l, T_DI);
+      const SV<T> ap = apply(X, apar) + c;
+      const T qdd = (u - dot(U, ap)) * Di;
       s.tp(l, T_QDD) = qdd;
       a = ap;
       a.w += qdd * ax;
+      tp_sv(s, l, T_AP, ap);
     } else {
       T L[21];
       for (int i = 0; i < 21; ++i) L[i] = s.tp(l, T_Ia + i);
-      a = chol6_solve(L, tp_sv(s, l, T_u));
+      const SV<T> u = tp_sv(s, l, T_u);
+      const SV<T> ap = apply(X, apar) + c;
+      a = chol6_solve(L, u);
       tp_sv(s, l, T_QDD, a - ap);
+      tp_sv(s, l, T_AP, ap);
     }
-    tp_sv(s, l, T_AP, ap);
     tp_sv(s, l, T_A, a);
+    a_prev = a;
   }
 }
 
@@ -308,215 +356,290 @@ SD void integrate(const Sys<T>& s, Col<T> q, Col<T> qd, T dt, int integ) {
 }
 
 // ------------------------------------------------------------------ adjoint
+// Integrator adjoint of one link (folded into the pass-3 adjoint loop): turns the
+// adjoint of x^{k+1} held in (gq, gqd) into the direct part of the adjoint of x^k
+// for this link's coordinates and returns the adjoint of its qdd in qddb[0..nv).
+template <class T>
+SD void integrator_adjoint(const Sys<T>& s, int l, int jt, int qo, int vo, Col<const T> q,
+                           Col<const T> qd, Col<T> gq, Col<T> gqd, T dt, int integ, T* qddb) {
+  const T half = T(0.5);
+  if (jt == J_REVOLUTE) {
+    const T qb = gq[qo], vb = gqd[vo];
+    if (integ == I_SEMI_IMPLICIT) {
+      const T vt = vb + dt * qb;
+      gqd[vo] = vt;
+      qddb[0] = dt * vt;
+    } else {
+      gqd[vo] = vb + dt * qb;
+      qddb[0] = dt * vb;
+    }
+    return;
+  }
+  T nu[6], nub[6];
+  for (int i = 0; i < 6; ++i) {
+    const T v0 = qd[vo + i];
+    nu[i] = integ == I_SEMI_IMPLICIT ? v0 + dt * s.tp(l, T_QDD + i) : v0;
+    nub[i] = gqd[vo + i];
+  }
+  const T qt[4] = {q[qo + 3], q[qo + 4], q[qo + 5], q[qo + 6]};
+  const T wq[4] = {nu[0], nu[1], nu[2], T(0)};
+  T r[4], raw[4];
+  quat_mul(qt, wq, r);
+  for (int i = 0; i < 4; ++i) raw[i] = qt[i] + half * dt * r[i];
+  const T n = sqrt_t(raw[0] * raw[0] + raw[1] * raw[1] + raw[2] * raw[2] + raw[3] * raw[3]);
+  T qn[4], qnb[4], rawb[4];
+  T d = 0;
+  for (int i = 0; i < 4; ++i) {
+    qn[i] = raw[i] / n;
+    qnb[i] = gq[qo + 3 + i];
+    d += qn[i] * qnb[i];
+  }
+  for (int i = 0; i < 4; ++i) rawb[i] = (qnb[i] - qn[i] * d) / n;
+  // raw = quat + dt/2 quat (x) (w, 0):  quat_bar += rawb (x) (w, 0)^*,  w_bar = vec(quat^* (x) rawb)
+  T qb[4] = {rawb[0], rawb[1], rawb[2], rawb[3]};
+  const T wconj[4] = {-nu[0], -nu[1], -nu[2], T(0)};
+  T t1[4];
+  quat_mul(rawb, wconj, t1);
+  for (int i = 0; i < 4; ++i) qb[i] += half * dt * t1[i];
+  const T qconj[4] = {-qt[0], -qt[1], -qt[2], qt[3]};
+  T t2[4];
+  quat_mul(qconj, rawb, t2);
+  T velb[6] = {half * dt * t2[0], half * dt * t2[1], half * dt * t2[2], 0, 0, 0};
+  // p' = p + dt R(quat) v
+  const V3<T> pb{gq[qo], gq[qo + 1], gq[qo + 2]};
+  const M3<T> R = quat_R(qt[0], qt[1], qt[2], qt[3]);
+  const V3<T> vvb = dt * mulT(R, pb);
+  velb[3] = vvb.x;
+  velb[4] = vvb.y;
+  velb[5] = vvb.z;
+  quat_R_adj(qt[0], qt[1], qt[2], qt[3], scale(dt, outer(pb, V3<T>{nu[3], nu[4], nu[5]})), qb);
+  for (int i = 0; i < 4; ++i) gq[qo + 3 + i] = qb[i];
+  for (int i = 0; i < 6; ++i) {
+    if (integ == I_SEMI_IMPLICIT) {
+      const T tot = nub[i] + velb[i];
+      gqd[vo + i] = tot;
+      qddb[i] = dt * tot;
+    } else {
+      gqd[vo + i] = nub[i] + velb[i];
+      qddb[i] = dt * nub[i];
+    }
+  }
+}
+
 // Requires aba_forward(q, qd, tau) to have filled the tape.  On entry gq, gqd hold
 // the adjoint of x^{k+1}; on exit they hold the adjoint of x^k.  Writes the
 // adjoint of tau into gtau and adds dPhi/dm of every link into gm[l * B].
+// Adjoints flowing between a link and its parent ride in registers when the
+// parent is the previous link; accumulators in the adjoint tape serve the other
+// (tree) children and are zeroed first only for links that have such children.
 template <class T>
 SD void step_adjoint(const Sys<T>& s, Col<const T> q, Col<const T> qd, Col<T> gq, Col<T> gqd,
                      Col<T> gtau, Col<T> gm, V3<T> grav, T dt, int integ) {
   const int nl = s.nl;
   const T half = T(0.5);
-  // integrator adjoint; zero the per-link accumulators
   for (int l = 0; l < nl; ++l) {
-    const int m = s.M(l);
-    const int jt = meta_jtype(m), qo = meta_qoff(m), vo = meta_voff(m);
-    for (int f = 0; f < NADJ; ++f) s.ad(l, f) = T(0);
-    if (jt == J_REVOLUTE) {
-      T qb = gq[qo], vb = gqd[vo];
-      if (integ == I_SEMI_IMPLICIT) {
-        T vt = vb + dt * qb;
-        gqd[vo] = vt;
-        s.ad(l, G_QDD) = dt * vt;
+    if (meta_treechild(s.M(l))) {
+      ad_sv(s, l, G_A, zeroSV<T>());
+      ad_sv(s, l, G_V, zeroSV<T>());
+    }
+  }
+  const SV<T> a0{zero3<T>(), -grav};
+  // integrator adjoint + pass 3 adjoint (leaves -> root)
+  {
+    SV<T> cab = zeroSV<T>();
+    bool carry = false;
+    for (int l = nl - 1; l >= 0; --l) {
+      const int m = s.M(l);
+      const int par = meta_parent(m), jt = meta_jtype(m), qo = meta_qoff(m), vo = meta_voff(m);
+      const XF<T> X = tp_xf(s, l, T_E);
+      SV<T> apar = a0;
+      if (par >= 0) apar = tp_sv(s, par, T_A);
+      SV<T> ab = meta_treechild(m) ? ad_sv(s, l, G_A) : zeroSV<T>();
+      if (carry) ab += cab;
+      carry = false;
+      T qddb[6];
+      integrator_adjoint(s, l, jt, qo, vo, q, qd, gq, gqd, dt, integ, qddb);
+      SV<T> apb;
+      if (jt == J_REVOLUTE) {
+        const V3<T> ax = s.pv3(l, P_AX);
+        const SV<T> U = tp_sv(s, l, T_U);
+        const SV<T> ap = tp_sv(s, l, T_AP);
+        const T Di = s.tp(l, T_DI), qdd = s.tp(l, T_QDD);
+        const T qb = qddb[0] + dot(ax, ab.w);
+        const T wb = qb * Di;
+        apb = ab - wb * U;
+        ad_sv(s, l, G_U, zeroSV<T>() - wb * ap);
+        s.ad(l, G_D) = -wb * qdd;
+        s.ad(l, G_u) = wb;
       } else {
-        gqd[vo] = vb + dt * qb;
-        s.ad(l, G_QDD) = dt * vb;
+        const SV<T> qb{{qddb[0], qddb[1], qddb[2]}, {qddb[3], qddb[4], qddb[5]}};
+        const SV<T> a = tp_sv(s, l, T_A);
+        T L[21];
+        for (int i = 0; i < 21; ++i) L[i] = s.tp(l, T_Ia + i);
+        const SV<T> ub = chol6_solve(L, ab + qb);
+        apb = zeroSV<T>() - qb;
+        ad_sv(s, l, G_u, ub);
+        ad_si(s, l, G_IA, scale(T(-1), sym_outer(ub, a)));
       }
-    } else {
-      T nu[6], nub[6];
-      for (int i = 0; i < 6; ++i) {
-        T v0 = qd[vo + i];
-        nu[i] = integ == I_SEMI_IMPLICIT ? v0 + dt * s.tp(l, T_QDD + i) : v0;
-        nub[i] = gqd[vo + i];
-      }
-      T qt[4] = {q[qo + 3], q[qo + 4], q[qo + 5], q[qo + 6]};
-      T wq[4] = {nu[0], nu[1], nu[2], T(0)};
-      T r[4], raw[4];
-      quat_mul(qt, wq, r);
-      for (int i = 0; i < 4; ++i) raw[i] = qt[i] + half * dt * r[i];
-      T n = sqrt_t(raw[0] * raw[0] + raw[1] * raw[1] + raw[2] * raw[2] + raw[3] * raw[3]);
-      T qn[4], qnb[4], rawb[4];
-      T d = 0;
-      for (int i = 0; i < 4; ++i) { qn[i] = raw[i] / n; qnb[i] = gq[qo + 3 + i]; d += qn[i] * qnb[i]; }
-      for (int i = 0; i < 4; ++i) rawb[i] = (qnb[i] - qn[i] * d) / n;
-      // raw = quat + dt/2 quat (x) (w, 0)
-      T qb[4] = {rawb[0], rawb[1], rawb[2], rawb[3]};
-      T wconj[4] = {-nu[0], -nu[1], -nu[2], T(0)};
-      T t1[4];
-      quat_mul(rawb, wconj, t1);
-      for (int i = 0; i < 4; ++i) qb[i] += half * dt * t1[i];
-      T qconj[4] = {-qt[0], -qt[1], -qt[2], qt[3]};
-      T t2[4];
-      quat_mul(qconj, rawb, t2);
-      T velb[6] = {half * dt * t2[0], half * dt * t2[1], half * dt * t2[2], 0, 0, 0};
-      // p' = p + dt R(quat) v
-      V3<T> pb{gq[qo], gq[qo + 1], gq[qo + 2]};
-      M3<T> R = quat_R(qt[0], qt[1], qt[2], qt[3]);
-      V3<T> vvb = dt * mulT(R, pb);
-      velb[3] = vvb.x; velb[4] = vvb.y; velb[5] = vvb.z;
-      quat_R_adj(qt[0], qt[1], qt[2], qt[3], scale(dt, outer(pb, V3<T>{nu[3], nu[4], nu[5]})), qb);
-      for (int i = 0; i < 4; ++i) gq[qo + 3 + i] = qb[i];
-      for (int i = 0; i < 6; ++i) {
-        if (integ == I_SEMI_IMPLICIT) {
-          T tot = nub[i] + velb[i];
-          gqd[vo + i] = tot;
-          s.ad(l, G_QDD + i) = dt * tot;
+      ad_sv(s, l, G_C, apb);
+      M3<T> Eb = zeroM3<T>();
+      V3<T> rb = zero3<T>();
+      SV<T> apar_b = zeroSV<T>();
+      apply_adj(X, apar, apb, Eb, rb, par >= 0 ? &apar_b : (SV<T>*)nullptr);
+      ad_m3(s, l, G_E, Eb);
+      ad_v3(s, l, G_R, rb);
+      if (par >= 0) {
+        if (par == l - 1) {
+          cab = apar_b;
+          carry = true;
         } else {
-          gqd[vo + i] = nub[i] + velb[i];
-          s.ad(l, G_QDD + i) = dt * nub[i];
+          ad_sv(s, par, G_A, ad_sv(s, par, G_A) + apar_b);
         }
       }
     }
   }
-  const SV<T> a0{zero3<T>(), -grav};
-  // pass 3 adjoint (leaves -> root)
-  for (int l = nl - 1; l >= 0; --l) {
-    const int m = s.M(l);
-    const int par = meta_parent(m), jt = meta_jtype(m);
-    XF<T> X = tp_xf(s, l, T_E);
-    SV<T> ab = ad_sv(s, l, G_A);
-    SV<T> apb;
-    if (jt == J_REVOLUTE) {
-      V3<T> ax = s.pv3(l, P_AX);
-      T qddb = s.ad(l, G_QDD) + dot(ax, ab.w);
-      apb = ab;
-      T wb = qddb * s.tp(l, T_DI);
-      s.ad(l, G_D) += -wb * s.tp(l, T_QDD);
-      s.ad(l, G_u) += wb;
-      SV<T> U = tp_sv(s, l, T_U);
-      ad_sv(s, l, G_U, ad_sv(s, l, G_U) - wb * tp_sv(s, l, T_AP));
-      apb -= wb * U;
-    } else {
-      SV<T> qddb = ad_sv(s, l, G_QDD);
-      SV<T> gb = ab + qddb;
-      apb = zeroSV<T>() - qddb;
-      T L[21];
-      for (int i = 0; i < 21; ++i) L[i] = s.tp(l, T_Ia + i);
-      SV<T> ub = chol6_solve(L, gb);
-      ad_sv(s, l, G_u, ub);
-      SI<T> IAb = ad_si(s, l, G_IA);
-      IAb += scale(T(-1), sym_outer(ub, tp_sv(s, l, T_A)));
-      ad_si(s, l, G_IA, IAb);
-    }
-    ad_sv(s, l, G_C, ad_sv(s, l, G_C) + apb);
-    M3<T> Eb = ad_m3(s, l, G_E);
-    V3<T> rb = ad_v3(s, l, G_R);
-    if (par >= 0) {
-      SV<T> apar_b = ad_sv(s, par, G_A);
-      apply_adj(X, tp_sv(s, par, T_A), apb, Eb, rb, &apar_b);
-      ad_sv(s, par, G_A, apar_b);
-    } else {
-      apply_adj(X, a0, apb, Eb, rb, (SV<T>*)nullptr);
-    }
-    ad_m3(s, l, G_E, Eb);
-    ad_v3(s, l, G_R, rb);
-  }
   // pass 2 adjoint (root -> leaves)
-  for (int l = 0; l < nl; ++l) {
-    const int m = s.M(l);
-    const int par = meta_parent(m), jt = meta_jtype(m), vo = meta_voff(m);
-    SI<T> IAb = ad_si(s, l, G_IA);
-    SV<T> pAb = ad_sv(s, l, G_PA);
-    if (jt == J_REVOLUTE) {
-      V3<T> ax = s.pv3(l, P_AX);
-      SV<T> Ub = ad_sv(s, l, G_U);
-      T Db = s.ad(l, G_D);
-      T ub = s.ad(l, G_u);
-      const T Di = s.tp(l, T_DI);
-      const T u = s.tp(l, T_u);
-      SV<T> U = tp_sv(s, l, T_U);
-      if (par >= 0) {
-        XF<T> X = tp_xf(s, l, T_E);
-        M3<T> Eb = ad_m3(s, l, G_E);
-        V3<T> rb = ad_v3(s, l, G_R);
-        SV<T> pab = zeroSV<T>();
-        SI<T> Iab = zeroSI<T>();
-        SI<T> Ia = tp_si(s, l, T_Ia);
-        applyT_adj(X, tp_sv(s, l, T_pa), ad_sv(s, par, G_PA), Eb, rb, &pab);
-        congruence_adj(X, Ia, ad_si(s, par, G_IA), Iab, Eb, rb);
-        ad_m3(s, l, G_E, Eb);
-        ad_v3(s, l, G_R, rb);
-        // pa = pA + Ia c + U (u / D)
-        SV<T> c = tp_sv(s, l, T_C);
-        pAb += pab;
-        Iab += sym_outer(pab, c);
-        ad_sv(s, l, G_C, ad_sv(s, l, G_C) + mul(Ia, pab));
-        Ub += (u * Di) * pab;
-        T gb = dot(U, pab);
-        ub += gb * Di;
-        Db -= gb * u * Di * Di;
-        // Ia = IA - U U^T / D
-        IAb += Iab;
-        SV<T> IbU = mul(Iab, U);
-        Ub -= (T(2) * Di) * IbU;
-        Db += Di * Di * dot(U, IbU);
+  {
+    SI<T> cIAb = zeroSI<T>();
+    SV<T> cpAb = zeroSV<T>();
+    for (int l = 0; l < nl; ++l) {
+      const int m = s.M(l);
+      const int par = meta_parent(m), jt = meta_jtype(m), vo = meta_voff(m);
+      SV<T> pAb = zeroSV<T>();
+      SI<T> IAb;
+      if (jt == J_REVOLUTE) {
+        const V3<T> ax = s.pv3(l, P_AX);
+        SV<T> Ub = ad_sv(s, l, G_U);
+        T Db = s.ad(l, G_D);
+        T ub = s.ad(l, G_u);
+        const T Di = s.tp(l, T_DI);
+        const T u = s.tp(l, T_u);
+        const SV<T> U = tp_sv(s, l, T_U);
+        IAb = zeroSI<T>();
+        if (par >= 0) {
+          const XF<T> X = tp_xf(s, l, T_E);
+          const SI<T> Ia = tp_si(s, l, T_Ia);
+          const SV<T> pa = tp_sv(s, l, T_pa);
+          const SV<T> c = tp_sv(s, l, T_C);
+          SV<T> cb = ad_sv(s, l, G_C);
+          M3<T> Eb = ad_m3(s, l, G_E);
+          V3<T> rb = ad_v3(s, l, G_R);
+          SI<T> IAbp;
+          SV<T> pAbp;
+          if (par == l - 1) {
+            IAbp = cIAb;
+            pAbp = cpAb;
+          } else {
+            IAbp = ad_si(s, par, G_IA);
+            pAbp = ad_sv(s, par, G_PA);
+          }
+          SV<T> pab = zeroSV<T>();
+          SI<T> Iab = zeroSI<T>();
+          applyT_adj(X, pa, pAbp, Eb, rb, &pab);
+          congruence_adj(X, Ia, IAbp, Iab, Eb, rb);
+          ad_m3(s, l, G_E, Eb);
+          ad_v3(s, l, G_R, rb);
+          // pa = pA + Ia c + U (u / D)
+          pAb += pab;
+          Iab += sym_outer(pab, c);
+          cb += mul(Ia, pab);
+          ad_sv(s, l, G_C, cb);
+          Ub += (u * Di) * pab;
+          const T gb = dot(U, pab);
+          ub += gb * Di;
+          Db -= gb * u * Di * Di;
+          // Ia = IA - U U^T / D
+          IAb += Iab;
+          const SV<T> IbU = mul(Iab, U);
+          Ub -= (T(2) * Di) * IbU;
+          Db += Di * Di * dot(U, IbU);
+        }
+        // u = tau - S^T pA,  D = S^T U,  U = IA S
+        gtau[vo] = ub;
+        pAb.w -= ub * ax;
+        Ub.w += Db * ax;
+        IAb.A += sym_outer(Ub.w, ax);
+        IAb.B += scale(half, outer(ax, Ub.v));
+      } else {
+        const SV<T> ub = ad_sv(s, l, G_u);
+        IAb = ad_si(s, l, G_IA);
+        gtau[vo] = ub.w.x;
+        gtau[vo + 1] = ub.w.y;
+        gtau[vo + 2] = ub.w.z;
+        gtau[vo + 3] = ub.v.x;
+        gtau[vo + 4] = ub.v.y;
+        gtau[vo + 5] = ub.v.z;
+        pAb -= ub;
       }
-      // u = tau - S^T pA,  D = S^T U,  U = IA S
-      gtau[vo] = ub;
-      pAb.w -= ub * ax;
-      Ub.w += Db * ax;
-      IAb.A += sym_outer(Ub.w, ax);
-      IAb.B += scale(half, outer(ax, Ub.v));
-    } else {
-      SV<T> ub = ad_sv(s, l, G_u);
-      gtau[vo] = ub.w.x; gtau[vo + 1] = ub.w.y; gtau[vo + 2] = ub.w.z;
-      gtau[vo + 3] = ub.v.x; gtau[vo + 4] = ub.v.y; gtau[vo + 5] = ub.v.z;
-      pAb -= ub;
+      if (meta_treechild(m)) ad_si(s, l, G_IA, IAb);
+      ad_sv(s, l, G_PA, pAb);
+      s.ad(l, G_M) = rbi_dmass(IAb, s.pv3(l, P_C));
+      cIAb = IAb;
+      cpAb = pAb;
     }
-    ad_si(s, l, G_IA, IAb);
-    ad_sv(s, l, G_PA, pAb);
-    gm[l] += rbi_dmass(IAb, s.pv3(l, P_C));
   }
   // pass 1 adjoint + jcalc adjoint (leaves -> root)
-  for (int l = nl - 1; l >= 0; --l) {
-    const int m = s.M(l);
-    const int par = meta_parent(m), jt = meta_jtype(m), qo = meta_qoff(m), vo = meta_voff(m);
-    SV<T> v = tp_sv(s, l, T_V);
-    SV<T> h = tp_sv(s, l, T_H);
-    SV<T> vb = ad_sv(s, l, G_V);
-    SV<T> hb = zeroSV<T>();
-    crossf_adj(v, h, ad_sv(s, l, G_PA), vb, hb);
-    V3<T> com = s.pv3(l, P_C);
-    SI<T> I = rbi(s.P(l, P_M), com, s.ps3(l, P_IC));
-    gm[l] += rbi_dmass_bilinear(hb, v, com);
-    vb += mul(I, hb);
-    SV<T> vJ;
-    if (jt == J_REVOLUTE) vJ = SV<T>{qd[vo] * s.pv3(l, P_AX), zero3<T>()};
-    else vJ = SV<T>{{qd[vo], qd[vo + 1], qd[vo + 2]}, {qd[vo + 3], qd[vo + 4], qd[vo + 5]}};
-    SV<T> vJb = zeroSV<T>();
-    crossm_adj(v, vJ, ad_sv(s, l, G_C), vb, vJb);
-    vJb += vb;
-    XF<T> X = tp_xf(s, l, T_E);
-    M3<T> Eb = ad_m3(s, l, G_E);
-    V3<T> rb = ad_v3(s, l, G_R);
-    if (par >= 0) {
-      SV<T> vpb = ad_sv(s, par, G_V);
-      apply_adj(X, tp_sv(s, par, T_V), vb, Eb, rb, &vpb);
-      ad_sv(s, par, G_V, vpb);
-    }
-    M3<T> Et = s.pm3(l, P_E);
-    M3<T> EJb = mmT(Eb, Et);  // E = E_J E_t
-    if (jt == J_REVOLUTE) {
-      V3<T> ax = s.pv3(l, P_AX);
-      gqd[vo] += dot(ax, vJb.w);
-      gq[qo] += rot_axis_T_dq(ax, s.tp(l, T_SC), s.tp(l, T_SC + 1), EJb);
-    } else {
-      T vv[6] = {vJb.w.x, vJb.w.y, vJb.w.z, vJb.v.x, vJb.v.y, vJb.v.z};
-      for (int i = 0; i < 6; ++i) gqd[vo + i] += vv[i];
-      V3<T> pb = mul(Et, rb);  // r = r_t + E_t^T p
-      gq[qo] += pb.x; gq[qo + 1] += pb.y; gq[qo + 2] += pb.z;
-      T qb[4] = {0, 0, 0, 0};
-      quat_R_adj(q[qo + 3], q[qo + 4], q[qo + 5], q[qo + 6], transpose(EJb), qb);
-      for (int i = 0; i < 4; ++i) gq[qo + 3 + i] += qb[i];
+  {
+    SV<T> cvb = zeroSV<T>();
+    bool carry = false;
+    for (int l = nl - 1; l >= 0; --l) {
+      const int m = s.M(l);
+      const int par = meta_parent(m), jt = meta_jtype(m), qo = meta_qoff(m), vo = meta_voff(m);
+      const SV<T> v = tp_sv(s, l, T_V);
+      const SV<T> h = tp_sv(s, l, T_H);
+      const SV<T> pAb = ad_sv(s, l, G_PA);
+      const SV<T> cb = ad_sv(s, l, G_C);
+      const XF<T> X = tp_xf(s, l, T_E);
+      M3<T> Eb = ad_m3(s, l, G_E);
+      V3<T> rb = ad_v3(s, l, G_R);
+      SV<T> vpar = zeroSV<T>();
+      if (par >= 0) vpar = tp_sv(s, par, T_V);
+      const V3<T> com = s.pv3(l, P_C);
+      const T mass = s.P(l, P_M);
+      const S3<T> Ic = s.ps3(l, P_IC);
+      const M3<T> Et = s.pm3(l, P_E);
+      T gml = s.ad(l, G_M);
+      SV<T> vb = meta_treechild(m) ? ad_sv(s, l, G_V) : zeroSV<T>();
+      if (carry) vb += cvb;
+      carry = false;
+      SV<T> hb = zeroSV<T>();
+      crossf_adj(v, h, pAb, vb, hb);
+      const SI<T> I = rbi(mass, com, Ic);
+      gml += rbi_dmass_bilinear(hb, v, com);
+      vb += mul(I, hb);
+      SV<T> vJ;
+      if (jt == J_REVOLUTE) vJ = SV<T>{qd[vo] * s.pv3(l, P_AX), zero3<T>()};
+      else vJ = SV<T>{{qd[vo], qd[vo + 1], qd[vo + 2]}, {qd[vo + 3], qd[vo + 4], qd[vo + 5]}};
+      SV<T> vJb = zeroSV<T>();
+      crossm_adj(v, vJ, cb, vb, vJb);
+      vJb += vb;
+      if (par >= 0) {
+        SV<T> vpb = zeroSV<T>();
+        apply_adj(X, vpar, vb, Eb, rb, &vpb);
+        if (par == l - 1) {
+          cvb = vpb;
+          carry = true;
+        } else {
+          ad_sv(s, par, G_V, ad_sv(s, par, G_V) + vpb);
+        }
+      }
+      const M3<T> EJb = mmT(Eb, Et);  // E = E_J E_t
+      if (jt == J_REVOLUTE) {
+        const V3<T> ax = s.pv3(l, P_AX);
+        gqd[vo] += dot(ax, vJb.w);
+        gq[qo] += rot_axis_T_dq(ax, s.tp(l, T_SC), s.tp(l, T_SC + 1), EJb);
+      } else {
+        const T vv[6] = {vJb.w.x, vJb.w.y, vJb.w.z, vJb.v.x, vJb.v.y, vJb.v.z};
+        for (int i = 0; i < 6; ++i) gqd[vo + i] += vv[i];
+        const V3<T> pb = mul(Et, rb);  // r = r_t + E_t^T p
+        gq[qo] += pb.x;
+        gq[qo + 1] += pb.y;
+        gq[qo + 2] += pb.z;
+        T qb[4] = {0, 0, 0, 0};
+        quat_R_adj(q[qo + 3], q[qo + 4], q[qo + 5], q[qo + 6], transpose(EJb), qb);
+        for (int i = 0; i < 4; ++i) gq[qo + 3 + i] += qb[i];
+      }
+      gm[l] += gml;
     }
   }
 }

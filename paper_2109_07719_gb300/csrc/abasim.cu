@@ -19,7 +19,7 @@ using namespace abasim;
 namespace {
 
 constexpr int kMaxLinks = 255;
-constexpr int kMaxCoords = 2047;
+constexpr int kMaxCoords = 1023;
 constexpr int kDefaultBlock = 32;
 
 thread_local std::string g_create_error;
@@ -423,7 +423,10 @@ int sim_create(const sim_model_desc* d, sim_handle** out) {
       }
       P(P_M) = d->mass[i];
       for (int x = 0; x < 6; ++x) P(P_IC + x) = d->I_com[6 * i + x];
-      meta[(size_t)l * B + b] = make_meta(d->parent[i], jt, qo, vo);
+      bool treechild = false;  // a child other than link l + 1
+      for (int c = l + 2; c < nl[b]; ++c)
+        if (d->parent[d->sys_link_offset[b] + c] == l) treechild = true;
+      meta[(size_t)l * B + b] = make_meta(d->parent[i], jt, treechild, qo, vo);
       slot[i] = l * B + b;
       qo += jt == SIM_FREE ? 7 : 1;
       vo += jt == SIM_FREE ? 6 : 1;

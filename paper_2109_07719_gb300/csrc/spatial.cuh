@@ -278,21 +278,23 @@ template <class T> SD void congruence_adj(const XF<T>& X, const SI<T>& I, const 
 
 // ------------------------------------------------------------------ rotations
 // E_J of a revolute joint about unit axis a by angle q: R(a, q)^T with Rodrigues'
-// R = 1 + s K + (1 - c) K^2, K = skew(a)
+// R = 1 + s K + (1 - c) K^2, K = skew(a); for a unit axis K^2 = a a^T - 1, so
+// E_J = c 1 - s K + (1 - c) a a^T
 template <class T> SD M3<T> rot_axis_T(V3<T> a, T s, T c) {
-  M3<T> K = skew(a);
-  M3<T> K2 = mm(K, K);
-  M3<T> o;
-  for (int i = 0; i < 9; ++i) o.a[i] = (i % 4 == 0 ? T(1) : T(0)) - s * K.a[i] + (T(1) - c) * K2.a[i];
-  return o;
+  const T k = T(1) - c;
+  const T xy = k * a.x * a.y, xz = k * a.x * a.z, yz = k * a.y * a.z;
+  return M3<T>{{c + k * a.x * a.x, xy + s * a.z, xz - s * a.y,
+                xy - s * a.z, c + k * a.y * a.y, yz + s * a.x,
+                xz + s * a.y, yz - s * a.x, c + k * a.z * a.z}};
 }
-// d/dq of rot_axis_T: -c K + s K^2
+// <Gb, dE_J/dq> with dE_J/dq = -s 1 - c K + s a a^T
 template <class T> SD T rot_axis_T_dq(V3<T> a, T s, T c, const M3<T>& Gb) {
-  M3<T> K = skew(a);
-  M3<T> K2 = mm(K, K);
-  T acc = 0;
-  for (int i = 0; i < 9; ++i) acc += Gb.a[i] * (-c * K.a[i] + s * K2.a[i]);
-  return acc;
+  const T* g = Gb.a;
+  const T tr = g[0] + g[4] + g[8];
+  // <G, K> = a.x (g7 - g5) + a.y (g2 - g6) + a.z (g3 - g1)
+  const T gk = a.x * (g[7] - g[5]) + a.y * (g[2] - g[6]) + a.z * (g[3] - g[1]);
+  const V3<T> Ga = mul(Gb, a);
+  return -s * tr - c * gk + s * dot(a, Ga);
 }
 // body -> world rotation of the unit quaternion (x, y, z, w)
 template <class T> SD M3<T> quat_R(T x, T y, T z, T w) {

@@ -48,7 +48,7 @@ static Counts count(int n, bool free_root) {
     for (int f = 0; f < 9; ++f) prm[l * NPRM + P_E + f] = F(f % 4 == 0 ? 1.0 : 0.0);
     prm[l * NPRM + P_AX] = 0; prm[l * NPRM + P_AX + 1] = 0; prm[l * NPRM + P_AX + 2] = 1;
     prm[l * NPRM + P_M] = 1;
-    meta[l] = make_meta(l == 0 ? -1 : 0, fr ? J_FREE : J_REVOLUTE, qo, vo);
+    meta[l] = make_meta(l == 0 ? -1 : 0, fr ? J_FREE : J_REVOLUTE, false, qo, vo);
     qo += fr ? 7 : 1;
     vo += fr ? 6 : 1;
   }
