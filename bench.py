@@ -109,8 +109,11 @@ def run_ours(args):
     m = work.model
     T, k = work.T, args.k
     sim = Simulator(m, precision=args.precision)
-    if args.block:
-        sim.set_block(args.block)
+    if args.autotune:
+        tuned = sim.autotune(torch.tensor(work.q0, dtype=sim.dtype, device=sim.device),
+                             torch.tensor(work.qd0, dtype=sim.dtype, device=sim.device))
+    elif args.block or args.persistent:
+        sim.set_launch(args.block, args.persistent)
     dev, dt = sim.device, sim.dtype
     B = sim.B
     q0 = torch.tensor(work.q0, dtype=dt, device=dev)
@@ -189,8 +192,10 @@ def run_ours(args):
     units = B * T * ws
     value = units / (step_ms / 1e3)
     # end to end through the public API with host buffers
-    e2e = run_e2e(sim, work, k, args.steps, tau.cpu().pin_memory(), q0.cpu().pin_memory(),
-                  qd0.cpu().pin_memory())
+    e2e = None
+    if args.e2e:
+        e2e = run_e2e(sim, work, k, args.steps, tau.cpu().pin_memory(), q0.cpu().pin_memory(),
+                      qd0.cpu().pin_memory())
     if rank != 0:
         return None
     f_fwd = flops_per_system_step(m, "fwd")
@@ -207,7 +212,8 @@ def run_ours(args):
         "data": "synthetic",
         "config": {"workload": m.name, "n_systems": B, "horizon": T, "dt": m.dt, "checkpoint_interval": k,
                    "precision": args.precision, "l2": "flushed between steps (256 MB write)",
-                   "parallelism": f"replicas x{ws}" if ws > 1 else "single GPU", "block": sim_block(args),
+                   "parallelism": f"replicas x{ws}" if ws > 1 else "single GPU",
+                   "block": sim.launch[0], "schedule": "persistent" if sim.launch[1] else "grid",
                    "cuda_graph": bool(args.graph)},
         "fwd_env_steps_per_s": B * T / (float(np.mean(fwd_ms)) / 1e3),
         "ms_fwd": float(np.mean(fwd_ms)), "ms_adj": float(np.mean(adj_ms)),
@@ -267,10 +273,6 @@ def plain_per_system(work, args, k, n_sys=64):
     return {"value": len(sims) * T / (ms / 1e3), "unit": "env-steps/s", "systems_timed": len(sims),
             "ms": ms, "note": "one system per launch (rollout + adjoint), systems serial; "
                               "rate per env-step from the timed systems"}
-
-
-def sim_block(args):
-    return args.block or 32
 
 
 def fp_peak(precision):
@@ -365,8 +367,11 @@ def main():
     ap.add_argument("--horizon", type=int, default=None)
     ap.add_argument("--k", type=int, default=1)
     ap.add_argument("--block", type=int, default=0)
+    ap.add_argument("--persistent", action="store_true")
+    ap.add_argument("--autotune", action="store_true")
     ap.add_argument("--no-cpu-baseline", dest="cpu_baseline", action="store_false")
     ap.add_argument("--no-plain", dest="plain", action="store_false")
+    ap.add_argument("--no-e2e", dest="e2e", action="store_false")
     ap.add_argument("--graph", action="store_true", help="replay the step as one CUDA graph")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)

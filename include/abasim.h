@@ -161,9 +161,21 @@ int sim_backward_rollout(sim_handle* h, const void* ckpt, const void* tau, int64
 int sim_status(sim_handle* h, int32_t* flags);
 int sim_clear_status(sim_handle* h, void* stream);
 
-/* Select the threads per block of the batched kernels (a multiple of 32, at
- * most 1024); 0 restores the default.  The autotuner drives this. */
-int sim_set_block(sim_handle* h, int32_t threads);
+/* Launch shape of the batched kernels (the autotuner drives this).  threads:
+ * threads per block, a multiple of 32 in [32, 1024] (0 = default 32); each block
+ * is one work unit of `threads` consecutive slots.  schedule SIM_SCHED_GRID
+ * launches one block per unit; SIM_SCHED_PERSISTENT launches as many blocks as
+ * fit on the device at once and each takes units from an atomic ticket until
+ * none is left (one persistent launch per rollout). */
+#define SIM_SCHED_GRID 0
+#define SIM_SCHED_PERSISTENT 1
+int sim_set_launch(sim_handle* h, int32_t threads, int32_t schedule);
+
+/* The packing of systems into slots (thread order): sys_of_slot[n_systems]
+ * (host memory) receives the system index run by each slot.  Systems are sorted
+ * by link count, longest first, so the systems of a warp walk equally many links
+ * and the longest work is issued first; results do not depend on it. */
+int sim_slot_order(const sim_handle* h, int32_t* sys_of_slot);
 
 /* Message of the last failed call on h (or of the last failed sim_create when h
  * is NULL).  Owned by the library, valid until the next call on h. */

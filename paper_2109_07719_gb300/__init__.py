@@ -15,6 +15,7 @@ Paper: Qiao et al., "Efficient Differentiable Simulation of Articulated Bodies"
 from __future__ import annotations
 
 import ctypes
+import hashlib
 import os
 
 import numpy as np
@@ -59,7 +60,8 @@ _SIGS = {
                                             _P, _P, _P, _P, _P, ctypes.c_size_t, _P]),
     "sim_status": (ctypes.c_int, [_P, _P]),
     "sim_clear_status": (ctypes.c_int, [_P, _P]),
-    "sim_set_block": (ctypes.c_int, [_P, ctypes.c_int32]),
+    "sim_set_launch": (ctypes.c_int, [_P, ctypes.c_int32, ctypes.c_int32]),
+    "sim_slot_order": (ctypes.c_int, [_P, _P]),
     "sim_last_error": (ctypes.c_char_p, [_P]),
 }
 
@@ -128,6 +130,10 @@ class Simulator:
         lib.sim_dims(h, *[ctypes.byref(x) for x in dims])
         self.B, self.nq_max, self.nv_max, self.n_links = [x.value for x in dims]
         self.mass0 = torch.as_tensor(keep["mass"], dtype=self.dtype, device=self.device)
+        self.launch = (32, False)
+        hist = np.bincount(np.diff(keep["sys_link_offset"])).astype(np.int64)
+        self.signature = (self.B, self.nq_max, self.nv_max, self.n_links, precision,
+                          hashlib.sha1(hist.tobytes()).hexdigest()[:16])
 
     # ------------------------------------------------------------ plumbing
     def _check(self, rc, what):
@@ -168,8 +174,21 @@ class Simulator:
     def work_bytes(self, k):
         return lib.sim_work_bytes(self._h, k)
 
-    def set_block(self, threads: int):
-        self._check(lib.sim_set_block(self._h, threads), "sim_set_block")
+    def set_launch(self, threads: int = 0, persistent: bool = False):
+        """Threads per block (one work unit each) and grid vs persistent scheduling."""
+        self._check(lib.sim_set_launch(self._h, int(threads), 1 if persistent else 0), "sim_set_launch")
+        self.launch = (int(threads) or 32, bool(persistent))
+
+    def slot_order(self):
+        """System index run by each slot (thread), longest systems first."""
+        out = np.zeros(self.B, np.int32)
+        self._check(lib.sim_slot_order(self._h, out.ctypes.data), "sim_slot_order")
+        return out
+
+    def autotune(self, q0, qd0, **kw):
+        """Pick the launch shape by timing short rollouts (see autotune.py)."""
+        from .autotune import autotune
+        return autotune(self, q0, qd0, **kw)
 
     def set_masses(self, mass):
         self._arg(mass, (self.n_links,), "mass")

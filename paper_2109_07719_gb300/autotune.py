@@ -1,0 +1,109 @@
+"""Launch-shape autotuner for the batched rollout kernels.
+
+Times a short forward + adjoint rollout for each candidate (threads per block,
+grid or persistent schedule) and keeps the fastest.  Results are cached in a
+JSON file keyed by the batch signature (systems, padded sizes, links, precision,
+link-count histogram) and the GPU name, so a model is tuned once per device type.
+"""
+from __future__ import annotations
+
+import json
+import os
+
+CANDIDATES = [(32, False), (64, False), (128, False), (32, True), (64, True), (128, True)]
+
+
+def cache_path() -> str:
+    return os.environ.get("ABASIM_TUNE_CACHE",
+                          os.path.join(os.path.expanduser("~"), ".cache", "abasim", "tune.json"))
+
+
+def cache_key(signature, device_name: str) -> str:
+    return json.dumps([list(signature), device_name])
+
+
+def load_cache(path=None) -> dict:
+    path = path or cache_path()
+    try:
+        with open(path) as f:
+            return json.load(f)
+    except (OSError, ValueError):
+        return {}
+
+
+def save_cache(table: dict, path=None) -> None:
+    path = path or cache_path()
+    os.makedirs(os.path.dirname(path), exist_ok=True)
+    tmp = path + f".tmp{os.getpid()}"
+    with open(tmp, "w") as f:
+        json.dump(table, f, indent=1, sort_keys=True)
+    os.replace(tmp, path)
+
+
+def choose(times: dict):
+    """The fastest candidate; ties go to the earlier (simpler) entry."""
+    best = None
+    for cand in CANDIDATES:
+        t = times.get(cand)
+        if t is not None and (best is None or t < times[best]):
+            best = cand
+    if best is None:
+        raise ValueError("no candidate was timed")
+    return best
+
+
+def autotune(sim, q0, qd0, T_probe: int = 16, reps: int = 3, k: int = 1, use_cache: bool = True,
+             timer=None, device_name: str | None = None):
+    """Select and apply the fastest launch shape for ``sim``; returns (threads, persistent).
+
+    ``timer(sim, cand)`` may replace the GPU measurement (it returns seconds)."""
+    import torch
+    name = device_name or torch.cuda.get_device_name(sim.device)
+    key = cache_key(sim.signature, name)
+    table = load_cache() if use_cache else {}
+    if key in table:
+        threads, persistent = table[key]["threads"], table[key]["persistent"]
+        sim.set_launch(threads, persistent)
+        return threads, persistent
+    if timer is None:
+        timer = _gpu_timer(q0, qd0, T_probe, reps, k)
+    times = {}
+    for cand in CANDIDATES:
+        if cand[0] > 32 and cand[0] // 2 >= sim.B:
+            continue
+        sim.set_launch(*cand)
+        times[cand] = timer(sim, cand)
+    best = choose(times)
+    sim.set_launch(*best)
+    if use_cache:
+        table[key] = {"threads": best[0], "persistent": best[1],
+                      "seconds": {f"{c[0]}/{'persistent' if c[1] else 'grid'}": t for c, t in times.items()}}
+        save_cache(table)
+    return best
+
+
+def _gpu_timer(q0, qd0, T_probe, reps, k):
+    import torch
+
+    def timer(sim, cand):
+        tau = torch.zeros(T_probe, sim.nv_max, sim.B, dtype=sim.dtype, device=sim.device)
+        ones = torch.zeros(sim.nq_max, sim.B, dtype=sim.dtype, device=sim.device)
+        zd = torch.zeros(sim.nv_max, sim.B, dtype=sim.dtype, device=sim.device)
+
+        def once():
+            qT, qdT, ck, _ = sim.rollout(q0, qd0, tau, k=k)
+            sim.backward(ck, tau, ones, zd, k=k, mass_grad=False)
+
+        once()
+        torch.cuda.synchronize()
+        best = float("inf")
+        for _ in range(reps):
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record()
+            once()
+            b.record()
+            torch.cuda.synchronize()
+            best = min(best, a.elapsed_time(b) / 1e3)
+        return best
+
+    return timer

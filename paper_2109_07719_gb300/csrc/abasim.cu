@@ -6,6 +6,7 @@
 
 #include <cmath>
 #include <cstdio>
+#include <algorithm>
 #include <cstring>
 #include <mutex>
 #include <string>
@@ -40,8 +41,13 @@ struct sim_handle {
   void* tape = nullptr;      // [maxL][NTAPE][B] scalar
   void* adj = nullptr;       // [maxL][NADJ][B] scalar
   void* gm_acc = nullptr;    // [maxL][B] scalar
-  int* link_slot = nullptr;  // [L_total] -> l * B + b
-  int* status = nullptr;     // [B]
+  int* link_slot = nullptr;  // [L_total] -> l * B + slot
+  int* status = nullptr;     // [B] by system
+  int* sys_of_slot = nullptr;  // [B]
+  unsigned* counter = nullptr;  // work-unit ticket of persistent launches
+  int schedule = SIM_SCHED_GRID;
+  int sms = 0;
+  std::vector<int> h_sys_of_slot;
   std::string err;
 };
 
@@ -66,17 +72,20 @@ template <class T> struct DevModel {
   T* tape;
   T* adj;
   int* status;
+  const int* sys_of_slot;
+  unsigned* counter;
   long long B;
   int nq_max, nv_max;
   T dt;
   T g0, g1, g2;
   int integ;
+  int persistent;
 };
 
 template <class T> DevModel<T> dev_model(const sim_handle* h) {
   return DevModel<T>{(const T*)h->prm, h->meta, h->nl, h->nqv, (T*)h->tape, (T*)h->adj, h->status,
-                     (long long)h->B, h->nq_max, h->nv_max, (T)h->dt,
-                     (T)h->g[0], (T)h->g[1], (T)h->g[2], h->integrator};
+                     h->sys_of_slot, h->counter, (long long)h->B, h->nq_max, h->nv_max, (T)h->dt,
+                     (T)h->g[0], (T)h->g[1], (T)h->g[2], h->integrator, 0};
 }
 
 template <class T> __device__ __forceinline__ Sys<T> sys_of(const DevModel<T>& m, int b) {
@@ -86,19 +95,21 @@ template <class T> __device__ __forceinline__ Sys<T> sys_of(const DevModel<T>& m
 template <class T> __device__ __forceinline__ bool finite_t(T x) { return isfinite(x); }
 
 // ------------------------------------------------------------------ kernels
+// Thread i of the launch handles slot i.  Slots hold the systems sorted by link
+// count (longest first) so a warp's systems walk the same number of links; the
+// model constants and tapes are stored by slot, the caller's arrays by system.
 
-// T steps of the whole batch; system b is thread b.  The working state lives in
-// (qT, qdT); checkpoints every k steps; optional full trajectory.
+// T steps of one system.  The working state lives in (qT, qdT); checkpoints every
+// k steps; optional full trajectory.
 template <class T>
-__global__ void k_rollout(DevModel<T> m, const T* __restrict__ q0, const T* __restrict__ qd0,
-                          const T* __restrict__ tau, long long Tn, int k, T* ckpt, T* qT, T* qdT,
-                          T* traj) {
-  const int b = blockIdx.x * blockDim.x + threadIdx.x;
-  if (b >= m.B) return;
+__device__ __forceinline__ void rollout_one(const DevModel<T>& m, int slot, const T* __restrict__ q0,
+                                            const T* __restrict__ qd0, const T* __restrict__ tau,
+                                            long long Tn, int k, T* ckpt, T* qT, T* qdT, T* traj) {
+  const int b = m.sys_of_slot[slot];
   const long long B = m.B;
   const int nqm = m.nq_max, nvm = m.nv_max, NX = nqm + nvm;
   const V3<T> g{m.g0, m.g1, m.g2};
-  Sys<T> s = sys_of(m, b);
+  Sys<T> s = sys_of(m, slot);
   Col<T> q{qT + b, B}, qd{qdT + b, B};
   for (int d = 0; d < nqm; ++d) q[d] = q0[d * B + b];
   for (int d = 0; d < nvm; ++d) qd[d] = qd0[d * B + b];
@@ -127,19 +138,20 @@ __global__ void k_rollout(DevModel<T> m, const T* __restrict__ q0, const T* __re
   if (!ok) m.status[b] |= 1;
 }
 
-// Adjoint of k_rollout.  (gq0, gqd0) carry the running state adjoint R^t = xbar^t.
+// Adjoint rollout of one system.  (gq0, gqd0) carry the running state adjoint
+// R^t = xbar^t.
 template <class T>
-__global__ void k_backward(DevModel<T> m, const T* __restrict__ ckpt, const T* __restrict__ tau,
-                           long long Tn, int k, const T* __restrict__ gqT, const T* __restrict__ gqdT,
-                           const T* __restrict__ gtraj, T* gq0, T* gqd0, T* gtau, T* gm_acc,
-                           T* ring) {
-  const int b = blockIdx.x * blockDim.x + threadIdx.x;
-  if (b >= m.B) return;
+__device__ __forceinline__ void backward_one(const DevModel<T>& m, int slot, const T* __restrict__ ckpt,
+                                             const T* __restrict__ tau, long long Tn, int k,
+                                             const T* __restrict__ gqT, const T* __restrict__ gqdT,
+                                             const T* __restrict__ gtraj, T* gq0, T* gqd0, T* gtau,
+                                             T* gm_acc, T* ring) {
+  const int b = m.sys_of_slot[slot];
   const long long B = m.B;
   const int nqm = m.nq_max, nvm = m.nv_max, NX = nqm + nvm;
-  const int nq = m.nqv[b] & 0xffff, nv = m.nqv[b] >> 16;
+  const int nq = m.nqv[slot] & 0xffff, nv = m.nqv[slot] >> 16;
   const V3<T> g{m.g0, m.g1, m.g2};
-  Sys<T> s = sys_of(m, b);
+  Sys<T> s = sys_of(m, slot);
   Col<T> gq{gq0 + b, B}, gqd{gqd0 + b, B};
   for (int d = 0; d < nqm; ++d) {
     T v = d < nq ? gqT[d * B + b] : T(0);
@@ -151,19 +163,19 @@ __global__ void k_backward(DevModel<T> m, const T* __restrict__ ckpt, const T* _
     if (gtraj && d < nv) v += gtraj[(Tn * NX + nqm + d) * B + b];
     gqd[d] = v;
   }
-  for (int l = 0; l < s.nl; ++l) gm_acc[l * B + b] = T(0);
-  Col<T> gm{gm_acc + b, B};
+  for (int l = 0; l < s.nl; ++l) gm_acc[l * B + slot] = T(0);
+  Col<T> gm{gm_acc + slot, B};
   const long long nseg = (Tn + k - 1) / k;
   for (long long seg = nseg - 1; seg >= 0; --seg) {
     const long long t0 = seg * k;
     const long long t1 = (t0 + k < Tn) ? t0 + k : Tn;
     const T* xs = ckpt + seg * NX * B + b;
-    if (k > 1) {  // replay the segment once, keeping its states
-      T* r0 = ring + b;
+    if (k > 1) {  // replay the segment once, keeping its states (ring is stored by slot)
+      T* r0 = ring + slot;
       for (int d = 0; d < NX; ++d) r0[d * B] = xs[d * B];
       for (long long j = 1; j < t1 - t0; ++j) {
-        const T* prev = ring + (j - 1) * NX * B + b;
-        T* cur = ring + j * NX * B + b;
+        const T* prev = ring + (j - 1) * NX * B + slot;
+        T* cur = ring + j * NX * B + slot;
         for (int d = 0; d < NX; ++d) cur[d * B] = prev[d * B];
         aba_forward<T>(s, Col<const T>{cur, B}, Col<const T>{cur + nqm * B, B},
                        Col<const T>{tau + (t0 + j - 1) * nvm * B + b, B}, g);
@@ -171,7 +183,7 @@ __global__ void k_backward(DevModel<T> m, const T* __restrict__ ckpt, const T* _
       }
     }
     for (long long t = t1 - 1; t >= t0; --t) {
-      const T* x = (k > 1) ? ring + (t - t0) * NX * B + b : xs;
+      const T* x = (k > 1) ? ring + (t - t0) * NX * B + slot : xs;
       Col<const T> q{x, B}, qd{x + nqm * B, B};
       aba_forward<T>(s, q, qd, Col<const T>{tau + t * nvm * B + b, B}, g);
       T* gt = gtau + t * nvm * B + b;
@@ -189,6 +201,44 @@ __global__ void k_backward(DevModel<T> m, const T* __restrict__ ckpt, const T* _
   for (int d = 0; d < nv; ++d) ok &= finite_t(gqd[d]);
   for (int l = 0; l < s.nl; ++l) ok &= finite_t(gm[l]);
   if (!ok) m.status[b] |= 1;
+}
+
+// Work distribution.  Grid mode: block i takes work unit i (blockDim slots).
+// Persistent mode: a grid sized to the resident capacity, each block taking the
+// next unit from an atomic counter until none is left (the counter is reset by
+// the host before every launch; the loop ends after at most units + 1 tickets).
+__device__ __forceinline__ int next_unit(unsigned* counter) {
+  __shared__ int unit_s;
+  if (threadIdx.x == 0) unit_s = (int)atomicAdd(counter, 1u);
+  __syncthreads();
+  const int unit = unit_s;
+  __syncthreads();
+  return unit;
+}
+
+#define ABASIM_FOR_EACH_SLOT(m, BODY)                                        \
+  int unit = (m).persistent ? next_unit((m).counter) : (int)blockIdx.x;      \
+  while ((long long)unit * blockDim.x < (m).B) {                             \
+    const int slot = unit * blockDim.x + threadIdx.x;                        \
+    if (slot < (m).B) { BODY; }                                              \
+    if (!(m).persistent) break;                                              \
+    unit = next_unit((m).counter);                                           \
+  }
+
+template <class T>
+__global__ void k_rollout(DevModel<T> m, const T* __restrict__ q0, const T* __restrict__ qd0,
+                          const T* __restrict__ tau, long long Tn, int k, T* ckpt, T* qT, T* qdT,
+                          T* traj) {
+  ABASIM_FOR_EACH_SLOT(m, rollout_one<T>(m, slot, q0, qd0, tau, Tn, k, ckpt, qT, qdT, traj))
+}
+
+template <class T>
+__global__ void k_backward(DevModel<T> m, const T* __restrict__ ckpt, const T* __restrict__ tau,
+                           long long Tn, int k, const T* __restrict__ gqT, const T* __restrict__ gqdT,
+                           const T* __restrict__ gtraj, T* gq0, T* gqd0, T* gtau, T* gm_acc,
+                           T* ring) {
+  ABASIM_FOR_EACH_SLOT(m, backward_one<T>(m, slot, ckpt, tau, Tn, k, gqT, gqdT, gtraj, gq0, gqd0,
+                                          gtau, gm_acc, ring))
 }
 
 template <class T>
@@ -212,13 +262,33 @@ __global__ void k_set_masses(T* prm, const int* __restrict__ link_slot, int L, l
 
 inline cudaStream_t S(void* s) { return (cudaStream_t)s; }
 
+// Grid size and mode of a batched launch; resets the ticket of persistent launches.
+template <class K>
+int launch_shape(sim_handle* h, K kernel, int* grid, int* persistent, void* stream) {
+  const int units = (h->B + h->block - 1) / h->block;
+  *grid = units;
+  *persistent = 0;
+  if (h->schedule != SIM_SCHED_PERSISTENT) return SIM_OK;
+  int per_sm = 0;
+  cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, h->block, 0);
+  if (e != cudaSuccess) return cuda_fail(h, e, "occupancy query");
+  const int cap = std::max(1, per_sm) * std::max(1, h->sms);
+  *grid = std::min(units, cap);
+  *persistent = 1;
+  e = cudaMemsetAsync(h->counter, 0, sizeof(unsigned), S(stream));
+  return e == cudaSuccess ? SIM_OK : cuda_fail(h, e, "work ticket reset");
+}
+
 template <class T>
 int launch_rollout(sim_handle* h, const void* q0, const void* qd0, const void* tau, int64_t T_,
                    int k, void* ckpt, void* qT, void* qdT, void* traj, void* stream) {
-  const int grid = (h->B + h->block - 1) / h->block;
-  k_rollout<T><<<grid, h->block, 0, S(stream)>>>(dev_model<T>(h), (const T*)q0, (const T*)qd0,
-                                                  (const T*)tau, (long long)T_, k, (T*)ckpt,
-                                                  (T*)qT, (T*)qdT, (T*)traj);
+  DevModel<T> m = dev_model<T>(h);
+  int grid = 0;
+  int rc = launch_shape(h, k_rollout<T>, &grid, &m.persistent, stream);
+  if (rc != SIM_OK) return rc;
+  k_rollout<T><<<grid, h->block, 0, S(stream)>>>(m, (const T*)q0, (const T*)qd0, (const T*)tau,
+                                                  (long long)T_, k, (T*)ckpt, (T*)qT, (T*)qdT,
+                                                  (T*)traj);
   cudaError_t e = cudaGetLastError();
   return e == cudaSuccess ? SIM_OK : cuda_fail(h, e, "rollout launch");
 }
@@ -227,10 +297,13 @@ template <class T>
 int launch_backward(sim_handle* h, const void* ckpt, const void* tau, int64_t T_, int k,
                     const void* gqT, const void* gqdT, const void* gtraj, void* gq0, void* gqd0,
                     void* gtau, void* gmass, void* work, void* stream) {
-  const int grid = (h->B + h->block - 1) / h->block;
+  DevModel<T> m = dev_model<T>(h);
+  int grid = 0;
+  int rc = launch_shape(h, k_backward<T>, &grid, &m.persistent, stream);
+  if (rc != SIM_OK) return rc;
   k_backward<T><<<grid, h->block, 0, S(stream)>>>(
-      dev_model<T>(h), (const T*)ckpt, (const T*)tau, (long long)T_, k, (const T*)gqT,
-      (const T*)gqdT, (const T*)gtraj, (T*)gq0, (T*)gqd0, (T*)gtau, (T*)h->gm_acc, (T*)work);
+      m, (const T*)ckpt, (const T*)tau, (long long)T_, k, (const T*)gqT, (const T*)gqdT,
+      (const T*)gtraj, (T*)gq0, (T*)gqd0, (T*)gtau, (T*)h->gm_acc, (T*)work);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return cuda_fail(h, e, "backward launch");
   if (gmass) {
@@ -402,20 +475,29 @@ int sim_create(const sim_model_desc* d, sim_handle** out) {
   h->L_total = d->sys_link_offset[h->B];
   cudaGetDevice(&h->device);
   const int B = h->B;
-  std::vector<int> nl(B), nqv(B);
+  std::vector<int> nl_sys(B);
   for (int b = 0; b < B; ++b) {
-    nl[b] = d->sys_link_offset[b + 1] - d->sys_link_offset[b];
-    h->maxL = std::max(h->maxL, nl[b]);
+    nl_sys[b] = d->sys_link_offset[b + 1] - d->sys_link_offset[b];
+    h->maxL = std::max(h->maxL, nl_sys[b]);
   }
+  // slots: systems sorted by link count, longest first (stable), so a warp's
+  // threads walk equally long link loops and the longest work starts first
+  std::vector<int> order(B);
+  for (int b = 0; b < B; ++b) order[b] = b;
+  std::stable_sort(order.begin(), order.end(), [&](int x, int y) { return nl_sys[x] > nl_sys[y]; });
+  h->h_sys_of_slot = order;
   const int maxL = h->maxL;
+  std::vector<int> nl(B), nqv(B);
   std::vector<double> prm((size_t)maxL * NPRM * B, 0.0);
   std::vector<int> meta((size_t)maxL * B, 0), slot(h->L_total);
-  for (int b = 0; b < B; ++b) {
+  for (int sl = 0; sl < B; ++sl) {
+    const int b = order[sl];
+    nl[sl] = nl_sys[b];
     int qo = 0, vo = 0;
-    for (int l = 0; l < nl[b]; ++l) {
+    for (int l = 0; l < nl[sl]; ++l) {
       const int i = d->sys_link_offset[b] + l;
       const int jt = d->joint_type[i];
-      auto P = [&](int f) -> double& { return prm[((size_t)l * NPRM + f) * B + b]; };
+      auto P = [&](int f) -> double& { return prm[((size_t)l * NPRM + f) * B + sl]; };
       for (int x = 0; x < 12; ++x) P(P_E + x) = d->X_tree[12 * i + x];
       for (int x = 0; x < 3; ++x) {
         P(P_AX + x) = jt == SIM_REVOLUTE ? d->axis[3 * i + x] : 0.0;
@@ -424,17 +506,18 @@ int sim_create(const sim_model_desc* d, sim_handle** out) {
       P(P_M) = d->mass[i];
       for (int x = 0; x < 6; ++x) P(P_IC + x) = d->I_com[6 * i + x];
       bool treechild = false;  // a child other than link l + 1
-      for (int c = l + 2; c < nl[b]; ++c)
+      for (int c = l + 2; c < nl[sl]; ++c)
         if (d->parent[d->sys_link_offset[b] + c] == l) treechild = true;
-      meta[(size_t)l * B + b] = make_meta(d->parent[i], jt, treechild, qo, vo);
-      slot[i] = l * B + b;
+      meta[(size_t)l * B + sl] = make_meta(d->parent[i], jt, treechild, qo, vo);
+      slot[i] = l * B + sl;
       qo += jt == SIM_FREE ? 7 : 1;
       vo += jt == SIM_FREE ? 6 : 1;
     }
-    nqv[b] = qo | (vo << 16);
+    nqv[sl] = qo | (vo << 16);
     h->nq_max = std::max(h->nq_max, qo);
     h->nv_max = std::max(h->nv_max, vo);
   }
+  cudaDeviceGetAttribute(&h->sms, cudaDevAttrMultiProcessorCount, h->device);
   int rc = h->precision == SIM_FP64 ? upload<double>(h, prm) : upload<float>(h, prm);
   auto alloc = [&](void** p, size_t bytes, const char* what) -> int {
     cudaError_t e = cudaMalloc(p, bytes);
@@ -456,6 +539,9 @@ int sim_create(const sim_model_desc* d, sim_handle** out) {
   if (rc == SIM_OK) rc = alloc(&h->adj, (size_t)maxL * NADJ * B * h->scalar, "adjoint tape");
   if (rc == SIM_OK) rc = alloc(&h->gm_acc, (size_t)maxL * B * h->scalar, "mass-gradient buffer");
   if (rc == SIM_OK) rc = alloc((void**)&h->status, B * sizeof(int), "status");
+  if (rc == SIM_OK) rc = alloc((void**)&h->sys_of_slot, B * sizeof(int), "slot order");
+  if (rc == SIM_OK) rc = put(h->sys_of_slot, order.data(), B * sizeof(int));
+  if (rc == SIM_OK) rc = alloc((void**)&h->counter, sizeof(unsigned), "work ticket");
   if (rc == SIM_OK) {
     cudaError_t e = cudaMemset(h->status, 0, B * sizeof(int));
     if (e != cudaSuccess) rc = cuda_fail(h, e, "status init");
@@ -471,7 +557,8 @@ int sim_create(const sim_model_desc* d, sim_handle** out) {
 
 void sim_destroy(sim_handle* h) {
   if (!h) return;
-  void* ptrs[] = {h->prm, h->meta, h->nl, h->nqv, h->tape, h->adj, h->gm_acc, h->link_slot, h->status};
+  void* ptrs[] = {h->prm, h->meta, h->nl, h->nqv, h->tape, h->adj, h->gm_acc, h->link_slot,
+                  h->status, h->sys_of_slot, h->counter};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   delete h;
@@ -577,12 +664,21 @@ int sim_clear_status(sim_handle* h, void* stream) {
   return e == cudaSuccess ? SIM_OK : cuda_fail(h, e, "status clear");
 }
 
-int sim_set_block(sim_handle* h, int32_t threads) {
+int sim_set_launch(sim_handle* h, int32_t threads, int32_t schedule) {
   if (!h) return SIM_EINVAL;
-  if (threads == 0) { h->block = kDefaultBlock; return SIM_OK; }
+  if (schedule != SIM_SCHED_GRID && schedule != SIM_SCHED_PERSISTENT)
+    return fail(h, SIM_EINVAL, "unknown schedule");
+  if (threads == 0) threads = kDefaultBlock;
   if (threads < 32 || threads > 1024 || threads % 32)
     return fail(h, SIM_EINVAL, "block size must be a multiple of 32 in [32, 1024]");
   h->block = threads;
+  h->schedule = schedule;
+  return SIM_OK;
+}
+
+int sim_slot_order(const sim_handle* h, int32_t* sys_of_slot) {
+  if (!h || !sys_of_slot) return SIM_EINVAL;
+  memcpy(sys_of_slot, h->h_sys_of_slot.data(), h->B * sizeof(int32_t));
   return SIM_OK;
 }
 
