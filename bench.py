@@ -355,6 +355,49 @@ def run_reference(args):
     return line
 
 
+def memory_sweep(args):
+    """Peak device memory of one forward + adjoint rollout versus horizon (Table 1's
+    'Ours' column shape): torch's allocator peak (inputs, outputs, checkpoints,
+    workspace) plus the handle's own buffers (model constants, per-step tape)."""
+    import torch
+    from paper_2109_07719_gb300 import Simulator
+    torch.cuda.set_device(0)
+    horizons = [int(x) for x in args.horizons.split(",")]
+    lines = []
+    for T in horizons:
+        work = workload(args.config, args.precision, args.batch, T)
+        m = work.model
+        torch.cuda.empty_cache()
+        torch.cuda.reset_peak_memory_stats()
+        base = torch.cuda.memory_allocated()
+        free0 = torch.cuda.mem_get_info()[0]
+        sim = Simulator(m, precision=args.precision)
+        handle_bytes = free0 - torch.cuda.mem_get_info()[0]
+        dt, dev = sim.dtype, sim.device
+        q0 = torch.tensor(work.q0, dtype=dt, device=dev)
+        qd0 = torch.tensor(work.qd0, dtype=dt, device=dev)
+        tau = work.tau(device=dev, dtype=dt)
+        t0 = time.perf_counter()
+        qT, qdT, ck, _ = sim.rollout(q0, qd0, tau, k=args.k)
+        g = sim.backward(ck, tau, torch.ones_like(qT), torch.zeros_like(qdT), k=args.k)
+        torch.cuda.synchronize()
+        el = time.perf_counter() - t0
+        peak = torch.cuda.max_memory_allocated() - base
+        line = {"metric": "peak device memory vs horizon", "workload": m.name, "n_systems": sim.B,
+                "horizon": T, "checkpoint_interval": args.k, "precision": args.precision,
+                "peak_torch_bytes": int(peak), "handle_bytes": int(handle_bytes),
+                "ckpt_bytes": int(sim.ckpt_bytes(T, args.k)), "tau_bytes": int(tau.numel() * tau.element_size()),
+                "seconds_fwd_adj": el}
+        lines.append(line)
+        print(json.dumps(line))
+        del sim, q0, qd0, tau, qT, qdT, ck, g
+    if len(lines) > 1:
+        a, b = lines[0], lines[-1]
+        slope = (b["peak_torch_bytes"] - a["peak_torch_bytes"]) / (b["horizon"] - a["horizon"])
+        print(json.dumps({"metric": "peak memory growth per step", "bytes_per_step": slope,
+                          "bytes_per_step_per_system": slope / a["n_systems"]}))
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -373,8 +416,13 @@ def main():
     ap.add_argument("--no-plain", dest="plain", action="store_false")
     ap.add_argument("--no-e2e", dest="e2e", action="store_false")
     ap.add_argument("--graph", action="store_true", help="replay the step as one CUDA graph")
+    ap.add_argument("--memory-sweep", action="store_true")
+    ap.add_argument("--horizons", default="1000,5000,10000,50000")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
+    if args.memory_sweep:
+        memory_sweep(args)
+        return
     line = run_reference(args) if args.impl == "reference" else run_ours(args)
     if line is not None:
         print(json.dumps(line))

@@ -126,7 +126,7 @@ int sim_step_batch(sim_handle* h, const void* q, const void* qd, const void* tau
  * paper has no counterpart; this is a deployment convenience.
  * Allocates nothing: the per-link tape is a file-scope device array of
  * SIM_STATIC_SCRATCH_BYTES (16 MiB) that every GPU loading the library holds
- * until exit; batches whose tape (links x 118 scalars x systems) exceeds it are
+ * until exit; batches whose tape (links x 119 scalars x systems) exceeds it are
  * rejected with SIM_ENOMEM.  The first call on each device looks up the array's
  * device address with that device current; make that first call before any
  * stream capture.  The array is shared by all calls and keeps the last call's

@@ -30,7 +30,8 @@ enum : int { P_E = 0, P_R = 9, P_AX = 12, P_M = 15, P_C = 16, P_IC = 19, NPRM = 
 // per-link forward tape
 enum : int {
   T_E = 0, T_R = 9, T_V = 12, T_C = 18, T_H = 24, T_IA = 30, T_PA = 51, T_U = 57, T_D = 63,
-  T_DI = 64, T_u = 65, T_Ia = 71, T_pa = 92, T_AP = 98, T_A = 104, T_QDD = 110, T_SC = 116, NTAPE = 118
+  T_DI = 64, T_u = 65, T_Ia = 71, T_pa = 92, T_AP = 98, T_A = 104, T_QDD = 110, T_SC = 116,
+  T_DI2 = 118, NTAPE = 119
 };
 // per-link adjoint accumulators
 enum : int {
@@ -176,13 +177,54 @@ template <class T> SD SV<T> chol6_solve(const T* L, SV<T> b) {
   return {{x[0], x[1], x[2]}, {x[3], x[4], x[5]}};
 }
 
+// ------------------------------------------------------------------ D-solve scalar
+// The articulated-inertia solves (D = S^T I^A S, 1/D, U D^-1 U^T, the free root's
+// 6x6 solve) run in the scalar DT: the storage type T, or double in the mixed
+// FP32 + FP64 mode.  1/D is kept on the tape as a hi/lo pair of T words.
+template <class T, class DT> SD void put_di(const Sys<T>& s, int l, DT di) {
+  const T hi = (T)di;
+  s.tp(l, T_DI) = hi;
+  s.tp(l, T_DI2) = (T)(di - (DT)hi);
+}
+template <class T, class DT> SD DT get_di(const Sys<T>& s, int l) {
+  return (DT)s.tp(l, T_DI) + (DT)s.tp(l, T_DI2);
+}
+template <class DT, class T> SD SI<DT> si_cast(const SI<T>& I) {
+  SI<DT> o;
+  o.A = S3<DT>{(DT)I.A.xx, (DT)I.A.yy, (DT)I.A.zz, (DT)I.A.xy, (DT)I.A.xz, (DT)I.A.yz};
+  o.C = S3<DT>{(DT)I.C.xx, (DT)I.C.yy, (DT)I.C.zz, (DT)I.C.xy, (DT)I.C.xz, (DT)I.C.yz};
+  for (int i = 0; i < 9; ++i) o.B.a[i] = (DT)I.B.a[i];
+  return o;
+}
+template <class DT, class T> SD SV<DT> sv_cast(const SV<T>& v) {
+  return SV<DT>{{(DT)v.w.x, (DT)v.w.y, (DT)v.w.z}, {(DT)v.v.x, (DT)v.v.y, (DT)v.v.z}};
+}
+// I - di u u^T formed in DT, rounded to T
+template <class T, class DT> SD SI<T> minus_scaled_outer(const SI<T>& I, DT di, SV<T> u) {
+  const SI<DT> Id = si_cast<DT>(I);
+  const SV<DT> ud = sv_cast<DT>(u);
+  const SI<DT> r = Id - scale(di, sym_outer(ud, ud));
+  SI<T> o;
+  o.A = S3<T>{(T)r.A.xx, (T)r.A.yy, (T)r.A.zz, (T)r.A.xy, (T)r.A.xz, (T)r.A.yz};
+  o.C = S3<T>{(T)r.C.xx, (T)r.C.yy, (T)r.C.zz, (T)r.C.xy, (T)r.C.xz, (T)r.C.yz};
+  for (int i = 0; i < 9; ++i) o.B.a[i] = (T)r.B.a[i];
+  return o;
+}
+// the free root's solve I^A x = b, Cholesky in DT
+template <class T, class DT> SD SV<T> spd_solve(const SI<T>& IA, SV<T> b) {
+  DT L[21];
+  chol6(si_cast<DT>(IA), L);
+  const SV<DT> x = chol6_solve(L, sv_cast<DT>(b));
+  return SV<T>{{(T)x.w.x, (T)x.w.y, (T)x.w.z}, {(T)x.v.x, (T)x.v.y, (T)x.v.z}};
+}
+
 // ------------------------------------------------------------------ forward
 // Runs jcalc and the three ABA passes for the state (q, qd) and joint force tau,
 // leaving every intermediate on the tape (qdd included).  Values passed between a
 // link and its parent ride in registers when the parent is the previous link (the
 // whole of a serial chain); other parents go through the tape.  Each iteration
 // loads what it needs before it stores anything, so the loads overlap.
-template <class T>
+template <class T, class DT>
 SD void aba_forward(const Sys<T>& s, Col<const T> q, Col<const T> qd, Col<const T> tau, V3<T> grav) {
   const int nl = s.nl;
   // jcalc + pass 1 (root -> leaves)
@@ -253,16 +295,16 @@ SD void aba_forward(const Sys<T>& s, Col<const T> q, Col<const T> qd, Col<const 
         X = tp_xf(s, l, T_E);
       }
       const SV<T> U{mul(IA.A, a), mulT(IA.B, a)};
-      const T D = dot(a, U.w);
-      const T Di = T(1) / D;
+      const DT D = (DT)a.x * (DT)U.w.x + (DT)a.y * (DT)U.w.y + (DT)a.z * (DT)U.w.z;
+      const DT Di = DT(1) / D;
       const T u = tl - dot(a, pA.w);
       tp_sv(s, l, T_U, U);
-      s.tp(l, T_D) = D;
-      s.tp(l, T_DI) = Di;
+      s.tp(l, T_D) = (T)D;
+      put_di<T, DT>(s, l, Di);
       s.tp(l, T_u) = u;
       if (par >= 0) {
-        const SI<T> Ia = IA - scale(Di, sym_outer(U, U));
-        const SV<T> pa = pA + mul(Ia, c) + (u * Di) * U;
+        const SI<T> Ia = minus_scaled_outer<T, DT>(IA, Di, U);
+        const SV<T> pa = pA + mul(Ia, c) + (T)((DT)u * Di) * U;
         tp_si(s, l, T_Ia, Ia);
         tp_sv(s, l, T_pa, pa);
         const SI<T> Cn = congruence(X, Ia);
@@ -276,12 +318,10 @@ SD void aba_forward(const Sys<T>& s, Col<const T> q, Col<const T> qd, Col<const 
           tp_sv(s, par, T_PA, tp_sv(s, par, T_PA) + pn);
         }
       }
-    } else {  // free root: D = I^A, u = tau - p^A
+    } else {  // free root: D = I^A (kept on the tape), u = tau - p^A
       SV<T> u{{tau[vo], tau[vo + 1], tau[vo + 2]}, {tau[vo + 3], tau[vo + 4], tau[vo + 5]}};
       u -= pA;
-      T L[21];
-      chol6(IA, L);
-      for (int i = 0; i < 21; ++i) s.tp(l, T_Ia + i) = L[i];
+      tp_si(s, l, T_IA, IA);
       tp_sv(s, l, T_u, u);
     }
   }
@@ -299,19 +339,19 @@ SD void aba_forward(const Sys<T>& s, Col<const T> q, Col<const T> qd, Col<const 
     if (jt == J_REVOLUTE) {
       const V3<T> ax = s.pv3(l, P_AX);
       const SV<T> U = tp_sv(s, l, T_U);
-      const T u = s.tp(l, T_u), Di = s.tp(l, T_DI);
+      const T u = s.tp(l, T_u);
+      const DT Di = get_di<T, DT>(s, l);
       const SV<T> ap = apply(X, apar) + c;
-      const T qdd = (u - dot(U, ap)) * Di;
+      const T qdd = (T)(((DT)u - (DT)dot(U, ap)) * Di);
       s.tp(l, T_QDD) = qdd;
       a = ap;
       a.w += qdd * ax;
       tp_sv(s, l, T_AP, ap);
     } else {
-      T L[21];
-      for (int i = 0; i < 21; ++i) L[i] = s.tp(l, T_Ia + i);
+      const SI<T> IA = tp_si(s, l, T_IA);
       const SV<T> u = tp_sv(s, l, T_u);
       const SV<T> ap = apply(X, apar) + c;
-      a = chol6_solve(L, u);
+      a = spd_solve<T, DT>(IA, u);
       tp_sv(s, l, T_QDD, a - ap);
       tp_sv(s, l, T_AP, ap);
     }
@@ -432,7 +472,7 @@ SD void integrator_adjoint(const Sys<T>& s, int l, int jt, int qo, int vo, Col<c
 // Adjoints flowing between a link and its parent ride in registers when the
 // parent is the previous link; accumulators in the adjoint tape serve the other
 // (tree) children and are zeroed first only for links that have such children.
-template <class T>
+template <class T, class DT>
 SD void step_adjoint(const Sys<T>& s, Col<const T> q, Col<const T> qd, Col<T> gq, Col<T> gqd,
                      Col<T> gtau, Col<T> gm, V3<T> grav, T dt, int integ) {
   const int nl = s.nl;
@@ -464,9 +504,10 @@ SD void step_adjoint(const Sys<T>& s, Col<const T> q, Col<const T> qd, Col<T> gq
         const V3<T> ax = s.pv3(l, P_AX);
         const SV<T> U = tp_sv(s, l, T_U);
         const SV<T> ap = tp_sv(s, l, T_AP);
-        const T Di = s.tp(l, T_DI), qdd = s.tp(l, T_QDD);
+        const DT Di = get_di<T, DT>(s, l);
+        const T qdd = s.tp(l, T_QDD);
         const T qb = qddb[0] + dot(ax, ab.w);
-        const T wb = qb * Di;
+        const T wb = (T)((DT)qb * Di);
         apb = ab - wb * U;
         ad_sv(s, l, G_U, zeroSV<T>() - wb * ap);
         s.ad(l, G_D) = -wb * qdd;
@@ -474,9 +515,7 @@ SD void step_adjoint(const Sys<T>& s, Col<const T> q, Col<const T> qd, Col<T> gq
       } else {
         const SV<T> qb{{qddb[0], qddb[1], qddb[2]}, {qddb[3], qddb[4], qddb[5]}};
         const SV<T> a = tp_sv(s, l, T_A);
-        T L[21];
-        for (int i = 0; i < 21; ++i) L[i] = s.tp(l, T_Ia + i);
-        const SV<T> ub = chol6_solve(L, ab + qb);
+        const SV<T> ub = spd_solve<T, DT>(tp_si(s, l, T_IA), ab + qb);
         apb = zeroSV<T>() - qb;
         ad_sv(s, l, G_u, ub);
         ad_si(s, l, G_IA, scale(T(-1), sym_outer(ub, a)));
@@ -512,7 +551,7 @@ SD void step_adjoint(const Sys<T>& s, Col<const T> q, Col<const T> qd, Col<T> gq
         SV<T> Ub = ad_sv(s, l, G_U);
         T Db = s.ad(l, G_D);
         T ub = s.ad(l, G_u);
-        const T Di = s.tp(l, T_DI);
+        const DT Di = get_di<T, DT>(s, l);
         const T u = s.tp(l, T_u);
         const SV<T> U = tp_sv(s, l, T_U);
         IAb = zeroSI<T>();
@@ -544,15 +583,15 @@ SD void step_adjoint(const Sys<T>& s, Col<const T> q, Col<const T> qd, Col<T> gq
           Iab += sym_outer(pab, c);
           cb += mul(Ia, pab);
           ad_sv(s, l, G_C, cb);
-          Ub += (u * Di) * pab;
+          Ub += (T)((DT)u * Di) * pab;
           const T gb = dot(U, pab);
-          ub += gb * Di;
-          Db -= gb * u * Di * Di;
+          ub += (T)((DT)gb * Di);
+          Db -= (T)((DT)gb * (DT)u * Di * Di);
           // Ia = IA - U U^T / D
           IAb += Iab;
           const SV<T> IbU = mul(Iab, U);
-          Ub -= (T(2) * Di) * IbU;
-          Db += Di * Di * dot(U, IbU);
+          Ub -= (T)(DT(2) * Di) * IbU;
+          Db += (T)(Di * Di * (DT)dot(U, IbU));
         }
         // u = tau - S^T pA,  D = S^T U,  U = IA S
         gtau[vo] = ub;

@@ -101,7 +101,7 @@ template <class T> __device__ __forceinline__ bool finite_t(T x) { return isfini
 
 // T steps of one system.  The working state lives in (qT, qdT); checkpoints every
 // k steps; optional full trajectory.
-template <class T>
+template <class T, class DT>
 __device__ __forceinline__ void rollout_one(const DevModel<T>& m, int slot, const T* __restrict__ q0,
                                             const T* __restrict__ qd0, const T* __restrict__ tau,
                                             long long Tn, int k, T* ckpt, T* qT, T* qdT, T* traj) {
@@ -123,7 +123,7 @@ __device__ __forceinline__ void rollout_one(const DevModel<T>& m, int slot, cons
       for (int d = 0; d < nqm; ++d) c[d * B] = q[d];
       for (int d = 0; d < nvm; ++d) c[(nqm + d) * B] = qd[d];
     }
-    aba_forward<T>(s, Col<const T>{qT + b, B}, Col<const T>{qdT + b, B},
+    aba_forward<T, DT>(s, Col<const T>{qT + b, B}, Col<const T>{qdT + b, B},
                    Col<const T>{tau + t * nvm * B + b, B}, g);
     integrate<T>(s, q, qd, m.dt, m.integ);
     if (traj) {
@@ -140,7 +140,7 @@ __device__ __forceinline__ void rollout_one(const DevModel<T>& m, int slot, cons
 
 // Adjoint rollout of one system.  (gq0, gqd0) carry the running state adjoint
 // R^t = xbar^t.
-template <class T>
+template <class T, class DT>
 __device__ __forceinline__ void backward_one(const DevModel<T>& m, int slot, const T* __restrict__ ckpt,
                                              const T* __restrict__ tau, long long Tn, int k,
                                              const T* __restrict__ gqT, const T* __restrict__ gqdT,
@@ -177,7 +177,7 @@ __device__ __forceinline__ void backward_one(const DevModel<T>& m, int slot, con
         const T* prev = ring + (j - 1) * NX * B + slot;
         T* cur = ring + j * NX * B + slot;
         for (int d = 0; d < NX; ++d) cur[d * B] = prev[d * B];
-        aba_forward<T>(s, Col<const T>{cur, B}, Col<const T>{cur + nqm * B, B},
+        aba_forward<T, DT>(s, Col<const T>{cur, B}, Col<const T>{cur + nqm * B, B},
                        Col<const T>{tau + (t0 + j - 1) * nvm * B + b, B}, g);
         integrate<T>(s, Col<T>{cur, B}, Col<T>{cur + nqm * B, B}, m.dt, m.integ);
       }
@@ -185,9 +185,9 @@ __device__ __forceinline__ void backward_one(const DevModel<T>& m, int slot, con
     for (long long t = t1 - 1; t >= t0; --t) {
       const T* x = (k > 1) ? ring + (t - t0) * NX * B + slot : xs;
       Col<const T> q{x, B}, qd{x + nqm * B, B};
-      aba_forward<T>(s, q, qd, Col<const T>{tau + t * nvm * B + b, B}, g);
+      aba_forward<T, DT>(s, q, qd, Col<const T>{tau + t * nvm * B + b, B}, g);
       T* gt = gtau + t * nvm * B + b;
-      step_adjoint<T>(s, q, qd, gq, gqd, Col<T>{gt, B}, gm, g, m.dt, m.integ);
+      step_adjoint<T, DT>(s, q, qd, gq, gqd, Col<T>{gt, B}, gm, g, m.dt, m.integ);
       for (int d = nv; d < nvm; ++d) gt[d * B] = T(0);
       if (gtraj) {
         const T* gx = gtraj + t * NX * B + b;
@@ -216,28 +216,28 @@ __device__ __forceinline__ int next_unit(unsigned* counter) {
   return unit;
 }
 
-#define ABASIM_FOR_EACH_SLOT(m, BODY)                                        \
+#define ABASIM_FOR_EACH_SLOT(m, ...)                                         \
   int unit = (m).persistent ? next_unit((m).counter) : (int)blockIdx.x;      \
   while ((long long)unit * blockDim.x < (m).B) {                             \
     const int slot = unit * blockDim.x + threadIdx.x;                        \
-    if (slot < (m).B) { BODY; }                                              \
+    if (slot < (m).B) { __VA_ARGS__; }                                       \
     if (!(m).persistent) break;                                              \
     unit = next_unit((m).counter);                                           \
   }
 
-template <class T>
+template <class T, class DT>
 __global__ void k_rollout(DevModel<T> m, const T* __restrict__ q0, const T* __restrict__ qd0,
                           const T* __restrict__ tau, long long Tn, int k, T* ckpt, T* qT, T* qdT,
                           T* traj) {
-  ABASIM_FOR_EACH_SLOT(m, rollout_one<T>(m, slot, q0, qd0, tau, Tn, k, ckpt, qT, qdT, traj))
+  ABASIM_FOR_EACH_SLOT(m, rollout_one<T, DT>(m, slot, q0, qd0, tau, Tn, k, ckpt, qT, qdT, traj))
 }
 
-template <class T>
+template <class T, class DT>
 __global__ void k_backward(DevModel<T> m, const T* __restrict__ ckpt, const T* __restrict__ tau,
                            long long Tn, int k, const T* __restrict__ gqT, const T* __restrict__ gqdT,
                            const T* __restrict__ gtraj, T* gq0, T* gqd0, T* gtau, T* gm_acc,
                            T* ring) {
-  ABASIM_FOR_EACH_SLOT(m, backward_one<T>(m, slot, ckpt, tau, Tn, k, gqT, gqdT, gtraj, gq0, gqd0,
+  ABASIM_FOR_EACH_SLOT(m, backward_one<T, DT>(m, slot, ckpt, tau, Tn, k, gqT, gqdT, gtraj, gq0, gqd0,
                                           gtau, gm_acc, ring))
 }
 
@@ -279,29 +279,29 @@ int launch_shape(sim_handle* h, K kernel, int* grid, int* persistent, void* stre
   return e == cudaSuccess ? SIM_OK : cuda_fail(h, e, "work ticket reset");
 }
 
-template <class T>
+template <class T, class DT>
 int launch_rollout(sim_handle* h, const void* q0, const void* qd0, const void* tau, int64_t T_,
                    int k, void* ckpt, void* qT, void* qdT, void* traj, void* stream) {
   DevModel<T> m = dev_model<T>(h);
   int grid = 0;
-  int rc = launch_shape(h, k_rollout<T>, &grid, &m.persistent, stream);
+  int rc = launch_shape(h, k_rollout<T, DT>, &grid, &m.persistent, stream);
   if (rc != SIM_OK) return rc;
-  k_rollout<T><<<grid, h->block, 0, S(stream)>>>(m, (const T*)q0, (const T*)qd0, (const T*)tau,
+  k_rollout<T, DT><<<grid, h->block, 0, S(stream)>>>(m, (const T*)q0, (const T*)qd0, (const T*)tau,
                                                   (long long)T_, k, (T*)ckpt, (T*)qT, (T*)qdT,
                                                   (T*)traj);
   cudaError_t e = cudaGetLastError();
   return e == cudaSuccess ? SIM_OK : cuda_fail(h, e, "rollout launch");
 }
 
-template <class T>
+template <class T, class DT>
 int launch_backward(sim_handle* h, const void* ckpt, const void* tau, int64_t T_, int k,
                     const void* gqT, const void* gqdT, const void* gtraj, void* gq0, void* gqd0,
                     void* gtau, void* gmass, void* work, void* stream) {
   DevModel<T> m = dev_model<T>(h);
   int grid = 0;
-  int rc = launch_shape(h, k_backward<T>, &grid, &m.persistent, stream);
+  int rc = launch_shape(h, k_backward<T, DT>, &grid, &m.persistent, stream);
   if (rc != SIM_OK) return rc;
-  k_backward<T><<<grid, h->block, 0, S(stream)>>>(
+  k_backward<T, DT><<<grid, h->block, 0, S(stream)>>>(
       m, (const T*)ckpt, (const T*)tau, (long long)T_, k, (const T*)gqT, (const T*)gqdT,
       (const T*)gtraj, (T*)gq0, (T*)gqd0, (T*)gtau, (T*)h->gm_acc, (T*)work);
   cudaError_t e = cudaGetLastError();
@@ -439,7 +439,7 @@ int static_tape(sim_handle* h, void** out) {
   return SIM_OK;
 }
 
-template <class T>
+template <class T, class DT>
 int launch_step_static(sim_handle* h, const void* q, const void* qd, const void* tau, void* q_out,
                        void* qd_out, void* stream) {
   void* tape = nullptr;
@@ -448,7 +448,7 @@ int launch_step_static(sim_handle* h, const void* q, const void* qd, const void*
   DevModel<T> m = dev_model<T>(h);
   m.tape = (T*)tape;
   const int grid = (h->B + h->block - 1) / h->block;
-  k_rollout<T><<<grid, h->block, 0, S(stream)>>>(m, (const T*)q, (const T*)qd, (const T*)tau, 1LL, 1,
+  k_rollout<T, DT><<<grid, h->block, 0, S(stream)>>>(m, (const T*)q, (const T*)qd, (const T*)tau, 1LL, 1,
                                                   (T*)nullptr, (T*)q_out, (T*)qd_out, (T*)nullptr);
   cudaError_t e = cudaGetLastError();
   return e == cudaSuccess ? SIM_OK : cuda_fail(h, e, "static step launch");
@@ -605,8 +605,11 @@ int sim_rollout(sim_handle* h, const void* q0, const void* qd0, const void* tau,
   if (T < 0 || k < 1) return fail(h, SIM_EINVAL, "need T >= 0 and k >= 1");
   if (!q0 || !qd0 || !qT || !qdT || (T > 0 && !tau))
     return fail(h, SIM_EINVAL, "null state or torque pointer");
-  return is_fp64(h) ? launch_rollout<double>(h, q0, qd0, tau, T, k, ckpt, qT, qdT, traj, stream)
-                    : launch_rollout<float>(h, q0, qd0, tau, T, k, ckpt, qT, qdT, traj, stream);
+  switch (h->precision) {
+    case SIM_FP64: return launch_rollout<double, double>(h, q0, qd0, tau, T, k, ckpt, qT, qdT, traj, stream);
+    case SIM_FP32: return launch_rollout<float, float>(h, q0, qd0, tau, T, k, ckpt, qT, qdT, traj, stream);
+    default: return launch_rollout<float, double>(h, q0, qd0, tau, T, k, ckpt, qT, qdT, traj, stream);
+  }
 }
 
 int sim_step_batch(sim_handle* h, const void* q, const void* qd, const void* tau, void* q_out,
@@ -627,8 +630,11 @@ int sim_step_batch_static(sim_handle* h, const void* q, const void* qd, const vo
              need, (size_t)SIM_STATIC_SCRATCH_BYTES);
     return fail(h, SIM_ENOMEM, buf);
   }
-  return is_fp64(h) ? launch_step_static<double>(h, q, qd, tau, q_out, qd_out, stream)
-                    : launch_step_static<float>(h, q, qd, tau, q_out, qd_out, stream);
+  switch (h->precision) {
+    case SIM_FP64: return launch_step_static<double, double>(h, q, qd, tau, q_out, qd_out, stream);
+    case SIM_FP32: return launch_step_static<float, float>(h, q, qd, tau, q_out, qd_out, stream);
+    default: return launch_step_static<float, double>(h, q, qd, tau, q_out, qd_out, stream);
+  }
 }
 
 int sim_backward_rollout(sim_handle* h, const void* ckpt, const void* tau, int64_t T, int32_t k,
@@ -641,9 +647,14 @@ int sim_backward_rollout(sim_handle* h, const void* ckpt, const void* tau, int64
     return fail(h, SIM_EINVAL, "null pointer argument");
   if (k > 1 && T > 0 && (!work || work_bytes < sim_work_bytes(h, k)))
     return fail(h, SIM_ENOMEM, "workspace smaller than sim_work_bytes(k)");
-  return is_fp64(h)
-             ? launch_backward<double>(h, ckpt, tau, T, k, gqT, gqdT, g_traj, gq0, gqd0, gtau, gmass, work, stream)
-             : launch_backward<float>(h, ckpt, tau, T, k, gqT, gqdT, g_traj, gq0, gqd0, gtau, gmass, work, stream);
+  switch (h->precision) {
+    case SIM_FP64:
+      return launch_backward<double, double>(h, ckpt, tau, T, k, gqT, gqdT, g_traj, gq0, gqd0, gtau, gmass, work, stream);
+    case SIM_FP32:
+      return launch_backward<float, float>(h, ckpt, tau, T, k, gqT, gqdT, g_traj, gq0, gqd0, gtau, gmass, work, stream);
+    default:
+      return launch_backward<float, double>(h, ckpt, tau, T, k, gqT, gqdT, g_traj, gq0, gqd0, gtau, gmass, work, stream);
+  }
 }
 
 int sim_status(sim_handle* h, int32_t* flags) {

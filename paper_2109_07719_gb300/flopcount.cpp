@@ -57,14 +57,14 @@ static Counts count(int n, bool free_root) {
   Sys<F> s{prm, meta, tape, adj, B, n};
   V3<F> g{F(0), F(0), F(-9.81)};
   g_flops = 0;
-  aba_forward<F>(s, Col<const F>{q, B}, Col<const F>{qd, B}, Col<const F>{tau, B}, g);
+  aba_forward<F, F>(s, Col<const F>{q, B}, Col<const F>{qd, B}, Col<const F>{tau, B}, g);
   F q2[64], qd2[64];
   for (int i = 0; i < 64; ++i) { q2[i] = q[i]; qd2[i] = qd[i]; }
   integrate<F>(s, Col<F>{q2, B}, Col<F>{qd2, B}, F(1e-3), I_SEMI_IMPLICIT);
   Counts c;
   c.fwd = g_flops;
   g_flops = 0;
-  step_adjoint<F>(s, Col<const F>{q, B}, Col<const F>{qd, B}, Col<F>{gq, B}, Col<F>{gqd, B},
+  step_adjoint<F, F>(s, Col<const F>{q, B}, Col<const F>{qd, B}, Col<F>{gq, B}, Col<F>{gqd, B},
                   Col<F>{gtau, B}, Col<F>{gm, B}, g, F(1e-3), I_SEMI_IMPLICIT);
   c.adj = g_flops;
   return c;

@@ -242,3 +242,30 @@ def test_autograd_double_pendulum_full_horizon():
     check("gq0", q0.grad.cpu().numpy(), o["gq0"], 1e-6)
     check("gqd0", qd0.grad.cpu().numpy(), o["gqd0"], 1e-6)
     check("gtau", tau.grad.cpu().numpy(), o["gtau"], 1e-6)
+
+
+@pytest.mark.parametrize("cfg", [2, 3, 5])
+def test_fp32_with_fp64_d_solves(cfg):
+    """SIM_FP32_D64: FP32 storage and arithmetic with the articulated-inertia D
+    solves in FP64; same tolerances as the FP32 path."""
+    B, T = 40, 100
+    work = _work(cfg, B, T, "fp32_d64")
+    sim = _sim(work, "fp32_d64")
+    assert sim.dtype == torch.float32
+    (q0, qd0, tau), (hq, hqd, ht) = _inputs(work, sim, T)
+    qT, qdT, ck, _ = sim.rollout(q0, qd0, tau)
+    gqT = torch.ones_like(qT)
+    gqdT = torch.zeros_like(qdT)
+    gq0, gqd0, gtau, gm = sim.backward(ck, tau, gqT, gqdT)
+    ts, tg = TOL["fp32"]
+    oq, oqd = oracle_forward(work.model, list(range(B)), hq, hqd, ht)
+    rep = {}
+    check("qT", qT.cpu().numpy(), oq, ts, rep)
+    check("qdT", qdT.cpu().numpy(), oqd, ts, rep)
+    sel = [0, 21, 39]
+    o = oracle_backward(work.model, sel, hq, hqd, ht, np.ones_like(hq), np.zeros_like(hqd))
+    check("gq0", gq0.cpu().numpy()[:, sel], o["gq0"], tg, rep)
+    check("gtau", gtau.cpu().numpy()[:, :, sel], o["gtau"], tg, rep)
+    gmd = mass_grad_of(work.model, gm.cpu().numpy(), sel)
+    check("gmass", np.concatenate([gmd[s] for s in sel]), np.concatenate([o["gm"][s] for s in sel]), tg, rep)
+    print(f"fp32_d64 cfg {cfg} relative errors:", rep)

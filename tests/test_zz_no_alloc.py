@@ -47,7 +47,7 @@ def test_static_step_matches_step_batch(cfg, B, precision, tol):
 
 def test_static_step_rejects_batches_beyond_the_static_scratch():
     from paper_2109_07719_gb300 import Simulator, SimError
-    work = wl.config(2, B=8192, T=1, precision="fp32")   # 7 x 118 x 8192 x 4 B > 16 MiB
+    work = wl.config(2, B=8192, T=1, precision="fp32")   # 7 x 119 x 8192 x 4 B > 16 MiB
     sim = Simulator(work.model, precision="fp32")
     q = torch.zeros(sim.nq_max, sim.B, dtype=sim.dtype, device=sim.device)
     qd = torch.zeros(sim.nv_max, sim.B, dtype=sim.dtype, device=sim.device)
