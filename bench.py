@@ -109,6 +109,7 @@ def run_ours(args):
     m = work.model
     T, k = work.T, args.k
     sim = Simulator(m, precision=args.precision)
+    sim.set_tape_space(args.tape)
     if args.autotune:
         tuned = sim.autotune(torch.tensor(work.q0, dtype=sim.dtype, device=sim.device),
                              torch.tensor(work.qd0, dtype=sim.dtype, device=sim.device))
@@ -214,6 +215,7 @@ def run_ours(args):
                    "precision": args.precision, "l2": "flushed between steps (256 MB write)",
                    "parallelism": f"replicas x{ws}" if ws > 1 else "single GPU",
                    "block": sim.launch[0], "schedule": "persistent" if sim.launch[1] else "grid",
+                   "tape": args.tape,
                    "cuda_graph": bool(args.graph)},
         "fwd_env_steps_per_s": B * T / (float(np.mean(fwd_ms)) / 1e3),
         "ms_fwd": float(np.mean(fwd_ms)), "ms_adj": float(np.mean(adj_ms)),
@@ -377,6 +379,8 @@ def memory_sweep(args):
         q0 = torch.tensor(work.q0, dtype=dt, device=dev)
         qd0 = torch.tensor(work.qd0, dtype=dt, device=dev)
         tau = work.tau(device=dev, dtype=dt)
+        torch.cuda.synchronize()
+        torch.cuda.reset_peak_memory_stats()   # drop the input generator's temporaries
         t0 = time.perf_counter()
         qT, qdT, ck, _ = sim.rollout(q0, qd0, tau, k=args.k)
         g = sim.backward(ck, tau, torch.ones_like(qT), torch.zeros_like(qdT), k=args.k)
@@ -412,6 +416,7 @@ def main():
     ap.add_argument("--block", type=int, default=0)
     ap.add_argument("--persistent", action="store_true")
     ap.add_argument("--autotune", action="store_true")
+    ap.add_argument("--tape", default="auto", choices=["auto", "global", "shared"])
     ap.add_argument("--no-cpu-baseline", dest="cpu_baseline", action="store_false")
     ap.add_argument("--no-plain", dest="plain", action="store_false")
     ap.add_argument("--no-e2e", dest="e2e", action="store_false")

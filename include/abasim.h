@@ -171,6 +171,16 @@ int sim_clear_status(sim_handle* h, void* stream);
 #define SIM_SCHED_PERSISTENT 1
 int sim_set_launch(sim_handle* h, int32_t threads, int32_t schedule);
 
+/* Where the per-step tape lives: SIM_TAPE_AUTO (default) puts it in shared
+ * memory when the block's tiles of 32 systems fit the per-block limit, else in
+ * the handle's global scratch; SIM_TAPE_GLOBAL / SIM_TAPE_SHARED force one
+ * (SHARED fails with SIM_EUNSUPPORTED at launch if it does not fit).  Results do
+ * not depend on it. */
+#define SIM_TAPE_AUTO 0
+#define SIM_TAPE_GLOBAL 1
+#define SIM_TAPE_SHARED 2
+int sim_set_tape_space(sim_handle* h, int32_t space);
+
 /* The packing of systems into slots (thread order): sys_of_slot[n_systems]
  * (host memory) receives the system index run by each slot.  Systems are sorted
  * by link count, longest first, so the systems of a warp walk equally many links

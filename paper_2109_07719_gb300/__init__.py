@@ -62,6 +62,7 @@ _SIGS = {
     "sim_clear_status": (ctypes.c_int, [_P, _P]),
     "sim_set_launch": (ctypes.c_int, [_P, ctypes.c_int32, ctypes.c_int32]),
     "sim_slot_order": (ctypes.c_int, [_P, _P]),
+    "sim_set_tape_space": (ctypes.c_int, [_P, ctypes.c_int32]),
     "sim_last_error": (ctypes.c_char_p, [_P]),
 }
 
@@ -178,6 +179,11 @@ class Simulator:
         """Threads per block (one work unit each) and grid vs persistent scheduling."""
         self._check(lib.sim_set_launch(self._h, int(threads), 1 if persistent else 0), "sim_set_launch")
         self.launch = (int(threads) or 32, bool(persistent))
+
+    def set_tape_space(self, space: str = "auto"):
+        """'auto' (shared memory when it fits), 'global' or 'shared'."""
+        code = {"auto": 0, "global": 1, "shared": 2}[space]
+        self._check(lib.sim_set_tape_space(self._h, code), "sim_set_tape_space")
 
     def slot_order(self):
         """System index run by each slot (thread), longest systems first."""

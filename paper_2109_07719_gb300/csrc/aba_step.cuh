@@ -75,18 +75,22 @@ template <class T> struct Col {
   SD T& operator[](int d) const { return p[(long long)d * B]; }
 };
 
-// The per-system view used by the step functions.
+// Model constants and tapes are stored tile-major: tiles of LANES consecutive
+// slots, [tile][link][field][lane], so a warp's 32 systems touch 32 consecutive
+// words and every field offset is a compile-time multiple of LANES.
+constexpr int LANES = 32;
+
+// The per-system view used by the step functions (pointers at this system's lane).
 template <class T> struct Sys {
-  const T* prm;   // [maxL][NPRM][B] + slot
-  const int* meta;  // [maxL][B] + slot
-  T* tape;        // [maxL][NTAPE][B] + slot
-  T* adj;         // [maxL][NADJ][B] + slot
-  long long B;
+  const T* prm;     // [maxL][NPRM][LANES] of this tile
+  const int* meta;  // [maxL][LANES]
+  T* tape;          // [maxL][NTAPE][LANES]
+  T* adj;           // [maxL][NADJ][LANES]
   int nl;
-  SD T P(int l, int f) const { return prm[((long long)l * NPRM + f) * B]; }
-  SD int M(int l) const { return meta[(long long)l * B]; }
-  SD T& tp(int l, int f) const { return tape[((long long)l * NTAPE + f) * B]; }
-  SD T& ad(int l, int f) const { return adj[((long long)l * NADJ + f) * B]; }
+  SD T P(int l, int f) const { return prm[(l * NPRM + f) * LANES]; }
+  SD int M(int l) const { return meta[l * LANES]; }
+  SD T& tp(int l, int f) const { return tape[(l * NTAPE + f) * LANES]; }
+  SD T& ad(int l, int f) const { return adj[(l * NADJ + f) * LANES]; }
 
   // ---- field helpers
   SD V3<T> pv3(int l, int f) const { return {P(l, f), P(l, f + 1), P(l, f + 2)}; }

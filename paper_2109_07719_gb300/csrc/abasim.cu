@@ -28,7 +28,7 @@ thread_local std::string g_create_error;
 }  // namespace
 
 struct sim_handle {
-  int B = 0, maxL = 0, nq_max = 0, nv_max = 0, L_total = 0;
+  int B = 0, Bpad = 0, maxL = 0, nq_max = 0, nv_max = 0, L_total = 0;
   int precision = SIM_FP64, integrator = SIM_SEMI_IMPLICIT_EULER;
   int block = kDefaultBlock;
   int device = 0;
@@ -46,6 +46,7 @@ struct sim_handle {
   int* sys_of_slot = nullptr;  // [B]
   unsigned* counter = nullptr;  // work-unit ticket of persistent launches
   int schedule = SIM_SCHED_GRID;
+  int tape_space = SIM_TAPE_AUTO;
   int sms = 0;
   std::vector<int> h_sys_of_slot;
   std::string err;
@@ -75,21 +76,43 @@ template <class T> struct DevModel {
   const int* sys_of_slot;
   unsigned* counter;
   long long B;
+  int maxL;
   int nq_max, nv_max;
   T dt;
   T g0, g1, g2;
   int integ;
   int persistent;
+  int smem;
 };
 
 template <class T> DevModel<T> dev_model(const sim_handle* h) {
   return DevModel<T>{(const T*)h->prm, h->meta, h->nl, h->nqv, (T*)h->tape, (T*)h->adj, h->status,
-                     h->sys_of_slot, h->counter, (long long)h->B, h->nq_max, h->nv_max, (T)h->dt,
-                     (T)h->g[0], (T)h->g[1], (T)h->g[2], h->integrator, 0};
+                     h->sys_of_slot, h->counter, (long long)h->B, h->maxL, h->nq_max, h->nv_max, (T)h->dt,
+                     (T)h->g[0], (T)h->g[1], (T)h->g[2], h->integrator, 0, 0};
 }
 
-template <class T> __device__ __forceinline__ Sys<T> sys_of(const DevModel<T>& m, int b) {
-  return Sys<T>{m.prm + b, m.meta + b, m.tape + b, m.adj + b, m.B, m.nl[b]};
+extern __shared__ __align__(16) unsigned char g_smem[];
+
+// With m.smem set, the tapes of the block's tiles live in dynamic shared memory
+// ([tile in block][link][field][lane], tape then adjoint); otherwise in the
+// handle's global scratch.
+template <class T, bool SMEM> __device__ __forceinline__ Sys<T> sys_of(const DevModel<T>& m, int slot) {
+  const long long tile = slot / LANES, lane = slot % LANES;
+  const long long L = m.maxL;
+  T* tape;
+  T* adj;
+  if (SMEM) {
+    const int tb = threadIdx.x / LANES;
+    const int tiles = blockDim.x / LANES;
+    T* base = reinterpret_cast<T*>(g_smem);
+    tape = base + (long long)tb * L * NTAPE * LANES + lane;
+    adj = base + (long long)tiles * L * NTAPE * LANES + (long long)tb * L * NADJ * LANES + lane;
+  } else {
+    tape = m.tape + tile * L * NTAPE * LANES + lane;
+    adj = m.adj + tile * L * NADJ * LANES + lane;
+  }
+  return Sys<T>{m.prm + tile * L * NPRM * LANES + lane, m.meta + tile * L * LANES + lane, tape, adj,
+                m.nl[slot]};
 }
 
 template <class T> __device__ __forceinline__ bool finite_t(T x) { return isfinite(x); }
@@ -101,7 +124,7 @@ template <class T> __device__ __forceinline__ bool finite_t(T x) { return isfini
 
 // T steps of one system.  The working state lives in (qT, qdT); checkpoints every
 // k steps; optional full trajectory.
-template <class T, class DT>
+template <class T, class DT, bool SMEM>
 __device__ __forceinline__ void rollout_one(const DevModel<T>& m, int slot, const T* __restrict__ q0,
                                             const T* __restrict__ qd0, const T* __restrict__ tau,
                                             long long Tn, int k, T* ckpt, T* qT, T* qdT, T* traj) {
@@ -109,7 +132,7 @@ __device__ __forceinline__ void rollout_one(const DevModel<T>& m, int slot, cons
   const long long B = m.B;
   const int nqm = m.nq_max, nvm = m.nv_max, NX = nqm + nvm;
   const V3<T> g{m.g0, m.g1, m.g2};
-  Sys<T> s = sys_of(m, slot);
+  Sys<T> s = sys_of<T, SMEM>(m, slot);
   Col<T> q{qT + b, B}, qd{qdT + b, B};
   for (int d = 0; d < nqm; ++d) q[d] = q0[d * B + b];
   for (int d = 0; d < nvm; ++d) qd[d] = qd0[d * B + b];
@@ -140,7 +163,7 @@ __device__ __forceinline__ void rollout_one(const DevModel<T>& m, int slot, cons
 
 // Adjoint rollout of one system.  (gq0, gqd0) carry the running state adjoint
 // R^t = xbar^t.
-template <class T, class DT>
+template <class T, class DT, bool SMEM>
 __device__ __forceinline__ void backward_one(const DevModel<T>& m, int slot, const T* __restrict__ ckpt,
                                              const T* __restrict__ tau, long long Tn, int k,
                                              const T* __restrict__ gqT, const T* __restrict__ gqdT,
@@ -151,7 +174,7 @@ __device__ __forceinline__ void backward_one(const DevModel<T>& m, int slot, con
   const int nqm = m.nq_max, nvm = m.nv_max, NX = nqm + nvm;
   const int nq = m.nqv[slot] & 0xffff, nv = m.nqv[slot] >> 16;
   const V3<T> g{m.g0, m.g1, m.g2};
-  Sys<T> s = sys_of(m, slot);
+  Sys<T> s = sys_of<T, SMEM>(m, slot);
   Col<T> gq{gq0 + b, B}, gqd{gqd0 + b, B};
   for (int d = 0; d < nqm; ++d) {
     T v = d < nq ? gqT[d * B + b] : T(0);
@@ -225,19 +248,19 @@ __device__ __forceinline__ int next_unit(unsigned* counter) {
     unit = next_unit((m).counter);                                           \
   }
 
-template <class T, class DT>
+template <class T, class DT, bool SMEM>
 __global__ void k_rollout(DevModel<T> m, const T* __restrict__ q0, const T* __restrict__ qd0,
                           const T* __restrict__ tau, long long Tn, int k, T* ckpt, T* qT, T* qdT,
                           T* traj) {
-  ABASIM_FOR_EACH_SLOT(m, rollout_one<T, DT>(m, slot, q0, qd0, tau, Tn, k, ckpt, qT, qdT, traj))
+  ABASIM_FOR_EACH_SLOT(m, rollout_one<T, DT, SMEM>(m, slot, q0, qd0, tau, Tn, k, ckpt, qT, qdT, traj))
 }
 
-template <class T, class DT>
+template <class T, class DT, bool SMEM>
 __global__ void k_backward(DevModel<T> m, const T* __restrict__ ckpt, const T* __restrict__ tau,
                            long long Tn, int k, const T* __restrict__ gqT, const T* __restrict__ gqdT,
                            const T* __restrict__ gtraj, T* gq0, T* gqd0, T* gtau, T* gm_acc,
                            T* ring) {
-  ABASIM_FOR_EACH_SLOT(m, backward_one<T, DT>(m, slot, ckpt, tau, Tn, k, gqT, gqdT, gtraj, gq0, gqd0,
+  ABASIM_FOR_EACH_SLOT(m, backward_one<T, DT, SMEM>(m, slot, ckpt, tau, Tn, k, gqT, gqdT, gtraj, gq0, gqd0,
                                           gtau, gm_acc, ring))
 }
 
@@ -249,13 +272,14 @@ __global__ void k_gather_mass_grad(const T* __restrict__ gm_acc, const int* __re
 }
 
 template <class T>
-__global__ void k_set_masses(T* prm, const int* __restrict__ link_slot, int L, long long B,
+__global__ void k_set_masses(T* prm, const int* __restrict__ link_slot, int L, long long B, int maxL,
                              const T* __restrict__ mass) {
   const int j = blockIdx.x * blockDim.x + threadIdx.x;
   if (j >= L) return;
   const int ls = link_slot[j];
-  const long long l = ls / B, b = ls % B;
-  prm[(l * NPRM + P_M) * B + b] = mass[j];
+  const long long l = ls / B, slot = ls % B;
+  const long long tile = slot / LANES, lane = slot % LANES;
+  prm[((tile * maxL + l) * NPRM + P_M) * LANES + lane] = mass[j];
 }
 
 // ------------------------------------------------------------------ launches
@@ -264,13 +288,13 @@ inline cudaStream_t S(void* s) { return (cudaStream_t)s; }
 
 // Grid size and mode of a batched launch; resets the ticket of persistent launches.
 template <class K>
-int launch_shape(sim_handle* h, K kernel, int* grid, int* persistent, void* stream) {
+int launch_shape(sim_handle* h, K kernel, int* grid, int* persistent, size_t shm, void* stream) {
   const int units = (h->B + h->block - 1) / h->block;
   *grid = units;
   *persistent = 0;
   if (h->schedule != SIM_SCHED_PERSISTENT) return SIM_OK;
   int per_sm = 0;
-  cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, h->block, 0);
+  cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, h->block, shm);
   if (e != cudaSuccess) return cuda_fail(h, e, "occupancy query");
   const int cap = std::max(1, per_sm) * std::max(1, h->sms);
   *grid = std::min(units, cap);
@@ -279,16 +303,40 @@ int launch_shape(sim_handle* h, K kernel, int* grid, int* persistent, void* stre
   return e == cudaSuccess ? SIM_OK : cuda_fail(h, e, "work ticket reset");
 }
 
+// Dynamic shared memory for on-chip tapes (0 = keep them in global scratch):
+// the block's tiles x links x fields, if it fits the per-block opt-in limit.
+template <class T, class K>
+int smem_bytes(sim_handle* h, K kernel, int fields, size_t* bytes) {
+  *bytes = 0;
+  if (h->tape_space == SIM_TAPE_GLOBAL) return SIM_OK;
+  const size_t need = (size_t)(h->block / LANES) * h->maxL * fields * LANES * sizeof(T);
+  int limit = 0;
+  cudaError_t e = cudaDeviceGetAttribute(&limit, cudaDevAttrMaxSharedMemoryPerBlockOptin, h->device);
+  if (e != cudaSuccess) return cuda_fail(h, e, "shared-memory limit query");
+  if (need > (size_t)limit) {
+    if (h->tape_space == SIM_TAPE_SHARED) return fail(h, SIM_EUNSUPPORTED, "tape does not fit in shared memory");
+    return SIM_OK;
+  }
+  e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)need);
+  if (e != cudaSuccess) return cuda_fail(h, e, "shared-memory opt-in");
+  *bytes = need;
+  return SIM_OK;
+}
+
 template <class T, class DT>
 int launch_rollout(sim_handle* h, const void* q0, const void* qd0, const void* tau, int64_t T_,
                    int k, void* ckpt, void* qT, void* qdT, void* traj, void* stream) {
   DevModel<T> m = dev_model<T>(h);
-  int grid = 0;
-  int rc = launch_shape(h, k_rollout<T, DT>, &grid, &m.persistent, stream);
+  size_t shm = 0;
+  int rc = SIM_OK;
+  if (sizeof(T) == 4) rc = smem_bytes<T>(h, k_rollout<T, DT, true>, NTAPE, &shm);
   if (rc != SIM_OK) return rc;
-  k_rollout<T, DT><<<grid, h->block, 0, S(stream)>>>(m, (const T*)q0, (const T*)qd0, (const T*)tau,
-                                                  (long long)T_, k, (T*)ckpt, (T*)qT, (T*)qdT,
-                                                  (T*)traj);
+  auto kern = shm ? k_rollout<T, DT, true> : k_rollout<T, DT, false>;
+  int grid = 0;
+  rc = launch_shape(h, kern, &grid, &m.persistent, shm, stream);
+  if (rc != SIM_OK) return rc;
+  kern<<<grid, h->block, shm, S(stream)>>>(m, (const T*)q0, (const T*)qd0, (const T*)tau, (long long)T_,
+                                           k, (T*)ckpt, (T*)qT, (T*)qdT, (T*)traj);
   cudaError_t e = cudaGetLastError();
   return e == cudaSuccess ? SIM_OK : cuda_fail(h, e, "rollout launch");
 }
@@ -298,12 +346,17 @@ int launch_backward(sim_handle* h, const void* ckpt, const void* tau, int64_t T_
                     const void* gqT, const void* gqdT, const void* gtraj, void* gq0, void* gqd0,
                     void* gtau, void* gmass, void* work, void* stream) {
   DevModel<T> m = dev_model<T>(h);
-  int grid = 0;
-  int rc = launch_shape(h, k_backward<T, DT>, &grid, &m.persistent, stream);
+  size_t shm = 0;
+  int rc = SIM_OK;
+  if (sizeof(T) == 4) rc = smem_bytes<T>(h, k_backward<T, DT, true>, NTAPE + NADJ, &shm);
   if (rc != SIM_OK) return rc;
-  k_backward<T, DT><<<grid, h->block, 0, S(stream)>>>(
-      m, (const T*)ckpt, (const T*)tau, (long long)T_, k, (const T*)gqT, (const T*)gqdT,
-      (const T*)gtraj, (T*)gq0, (T*)gqd0, (T*)gtau, (T*)h->gm_acc, (T*)work);
+  auto kern = shm ? k_backward<T, DT, true> : k_backward<T, DT, false>;
+  int grid = 0;
+  rc = launch_shape(h, kern, &grid, &m.persistent, shm, stream);
+  if (rc != SIM_OK) return rc;
+  kern<<<grid, h->block, shm, S(stream)>>>(m, (const T*)ckpt, (const T*)tau, (long long)T_, k,
+                                           (const T*)gqT, (const T*)gqdT, (const T*)gtraj, (T*)gq0,
+                                           (T*)gqd0, (T*)gtau, (T*)h->gm_acc, (T*)work);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return cuda_fail(h, e, "backward launch");
   if (gmass) {
@@ -448,7 +501,7 @@ int launch_step_static(sim_handle* h, const void* q, const void* qd, const void*
   DevModel<T> m = dev_model<T>(h);
   m.tape = (T*)tape;
   const int grid = (h->B + h->block - 1) / h->block;
-  k_rollout<T, DT><<<grid, h->block, 0, S(stream)>>>(m, (const T*)q, (const T*)qd, (const T*)tau, 1LL, 1,
+  k_rollout<T, DT, false><<<grid, h->block, 0, S(stream)>>>(m, (const T*)q, (const T*)qd, (const T*)tau, 1LL, 1,
                                                   (T*)nullptr, (T*)q_out, (T*)qd_out, (T*)nullptr);
   cudaError_t e = cudaGetLastError();
   return e == cudaSuccess ? SIM_OK : cuda_fail(h, e, "static step launch");
@@ -487,9 +540,11 @@ int sim_create(const sim_model_desc* d, sim_handle** out) {
   std::stable_sort(order.begin(), order.end(), [&](int x, int y) { return nl_sys[x] > nl_sys[y]; });
   h->h_sys_of_slot = order;
   const int maxL = h->maxL;
+  const size_t Bpad = (size_t)((B + LANES - 1) / LANES) * LANES;
+  h->Bpad = (int)Bpad;
   std::vector<int> nl(B), nqv(B);
-  std::vector<double> prm((size_t)maxL * NPRM * B, 0.0);
-  std::vector<int> meta((size_t)maxL * B, 0), slot(h->L_total);
+  std::vector<double> prm((size_t)maxL * NPRM * Bpad, 0.0);
+  std::vector<int> meta((size_t)maxL * Bpad, 0), slot(h->L_total);
   for (int sl = 0; sl < B; ++sl) {
     const int b = order[sl];
     nl[sl] = nl_sys[b];
@@ -497,7 +552,8 @@ int sim_create(const sim_model_desc* d, sim_handle** out) {
     for (int l = 0; l < nl[sl]; ++l) {
       const int i = d->sys_link_offset[b] + l;
       const int jt = d->joint_type[i];
-      auto P = [&](int f) -> double& { return prm[((size_t)l * NPRM + f) * B + sl]; };
+      const size_t tile = sl / LANES, lane = sl % LANES;
+      auto P = [&](int f) -> double& { return prm[((tile * maxL + l) * NPRM + f) * LANES + lane]; };
       for (int x = 0; x < 12; ++x) P(P_E + x) = d->X_tree[12 * i + x];
       for (int x = 0; x < 3; ++x) {
         P(P_AX + x) = jt == SIM_REVOLUTE ? d->axis[3 * i + x] : 0.0;
@@ -508,7 +564,7 @@ int sim_create(const sim_model_desc* d, sim_handle** out) {
       bool treechild = false;  // a child other than link l + 1
       for (int c = l + 2; c < nl[sl]; ++c)
         if (d->parent[d->sys_link_offset[b] + c] == l) treechild = true;
-      meta[(size_t)l * B + sl] = make_meta(d->parent[i], jt, treechild, qo, vo);
+      meta[(tile * maxL + l) * LANES + lane] = make_meta(d->parent[i], jt, treechild, qo, vo);
       slot[i] = l * B + sl;
       qo += jt == SIM_FREE ? 7 : 1;
       vo += jt == SIM_FREE ? 6 : 1;
@@ -535,8 +591,8 @@ int sim_create(const sim_model_desc* d, sim_handle** out) {
   if (rc == SIM_OK) rc = put(h->nqv, nqv.data(), B * sizeof(int));
   if (rc == SIM_OK) rc = alloc((void**)&h->link_slot, slot.size() * sizeof(int), "link map");
   if (rc == SIM_OK) rc = put(h->link_slot, slot.data(), slot.size() * sizeof(int));
-  if (rc == SIM_OK) rc = alloc(&h->tape, (size_t)maxL * NTAPE * B * h->scalar, "tape");
-  if (rc == SIM_OK) rc = alloc(&h->adj, (size_t)maxL * NADJ * B * h->scalar, "adjoint tape");
+  if (rc == SIM_OK) rc = alloc(&h->tape, (size_t)maxL * NTAPE * Bpad * h->scalar, "tape");
+  if (rc == SIM_OK) rc = alloc(&h->adj, (size_t)maxL * NADJ * Bpad * h->scalar, "adjoint tape");
   if (rc == SIM_OK) rc = alloc(&h->gm_acc, (size_t)maxL * B * h->scalar, "mass-gradient buffer");
   if (rc == SIM_OK) rc = alloc((void**)&h->status, B * sizeof(int), "status");
   if (rc == SIM_OK) rc = alloc((void**)&h->sys_of_slot, B * sizeof(int), "slot order");
@@ -591,10 +647,10 @@ int sim_set_masses(sim_handle* h, const void* mass, void* stream) {
   const int grid = (h->L_total + 255) / 256;
   if (is_fp64(h))
     k_set_masses<double><<<grid, 256, 0, S(stream)>>>((double*)h->prm, h->link_slot, h->L_total,
-                                                      h->B, (const double*)mass);
+                                                      h->B, h->maxL, (const double*)mass);
   else
     k_set_masses<float><<<grid, 256, 0, S(stream)>>>((float*)h->prm, h->link_slot, h->L_total,
-                                                     h->B, (const float*)mass);
+                                                     h->B, h->maxL, (const float*)mass);
   cudaError_t e = cudaGetLastError();
   return e == cudaSuccess ? SIM_OK : cuda_fail(h, e, "set_masses launch");
 }
@@ -623,7 +679,7 @@ int sim_step_batch_static(sim_handle* h, const void* q, const void* qd, const vo
                           void* q_out, void* qd_out, void* stream) {
   if (!h) return SIM_EINVAL;
   if (!q || !qd || !tau || !q_out || !qd_out) return fail(h, SIM_EINVAL, "null state or torque pointer");
-  const size_t need = (size_t)h->maxL * NTAPE * h->B * h->scalar;
+  const size_t need = (size_t)h->maxL * NTAPE * h->Bpad * h->scalar;
   if (need > (size_t)SIM_STATIC_SCRATCH_BYTES) {
     char buf[200];
     snprintf(buf, sizeof buf, "batch needs %zu bytes of step scratch; the static array holds %zu",
@@ -684,6 +740,14 @@ int sim_set_launch(sim_handle* h, int32_t threads, int32_t schedule) {
     return fail(h, SIM_EINVAL, "block size must be a multiple of 32 in [32, 1024]");
   h->block = threads;
   h->schedule = schedule;
+  return SIM_OK;
+}
+
+int sim_set_tape_space(sim_handle* h, int32_t space) {
+  if (!h) return SIM_EINVAL;
+  if (space != SIM_TAPE_AUTO && space != SIM_TAPE_GLOBAL && space != SIM_TAPE_SHARED)
+    return fail(h, SIM_EINVAL, "unknown tape space");
+  h->tape_space = space;
   return SIM_OK;
 }
 

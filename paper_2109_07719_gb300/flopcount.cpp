@@ -38,23 +38,24 @@ struct Counts { long long fwd, adj; };
 // one system of n links: link 0 is free or revolute, links 1.. revolute children of 0
 static Counts count(int n, bool free_root) {
   const int B = 1;
-  static F prm[8 * NPRM], tape[8 * NTAPE], adj[8 * NADJ];
-  static int meta[8];
+  static F prm[8 * NPRM * LANES], tape[8 * NTAPE * LANES], adj[8 * NADJ * LANES];
+  static int meta[8 * LANES];
   F q[64], qd[64], tau[64], gq[64], gqd[64], gtau[64], gm[8];
   int qo = 0, vo = 0;
   for (int l = 0; l < n; ++l) {
     const bool fr = free_root && l == 0;
-    for (int f = 0; f < NPRM; ++f) prm[l * NPRM + f] = F(0.1 * (f + 1));
-    for (int f = 0; f < 9; ++f) prm[l * NPRM + P_E + f] = F(f % 4 == 0 ? 1.0 : 0.0);
-    prm[l * NPRM + P_AX] = 0; prm[l * NPRM + P_AX + 1] = 0; prm[l * NPRM + P_AX + 2] = 1;
-    prm[l * NPRM + P_M] = 1;
-    meta[l] = make_meta(l == 0 ? -1 : 0, fr ? J_FREE : J_REVOLUTE, false, qo, vo);
+    auto P = [&](int f) -> F& { return prm[(l * NPRM + f) * LANES]; };
+    for (int f = 0; f < NPRM; ++f) P(f) = F(0.1 * (f + 1));
+    for (int f = 0; f < 9; ++f) P(P_E + f) = F(f % 4 == 0 ? 1.0 : 0.0);
+    P(P_AX) = 0; P(P_AX + 1) = 0; P(P_AX + 2) = 1;
+    P(P_M) = 1;
+    meta[l * LANES] = make_meta(l == 0 ? -1 : 0, fr ? J_FREE : J_REVOLUTE, false, qo, vo);
     qo += fr ? 7 : 1;
     vo += fr ? 6 : 1;
   }
   for (int i = 0; i < 64; ++i) { q[i] = F(0.1 * i); qd[i] = F(0.2); tau[i] = F(0.3); gq[i] = F(1); gqd[i] = F(1); gm[i % 8] = F(0); }
   if (free_root) { q[3] = 0; q[4] = 0; q[5] = 0; q[6] = 1; }
-  Sys<F> s{prm, meta, tape, adj, B, n};
+  Sys<F> s{prm, meta, tape, adj, n};
   V3<F> g{F(0), F(0), F(-9.81)};
   g_flops = 0;
   aba_forward<F, F>(s, Col<const F>{q, B}, Col<const F>{qd, B}, Col<const F>{tau, B}, g);

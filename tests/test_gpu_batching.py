@@ -88,3 +88,17 @@ def test_autotune_keeps_results(tmp_path, monkeypatch):
     out = _run(sim, q0, qd0, tau)
     for a, b in zip(ref, out):
         assert torch.equal(a, b)
+
+
+@pytest.mark.parametrize("cfg", [2, 3, 4])
+def test_shared_memory_tape_matches_global(cfg):
+    """The per-step tape in shared memory or in global scratch gives the same
+    results (the two are separately compiled kernels, so to FP32 round-off)."""
+    work, sim, q0, qd0, tau = _setup(cfg=cfg, B=96, T=40)
+    sim.set_tape_space("global")
+    ref = _run(sim, q0, qd0, tau)
+    sim.set_tape_space("auto")
+    out = _run(sim, q0, qd0, tau)
+    for a, b in zip(ref, out):
+        err = float((a - b).abs().max() / (b.abs().max() + 1e-30))
+        assert err < 1e-5
