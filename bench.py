@@ -82,9 +82,10 @@ def _dist():
     return ws, rank
 
 
-def workload(cfg: int, precision: str, B=None, T=None):
+def workload(cfg: int, precision: str, B=None, T=None, rank: int = 0):
+    """The workload of this rank: ranks simulate disjoint batches (their own seed)."""
     import workloads as wl
-    kw = {}
+    kw = {"seed": wl.SEED_BASE + cfg + 1000 * rank}
     if B:
         kw["B"] = B
     if T:
@@ -105,11 +106,12 @@ def run_ours(args):
     torch.cuda.set_device(local)
     if ws > 1:
         dist.init_process_group("nccl")
-    work = workload(args.config, args.precision, args.batch, args.horizon)
+    work = workload(args.config, args.precision, args.batch, args.horizon, rank)
     m = work.model
     T, k = work.T, args.k
     sim = Simulator(m, precision=args.precision)
     sim.set_tape_space(args.tape)
+    sim.set_replay(args.replay)
     if args.autotune:
         tuned = sim.autotune(torch.tensor(work.q0, dtype=sim.dtype, device=sim.device),
                              torch.tensor(work.qd0, dtype=sim.dtype, device=sim.device))
@@ -185,12 +187,8 @@ def run_ours(args):
         torch.cuda.synchronize()
         graph_ms = float(np.mean([a.elapsed_time(b) for a, b in gev]))
     step_ms = float(np.sum(fwd_ms) + np.sum(adj_ms)) / args.steps
-    t = torch.tensor([step_ms], device=dev)
-    if ws > 1:
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-    step_ms = float(t.item())
+    step_ms, units = aggregate(step_ms, B * T, dev)
     flags = sim.status()
-    units = B * T * ws
     value = units / (step_ms / 1e3)
     # end to end through the public API with host buffers
     e2e = None
@@ -215,7 +213,7 @@ def run_ours(args):
                    "precision": args.precision, "l2": "flushed between steps (256 MB write)",
                    "parallelism": f"replicas x{ws}" if ws > 1 else "single GPU",
                    "block": sim.launch[0], "schedule": "persistent" if sim.launch[1] else "grid",
-                   "tape": args.tape,
+                   "tape": args.tape, "replay": args.replay,
                    "cuda_graph": bool(args.graph)},
         "fwd_env_steps_per_s": B * T / (float(np.mean(fwd_ms)) / 1e3),
         "ms_fwd": float(np.mean(fwd_ms)), "ms_adj": float(np.mean(adj_ms)),
@@ -275,6 +273,20 @@ def plain_per_system(work, args, k, n_sys=64):
     return {"value": len(sims) * T / (ms / 1e3), "unit": "env-steps/s", "systems_timed": len(sims),
             "ms": ms, "note": "one system per launch (rollout + adjoint), systems serial; "
                               "rate per env-step from the timed systems"}
+
+
+def aggregate(step_ms: float, units: int, device="cpu"):
+    """Whole-job timing over ranks: the slowest rank's time per step and the env-steps
+    all ranks processed (each rank runs its own batch, no data exchange)."""
+    import torch
+    import torch.distributed as dist
+    if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size() == 1:
+        return step_ms, units
+    t = torch.tensor([step_ms], dtype=torch.float64, device=device)
+    u = torch.tensor([units], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    dist.all_reduce(u, op=dist.ReduceOp.SUM)
+    return float(t.item()), int(u.item())
 
 
 def fp_peak(precision):
@@ -417,6 +429,7 @@ def main():
     ap.add_argument("--persistent", action="store_true")
     ap.add_argument("--autotune", action="store_true")
     ap.add_argument("--tape", default="auto", choices=["auto", "global", "shared"])
+    ap.add_argument("--replay", default="segment", choices=["segment", "quadratic"])
     ap.add_argument("--no-cpu-baseline", dest="cpu_baseline", action="store_false")
     ap.add_argument("--no-plain", dest="plain", action="store_false")
     ap.add_argument("--no-e2e", dest="e2e", action="store_false")

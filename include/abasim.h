@@ -181,6 +181,16 @@ int sim_set_launch(sim_handle* h, int32_t threads, int32_t schedule);
 #define SIM_TAPE_SHARED 2
 int sim_set_tape_space(sim_handle* h, int32_t space);
 
+/* How sim_backward_rollout rebuilds the states inside a checkpoint segment when
+ * k > 1.  SIM_REPLAY_SEGMENT (default): replay the segment once into the caller
+ * workspace, then differentiate it backwards (≈ one extra forward step per step).
+ * SIM_REPLAY_QUADRATIC: the supplement's scheme (Sec. B) — every state x^t is
+ * recomputed from the segment's checkpoint, (k+1)k/2 forward steps per segment,
+ * giving its (k+1)/2 · t_forward + t_backward time per step.  Same gradients. */
+#define SIM_REPLAY_SEGMENT 0
+#define SIM_REPLAY_QUADRATIC 1
+int sim_set_replay(sim_handle* h, int32_t mode);
+
 /* The packing of systems into slots (thread order): sys_of_slot[n_systems]
  * (host memory) receives the system index run by each slot.  Systems are sorted
  * by link count, longest first, so the systems of a warp walk equally many links

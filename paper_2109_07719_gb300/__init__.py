@@ -63,6 +63,7 @@ _SIGS = {
     "sim_set_launch": (ctypes.c_int, [_P, ctypes.c_int32, ctypes.c_int32]),
     "sim_slot_order": (ctypes.c_int, [_P, _P]),
     "sim_set_tape_space": (ctypes.c_int, [_P, ctypes.c_int32]),
+    "sim_set_replay": (ctypes.c_int, [_P, ctypes.c_int32]),
     "sim_last_error": (ctypes.c_char_p, [_P]),
 }
 
@@ -184,6 +185,11 @@ class Simulator:
         """'auto' (shared memory when it fits), 'global' or 'shared'."""
         code = {"auto": 0, "global": 1, "shared": 2}[space]
         self._check(lib.sim_set_tape_space(self._h, code), "sim_set_tape_space")
+
+    def set_replay(self, mode: str = "segment"):
+        """k > 1 state rebuild: 'segment' (replay once) or 'quadratic' (from the checkpoint)."""
+        code = {"segment": 0, "quadratic": 1}[mode]
+        self._check(lib.sim_set_replay(self._h, code), "sim_set_replay")
 
     def slot_order(self):
         """System index run by each slot (thread), longest systems first."""

@@ -224,11 +224,12 @@ template <class T, class DT> SD SV<T> spd_solve(const SI<T>& IA, SV<T> b) {
 
 // ------------------------------------------------------------------ forward
 // Runs jcalc and the three ABA passes for the state (q, qd) and joint force tau,
-// leaving every intermediate on the tape (qdd included).  Values passed between a
+// leaving qdd on the tape; with ADJ set, also every intermediate the adjoint
+// step reads (a forward-only rollout skips those stores).  Values passed between a
 // link and its parent ride in registers when the parent is the previous link (the
 // whole of a serial chain); other parents go through the tape.  Each iteration
 // loads what it needs before it stores anything, so the loads overlap.
-template <class T, class DT>
+template <class T, class DT, bool ADJ = true>
 SD void aba_forward(const Sys<T>& s, Col<const T> q, Col<const T> qd, Col<const T> tau, V3<T> grav) {
   const int nl = s.nl;
   // jcalc + pass 1 (root -> leaves)
@@ -266,10 +267,10 @@ SD void aba_forward(const Sys<T>& s, Col<const T> q, Col<const T> qd, Col<const 
     tp_xf(s, l, T_E, X);
     tp_sv(s, l, T_V, v);
     tp_sv(s, l, T_C, c);
-    tp_sv(s, l, T_H, h);
+    if (ADJ) tp_sv(s, l, T_H, h);
     tp_si(s, l, T_IA, I);
     tp_sv(s, l, T_PA, crossf(v, h));
-    if (jt == J_REVOLUTE) {
+    if (ADJ && jt == J_REVOLUTE) {
       s.tp(l, T_SC) = sn;
       s.tp(l, T_SC + 1) = cs;
     }
@@ -303,14 +304,15 @@ SD void aba_forward(const Sys<T>& s, Col<const T> q, Col<const T> qd, Col<const 
       const DT Di = DT(1) / D;
       const T u = tl - dot(a, pA.w);
       tp_sv(s, l, T_U, U);
-      s.tp(l, T_D) = (T)D;
       put_di<T, DT>(s, l, Di);
       s.tp(l, T_u) = u;
       if (par >= 0) {
         const SI<T> Ia = minus_scaled_outer<T, DT>(IA, Di, U);
         const SV<T> pa = pA + mul(Ia, c) + (T)((DT)u * Di) * U;
-        tp_si(s, l, T_Ia, Ia);
-        tp_sv(s, l, T_pa, pa);
+        if (ADJ) {
+          tp_si(s, l, T_Ia, Ia);
+          tp_sv(s, l, T_pa, pa);
+        }
         const SI<T> Cn = congruence(X, Ia);
         const SV<T> pn = applyT(X, pa);
         if (par == l - 1) {
@@ -350,14 +352,14 @@ SD void aba_forward(const Sys<T>& s, Col<const T> q, Col<const T> qd, Col<const 
       s.tp(l, T_QDD) = qdd;
       a = ap;
       a.w += qdd * ax;
-      tp_sv(s, l, T_AP, ap);
+      if (ADJ) tp_sv(s, l, T_AP, ap);
     } else {
       const SI<T> IA = tp_si(s, l, T_IA);
       const SV<T> u = tp_sv(s, l, T_u);
       const SV<T> ap = apply(X, apar) + c;
       a = spd_solve<T, DT>(IA, u);
       tp_sv(s, l, T_QDD, a - ap);
-      tp_sv(s, l, T_AP, ap);
+      if (ADJ) tp_sv(s, l, T_AP, ap);
     }
     tp_sv(s, l, T_A, a);
     a_prev = a;

@@ -47,6 +47,7 @@ struct sim_handle {
   unsigned* counter = nullptr;  // work-unit ticket of persistent launches
   int schedule = SIM_SCHED_GRID;
   int tape_space = SIM_TAPE_AUTO;
+  int replay = SIM_REPLAY_SEGMENT;
   int sms = 0;
   std::vector<int> h_sys_of_slot;
   std::string err;
@@ -83,12 +84,14 @@ template <class T> struct DevModel {
   int integ;
   int persistent;
   int smem;
+  int quadratic;
 };
 
 template <class T> DevModel<T> dev_model(const sim_handle* h) {
   return DevModel<T>{(const T*)h->prm, h->meta, h->nl, h->nqv, (T*)h->tape, (T*)h->adj, h->status,
                      h->sys_of_slot, h->counter, (long long)h->B, h->maxL, h->nq_max, h->nv_max, (T)h->dt,
-                     (T)h->g[0], (T)h->g[1], (T)h->g[2], h->integrator, 0, 0};
+                     (T)h->g[0], (T)h->g[1], (T)h->g[2], h->integrator, 0, 0,
+                     h->replay == SIM_REPLAY_QUADRATIC};
 }
 
 extern __shared__ __align__(16) unsigned char g_smem[];
@@ -146,8 +149,8 @@ __device__ __forceinline__ void rollout_one(const DevModel<T>& m, int slot, cons
       for (int d = 0; d < nqm; ++d) c[d * B] = q[d];
       for (int d = 0; d < nvm; ++d) c[(nqm + d) * B] = qd[d];
     }
-    aba_forward<T, DT>(s, Col<const T>{qT + b, B}, Col<const T>{qdT + b, B},
-                   Col<const T>{tau + t * nvm * B + b, B}, g);
+    aba_forward<T, DT, false>(s, Col<const T>{qT + b, B}, Col<const T>{qdT + b, B},
+                              Col<const T>{tau + t * nvm * B + b, B}, g);
     integrate<T>(s, q, qd, m.dt, m.integ);
     if (traj) {
       T* c = traj + (t + 1) * NX * B + b;
@@ -193,22 +196,32 @@ __device__ __forceinline__ void backward_one(const DevModel<T>& m, int slot, con
     const long long t0 = seg * k;
     const long long t1 = (t0 + k < Tn) ? t0 + k : Tn;
     const T* xs = ckpt + seg * NX * B + b;
-    if (k > 1) {  // replay the segment once, keeping its states (ring is stored by slot)
+    if (k > 1 && !m.quadratic) {  // replay the segment once, keeping its states (ring by slot)
       T* r0 = ring + slot;
       for (int d = 0; d < NX; ++d) r0[d * B] = xs[d * B];
       for (long long j = 1; j < t1 - t0; ++j) {
         const T* prev = ring + (j - 1) * NX * B + slot;
         T* cur = ring + j * NX * B + slot;
         for (int d = 0; d < NX; ++d) cur[d * B] = prev[d * B];
-        aba_forward<T, DT>(s, Col<const T>{cur, B}, Col<const T>{cur + nqm * B, B},
+        aba_forward<T, DT, false>(s, Col<const T>{cur, B}, Col<const T>{cur + nqm * B, B},
                        Col<const T>{tau + (t0 + j - 1) * nvm * B + b, B}, g);
         integrate<T>(s, Col<T>{cur, B}, Col<T>{cur + nqm * B, B}, m.dt, m.integ);
       }
     }
     for (long long t = t1 - 1; t >= t0; --t) {
       const T* x = (k > 1) ? ring + (t - t0) * NX * B + slot : xs;
+      if (k > 1 && m.quadratic) {  // recompute x^t from the segment checkpoint: t - t0 steps
+        T* cur = ring + slot;
+        x = cur;
+        for (int d = 0; d < NX; ++d) cur[d * B] = xs[d * B];
+        for (long long j = t0; j < t; ++j) {
+          aba_forward<T, DT, false>(s, Col<const T>{cur, B}, Col<const T>{cur + nqm * B, B},
+                                    Col<const T>{tau + j * nvm * B + b, B}, g);
+          integrate<T>(s, Col<T>{cur, B}, Col<T>{cur + nqm * B, B}, m.dt, m.integ);
+        }
+      }
       Col<const T> q{x, B}, qd{x + nqm * B, B};
-      aba_forward<T, DT>(s, q, qd, Col<const T>{tau + t * nvm * B + b, B}, g);
+      aba_forward<T, DT, true>(s, q, qd, Col<const T>{tau + t * nvm * B + b, B}, g);
       T* gt = gtau + t * nvm * B + b;
       step_adjoint<T, DT>(s, q, qd, gq, gqd, Col<T>{gt, B}, gm, g, m.dt, m.integ);
       for (int d = nv; d < nvm; ++d) gt[d * B] = T(0);
@@ -304,9 +317,11 @@ int launch_shape(sim_handle* h, K kernel, int* grid, int* persistent, size_t shm
 }
 
 // Dynamic shared memory for on-chip tapes (0 = keep them in global scratch):
-// the block's tiles x links x fields, if it fits the per-block opt-in limit.
-template <class T, class K>
-int smem_bytes(sim_handle* h, K kernel, int fields, size_t* bytes) {
+// the block's tiles x links x fields, if it fits the per-block opt-in limit and,
+// in auto mode, if the smaller residency it implies adds no wave of blocks over
+// the global-tape kernel.
+template <class T, class KS, class KG>
+int smem_bytes(sim_handle* h, KS kernel_smem, KG kernel_global, int fields, size_t* bytes) {
   *bytes = 0;
   if (h->tape_space == SIM_TAPE_GLOBAL) return SIM_OK;
   const size_t need = (size_t)(h->block / LANES) * h->maxL * fields * LANES * sizeof(T);
@@ -317,8 +332,19 @@ int smem_bytes(sim_handle* h, K kernel, int fields, size_t* bytes) {
     if (h->tape_space == SIM_TAPE_SHARED) return fail(h, SIM_EUNSUPPORTED, "tape does not fit in shared memory");
     return SIM_OK;
   }
-  e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)need);
+  e = cudaFuncSetAttribute(kernel_smem, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)need);
   if (e != cudaSuccess) return cuda_fail(h, e, "shared-memory opt-in");
+  if (h->tape_space == SIM_TAPE_AUTO) {
+    int per_sm_s = 0, per_sm_g = 0;
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm_s, kernel_smem, h->block, need);
+    if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm_g, kernel_global, h->block, 0);
+    if (e != cudaSuccess) return cuda_fail(h, e, "occupancy query");
+    const long long units = (h->B + h->block - 1) / h->block;
+    const long long sms = std::max(1, h->sms);
+    const long long waves_s = per_sm_s > 0 ? (units + sms * per_sm_s - 1) / (sms * per_sm_s) : 1LL << 40;
+    const long long waves_g = per_sm_g > 0 ? (units + sms * per_sm_g - 1) / (sms * per_sm_g) : 1LL << 40;
+    if (waves_s > waves_g) return SIM_OK;
+  }
   *bytes = need;
   return SIM_OK;
 }
@@ -329,7 +355,7 @@ int launch_rollout(sim_handle* h, const void* q0, const void* qd0, const void* t
   DevModel<T> m = dev_model<T>(h);
   size_t shm = 0;
   int rc = SIM_OK;
-  if (sizeof(T) == 4) rc = smem_bytes<T>(h, k_rollout<T, DT, true>, NTAPE, &shm);
+  if (sizeof(T) == 4) rc = smem_bytes<T>(h, k_rollout<T, DT, true>, k_rollout<T, DT, false>, NTAPE, &shm);
   if (rc != SIM_OK) return rc;
   auto kern = shm ? k_rollout<T, DT, true> : k_rollout<T, DT, false>;
   int grid = 0;
@@ -348,7 +374,7 @@ int launch_backward(sim_handle* h, const void* ckpt, const void* tau, int64_t T_
   DevModel<T> m = dev_model<T>(h);
   size_t shm = 0;
   int rc = SIM_OK;
-  if (sizeof(T) == 4) rc = smem_bytes<T>(h, k_backward<T, DT, true>, NTAPE + NADJ, &shm);
+  if (sizeof(T) == 4) rc = smem_bytes<T>(h, k_backward<T, DT, true>, k_backward<T, DT, false>, NTAPE + NADJ, &shm);
   if (rc != SIM_OK) return rc;
   auto kern = shm ? k_backward<T, DT, true> : k_backward<T, DT, false>;
   int grid = 0;
@@ -748,6 +774,13 @@ int sim_set_tape_space(sim_handle* h, int32_t space) {
   if (space != SIM_TAPE_AUTO && space != SIM_TAPE_GLOBAL && space != SIM_TAPE_SHARED)
     return fail(h, SIM_EINVAL, "unknown tape space");
   h->tape_space = space;
+  return SIM_OK;
+}
+
+int sim_set_replay(sim_handle* h, int32_t mode) {
+  if (!h) return SIM_EINVAL;
+  if (mode != SIM_REPLAY_SEGMENT && mode != SIM_REPLAY_QUADRATIC) return fail(h, SIM_EINVAL, "unknown replay mode");
+  h->replay = mode;
   return SIM_OK;
 }
 

@@ -269,3 +269,21 @@ def test_fp32_with_fp64_d_solves(cfg):
     gmd = mass_grad_of(work.model, gm.cpu().numpy(), sel)
     check("gmass", np.concatenate([gmd[s] for s in sel]), np.concatenate([o["gm"][s] for s in sel]), tg, rep)
     print(f"fp32_d64 cfg {cfg} relative errors:", rep)
+
+
+@pytest.mark.parametrize("cfg,k", [(2, 7), (3, 10)])
+def test_quadratic_replay_gives_same_gradients(cfg, k):
+    """The supplement's recompute-from-checkpoint scheme and the one-pass segment
+    replay give the same gradients (to round-off), T not a multiple of k."""
+    B, T = 37, 53
+    work = _work(cfg, B, T)
+    sim = _sim(work)
+    (q0, qd0, tau), _ = _inputs(work, sim, T)
+    qT, qdT, ck, _ = sim.rollout(q0, qd0, tau, k=k)
+    gqT, gqdT = torch.ones_like(qT), -torch.ones_like(qdT)
+    a = sim.backward(ck, tau, gqT, gqdT, k=k)
+    sim.set_replay("quadratic")
+    b = sim.backward(ck, tau, gqT, gqdT, k=k)
+    sim.set_replay("segment")
+    for name, x, y in zip(("gq0", "gqd0", "gtau", "gmass"), a, b):
+        check(name, y.cpu().numpy(), x.cpu().numpy(), 1e-10)
