@@ -66,6 +66,8 @@ enum sim_joint { SIM_REVOLUTE = 0, SIM_FREE = 1 };
  *               [E w; E (v - r x w)] (the supplement's st_apply)
  *   mass, com[3], I_com[6]  rigid-body inertia: mass, centre of mass in the link
  *               frame, rotational inertia about the COM (xx yy zz xy xz yz)
+ *   damping     viscous damping of a revolute joint: the joint force is
+ *               tau - damping * qd (NULL: none; ignored for free joints)
  * gravity[3] is the world-frame gravitational acceleration (e.g. 0 0 -9.81).  */
 typedef struct sim_model_desc {
   int32_t n_systems;
@@ -82,6 +84,7 @@ typedef struct sim_model_desc {
   const double* mass;
   const double* com;
   const double* I_com;
+  const double* damping;  /* [1] per link or NULL: viscous joint damping b >= 0 */
 } sim_model_desc;
 
 typedef struct sim_handle sim_handle;
@@ -142,6 +145,17 @@ int sim_step_batch_static(sim_handle* h, const void* q, const void* qd, const vo
  * bytes) and every state to traj (if non-NULL).  T == 0 copies the input. */
 int sim_rollout(sim_handle* h, const void* q0, const void* qd0, const void* tau, int64_t T,
                 int32_t k, void* ckpt, void* qT, void* qdT, void* traj, void* stream);
+
+/* Forward-mode derivative of one step (the Jacobian-vector product the paper's
+ * RL sample enhancement needs, Sec. 4: s'(a + da) ~ s'(a) + ds'/da da):
+ * (q_out, qd_out) = x' as sim_step_batch, (dq_out, dqd_out) = dx'/dx (dq, dqd)
+ * + dx'/dtau dtau.  Any of dq, dqd, dtau may be NULL (zero tangent).  The step
+ * runs on dual numbers in the caller's workspace of sim_jvp_work_bytes() bytes.
+ * The SIM_FP32_D64 mode runs this call in plain FP32. */
+size_t sim_jvp_work_bytes(const sim_handle* h);
+int sim_step_jvp(sim_handle* h, const void* q, const void* qd, const void* tau, const void* dq,
+                 const void* dqd, const void* dtau, void* q_out, void* qd_out, void* dq_out,
+                 void* dqd_out, void* work, size_t work_bytes, void* stream);
 
 /* Adjoint of sim_rollout (Sec. 3.1 Eq. 3-4: R^k = xbar^k pulled back step by step;
  * Sec. 3.2 Eq. 7: each step recomputed from its checkpoint; for k > 1 each

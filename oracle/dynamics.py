@@ -14,7 +14,8 @@ Joint models (a reading of the paper, which names no joint convention):
 * free (floating base): q = (p, quaternion x y z w), the base pose in the world;
   E_J = R(quat)^T, r_J = p; qd = body-frame spatial velocity (w, v); S = 1_6.
 Link i's transform from its parent is X_i = X_J(q_i) X_tree,i.  Gravity enters
-as the fictitious base acceleration a_0 = [0; -g].
+as the fictitious base acceleration a_0 = [0; -g].  Viscous joint damping b (a
+joint force -b qd on revolute joints) is applied by the integrator step.
 """
 from __future__ import annotations
 
@@ -65,6 +66,8 @@ class OracleModel:
                                torch.stack([xz, yz, zz], -1)], -2)
         self.gravity = torch.as_tensor(desc.gravity, dtype=f64)
         self.dt = float(desc.dt)
+        damp = getattr(desc, "damping", None)
+        self.link_damping = t(damp) if damp is not None else torch.zeros(self.B, n, dtype=f64)
         self.qs, self.vs = [], []
         qo = vo = 0
         for j in self.jtype:
@@ -74,6 +77,11 @@ class OracleModel:
             qo += nq
             vo += nv
         self.nq, self.nv = qo, vo
+        # viscous damping per velocity coordinate (revolute joints only)
+        self.damping = torch.zeros(self.B, vo, dtype=f64)
+        for i, j in enumerate(self.jtype):
+            if j != FREE:
+                self.damping[:, self.vs[i]] = self.link_damping[:, i:i + 1]
 
     def inertias(self, mass=None):
         """Spatial inertia of every link [B, N, 6, 6]; ``mass`` [B, N] overrides."""

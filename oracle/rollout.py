@@ -32,8 +32,8 @@ def qdd_of(model, q, qd, tau, fd="crba", mass=None):
 
 
 def step(model: OracleModel, q, qd, tau, integrator="semi", fd="crba", mass=None):
-    """One time step x^k -> x^{k+1}."""
-    qdd = qdd_of(model, q, qd, tau, fd, mass)
+    """One time step x^k -> x^{k+1}; joint forces are tau - b qd (viscous damping)."""
+    qdd = qdd_of(model, q, qd, tau - model.damping * qd, fd, mass)
     dt = model.dt
     qd_new = qd + dt * qdd
     qv = qd_new if integrator == "semi" else qd

@@ -42,7 +42,7 @@ class _Desc(ctypes.Structure):
                 ("sys_link_offset", ctypes.c_void_p), ("parent", ctypes.c_void_p),
                 ("joint_type", ctypes.c_void_p), ("axis", ctypes.c_void_p),
                 ("X_tree", ctypes.c_void_p), ("mass", ctypes.c_void_p), ("com", ctypes.c_void_p),
-                ("I_com", ctypes.c_void_p)]
+                ("I_com", ctypes.c_void_p), ("damping", ctypes.c_void_p)]
 
 
 _P = ctypes.c_void_p
@@ -64,6 +64,8 @@ _SIGS = {
     "sim_slot_order": (ctypes.c_int, [_P, _P]),
     "sim_set_tape_space": (ctypes.c_int, [_P, ctypes.c_int32]),
     "sim_set_replay": (ctypes.c_int, [_P, ctypes.c_int32]),
+    "sim_jvp_work_bytes": (ctypes.c_size_t, [_P]),
+    "sim_step_jvp": (ctypes.c_int, [_P] * 11 + [_P, ctypes.c_size_t, _P]),
     "sim_last_error": (ctypes.c_char_p, [_P]),
 }
 
@@ -114,6 +116,8 @@ class Simulator:
             mass=np.ascontiguousarray(model.mass, np.float64),
             com=np.ascontiguousarray(model.com, np.float64),
             I_com=np.ascontiguousarray(model.I_com, np.float64))
+        if getattr(model, "damping", None) is not None:
+            keep["damping"] = np.ascontiguousarray(model.damping, np.float64)
         d = _Desc()
         d.n_systems = len(keep["sys_link_offset"]) - 1
         d.precision = PRECISIONS[precision]
@@ -229,6 +233,26 @@ class Simulator:
         self._check(lib.sim_step_batch_static(self._h, _ptr(q), _ptr(qd), _ptr(tau), _ptr(q_out),
                                               _ptr(qd_out), _stream()), "sim_step_batch_static")
         return q_out, qd_out
+
+    def jvp(self, q, qd, tau, dq=None, dqd=None, dtau=None, work=None):
+        """One step and its forward-mode derivative (sim_step_jvp): returns
+        (q', qd', dq', dqd') with (dq', dqd') = J_x (dq, dqd) + J_tau dtau."""
+        B = self.B
+        self._arg(q, (self.nq_max, B), "q")
+        self._arg(qd, (self.nv_max, B), "qd")
+        self._arg(tau, (self.nv_max, B), "tau")
+        self._arg(dq, (self.nq_max, B), "dq")
+        self._arg(dqd, (self.nv_max, B), "dqd")
+        self._arg(dtau, (self.nv_max, B), "dtau")
+        outs = [self.empty(self.nq_max, B), self.empty(self.nv_max, B), self.empty(self.nq_max, B),
+                self.empty(self.nv_max, B)]
+        wb = lib.sim_jvp_work_bytes(self._h)
+        if work is None:
+            work = torch.empty(wb, dtype=torch.uint8, device=self.device)
+        self._check(lib.sim_step_jvp(self._h, _ptr(q), _ptr(qd), _ptr(tau), _ptr(dq), _ptr(dqd),
+                                     _ptr(dtau), *[_ptr(o) for o in outs], _ptr(work), wb, _stream()),
+                    "sim_step_jvp")
+        return tuple(outs)
 
     def rollout(self, q0, qd0, tau, k=1, ckpt=True, traj=False, out=None):
         """Returns (qT, qdT, ckpt or None, traj or None)."""

@@ -26,7 +26,7 @@ enum JointType : int { J_REVOLUTE = 0, J_FREE = 1 };
 enum Integrator : int { I_SEMI_IMPLICIT = 0, I_EXPLICIT = 1 };
 
 // per-link model parameters, [link][field][system]
-enum : int { P_E = 0, P_R = 9, P_AX = 12, P_M = 15, P_C = 16, P_IC = 19, NPRM = 25 };
+enum : int { P_E = 0, P_R = 9, P_AX = 12, P_M = 15, P_C = 16, P_IC = 19, P_DAMP = 25, NPRM = 26 };
 // per-link forward tape
 enum : int {
   T_E = 0, T_R = 9, T_V = 12, T_C = 18, T_H = 24, T_IA = 30, T_PA = 51, T_U = 57, T_D = 63,
@@ -81,13 +81,15 @@ template <class T> struct Col {
 constexpr int LANES = 32;
 
 // The per-system view used by the step functions (pointers at this system's lane).
-template <class T> struct Sys {
-  const T* prm;     // [maxL][NPRM][LANES] of this tile
+// T is the arithmetic scalar, PT the stored type of the model constants (they
+// differ when T carries derivatives, e.g. a dual number for forward mode).
+template <class T, class PT = T> struct Sys {
+  const PT* prm;    // [maxL][NPRM][LANES] of this tile
   const int* meta;  // [maxL][LANES]
   T* tape;          // [maxL][NTAPE][LANES]
   T* adj;           // [maxL][NADJ][LANES]
   int nl;
-  SD T P(int l, int f) const { return prm[(l * NPRM + f) * LANES]; }
+  SD T P(int l, int f) const { return T(prm[(l * NPRM + f) * LANES]); }
   SD int M(int l) const { return meta[l * LANES]; }
   SD T& tp(int l, int f) const { return tape[(l * NTAPE + f) * LANES]; }
   SD T& ad(int l, int f) const { return adj[(l * NADJ + f) * LANES]; }
@@ -99,41 +101,41 @@ template <class T> struct Sys {
 };
 
 #define ABASIM_FIELD_IO(NAME, ACC)                                                                   \
-  template <class T> SD V3<T> NAME##_v3(const Sys<T>& s, int l, int f) {                              \
+  template <class T, class PT> SD V3<T> NAME##_v3(const Sys<T, PT>& s, int l, int f) {                              \
     return {s.ACC(l, f), s.ACC(l, f + 1), s.ACC(l, f + 2)};                                           \
   }                                                                                                  \
-  template <class T> SD void NAME##_v3(const Sys<T>& s, int l, int f, V3<T> v) {                      \
+  template <class T, class PT> SD void NAME##_v3(const Sys<T, PT>& s, int l, int f, V3<T> v) {                      \
     s.ACC(l, f) = v.x; s.ACC(l, f + 1) = v.y; s.ACC(l, f + 2) = v.z;                                  \
   }                                                                                                  \
-  template <class T> SD SV<T> NAME##_sv(const Sys<T>& s, int l, int f) {                              \
+  template <class T, class PT> SD SV<T> NAME##_sv(const Sys<T, PT>& s, int l, int f) {                              \
     return {NAME##_v3(s, l, f), NAME##_v3(s, l, f + 3)};                                              \
   }                                                                                                  \
-  template <class T> SD void NAME##_sv(const Sys<T>& s, int l, int f, SV<T> v) {                      \
+  template <class T, class PT> SD void NAME##_sv(const Sys<T, PT>& s, int l, int f, SV<T> v) {                      \
     NAME##_v3(s, l, f, v.w); NAME##_v3(s, l, f + 3, v.v);                                             \
   }                                                                                                  \
-  template <class T> SD M3<T> NAME##_m3(const Sys<T>& s, int l, int f) {                              \
+  template <class T, class PT> SD M3<T> NAME##_m3(const Sys<T, PT>& s, int l, int f) {                              \
     M3<T> m; for (int i = 0; i < 9; ++i) m.a[i] = s.ACC(l, f + i); return m;                          \
   }                                                                                                  \
-  template <class T> SD void NAME##_m3(const Sys<T>& s, int l, int f, const M3<T>& m) {               \
+  template <class T, class PT> SD void NAME##_m3(const Sys<T, PT>& s, int l, int f, const M3<T>& m) {               \
     for (int i = 0; i < 9; ++i) s.ACC(l, f + i) = m.a[i];                                             \
   }                                                                                                  \
-  template <class T> SD S3<T> NAME##_s3(const Sys<T>& s, int l, int f) {                              \
+  template <class T, class PT> SD S3<T> NAME##_s3(const Sys<T, PT>& s, int l, int f) {                              \
     return {s.ACC(l, f), s.ACC(l, f + 1), s.ACC(l, f + 2), s.ACC(l, f + 3), s.ACC(l, f + 4), s.ACC(l, f + 5)}; \
   }                                                                                                  \
-  template <class T> SD void NAME##_s3(const Sys<T>& s, int l, int f, const S3<T>& v) {               \
+  template <class T, class PT> SD void NAME##_s3(const Sys<T, PT>& s, int l, int f, const S3<T>& v) {               \
     s.ACC(l, f) = v.xx; s.ACC(l, f + 1) = v.yy; s.ACC(l, f + 2) = v.zz;                               \
     s.ACC(l, f + 3) = v.xy; s.ACC(l, f + 4) = v.xz; s.ACC(l, f + 5) = v.yz;                           \
   }                                                                                                  \
-  template <class T> SD SI<T> NAME##_si(const Sys<T>& s, int l, int f) {                              \
+  template <class T, class PT> SD SI<T> NAME##_si(const Sys<T, PT>& s, int l, int f) {                              \
     return {NAME##_s3(s, l, f), NAME##_m3(s, l, f + 6), NAME##_s3(s, l, f + 15)};                     \
   }                                                                                                  \
-  template <class T> SD void NAME##_si(const Sys<T>& s, int l, int f, const SI<T>& v) {               \
+  template <class T, class PT> SD void NAME##_si(const Sys<T, PT>& s, int l, int f, const SI<T>& v) {               \
     NAME##_s3(s, l, f, v.A); NAME##_m3(s, l, f + 6, v.B); NAME##_s3(s, l, f + 15, v.C);               \
   }                                                                                                  \
-  template <class T> SD XF<T> NAME##_xf(const Sys<T>& s, int l, int f) {                              \
+  template <class T, class PT> SD XF<T> NAME##_xf(const Sys<T, PT>& s, int l, int f) {                              \
     return {NAME##_m3(s, l, f), NAME##_v3(s, l, f + 9)};                                              \
   }                                                                                                  \
-  template <class T> SD void NAME##_xf(const Sys<T>& s, int l, int f, const XF<T>& v) {               \
+  template <class T, class PT> SD void NAME##_xf(const Sys<T, PT>& s, int l, int f, const XF<T>& v) {               \
     NAME##_m3(s, l, f, v.E); NAME##_v3(s, l, f + 9, v.r);                                             \
   }
 
@@ -185,12 +187,12 @@ template <class T> SD SV<T> chol6_solve(const T* L, SV<T> b) {
 // The articulated-inertia solves (D = S^T I^A S, 1/D, U D^-1 U^T, the free root's
 // 6x6 solve) run in the scalar DT: the storage type T, or double in the mixed
 // FP32 + FP64 mode.  1/D is kept on the tape as a hi/lo pair of T words.
-template <class T, class DT> SD void put_di(const Sys<T>& s, int l, DT di) {
+template <class T, class DT, class PT> SD void put_di(const Sys<T, PT>& s, int l, DT di) {
   const T hi = (T)di;
   s.tp(l, T_DI) = hi;
   s.tp(l, T_DI2) = (T)(di - (DT)hi);
 }
-template <class T, class DT> SD DT get_di(const Sys<T>& s, int l) {
+template <class T, class DT, class PT> SD DT get_di(const Sys<T, PT>& s, int l) {
   return (DT)s.tp(l, T_DI) + (DT)s.tp(l, T_DI2);
 }
 template <class DT, class T> SD SI<DT> si_cast(const SI<T>& I) {
@@ -229,8 +231,8 @@ template <class T, class DT> SD SV<T> spd_solve(const SI<T>& IA, SV<T> b) {
 // link and its parent ride in registers when the parent is the previous link (the
 // whole of a serial chain); other parents go through the tape.  Each iteration
 // loads what it needs before it stores anything, so the loads overlap.
-template <class T, class DT, bool ADJ = true>
-SD void aba_forward(const Sys<T>& s, Col<const T> q, Col<const T> qd, Col<const T> tau, V3<T> grav) {
+template <class T, class DT, bool ADJ = true, class PT>
+SD void aba_forward(const Sys<T, PT>& s, Col<const T> q, Col<const T> qd, Col<const T> tau, V3<T> grav) {
   const int nl = s.nl;
   // jcalc + pass 1 (root -> leaves)
   SV<T> v_prev = zeroSV<T>();
@@ -292,7 +294,7 @@ SD void aba_forward(const Sys<T>& s, Col<const T> q, Col<const T> qd, Col<const 
     carry = false;
     if (jt == J_REVOLUTE) {
       const V3<T> a = s.pv3(l, P_AX);
-      const T tl = tau[vo];
+      const T tl = tau[vo] - s.P(l, P_DAMP) * qd[vo];  // viscous damping: joint force -b qd
       SV<T> c = zeroSV<T>();
       XF<T> X;
       if (par >= 0) {
@@ -304,7 +306,7 @@ SD void aba_forward(const Sys<T>& s, Col<const T> q, Col<const T> qd, Col<const 
       const DT Di = DT(1) / D;
       const T u = tl - dot(a, pA.w);
       tp_sv(s, l, T_U, U);
-      put_di<T, DT>(s, l, Di);
+      put_di<T, DT, PT>(s, l, Di);
       s.tp(l, T_u) = u;
       if (par >= 0) {
         const SI<T> Ia = minus_scaled_outer<T, DT>(IA, Di, U);
@@ -346,7 +348,7 @@ SD void aba_forward(const Sys<T>& s, Col<const T> q, Col<const T> qd, Col<const 
       const V3<T> ax = s.pv3(l, P_AX);
       const SV<T> U = tp_sv(s, l, T_U);
       const T u = s.tp(l, T_u);
-      const DT Di = get_di<T, DT>(s, l);
+      const DT Di = get_di<T, DT, PT>(s, l);
       const SV<T> ap = apply(X, apar) + c;
       const T qdd = (T)(((DT)u - (DT)dot(U, ap)) * Di);
       s.tp(l, T_QDD) = qdd;
@@ -367,8 +369,8 @@ SD void aba_forward(const Sys<T>& s, Col<const T> q, Col<const T> qd, Col<const 
 }
 
 // Integrates x -> x' in place from the qdd on the tape.
-template <class T>
-SD void integrate(const Sys<T>& s, Col<T> q, Col<T> qd, T dt, int integ) {
+template <class T, class PT>
+SD void integrate(const Sys<T, PT>& s, Col<T> q, Col<T> qd, T dt, int integ) {
   for (int l = 0; l < s.nl; ++l) {
     const int m = s.M(l);
     const int jt = meta_jtype(m), qo = meta_qoff(m), vo = meta_voff(m);
@@ -405,8 +407,8 @@ SD void integrate(const Sys<T>& s, Col<T> q, Col<T> qd, T dt, int integ) {
 // Integrator adjoint of one link (folded into the pass-3 adjoint loop): turns the
 // adjoint of x^{k+1} held in (gq, gqd) into the direct part of the adjoint of x^k
 // for this link's coordinates and returns the adjoint of its qdd in qddb[0..nv).
-template <class T>
-SD void integrator_adjoint(const Sys<T>& s, int l, int jt, int qo, int vo, Col<const T> q,
+template <class T, class PT>
+SD void integrator_adjoint(const Sys<T, PT>& s, int l, int jt, int qo, int vo, Col<const T> q,
                            Col<const T> qd, Col<T> gq, Col<T> gqd, T dt, int integ, T* qddb) {
   const T half = T(0.5);
   if (jt == J_REVOLUTE) {
@@ -478,8 +480,8 @@ SD void integrator_adjoint(const Sys<T>& s, int l, int jt, int qo, int vo, Col<c
 // Adjoints flowing between a link and its parent ride in registers when the
 // parent is the previous link; accumulators in the adjoint tape serve the other
 // (tree) children and are zeroed first only for links that have such children.
-template <class T, class DT>
-SD void step_adjoint(const Sys<T>& s, Col<const T> q, Col<const T> qd, Col<T> gq, Col<T> gqd,
+template <class T, class DT, class PT>
+SD void step_adjoint(const Sys<T, PT>& s, Col<const T> q, Col<const T> qd, Col<T> gq, Col<T> gqd,
                      Col<T> gtau, Col<T> gm, V3<T> grav, T dt, int integ) {
   const int nl = s.nl;
   const T half = T(0.5);
@@ -510,7 +512,7 @@ SD void step_adjoint(const Sys<T>& s, Col<const T> q, Col<const T> qd, Col<T> gq
         const V3<T> ax = s.pv3(l, P_AX);
         const SV<T> U = tp_sv(s, l, T_U);
         const SV<T> ap = tp_sv(s, l, T_AP);
-        const DT Di = get_di<T, DT>(s, l);
+        const DT Di = get_di<T, DT, PT>(s, l);
         const T qdd = s.tp(l, T_QDD);
         const T qb = qddb[0] + dot(ax, ab.w);
         const T wb = (T)((DT)qb * Di);
@@ -557,7 +559,7 @@ SD void step_adjoint(const Sys<T>& s, Col<const T> q, Col<const T> qd, Col<T> gq
         SV<T> Ub = ad_sv(s, l, G_U);
         T Db = s.ad(l, G_D);
         T ub = s.ad(l, G_u);
-        const DT Di = get_di<T, DT>(s, l);
+        const DT Di = get_di<T, DT, PT>(s, l);
         const T u = s.tp(l, T_u);
         const SV<T> U = tp_sv(s, l, T_U);
         IAb = zeroSI<T>();
@@ -599,8 +601,9 @@ SD void step_adjoint(const Sys<T>& s, Col<const T> q, Col<const T> qd, Col<T> gq
           Ub -= (T)(DT(2) * Di) * IbU;
           Db += (T)(Di * Di * (DT)dot(U, IbU));
         }
-        // u = tau - S^T pA,  D = S^T U,  U = IA S
+        // u = tau - b qd - S^T pA,  D = S^T U,  U = IA S
         gtau[vo] = ub;
+        gqd[vo] -= s.P(l, P_DAMP) * ub;
         pAb.w -= ub * ax;
         Ub.w += Db * ax;
         IAb.A += sym_outer(Ub.w, ax);

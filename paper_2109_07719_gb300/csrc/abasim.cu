@@ -14,6 +14,7 @@
 
 #include "../../include/abasim.h"
 #include "aba_step.cuh"
+#include "dual.cuh"
 
 using namespace abasim;
 
@@ -277,6 +278,49 @@ __global__ void k_backward(DevModel<T> m, const T* __restrict__ ckpt, const T* _
                                           gtau, gm_acc, ring))
 }
 
+// One step with tangents: the state, torque and tape are dual numbers staged in
+// the caller's workspace [tile][...][lane]; model constants stay plain.
+template <class T, class DT>
+__global__ void k_step_jvp(DevModel<T> m, const T* __restrict__ q, const T* __restrict__ qd,
+                           const T* __restrict__ tau, const T* __restrict__ dq,
+                           const T* __restrict__ dqd, const T* __restrict__ dtau, T* q_out,
+                           T* qd_out, T* dq_out, T* dqd_out, Dual<T>* work) {
+  const int slot = blockIdx.x * blockDim.x + threadIdx.x;
+  if (slot >= m.B) return;
+  using D = Dual<T>;
+  using DD = Dual<DT>;
+  const int b = m.sys_of_slot[slot];
+  const long long B = m.B;
+  const int nqm = m.nq_max, nvm = m.nv_max;
+  const long long tile = slot / LANES, lane = slot % LANES;
+  const long long L = m.maxL;
+  const long long per_tile = L * NTAPE + nqm + 2LL * nvm;  // tape, q, qd, tau
+  D* base = work + tile * per_tile * LANES + lane;
+  Sys<D, T> s{m.prm + tile * L * NPRM * LANES + lane, m.meta + tile * L * LANES + lane, base, nullptr,
+              m.nl[slot]};
+  Col<D> xq{base + L * NTAPE * LANES, LANES};
+  Col<D> xqd{base + (L * NTAPE + nqm) * LANES, LANES};
+  Col<D> xt{base + (L * NTAPE + nqm + nvm) * LANES, LANES};
+  for (int d = 0; d < nqm; ++d) xq[d] = D(q[d * B + b], dq ? dq[d * B + b] : T(0));
+  for (int d = 0; d < nvm; ++d) {
+    xqd[d] = D(qd[d * B + b], dqd ? dqd[d * B + b] : T(0));
+    xt[d] = D(tau[d * B + b], dtau ? dtau[d * B + b] : T(0));
+  }
+  const V3<D> g{D(m.g0), D(m.g1), D(m.g2)};
+  static_assert(sizeof(DD) == 2 * sizeof(DT), "dual layout");
+  aba_forward<D, D, false>(s, Col<const D>{xq.p, LANES}, Col<const D>{xqd.p, LANES},
+                           Col<const D>{xt.p, LANES}, g);
+  integrate<D>(s, xq, xqd, D(m.dt), m.integ);
+  for (int d = 0; d < nqm; ++d) {
+    q_out[d * B + b] = xq[d].v;
+    dq_out[d * B + b] = xq[d].d;
+  }
+  for (int d = 0; d < nvm; ++d) {
+    qd_out[d * B + b] = xqd[d].v;
+    dqd_out[d * B + b] = xqd[d].d;
+  }
+}
+
 template <class T>
 __global__ void k_gather_mass_grad(const T* __restrict__ gm_acc, const int* __restrict__ link_slot,
                                    int L, T* gmass) {
@@ -469,6 +513,10 @@ int validate(const sim_model_desc* d, std::string& why) {
       for (int x = 0; x < 6; ++x)
         if (!std::isfinite(Ic[x]) || !std::isfinite(d->com[3 * i + x % 3]))
           return bad("non-finite inertia or COM");
+      if (d->damping && (!(d->damping[i] >= 0) || !std::isfinite(d->damping[i]))) {
+        snprintf(buf, sizeof buf, "system %d link %d: damping must be finite and >= 0", b, l);
+        return bad(buf);
+      }
       if (Ic[0] < 0 || Ic[1] < 0 || Ic[2] < 0) {
         snprintf(buf, sizeof buf, "system %d link %d: negative principal inertia", b, l);
         return bad(buf);
@@ -587,6 +635,7 @@ int sim_create(const sim_model_desc* d, sim_handle** out) {
       }
       P(P_M) = d->mass[i];
       for (int x = 0; x < 6; ++x) P(P_IC + x) = d->I_com[6 * i + x];
+      P(P_DAMP) = (d->damping && jt == SIM_REVOLUTE) ? d->damping[i] : 0.0;
       bool treechild = false;  // a child other than link l + 1
       for (int c = l + 2; c < nl[sl]; ++c)
         if (d->parent[d->sys_link_offset[b] + c] == l) treechild = true;
@@ -717,6 +766,39 @@ int sim_step_batch_static(sim_handle* h, const void* q, const void* qd, const vo
     case SIM_FP32: return launch_step_static<float, float>(h, q, qd, tau, q_out, qd_out, stream);
     default: return launch_step_static<float, double>(h, q, qd, tau, q_out, qd_out, stream);
   }
+}
+
+size_t sim_jvp_work_bytes(const sim_handle* h) {
+  if (!h) return 0;
+  const size_t per_tile = (size_t)h->maxL * NTAPE + h->nq_max + 2 * (size_t)h->nv_max;
+  return per_tile * h->Bpad * 2 * h->scalar;
+}
+
+int sim_step_jvp(sim_handle* h, const void* q, const void* qd, const void* tau, const void* dq,
+                 const void* dqd, const void* dtau, void* q_out, void* qd_out, void* dq_out,
+                 void* dqd_out, void* work, size_t work_bytes, void* stream) {
+  if (!h) return SIM_EINVAL;
+  if (!q || !qd || !tau || !q_out || !qd_out || !dq_out || !dqd_out)
+    return fail(h, SIM_EINVAL, "null state, torque or output pointer");
+  if (!work || work_bytes < sim_jvp_work_bytes(h))
+    return fail(h, SIM_ENOMEM, "workspace smaller than sim_jvp_work_bytes");
+  const int grid = (h->B + h->block - 1) / h->block;
+  switch (h->precision) {
+    case SIM_FP64:
+      k_step_jvp<double, double><<<grid, h->block, 0, S(stream)>>>(
+          dev_model<double>(h), (const double*)q, (const double*)qd, (const double*)tau,
+          (const double*)dq, (const double*)dqd, (const double*)dtau, (double*)q_out,
+          (double*)qd_out, (double*)dq_out, (double*)dqd_out, (Dual<double>*)work);
+      break;
+    default:
+      k_step_jvp<float, float><<<grid, h->block, 0, S(stream)>>>(
+          dev_model<float>(h), (const float*)q, (const float*)qd, (const float*)tau,
+          (const float*)dq, (const float*)dqd, (const float*)dtau, (float*)q_out, (float*)qd_out,
+          (float*)dq_out, (float*)dqd_out, (Dual<float>*)work);
+      break;
+  }
+  cudaError_t e = cudaGetLastError();
+  return e == cudaSuccess ? SIM_OK : cuda_fail(h, e, "jvp launch");
 }
 
 int sim_backward_rollout(sim_handle* h, const void* ckpt, const void* tau, int64_t T, int32_t k,

@@ -40,6 +40,8 @@ def _desc(model, precision=0, integrator=0, **override):
     for k, v in override.items():
         if k in arrs:
             arrs[k] = np.ascontiguousarray(v, arrs[k].dtype)
+        elif k == "damping":
+            arrs[k] = np.ascontiguousarray(v, np.float64)
     d = p._Desc()
     d.n_systems = override.get("n_systems", len(arrs["sys_link_offset"]) - 1)
     d.precision = precision
@@ -83,11 +85,12 @@ def _bad_cases():
         (m, dict(sys_link_offset=off), "links"),
         (m, dict(dt=0.0), "dt"),
         (m, dict(n_systems=0), "n_systems"),
+        (m, dict(damping=-np.ones(m.n_links_total)), "damping"),
         (q, dict(), None),
     ]
 
 
-@pytest.mark.parametrize("case", range(11))
+@pytest.mark.parametrize("case", range(12))
 def test_model_validation(case):
     model, over, needle = _bad_cases()[case]
     d, _keep = _desc(model, **over)

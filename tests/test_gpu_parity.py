@@ -287,3 +287,26 @@ def test_quadratic_replay_gives_same_gradients(cfg, k):
     sim.set_replay("segment")
     for name, x, y in zip(("gq0", "gqd0", "gtau", "gmass"), a, b):
         check(name, y.cpu().numpy(), x.cpu().numpy(), 1e-10)
+
+
+@pytest.mark.parametrize("cfg", [2, 4])
+def test_joint_damping_fp64(cfg):
+    """Viscous joint damping (joint force tau - b qd) forward and adjoint."""
+    B, T = 37, 60
+    work = _work(cfg, B, T)
+    work.model = work.model.with_damping(seed=cfg + 20)
+    sim = _sim(work)
+    (q0, qd0, tau), (hq, hqd, ht) = _inputs(work, sim, T)
+    qT, qdT, ck, _ = sim.rollout(q0, qd0, tau)
+    gqT = torch.ones_like(qT)
+    gqdT = torch.ones_like(qdT)
+    gq0, gqd0, gtau, gm = sim.backward(ck, tau, gqT, gqdT)
+    oq, oqd = oracle_forward(work.model, list(range(B)), hq, hqd, ht)
+    check("qT", qT.cpu().numpy(), oq, 1e-8)
+    check("qdT", qdT.cpu().numpy(), oqd, 1e-8)
+    sel = [0, 17, 36]
+    o = oracle_backward(work.model, sel, hq, hqd, ht, np.ones_like(hq), np.ones_like(hqd))
+    check("gqd0", gqd0.cpu().numpy()[:, sel], o["gqd0"], 1e-6)
+    check("gtau", gtau.cpu().numpy()[:, :, sel], o["gtau"], 1e-6)
+    gmd = mass_grad_of(work.model, gm.cpu().numpy(), sel)
+    check("gmass", np.concatenate([gmd[s] for s in sel]), np.concatenate([o["gm"][s] for s in sel]), 1e-6)

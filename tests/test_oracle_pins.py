@@ -146,6 +146,21 @@ def test_power_balance(cfg):
     assert torch.allclose(rate, power, atol=1e-6 * scale), (rate, power)
 
 
+@pytest.mark.parametrize("cfg", [2, 3])
+def test_damped_power_balance(cfg):
+    """With viscous joint damping b: dE/dt = qd . tau - sum b qd^2."""
+    work = wl.config(cfg, B=3)
+    work.model = work.model.with_damping(seed=cfg)
+    om = _om(work)
+    q, qd, tau = _state(work, om, seed=cfg + 10)
+    if cfg == 3:
+        tau[:, :6] = 0.0
+    rate = _power_balance(om, q, qd, tau)
+    power = (qd * tau).sum(1) - (om.damping * qd * qd).sum(1)
+    assert (om.damping > 0).any()
+    assert torch.allclose(rate, power, atol=1e-6 * (1 + power.abs().max())), (rate, power)
+
+
 @pytest.mark.parametrize("cfg", [3, 5])
 def test_momentum_conservation_rate(cfg):
     """With g = 0 and an unactuated base, joint torques are internal: dh/dt = 0."""
@@ -223,12 +238,15 @@ def _loss_and_grads(om, q0, qd0, tau, wq, wqd, integrator="semi"):
     return phi, g
 
 
-@pytest.mark.parametrize("cfg,T,integrator", [(1, 40, "semi"), (2, 15, "semi"), (3, 10, "semi"),
-                                              (5, 6, "semi"), (2, 10, "explicit")])
-def test_adjoint_matches_central_fd(cfg, T, integrator):
+@pytest.mark.parametrize("cfg,T,integrator,damped", [(1, 40, "semi", False), (2, 15, "semi", False),
+                                                     (3, 10, "semi", False), (5, 6, "semi", False),
+                                                     (2, 10, "explicit", False), (2, 12, "semi", True)])
+def test_adjoint_matches_central_fd(cfg, T, integrator, damped):
     """Gradients w.r.t. q0, qd0, tau and link masses vs central differences along
     random directions (FP64, h = 1e-6: truncation O(h^2))."""
     work = wl.config(cfg, B=2) if cfg != 1 else wl.config(1, B=1)
+    if damped:
+        work.model = work.model.with_damping(seed=4)
     om = _om(work)
     q0, qd0, _ = _state(work, om, seed=3)
     gen = torch.Generator().manual_seed(9)

@@ -18,6 +18,7 @@ links stored CSR by system, each system's links in topological order):
   mass             f64  [L]
   com              f64  [L,3]    centre of mass in the link frame
   I_com            f64  [L,6]    rotational inertia about the COM: xx yy zz xy xz yz
+  damping          f64  [L]      viscous joint damping b (joint force -b qd), or None
 
 State layout (structure of arrays, system index fastest, zero padded to the
 batch maximum): q [nq_max, B], qd [nv_max, B], tau [T, nv_max, B].
@@ -54,6 +55,7 @@ class ModelDesc:
     dt: float
     gravity: np.ndarray
     name: str = ""
+    damping: np.ndarray = None
 
     @property
     def n_systems(self) -> int:
@@ -93,7 +95,16 @@ class ModelDesc:
         return ModelDesc(off, self.parent[idx].copy(), self.joint_type[idx].copy(),
                          self.axis[idx].copy(), self.X_tree[idx].copy(), self.mass[idx].copy(),
                          self.com[idx].copy(), self.I_com[idx].copy(), self.dt,
-                         self.gravity.copy(), self.name + "[subset]")
+                         self.gravity.copy(), self.name + "[subset]",
+                         None if self.damping is None else self.damping[idx].copy())
+
+    def with_damping(self, seed: int, lo: float = 0.05, hi: float = 0.5) -> "ModelDesc":
+        """A copy with viscous damping ~ U(lo, hi) on every revolute joint."""
+        rng = np.random.default_rng(seed)
+        d = rng.uniform(lo, hi, self.n_links_total) * (self.joint_type == REVOLUTE)
+        m = ModelDesc(**{k: getattr(self, k) for k in self.__dataclass_fields__})
+        m.damping = d
+        return m
 
 
 @dataclass
