@@ -97,26 +97,57 @@ template <class T> DevModel<T> dev_model(const sim_handle* h) {
 
 extern __shared__ __align__(16) unsigned char g_smem[];
 
-// With m.smem set, the tapes of the block's tiles live in dynamic shared memory
-// ([tile in block][link][field][lane], tape then adjoint); otherwise in the
-// handle's global scratch.
-template <class T, bool SMEM> __device__ __forceinline__ Sys<T> sys_of(const DevModel<T>& m, int slot) {
-  const long long tile = slot / LANES, lane = slot % LANES;
-  const long long L = m.maxL;
+// Scalars per tile (32 systems) a kernel keeps in dynamic shared memory when it
+// runs with on-chip storage: the tape (and, for the adjoint, its accumulators and
+// the per-link mass-gradient sums), the tile's model constants and its working
+// state (x for the forward rollout, the state adjoint for the backward one).
+__host__ __device__ __forceinline__ long long smem_per_tile(int maxL, int nx, bool bwd) {
+  return (long long)maxL * (NTAPE + NPRM + (bwd ? NADJ + 1 : 0)) + nx;
+}
+
+// On-chip regions of one tile, [tile in block] outermost, lane innermost.
+template <class T> struct SmemTile {
   T* tape;
   T* adj;
+  T* prm;
+  T* state;
+  T* gm;
+};
+
+template <class T, bool BWD> __device__ __forceinline__ SmemTile<T> smem_tile(int maxL, int nx, int lane) {
+  const int tb = threadIdx.x / LANES;
+  const long long L = maxL;
+  T* base = reinterpret_cast<T*>(g_smem) + (long long)tb * smem_per_tile(maxL, nx, BWD) * LANES + lane;
+  SmemTile<T> t;
+  t.tape = base;
+  base += L * NTAPE * LANES;
+  t.adj = base;
+  if (BWD) base += L * NADJ * LANES;
+  t.prm = base;
+  base += L * NPRM * LANES;
+  t.state = base;
+  base += (long long)nx * LANES;
+  t.gm = base;
+  return t;
+}
+
+// With SMEM the tile's tape, constants and working state live in shared memory
+// (the constants are copied in by the caller of sys_of); otherwise the tapes are
+// in the handle's global scratch and the constants are read from global memory.
+template <class T, bool SMEM, bool BWD>
+__device__ __forceinline__ Sys<T> sys_of(const DevModel<T>& m, int slot) {
+  const long long tile = slot / LANES, lane = slot % LANES;
+  const long long L = m.maxL;
+  const T* gprm = m.prm + tile * L * NPRM * LANES + lane;
   if (SMEM) {
-    const int tb = threadIdx.x / LANES;
-    const int tiles = blockDim.x / LANES;
-    T* base = reinterpret_cast<T*>(g_smem);
-    tape = base + (long long)tb * L * NTAPE * LANES + lane;
-    adj = base + (long long)tiles * L * NTAPE * LANES + (long long)tb * L * NADJ * LANES + lane;
-  } else {
-    tape = m.tape + tile * L * NTAPE * LANES + lane;
-    adj = m.adj + tile * L * NADJ * LANES + lane;
+    const SmemTile<T> st = smem_tile<T, BWD>(m.maxL, m.nq_max + m.nv_max, (int)lane);
+    const int nl = m.nl[slot];
+    for (int l = 0; l < nl; ++l)
+      for (int f = 0; f < NPRM; ++f) st.prm[(l * NPRM + f) * LANES] = gprm[(l * NPRM + f) * LANES];
+    return Sys<T>{st.prm, m.meta + tile * L * LANES + lane, st.tape, st.adj, nl};
   }
-  return Sys<T>{m.prm + tile * L * NPRM * LANES + lane, m.meta + tile * L * LANES + lane, tape, adj,
-                m.nl[slot]};
+  return Sys<T>{gprm, m.meta + tile * L * LANES + lane, m.tape + tile * L * NTAPE * LANES + lane,
+                m.adj + tile * L * NADJ * LANES + lane, m.nl[slot]};
 }
 
 template <class T> __device__ __forceinline__ bool finite_t(T x) { return isfinite(x); }
@@ -136,8 +167,13 @@ __device__ __forceinline__ void rollout_one(const DevModel<T>& m, int slot, cons
   const long long B = m.B;
   const int nqm = m.nq_max, nvm = m.nv_max, NX = nqm + nvm;
   const V3<T> g{m.g0, m.g1, m.g2};
-  Sys<T> s = sys_of<T, SMEM>(m, slot);
+  Sys<T> s = sys_of<T, SMEM, false>(m, slot);
   Col<T> q{qT + b, B}, qd{qdT + b, B};
+  if (SMEM) {  // the working state on chip; written to (qT, qdT) at the end
+    T* st = smem_tile<T, false>(m.maxL, NX, slot % LANES).state;
+    q = Col<T>{st, LANES};
+    qd = Col<T>{st + nqm * LANES, LANES};
+  }
   for (int d = 0; d < nqm; ++d) q[d] = q0[d * B + b];
   for (int d = 0; d < nvm; ++d) qd[d] = qd0[d * B + b];
   if (traj) {
@@ -150,7 +186,7 @@ __device__ __forceinline__ void rollout_one(const DevModel<T>& m, int slot, cons
       for (int d = 0; d < nqm; ++d) c[d * B] = q[d];
       for (int d = 0; d < nvm; ++d) c[(nqm + d) * B] = qd[d];
     }
-    aba_forward<T, DT, false>(s, Col<const T>{qT + b, B}, Col<const T>{qdT + b, B},
+    aba_forward<T, DT, false>(s, Col<const T>{q.p, q.B}, Col<const T>{qd.p, qd.B},
                               Col<const T>{tau + t * nvm * B + b, B}, g);
     integrate<T>(s, q, qd, m.dt, m.integ);
     if (traj) {
@@ -163,6 +199,10 @@ __device__ __forceinline__ void rollout_one(const DevModel<T>& m, int slot, cons
   for (int d = 0; d < nqm; ++d) ok &= finite_t(q[d]);
   for (int d = 0; d < nvm; ++d) ok &= finite_t(qd[d]);
   if (!ok) m.status[b] |= 1;
+  if (SMEM) {
+    for (int d = 0; d < nqm; ++d) qT[d * B + b] = q[d];
+    for (int d = 0; d < nvm; ++d) qdT[d * B + b] = qd[d];
+  }
 }
 
 // Adjoint rollout of one system.  (gq0, gqd0) carry the running state adjoint
@@ -178,8 +218,15 @@ __device__ __forceinline__ void backward_one(const DevModel<T>& m, int slot, con
   const int nqm = m.nq_max, nvm = m.nv_max, NX = nqm + nvm;
   const int nq = m.nqv[slot] & 0xffff, nv = m.nqv[slot] >> 16;
   const V3<T> g{m.g0, m.g1, m.g2};
-  Sys<T> s = sys_of<T, SMEM>(m, slot);
+  Sys<T> s = sys_of<T, SMEM, true>(m, slot);
   Col<T> gq{gq0 + b, B}, gqd{gqd0 + b, B};
+  Col<T> gm{gm_acc + slot, B};
+  if (SMEM) {  // state adjoint and mass-gradient sums on chip; written out at the end
+    const SmemTile<T> st = smem_tile<T, true>(m.maxL, NX, slot % LANES);
+    gq = Col<T>{st.state, LANES};
+    gqd = Col<T>{st.state + nqm * LANES, LANES};
+    gm = Col<T>{st.gm, LANES};
+  }
   for (int d = 0; d < nqm; ++d) {
     T v = d < nq ? gqT[d * B + b] : T(0);
     if (gtraj && d < nq) v += gtraj[(Tn * NX + d) * B + b];
@@ -190,8 +237,7 @@ __device__ __forceinline__ void backward_one(const DevModel<T>& m, int slot, con
     if (gtraj && d < nv) v += gtraj[(Tn * NX + nqm + d) * B + b];
     gqd[d] = v;
   }
-  for (int l = 0; l < s.nl; ++l) gm_acc[l * B + slot] = T(0);
-  Col<T> gm{gm_acc + slot, B};
+  for (int l = 0; l < s.nl; ++l) gm[l] = T(0);
   const long long nseg = (Tn + k - 1) / k;
   for (long long seg = nseg - 1; seg >= 0; --seg) {
     const long long t0 = seg * k;
@@ -238,6 +284,11 @@ __device__ __forceinline__ void backward_one(const DevModel<T>& m, int slot, con
   for (int d = 0; d < nv; ++d) ok &= finite_t(gqd[d]);
   for (int l = 0; l < s.nl; ++l) ok &= finite_t(gm[l]);
   if (!ok) m.status[b] |= 1;
+  if (SMEM) {
+    for (int d = 0; d < nqm; ++d) gq0[d * B + b] = gq[d];
+    for (int d = 0; d < nvm; ++d) gqd0[d * B + b] = gqd[d];
+    for (int l = 0; l < s.nl; ++l) gm_acc[l * B + slot] = gm[l];
+  }
 }
 
 // Work distribution.  Grid mode: block i takes work unit i (blockDim slots).
@@ -365,10 +416,11 @@ int launch_shape(sim_handle* h, K kernel, int* grid, int* persistent, size_t shm
 // in auto mode, if the smaller residency it implies adds no wave of blocks over
 // the global-tape kernel.
 template <class T, class KS, class KG>
-int smem_bytes(sim_handle* h, KS kernel_smem, KG kernel_global, int fields, size_t* bytes) {
+int smem_bytes(sim_handle* h, KS kernel_smem, KG kernel_global, bool bwd, size_t* bytes) {
   *bytes = 0;
   if (h->tape_space == SIM_TAPE_GLOBAL) return SIM_OK;
-  const size_t need = (size_t)(h->block / LANES) * h->maxL * fields * LANES * sizeof(T);
+  const size_t need = (size_t)(h->block / LANES) * smem_per_tile(h->maxL, h->nq_max + h->nv_max, bwd) *
+                      LANES * sizeof(T);
   int limit = 0;
   cudaError_t e = cudaDeviceGetAttribute(&limit, cudaDevAttrMaxSharedMemoryPerBlockOptin, h->device);
   if (e != cudaSuccess) return cuda_fail(h, e, "shared-memory limit query");
@@ -399,7 +451,7 @@ int launch_rollout(sim_handle* h, const void* q0, const void* qd0, const void* t
   DevModel<T> m = dev_model<T>(h);
   size_t shm = 0;
   int rc = SIM_OK;
-  if (sizeof(T) == 4) rc = smem_bytes<T>(h, k_rollout<T, DT, true>, k_rollout<T, DT, false>, NTAPE, &shm);
+  if (sizeof(T) == 4) rc = smem_bytes<T>(h, k_rollout<T, DT, true>, k_rollout<T, DT, false>, false, &shm);
   if (rc != SIM_OK) return rc;
   auto kern = shm ? k_rollout<T, DT, true> : k_rollout<T, DT, false>;
   int grid = 0;
@@ -418,7 +470,7 @@ int launch_backward(sim_handle* h, const void* ckpt, const void* tau, int64_t T_
   DevModel<T> m = dev_model<T>(h);
   size_t shm = 0;
   int rc = SIM_OK;
-  if (sizeof(T) == 4) rc = smem_bytes<T>(h, k_backward<T, DT, true>, k_backward<T, DT, false>, NTAPE + NADJ, &shm);
+  if (sizeof(T) == 4) rc = smem_bytes<T>(h, k_backward<T, DT, true>, k_backward<T, DT, false>, true, &shm);
   if (rc != SIM_OK) return rc;
   auto kern = shm ? k_backward<T, DT, true> : k_backward<T, DT, false>;
   int grid = 0;
