@@ -85,12 +85,13 @@ constexpr int LANES = 32;
 // differ when T carries derivatives, e.g. a dual number for forward mode).
 template <class T, class PT = T> struct Sys {
   const PT* prm;    // [maxL][NPRM][LANES] of this tile
-  const int* meta;  // [maxL][LANES]
+  const int* meta;  // [maxL][LANES] (ints spaced mstride apart)
   T* tape;          // [maxL][NTAPE][LANES]
   T* adj;           // [maxL][NADJ][LANES]
   int nl;
+  int mstride = 1;
   SD T P(int l, int f) const { return T(prm[(l * NPRM + f) * LANES]); }
-  SD int M(int l) const { return meta[l * LANES]; }
+  SD int M(int l) const { return meta[l * LANES * mstride]; }
   SD T& tp(int l, int f) const { return tape[(l * NTAPE + f) * LANES]; }
   SD T& ad(int l, int f) const { return adj[(l * NADJ + f) * LANES]; }
 

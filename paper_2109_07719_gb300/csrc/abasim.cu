@@ -99,10 +99,12 @@ extern __shared__ __align__(16) unsigned char g_smem[];
 
 // Scalars per tile (32 systems) a kernel keeps in dynamic shared memory when it
 // runs with on-chip storage: the tape (and, for the adjoint, its accumulators and
-// the per-link mass-gradient sums), the tile's model constants and its working
-// state (x for the forward rollout, the state adjoint for the backward one).
-__host__ __device__ __forceinline__ long long smem_per_tile(int maxL, int nx, bool bwd) {
-  return (long long)maxL * (NTAPE + NPRM + (bwd ? NADJ + 1 : 0)) + nx;
+// the per-link mass-gradient sums), the tile's model constants and meta words,
+// its working state (x for the forward rollout, the state adjoint for the
+// backward one) and a double buffer for the per-step input streams (tau, plus the
+// checkpointed state for the adjoint) fetched one step ahead.
+__host__ __device__ __forceinline__ long long smem_per_tile(int maxL, int nx, int nv, bool bwd) {
+  return (long long)maxL * (NTAPE + NPRM + 1 + (bwd ? NADJ + 1 : 0)) + nx + 2LL * (nv + (bwd ? nx : 0));
 }
 
 // On-chip regions of one tile, [tile in block] outermost, lane innermost.
@@ -110,14 +112,17 @@ template <class T> struct SmemTile {
   T* tape;
   T* adj;
   T* prm;
+  int* meta;
   T* state;
   T* gm;
+  T* stream;
 };
 
-template <class T, bool BWD> __device__ __forceinline__ SmemTile<T> smem_tile(int maxL, int nx, int lane) {
+template <class T, bool BWD>
+__device__ __forceinline__ SmemTile<T> smem_tile(int maxL, int nx, int nv, int lane) {
   const int tb = threadIdx.x / LANES;
   const long long L = maxL;
-  T* base = reinterpret_cast<T*>(g_smem) + (long long)tb * smem_per_tile(maxL, nx, BWD) * LANES + lane;
+  T* base = reinterpret_cast<T*>(g_smem) + (long long)tb * smem_per_tile(maxL, nx, nv, BWD) * LANES + lane;
   SmemTile<T> t;
   t.tape = base;
   base += L * NTAPE * LANES;
@@ -125,29 +130,48 @@ template <class T, bool BWD> __device__ __forceinline__ SmemTile<T> smem_tile(in
   if (BWD) base += L * NADJ * LANES;
   t.prm = base;
   base += L * NPRM * LANES;
+  t.meta = reinterpret_cast<int*>(base);  // one scalar slot per int (T is 4 or 8 bytes)
+  base += L * LANES;
   t.state = base;
   base += (long long)nx * LANES;
   t.gm = base;
+  if (BWD) base += L * LANES;
+  t.stream = base;
   return t;
 }
 
-// With SMEM the tile's tape, constants and working state live in shared memory
-// (the constants are copied in by the caller of sys_of); otherwise the tapes are
-// in the handle's global scratch and the constants are read from global memory.
+// Asynchronous global -> shared copies (cp.async), one element per call.
+template <class T> __device__ __forceinline__ void cp_async(T* smem_dst, const T* gsrc) {
+  const unsigned dst = (unsigned)__cvta_generic_to_shared(smem_dst);
+  if (sizeof(T) == 8)
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(dst), "l"(gsrc) : "memory");
+  else
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(dst), "l"(gsrc) : "memory");
+}
+__device__ __forceinline__ void cp_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+__device__ __forceinline__ void cp_wait_all_but_newest() { asm volatile("cp.async.wait_group 1;\n" ::: "memory"); }
+__device__ __forceinline__ void cp_wait_all() { asm volatile("cp.async.wait_group 0;\n" ::: "memory"); }
+
+// With SMEM the tile's tape, constants, meta words and working state live in
+// shared memory (copied in here); otherwise the tapes are in the handle's global
+// scratch and the constants are read from global memory.
 template <class T, bool SMEM, bool BWD>
 __device__ __forceinline__ Sys<T> sys_of(const DevModel<T>& m, int slot) {
   const long long tile = slot / LANES, lane = slot % LANES;
   const long long L = m.maxL;
   const T* gprm = m.prm + tile * L * NPRM * LANES + lane;
+  const int* gmeta = m.meta + tile * L * LANES + lane;
   if (SMEM) {
-    const SmemTile<T> st = smem_tile<T, BWD>(m.maxL, m.nq_max + m.nv_max, (int)lane);
+    const SmemTile<T> st = smem_tile<T, BWD>(m.maxL, m.nq_max + m.nv_max, m.nv_max, (int)lane);
     const int nl = m.nl[slot];
-    for (int l = 0; l < nl; ++l)
+    for (int l = 0; l < nl; ++l) {
       for (int f = 0; f < NPRM; ++f) st.prm[(l * NPRM + f) * LANES] = gprm[(l * NPRM + f) * LANES];
-    return Sys<T>{st.prm, m.meta + tile * L * LANES + lane, st.tape, st.adj, nl};
+      st.meta[l * LANES * (int)(sizeof(T) / sizeof(int))] = gmeta[l * LANES];
+    }
+    return Sys<T>{st.prm, st.meta, st.tape, st.adj, nl, (int)(sizeof(T) / sizeof(int))};
   }
-  return Sys<T>{gprm, m.meta + tile * L * LANES + lane, m.tape + tile * L * NTAPE * LANES + lane,
-                m.adj + tile * L * NADJ * LANES + lane, m.nl[slot]};
+  return Sys<T>{gprm, gmeta, m.tape + tile * L * NTAPE * LANES + lane,
+                m.adj + tile * L * NADJ * LANES + lane, m.nl[slot], 1};
 }
 
 template <class T> __device__ __forceinline__ bool finite_t(T x) { return isfinite(x); }
@@ -169,10 +193,15 @@ __device__ __forceinline__ void rollout_one(const DevModel<T>& m, int slot, cons
   const V3<T> g{m.g0, m.g1, m.g2};
   Sys<T> s = sys_of<T, SMEM, false>(m, slot);
   Col<T> q{qT + b, B}, qd{qdT + b, B};
+  T* sbuf = nullptr;  // [2][nvm][LANES] double buffer for tau
   if (SMEM) {  // the working state on chip; written to (qT, qdT) at the end
-    T* st = smem_tile<T, false>(m.maxL, NX, slot % LANES).state;
-    q = Col<T>{st, LANES};
-    qd = Col<T>{st + nqm * LANES, LANES};
+    const SmemTile<T> st = smem_tile<T, false>(m.maxL, NX, nvm, slot % LANES);
+    q = Col<T>{st.state, LANES};
+    qd = Col<T>{st.state + nqm * LANES, LANES};
+    sbuf = st.stream;
+    if (Tn > 0)
+      for (int d = 0; d < nvm; ++d) cp_async(sbuf + d * LANES, tau + (long long)d * B + b);
+    cp_commit();
   }
   for (int d = 0; d < nqm; ++d) q[d] = q0[d * B + b];
   for (int d = 0; d < nvm; ++d) qd[d] = qd0[d * B + b];
@@ -186,8 +215,17 @@ __device__ __forceinline__ void rollout_one(const DevModel<T>& m, int slot, cons
       for (int d = 0; d < nqm; ++d) c[d * B] = q[d];
       for (int d = 0; d < nvm; ++d) c[(nqm + d) * B] = qd[d];
     }
-    aba_forward<T, DT, false>(s, Col<const T>{q.p, q.B}, Col<const T>{qd.p, qd.B},
-                              Col<const T>{tau + t * nvm * B + b, B}, g);
+    Col<const T> tau_t{tau + t * nvm * B + b, B};
+    if (SMEM) {  // fetch tau^{t+1} while step t runs
+      if (t + 1 < Tn) {
+        T* nb = sbuf + ((t + 1) & 1) * nvm * LANES;
+        for (int d = 0; d < nvm; ++d) cp_async(nb + d * LANES, tau + ((t + 1) * nvm + d) * B + b);
+      }
+      cp_commit();
+      cp_wait_all_but_newest();
+      tau_t = Col<const T>{sbuf + (t & 1) * nvm * LANES, LANES};
+    }
+    aba_forward<T, DT, false>(s, Col<const T>{q.p, q.B}, Col<const T>{qd.p, qd.B}, tau_t, g);
     integrate<T>(s, q, qd, m.dt, m.integ);
     if (traj) {
       T* c = traj + (t + 1) * NX * B + b;
@@ -195,6 +233,7 @@ __device__ __forceinline__ void rollout_one(const DevModel<T>& m, int slot, cons
       for (int d = 0; d < nvm; ++d) c[(nqm + d) * B] = qd[d];
     }
   }
+  if (SMEM) cp_wait_all();
   bool ok = true;
   for (int d = 0; d < nqm; ++d) ok &= finite_t(q[d]);
   for (int d = 0; d < nvm; ++d) ok &= finite_t(qd[d]);
@@ -221,11 +260,13 @@ __device__ __forceinline__ void backward_one(const DevModel<T>& m, int slot, con
   Sys<T> s = sys_of<T, SMEM, true>(m, slot);
   Col<T> gq{gq0 + b, B}, gqd{gqd0 + b, B};
   Col<T> gm{gm_acc + slot, B};
+  T* sbuf = nullptr;  // [2][NX + nvm][LANES]: checkpointed state and tau, one step ahead
   if (SMEM) {  // state adjoint and mass-gradient sums on chip; written out at the end
-    const SmemTile<T> st = smem_tile<T, true>(m.maxL, NX, slot % LANES);
+    const SmemTile<T> st = smem_tile<T, true>(m.maxL, NX, nvm, slot % LANES);
     gq = Col<T>{st.state, LANES};
     gqd = Col<T>{st.state + nqm * LANES, LANES};
     gm = Col<T>{st.gm, LANES};
+    sbuf = st.stream;
   }
   for (int d = 0; d < nqm; ++d) {
     T v = d < nq ? gqT[d * B + b] : T(0);
@@ -239,36 +280,24 @@ __device__ __forceinline__ void backward_one(const DevModel<T>& m, int slot, con
   }
   for (int l = 0; l < s.nl; ++l) gm[l] = T(0);
   const long long nseg = (Tn + k - 1) / k;
-  for (long long seg = nseg - 1; seg >= 0; --seg) {
-    const long long t0 = seg * k;
-    const long long t1 = (t0 + k < Tn) ? t0 + k : Tn;
-    const T* xs = ckpt + seg * NX * B + b;
-    if (k > 1 && !m.quadratic) {  // replay the segment once, keeping its states (ring by slot)
-      T* r0 = ring + slot;
-      for (int d = 0; d < NX; ++d) r0[d * B] = xs[d * B];
-      for (long long j = 1; j < t1 - t0; ++j) {
-        const T* prev = ring + (j - 1) * NX * B + slot;
-        T* cur = ring + j * NX * B + slot;
-        for (int d = 0; d < NX; ++d) cur[d * B] = prev[d * B];
-        aba_forward<T, DT, false>(s, Col<const T>{cur, B}, Col<const T>{cur + nqm * B, B},
-                       Col<const T>{tau + (t0 + j - 1) * nvm * B + b, B}, g);
-        integrate<T>(s, Col<T>{cur, B}, Col<T>{cur + nqm * B, B}, m.dt, m.integ);
-      }
-    }
-    for (long long t = t1 - 1; t >= t0; --t) {
-      const T* x = (k > 1) ? ring + (t - t0) * NX * B + slot : xs;
-      if (k > 1 && m.quadratic) {  // recompute x^t from the segment checkpoint: t - t0 steps
-        T* cur = ring + slot;
-        x = cur;
-        for (int d = 0; d < NX; ++d) cur[d * B] = xs[d * B];
-        for (long long j = t0; j < t; ++j) {
-          aba_forward<T, DT, false>(s, Col<const T>{cur, B}, Col<const T>{cur + nqm * B, B},
-                                    Col<const T>{tau + j * nvm * B + b, B}, g);
-          integrate<T>(s, Col<T>{cur, B}, Col<T>{cur + nqm * B, B}, m.dt, m.integ);
-        }
-      }
-      Col<const T> q{x, B}, qd{x + nqm * B, B};
-      aba_forward<T, DT, true>(s, q, qd, Col<const T>{tau + t * nvm * B + b, B}, g);
+  if (SMEM && k == 1) {
+    // every step has its own checkpoint: stream x^t and tau^t into shared memory,
+    // fetching step t-1's while step t is differentiated
+    const int W = NX + nvm;
+    auto fetch = [&](long long t, int buf) {
+      T* dst = sbuf + buf * W * LANES;
+      for (int d = 0; d < NX; ++d) cp_async(dst + d * LANES, ckpt + (t * NX + d) * B + b);
+      for (int d = 0; d < nvm; ++d) cp_async(dst + (NX + d) * LANES, tau + (t * nvm + d) * B + b);
+    };
+    if (Tn > 0) fetch(Tn - 1, (int)((Tn - 1) & 1));
+    cp_commit();
+    for (long long t = Tn - 1; t >= 0; --t) {
+      if (t > 0) fetch(t - 1, (int)((t - 1) & 1));
+      cp_commit();
+      cp_wait_all_but_newest();
+      const T* xb = sbuf + (t & 1) * W * LANES;
+      Col<const T> q{xb, LANES}, qd{xb + nqm * LANES, LANES};
+      aba_forward<T, DT, true>(s, q, qd, Col<const T>{xb + NX * LANES, LANES}, g);
       T* gt = gtau + t * nvm * B + b;
       step_adjoint<T, DT>(s, q, qd, gq, gqd, Col<T>{gt, B}, gm, g, m.dt, m.integ);
       for (int d = nv; d < nvm; ++d) gt[d * B] = T(0);
@@ -276,6 +305,48 @@ __device__ __forceinline__ void backward_one(const DevModel<T>& m, int slot, con
         const T* gx = gtraj + t * NX * B + b;
         for (int d = 0; d < nq; ++d) gq[d] += gx[d * B];
         for (int d = 0; d < nv; ++d) gqd[d] += gx[(nqm + d) * B];
+      }
+    }
+    cp_wait_all();
+  } else {
+    for (long long seg = nseg - 1; seg >= 0; --seg) {
+      const long long t0 = seg * k;
+      const long long t1 = (t0 + k < Tn) ? t0 + k : Tn;
+      const T* xs = ckpt + seg * NX * B + b;
+      if (k > 1 && !m.quadratic) {  // replay the segment once, keeping its states (ring by slot)
+        T* r0 = ring + slot;
+        for (int d = 0; d < NX; ++d) r0[d * B] = xs[d * B];
+        for (long long j = 1; j < t1 - t0; ++j) {
+          const T* prev = ring + (j - 1) * NX * B + slot;
+          T* cur = ring + j * NX * B + slot;
+          for (int d = 0; d < NX; ++d) cur[d * B] = prev[d * B];
+          aba_forward<T, DT, false>(s, Col<const T>{cur, B}, Col<const T>{cur + nqm * B, B},
+                         Col<const T>{tau + (t0 + j - 1) * nvm * B + b, B}, g);
+          integrate<T>(s, Col<T>{cur, B}, Col<T>{cur + nqm * B, B}, m.dt, m.integ);
+        }
+      }
+      for (long long t = t1 - 1; t >= t0; --t) {
+        const T* x = (k > 1) ? ring + (t - t0) * NX * B + slot : xs;
+        if (k > 1 && m.quadratic) {  // recompute x^t from the segment checkpoint: t - t0 steps
+          T* cur = ring + slot;
+          x = cur;
+          for (int d = 0; d < NX; ++d) cur[d * B] = xs[d * B];
+          for (long long j = t0; j < t; ++j) {
+            aba_forward<T, DT, false>(s, Col<const T>{cur, B}, Col<const T>{cur + nqm * B, B},
+                                      Col<const T>{tau + j * nvm * B + b, B}, g);
+            integrate<T>(s, Col<T>{cur, B}, Col<T>{cur + nqm * B, B}, m.dt, m.integ);
+          }
+        }
+        Col<const T> q{x, B}, qd{x + nqm * B, B};
+        aba_forward<T, DT, true>(s, q, qd, Col<const T>{tau + t * nvm * B + b, B}, g);
+        T* gt = gtau + t * nvm * B + b;
+        step_adjoint<T, DT>(s, q, qd, gq, gqd, Col<T>{gt, B}, gm, g, m.dt, m.integ);
+        for (int d = nv; d < nvm; ++d) gt[d * B] = T(0);
+        if (gtraj) {
+          const T* gx = gtraj + t * NX * B + b;
+          for (int d = 0; d < nq; ++d) gq[d] += gx[d * B];
+          for (int d = 0; d < nv; ++d) gqd[d] += gx[(nqm + d) * B];
+        }
       }
     }
   }
@@ -419,8 +490,8 @@ template <class T, class KS, class KG>
 int smem_bytes(sim_handle* h, KS kernel_smem, KG kernel_global, bool bwd, size_t* bytes) {
   *bytes = 0;
   if (h->tape_space == SIM_TAPE_GLOBAL) return SIM_OK;
-  const size_t need = (size_t)(h->block / LANES) * smem_per_tile(h->maxL, h->nq_max + h->nv_max, bwd) *
-                      LANES * sizeof(T);
+  const size_t need = (size_t)(h->block / LANES) *
+                      smem_per_tile(h->maxL, h->nq_max + h->nv_max, h->nv_max, bwd) * LANES * sizeof(T);
   int limit = 0;
   cudaError_t e = cudaDeviceGetAttribute(&limit, cudaDevAttrMaxSharedMemoryPerBlockOptin, h->device);
   if (e != cudaSuccess) return cuda_fail(h, e, "shared-memory limit query");
