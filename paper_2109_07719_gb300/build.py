@@ -1,13 +1,15 @@
-"""Build the CUDA library in-tree: ``csrc/abasim.cu`` -> ``_lib/libabasim.so``.
+"""Build the CUDA library in-tree: ``csrc/*.cu`` -> ``_lib/libabasim.so``.
 
-One translation unit, compiled by nvcc for sm_103a only.  Called by
-``__graft_entry__.build()`` and, lazily, by the binding when the library is
-missing or older than its sources.
+Six translation units (the host side of the C ABI and kernel instantiation
+units per precision and direction), compiled by nvcc for sm_103a only, in
+parallel, then linked.  Called by ``__graft_entry__.build()`` and, lazily, by
+the binding when the library is missing or older than its sources.
 """
 from __future__ import annotations
 
 import os
 import subprocess
+from concurrent.futures import ThreadPoolExecutor
 
 HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
@@ -15,11 +17,12 @@ LIBDIR = os.path.join(HERE, "_lib")
 LIB = os.path.join(LIBDIR, "libabasim.so")
 INCLUDE = os.path.join(os.path.dirname(HERE), "include")
 
-SOURCES = ["abasim.cu"]
-DEPS = ["abasim.cu", "aba_step.cuh", "spatial.cuh"]
+SOURCES = ["abasim.cu", "inst_fp32_fwd.cu", "inst_fp32_bwd.cu", "inst_mixed_fwd.cu", "inst_mixed_bwd.cu",
+           "inst_fp64.cu"]
+DEPS = SOURCES + ["aba_step.cuh", "spatial.cuh", "dual.cuh", "kernels.cuh", "handle.h"]
 
 NVCC_FLAGS = ["-gencode", "arch=compute_103a,code=sm_103a", "-lineinfo", "-O3", "-std=c++17",
-              "-Xcompiler", "-fPIC", "-shared", "-diag-suppress", "177"]
+              "-Xcompiler", "-fPIC", "-diag-suppress", "177"]
 
 
 def nvcc() -> str:
@@ -40,13 +43,29 @@ def build(force: bool = False, verbose: bool = False) -> str:
     if not force and not stale():
         return LIB
     os.makedirs(LIBDIR, exist_ok=True)
-    tmp = LIB + f".tmp{os.getpid()}"
-    cmd = [nvcc(), *NVCC_FLAGS, "-I", INCLUDE, "-o", tmp] + [os.path.join(CSRC, s) for s in SOURCES]
-    if verbose:
-        print(" ".join(cmd))
+    tag = f".tmp{os.getpid()}"
+    objs = [os.path.join(LIBDIR, os.path.splitext(src)[0] + tag + ".o") for src in SOURCES]
+
+    def compile_one(src_obj):
+        src, obj = src_obj
+        cmd = [nvcc(), *NVCC_FLAGS, "-I", INCLUDE, "-c", "-o", obj, os.path.join(CSRC, src)]
+        if verbose:
+            print(" ".join(cmd), flush=True)
+        return subprocess.run(cmd, capture_output=True, text=True)
+
+    with ThreadPoolExecutor(max_workers=len(SOURCES)) as pool:
+        results = list(pool.map(compile_one, zip(SOURCES, objs)))
+    for src, r in zip(SOURCES, results):
+        if r.returncode != 0:
+            raise RuntimeError(f"nvcc failed on {src} ({r.returncode}):\n{r.stdout}\n{r.stderr}")
+    tmp = os.path.join(LIBDIR, "libabasim" + tag + ".so")
+    cmd = [nvcc(), "-shared", "-o", tmp, *objs]
     r = subprocess.run(cmd, capture_output=True, text=True)
+    for o in objs:
+        if os.path.exists(o):
+            os.remove(o)
     if r.returncode != 0:
-        raise RuntimeError(f"nvcc failed ({r.returncode}):\n{r.stdout}\n{r.stderr}")
+        raise RuntimeError(f"link failed ({r.returncode}):\n{r.stdout}\n{r.stderr}")
     os.replace(tmp, LIB)
     return LIB
 

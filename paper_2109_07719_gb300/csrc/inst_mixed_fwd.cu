@@ -1,0 +1,14 @@
+// Explicit instantiation of the batched kernels for storage float, D-solves double
+// (forward kernels; the units compile in parallel).
+#include "kernels.cuh"
+
+namespace abasim {
+namespace host {
+
+template int launch_rollout<float, double>(sim_handle*, const void*, const void*, const void*, int64_t, int,
+                                      void*, void*, void*, void*, void*);
+template int launch_step_with_tape<float, double>(sim_handle*, const void*, const void*, const void*, void*,
+                                             void*, void*, void*);
+
+}  // namespace host
+}  // namespace abasim

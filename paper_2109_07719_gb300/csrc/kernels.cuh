@@ -1,0 +1,575 @@
+// Batched rollout / adjoint / JVP kernels and their launch functions (templated;
+// instantiated per precision in inst_*.cu).  Thread i of a launch handles slot i;
+// slots hold the systems sorted by link count (longest first); model constants
+// and tapes are stored by slot in 32-system tiles, the caller's arrays by system.
+#pragma once
+
+#include <algorithm>
+
+#include "dual.cuh"
+#include "handle.h"
+
+namespace abasim {
+namespace host {
+
+template <class T> struct DevModel {
+  const T* prm;
+  const int* meta;
+  const int* nl;
+  const int* nqv;
+  T* tape;
+  T* adj;
+  int* status;
+  const int* sys_of_slot;
+  unsigned* counter;
+  long long B;
+  int maxL;
+  int nq_max, nv_max;
+  T dt;
+  T g0, g1, g2;
+  int integ;
+  int persistent;
+  int smem;
+  int quadratic;
+};
+
+template <class T> DevModel<T> dev_model(const sim_handle* h) {
+  return DevModel<T>{(const T*)h->prm, h->meta, h->nl, h->nqv, (T*)h->tape, (T*)h->adj, h->status,
+                     h->sys_of_slot, h->counter, (long long)h->B, h->maxL, h->nq_max, h->nv_max, (T)h->dt,
+                     (T)h->g[0], (T)h->g[1], (T)h->g[2], h->integrator, 0, 0,
+                     h->replay == SIM_REPLAY_QUADRATIC};
+}
+
+extern __shared__ __align__(16) unsigned char g_smem[];
+
+// Storage modes of the batched kernels: everything per system in global memory
+// (ST_GLOBAL); tape and model constants global but the working state and the
+// prefetched input streams on chip (ST_HYBRID); everything on chip (ST_SMEM).
+enum : int { ST_GLOBAL = 0, ST_HYBRID = 1, ST_SMEM = 2 };
+
+// Scalars per tile (32 systems) a kernel keeps in dynamic shared memory when it
+// runs with on-chip storage: the tape (and, for the adjoint, its accumulators and
+// the per-link mass-gradient sums), the tile's model constants and meta words,
+// its working state (x for the forward rollout, the state adjoint for the
+// backward one) and a double buffer for the per-step input streams (tau, plus the
+// checkpointed state for the adjoint) fetched one step ahead.
+__host__ __device__ __forceinline__ long long smem_per_tile(int maxL, int nx, int nv, bool bwd, int st) {
+  if (st == ST_GLOBAL) return 0;
+  const long long streams = nx + 2LL * (nv + (bwd ? nx : 0)) + (bwd ? maxL : 0);  // state, buffers, gm
+  if (st == ST_HYBRID) return streams;
+  return (long long)maxL * (NTAPE + NPRM + 1 + (bwd ? NADJ : 0)) + streams;
+}
+
+// On-chip regions of one tile, [tile in block] outermost, lane innermost.
+template <class T> struct SmemTile {
+  T* tape;
+  T* adj;
+  T* prm;
+  int* meta;
+  T* state;
+  T* gm;
+  T* stream;
+};
+
+template <class T, bool BWD, int ST>
+__device__ __forceinline__ SmemTile<T> smem_tile(int maxL, int nx, int nv, int lane) {
+  const int tb = threadIdx.x / LANES;
+  const long long L = maxL;
+  T* base = reinterpret_cast<T*>(g_smem) + (long long)tb * smem_per_tile(maxL, nx, nv, BWD, ST) * LANES + lane;
+  SmemTile<T> t{};
+  if (ST == ST_SMEM) {
+    t.tape = base;
+    base += L * NTAPE * LANES;
+    t.adj = base;
+    if (BWD) base += L * NADJ * LANES;
+    t.prm = base;
+    base += L * NPRM * LANES;
+    t.meta = reinterpret_cast<int*>(base);  // one scalar slot per int (T is 4 or 8 bytes)
+    base += L * LANES;
+  }
+  t.state = base;
+  base += (long long)nx * LANES;
+  t.gm = base;
+  if (BWD) base += L * LANES;
+  t.stream = base;
+  return t;
+}
+
+// Asynchronous global -> shared copies (cp.async), one element per call.
+template <class T> __device__ __forceinline__ void cp_async(T* smem_dst, const T* gsrc) {
+  const unsigned dst = (unsigned)__cvta_generic_to_shared(smem_dst);
+  if (sizeof(T) == 8)
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(dst), "l"(gsrc) : "memory");
+  else
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(dst), "l"(gsrc) : "memory");
+}
+__device__ __forceinline__ void cp_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+__device__ __forceinline__ void cp_wait_all_but_newest() { asm volatile("cp.async.wait_group 1;\n" ::: "memory"); }
+__device__ __forceinline__ void cp_wait_all() { asm volatile("cp.async.wait_group 0;\n" ::: "memory"); }
+
+// With SMEM the tile's tape, constants, meta words and working state live in
+// shared memory (copied in here); otherwise the tapes are in the handle's global
+// scratch and the constants are read from global memory.
+template <class T, int ST, bool BWD>
+__device__ __forceinline__ Sys<T> sys_of(const DevModel<T>& m, int slot) {
+  const long long tile = slot / LANES, lane = slot % LANES;
+  const long long L = m.maxL;
+  const T* gprm = m.prm + tile * L * NPRM * LANES + lane;
+  const int* gmeta = m.meta + tile * L * LANES + lane;
+  if (ST == ST_SMEM) {
+    const SmemTile<T> st = smem_tile<T, BWD, ST>(m.maxL, m.nq_max + m.nv_max, m.nv_max, (int)lane);
+    const int nl = m.nl[slot];
+    for (int l = 0; l < nl; ++l) {
+      for (int f = 0; f < NPRM; ++f) st.prm[(l * NPRM + f) * LANES] = gprm[(l * NPRM + f) * LANES];
+      st.meta[l * LANES * (int)(sizeof(T) / sizeof(int))] = gmeta[l * LANES];
+    }
+    return Sys<T>{st.prm, st.meta, st.tape, st.adj, nl, (int)(sizeof(T) / sizeof(int))};
+  }
+  return Sys<T>{gprm, gmeta, m.tape + tile * L * NTAPE * LANES + lane,
+                m.adj + tile * L * NADJ * LANES + lane, m.nl[slot], 1};
+}
+
+template <class T> __device__ __forceinline__ bool finite_t(T x) { return isfinite(x); }
+
+// ------------------------------------------------------------------ kernels
+// Thread i of the launch handles slot i.  Slots hold the systems sorted by link
+// count (longest first) so a warp's systems walk the same number of links; the
+// model constants and tapes are stored by slot, the caller's arrays by system.
+
+// T steps of one system.  The working state lives in (qT, qdT); checkpoints every
+// k steps; optional full trajectory.
+template <class T, class DT, int ST>
+__device__ __forceinline__ void rollout_one(const DevModel<T>& m, int slot, const T* __restrict__ q0,
+                                            const T* __restrict__ qd0, const T* __restrict__ tau,
+                                            long long Tn, int k, T* ckpt, T* qT, T* qdT, T* traj) {
+  const int b = m.sys_of_slot[slot];
+  const long long B = m.B;
+  const int nqm = m.nq_max, nvm = m.nv_max, NX = nqm + nvm;
+  const V3<T> g{m.g0, m.g1, m.g2};
+  constexpr bool SMEM = ST != ST_GLOBAL;  // on-chip state and streams
+  Sys<T> s = sys_of<T, ST, false>(m, slot);
+  Col<T> q{qT + b, B}, qd{qdT + b, B};
+  T* sbuf = nullptr;  // [2][nvm][LANES] double buffer for tau
+  if (SMEM) {  // the working state on chip; written to (qT, qdT) at the end
+    const SmemTile<T> st = smem_tile<T, false, ST>(m.maxL, NX, nvm, slot % LANES);
+    q = Col<T>{st.state, LANES};
+    qd = Col<T>{st.state + nqm * LANES, LANES};
+    sbuf = st.stream;
+    if (Tn > 0)
+      for (int d = 0; d < nvm; ++d) cp_async(sbuf + d * LANES, tau + (long long)d * B + b);
+    cp_commit();
+  }
+  for (int d = 0; d < nqm; ++d) q[d] = q0[d * B + b];
+  for (int d = 0; d < nvm; ++d) qd[d] = qd0[d * B + b];
+  if (traj) {
+    for (int d = 0; d < nqm; ++d) traj[d * B + b] = q[d];
+    for (int d = 0; d < nvm; ++d) traj[(nqm + d) * B + b] = qd[d];
+  }
+  for (long long t = 0; t < Tn; ++t) {
+    if (ckpt && t % k == 0) {
+      T* c = ckpt + (t / k) * NX * B + b;
+      for (int d = 0; d < nqm; ++d) c[d * B] = q[d];
+      for (int d = 0; d < nvm; ++d) c[(nqm + d) * B] = qd[d];
+    }
+    Col<const T> tau_t{tau + t * nvm * B + b, B};
+    if (SMEM) {  // fetch tau^{t+1} while step t runs
+      if (t + 1 < Tn) {
+        T* nb = sbuf + ((t + 1) & 1) * nvm * LANES;
+        for (int d = 0; d < nvm; ++d) cp_async(nb + d * LANES, tau + ((t + 1) * nvm + d) * B + b);
+      }
+      cp_commit();
+      cp_wait_all_but_newest();
+      tau_t = Col<const T>{sbuf + (t & 1) * nvm * LANES, LANES};
+    }
+    aba_forward<T, DT, false>(s, Col<const T>{q.p, q.B}, Col<const T>{qd.p, qd.B}, tau_t, g);
+    integrate<T>(s, q, qd, m.dt, m.integ);
+    if (traj) {
+      T* c = traj + (t + 1) * NX * B + b;
+      for (int d = 0; d < nqm; ++d) c[d * B] = q[d];
+      for (int d = 0; d < nvm; ++d) c[(nqm + d) * B] = qd[d];
+    }
+  }
+  if (SMEM) cp_wait_all();
+  bool ok = true;
+  for (int d = 0; d < nqm; ++d) ok &= finite_t(q[d]);
+  for (int d = 0; d < nvm; ++d) ok &= finite_t(qd[d]);
+  if (!ok) m.status[b] |= 1;
+  if (SMEM) {
+    for (int d = 0; d < nqm; ++d) qT[d * B + b] = q[d];
+    for (int d = 0; d < nvm; ++d) qdT[d * B + b] = qd[d];
+  }
+}
+
+// Adjoint rollout of one system.  (gq0, gqd0) carry the running state adjoint
+// R^t = xbar^t.
+template <class T, class DT, int ST>
+__device__ __forceinline__ void backward_one(const DevModel<T>& m, int slot, const T* __restrict__ ckpt,
+                                             const T* __restrict__ tau, long long Tn, int k,
+                                             const T* __restrict__ gqT, const T* __restrict__ gqdT,
+                                             const T* __restrict__ gtraj, T* gq0, T* gqd0, T* gtau,
+                                             T* gm_acc, T* ring) {
+  const int b = m.sys_of_slot[slot];
+  const long long B = m.B;
+  const int nqm = m.nq_max, nvm = m.nv_max, NX = nqm + nvm;
+  const int nq = m.nqv[slot] & 0xffff, nv = m.nqv[slot] >> 16;
+  const V3<T> g{m.g0, m.g1, m.g2};
+  constexpr bool SMEM = ST != ST_GLOBAL;  // on-chip state and streams
+  Sys<T> s = sys_of<T, ST, true>(m, slot);
+  Col<T> gq{gq0 + b, B}, gqd{gqd0 + b, B};
+  Col<T> gm{gm_acc + slot, B};
+  T* sbuf = nullptr;  // [2][NX + nvm][LANES]: checkpointed state and tau, one step ahead
+  if (SMEM) {  // state adjoint and mass-gradient sums on chip; written out at the end
+    const SmemTile<T> st = smem_tile<T, true, ST>(m.maxL, NX, nvm, slot % LANES);
+    gq = Col<T>{st.state, LANES};
+    gqd = Col<T>{st.state + nqm * LANES, LANES};
+    gm = Col<T>{st.gm, LANES};
+    sbuf = st.stream;
+  }
+  for (int d = 0; d < nqm; ++d) {
+    T v = d < nq ? gqT[d * B + b] : T(0);
+    if (gtraj && d < nq) v += gtraj[(Tn * NX + d) * B + b];
+    gq[d] = v;
+  }
+  for (int d = 0; d < nvm; ++d) {
+    T v = d < nv ? gqdT[d * B + b] : T(0);
+    if (gtraj && d < nv) v += gtraj[(Tn * NX + nqm + d) * B + b];
+    gqd[d] = v;
+  }
+  for (int l = 0; l < s.nl; ++l) gm[l] = T(0);
+  const long long nseg = (Tn + k - 1) / k;
+  if (SMEM && k == 1) {
+    // every step has its own checkpoint: stream x^t and tau^t into shared memory,
+    // fetching step t-1's while step t is differentiated
+    const int W = NX + nvm;
+    auto fetch = [&](long long t, int buf) {
+      T* dst = sbuf + buf * W * LANES;
+      for (int d = 0; d < NX; ++d) cp_async(dst + d * LANES, ckpt + (t * NX + d) * B + b);
+      for (int d = 0; d < nvm; ++d) cp_async(dst + (NX + d) * LANES, tau + (t * nvm + d) * B + b);
+    };
+    if (Tn > 0) fetch(Tn - 1, (int)((Tn - 1) & 1));
+    cp_commit();
+    for (long long t = Tn - 1; t >= 0; --t) {
+      if (t > 0) fetch(t - 1, (int)((t - 1) & 1));
+      cp_commit();
+      cp_wait_all_but_newest();
+      const T* xb = sbuf + (t & 1) * W * LANES;
+      Col<const T> q{xb, LANES}, qd{xb + nqm * LANES, LANES};
+      aba_forward<T, DT, true>(s, q, qd, Col<const T>{xb + NX * LANES, LANES}, g);
+      T* gt = gtau + t * nvm * B + b;
+      step_adjoint<T, DT>(s, q, qd, gq, gqd, Col<T>{gt, B}, gm, g, m.dt, m.integ);
+      for (int d = nv; d < nvm; ++d) gt[d * B] = T(0);
+      if (gtraj) {
+        const T* gx = gtraj + t * NX * B + b;
+        for (int d = 0; d < nq; ++d) gq[d] += gx[d * B];
+        for (int d = 0; d < nv; ++d) gqd[d] += gx[(nqm + d) * B];
+      }
+    }
+    cp_wait_all();
+  } else {
+    for (long long seg = nseg - 1; seg >= 0; --seg) {
+      const long long t0 = seg * k;
+      const long long t1 = (t0 + k < Tn) ? t0 + k : Tn;
+      const T* xs = ckpt + seg * NX * B + b;
+      if (k > 1 && !m.quadratic) {  // replay the segment once, keeping its states (ring by slot)
+        T* r0 = ring + slot;
+        for (int d = 0; d < NX; ++d) r0[d * B] = xs[d * B];
+        for (long long j = 1; j < t1 - t0; ++j) {
+          const T* prev = ring + (j - 1) * NX * B + slot;
+          T* cur = ring + j * NX * B + slot;
+          for (int d = 0; d < NX; ++d) cur[d * B] = prev[d * B];
+          aba_forward<T, DT, false>(s, Col<const T>{cur, B}, Col<const T>{cur + nqm * B, B},
+                         Col<const T>{tau + (t0 + j - 1) * nvm * B + b, B}, g);
+          integrate<T>(s, Col<T>{cur, B}, Col<T>{cur + nqm * B, B}, m.dt, m.integ);
+        }
+      }
+      for (long long t = t1 - 1; t >= t0; --t) {
+        const T* x = (k > 1) ? ring + (t - t0) * NX * B + slot : xs;
+        if (k > 1 && m.quadratic) {  // recompute x^t from the segment checkpoint: t - t0 steps
+          T* cur = ring + slot;
+          x = cur;
+          for (int d = 0; d < NX; ++d) cur[d * B] = xs[d * B];
+          for (long long j = t0; j < t; ++j) {
+            aba_forward<T, DT, false>(s, Col<const T>{cur, B}, Col<const T>{cur + nqm * B, B},
+                                      Col<const T>{tau + j * nvm * B + b, B}, g);
+            integrate<T>(s, Col<T>{cur, B}, Col<T>{cur + nqm * B, B}, m.dt, m.integ);
+          }
+        }
+        Col<const T> q{x, B}, qd{x + nqm * B, B};
+        aba_forward<T, DT, true>(s, q, qd, Col<const T>{tau + t * nvm * B + b, B}, g);
+        T* gt = gtau + t * nvm * B + b;
+        step_adjoint<T, DT>(s, q, qd, gq, gqd, Col<T>{gt, B}, gm, g, m.dt, m.integ);
+        for (int d = nv; d < nvm; ++d) gt[d * B] = T(0);
+        if (gtraj) {
+          const T* gx = gtraj + t * NX * B + b;
+          for (int d = 0; d < nq; ++d) gq[d] += gx[d * B];
+          for (int d = 0; d < nv; ++d) gqd[d] += gx[(nqm + d) * B];
+        }
+      }
+    }
+  }
+  bool ok = true;
+  for (int d = 0; d < nq; ++d) ok &= finite_t(gq[d]);
+  for (int d = 0; d < nv; ++d) ok &= finite_t(gqd[d]);
+  for (int l = 0; l < s.nl; ++l) ok &= finite_t(gm[l]);
+  if (!ok) m.status[b] |= 1;
+  if (SMEM) {
+    for (int d = 0; d < nqm; ++d) gq0[d * B + b] = gq[d];
+    for (int d = 0; d < nvm; ++d) gqd0[d * B + b] = gqd[d];
+    for (int l = 0; l < s.nl; ++l) gm_acc[l * B + slot] = gm[l];
+  }
+}
+
+// Work distribution.  Grid mode: block i takes work unit i (blockDim slots).
+// Persistent mode: a grid sized to the resident capacity, each block taking the
+// next unit from an atomic counter until none is left (the counter is reset by
+// the host before every launch; the loop ends after at most units + 1 tickets).
+__device__ __forceinline__ int next_unit(unsigned* counter) {
+  __shared__ int unit_s;
+  if (threadIdx.x == 0) unit_s = (int)atomicAdd(counter, 1u);
+  __syncthreads();
+  const int unit = unit_s;
+  __syncthreads();
+  return unit;
+}
+
+#define ABASIM_FOR_EACH_SLOT(m, ...)                                         \
+  int unit = (m).persistent ? next_unit((m).counter) : (int)blockIdx.x;      \
+  while ((long long)unit * blockDim.x < (m).B) {                             \
+    const int slot = unit * blockDim.x + threadIdx.x;                        \
+    if (slot < (m).B) { __VA_ARGS__; }                                       \
+    if (!(m).persistent) break;                                              \
+    unit = next_unit((m).counter);                                           \
+  }
+
+template <class T, class DT, int ST>
+__global__ void k_rollout(DevModel<T> m, const T* __restrict__ q0, const T* __restrict__ qd0,
+                          const T* __restrict__ tau, long long Tn, int k, T* ckpt, T* qT, T* qdT,
+                          T* traj) {
+  ABASIM_FOR_EACH_SLOT(m, rollout_one<T, DT, ST>(m, slot, q0, qd0, tau, Tn, k, ckpt, qT, qdT, traj))
+}
+
+template <class T, class DT, int ST>
+__global__ void k_backward(DevModel<T> m, const T* __restrict__ ckpt, const T* __restrict__ tau,
+                           long long Tn, int k, const T* __restrict__ gqT, const T* __restrict__ gqdT,
+                           const T* __restrict__ gtraj, T* gq0, T* gqd0, T* gtau, T* gm_acc,
+                           T* ring) {
+  ABASIM_FOR_EACH_SLOT(m, backward_one<T, DT, ST>(m, slot, ckpt, tau, Tn, k, gqT, gqdT, gtraj, gq0, gqd0,
+                                          gtau, gm_acc, ring))
+}
+
+// One step with tangents: the state, torque and tape are dual numbers staged in
+// the caller's workspace [tile][...][lane]; model constants stay plain.
+template <class T, class DT>
+__global__ void k_step_jvp(DevModel<T> m, const T* __restrict__ q, const T* __restrict__ qd,
+                           const T* __restrict__ tau, const T* __restrict__ dq,
+                           const T* __restrict__ dqd, const T* __restrict__ dtau, T* q_out,
+                           T* qd_out, T* dq_out, T* dqd_out, Dual<T>* work) {
+  const int slot = blockIdx.x * blockDim.x + threadIdx.x;
+  if (slot >= m.B) return;
+  using D = Dual<T>;
+  using DD = Dual<DT>;
+  const int b = m.sys_of_slot[slot];
+  const long long B = m.B;
+  const int nqm = m.nq_max, nvm = m.nv_max;
+  const long long tile = slot / LANES, lane = slot % LANES;
+  const long long L = m.maxL;
+  const long long per_tile = L * NTAPE + nqm + 2LL * nvm;  // tape, q, qd, tau
+  D* base = work + tile * per_tile * LANES + lane;
+  Sys<D, T> s{m.prm + tile * L * NPRM * LANES + lane, m.meta + tile * L * LANES + lane, base, nullptr,
+              m.nl[slot]};
+  Col<D> xq{base + L * NTAPE * LANES, LANES};
+  Col<D> xqd{base + (L * NTAPE + nqm) * LANES, LANES};
+  Col<D> xt{base + (L * NTAPE + nqm + nvm) * LANES, LANES};
+  for (int d = 0; d < nqm; ++d) xq[d] = D(q[d * B + b], dq ? dq[d * B + b] : T(0));
+  for (int d = 0; d < nvm; ++d) {
+    xqd[d] = D(qd[d * B + b], dqd ? dqd[d * B + b] : T(0));
+    xt[d] = D(tau[d * B + b], dtau ? dtau[d * B + b] : T(0));
+  }
+  const V3<D> g{D(m.g0), D(m.g1), D(m.g2)};
+  static_assert(sizeof(DD) == 2 * sizeof(DT), "dual layout");
+  aba_forward<D, D, false>(s, Col<const D>{xq.p, LANES}, Col<const D>{xqd.p, LANES},
+                           Col<const D>{xt.p, LANES}, g);
+  integrate<D>(s, xq, xqd, D(m.dt), m.integ);
+  for (int d = 0; d < nqm; ++d) {
+    q_out[d * B + b] = xq[d].v;
+    dq_out[d * B + b] = xq[d].d;
+  }
+  for (int d = 0; d < nvm; ++d) {
+    qd_out[d * B + b] = xqd[d].v;
+    dqd_out[d * B + b] = xqd[d].d;
+  }
+}
+
+template <class T>
+__global__ void k_gather_mass_grad(const T* __restrict__ gm_acc, const int* __restrict__ link_slot,
+                                   int L, T* gmass) {
+  const int j = blockIdx.x * blockDim.x + threadIdx.x;
+  if (j < L) gmass[j] = gm_acc[link_slot[j]];
+}
+
+template <class T>
+__global__ void k_set_masses(T* prm, const int* __restrict__ link_slot, int L, long long B, int maxL,
+                             const T* __restrict__ mass) {
+  const int j = blockIdx.x * blockDim.x + threadIdx.x;
+  if (j >= L) return;
+  const int ls = link_slot[j];
+  const long long l = ls / B, slot = ls % B;
+  const long long tile = slot / LANES, lane = slot % LANES;
+  prm[((tile * maxL + l) * NPRM + P_M) * LANES + lane] = mass[j];
+}
+
+// ------------------------------------------------------------------ launches
+
+
+// Grid size and mode of a batched launch; resets the ticket of persistent launches.
+template <class K>
+int launch_shape(sim_handle* h, K kernel, int* grid, int* persistent, size_t shm, void* stream) {
+  const int units = (h->B + h->block - 1) / h->block;
+  *grid = units;
+  *persistent = 0;
+  if (h->schedule != SIM_SCHED_PERSISTENT) return SIM_OK;
+  int per_sm = 0;
+  cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, h->block, shm);
+  if (e != cudaSuccess) return cuda_fail(h, e, "occupancy query");
+  const int cap = std::max(1, per_sm) * std::max(1, h->sms);
+  *grid = std::min(units, cap);
+  *persistent = 1;
+  e = cudaMemsetAsync(h->counter, 0, sizeof(unsigned), S(stream));
+  return e == cudaSuccess ? SIM_OK : cuda_fail(h, e, "work ticket reset");
+}
+
+// Storage mode and dynamic shared memory of a launch: the most on-chip mode that
+// fits the per-block opt-in limit and (in auto mode) adds no wave of blocks over
+// the all-global kernel.
+template <class T, class K0, class K1, class K2>
+int choose_storage(sim_handle* h, K0 k_global, K1 k_hybrid, K2 k_smem, bool bwd, int* st, size_t* bytes) {
+  *st = ST_GLOBAL;
+  *bytes = 0;
+  if (h->tape_space == SIM_TAPE_GLOBAL || sizeof(T) != 4) return SIM_OK;
+  int limit = 0;
+  cudaError_t e = cudaDeviceGetAttribute(&limit, cudaDevAttrMaxSharedMemoryPerBlockOptin, h->device);
+  if (e != cudaSuccess) return cuda_fail(h, e, "shared-memory limit query");
+  int per_sm_g = 0;
+  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm_g, k_global, h->block, 0);
+  if (e != cudaSuccess) return cuda_fail(h, e, "occupancy query");
+  const long long units = (h->B + h->block - 1) / h->block;
+  const long long sms = std::max(1, h->sms);
+  auto waves = [&](int per_sm) { return per_sm > 0 ? (units + sms * per_sm - 1) / (sms * per_sm) : 1LL << 40; };
+  const int modes[2] = {ST_SMEM, ST_HYBRID};
+  for (int mode : modes) {
+    const size_t need = (size_t)(h->block / LANES) *
+                        smem_per_tile(h->maxL, h->nq_max + h->nv_max, h->nv_max, bwd, mode) * LANES * sizeof(T);
+    if (need > (size_t)limit) continue;
+    const void* kern = mode == ST_SMEM ? (const void*)k_smem : (const void*)k_hybrid;
+    e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)need);
+    if (e != cudaSuccess) return cuda_fail(h, e, "shared-memory opt-in");
+    int per_sm = 0;
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, h->block, need);
+    if (e != cudaSuccess) return cuda_fail(h, e, "occupancy query");
+    if (h->tape_space == SIM_TAPE_AUTO && waves(per_sm) > waves(per_sm_g)) continue;
+    if (h->tape_space == SIM_TAPE_SHARED && mode != ST_SMEM) break;
+    *st = mode;
+    *bytes = need;
+    return SIM_OK;
+  }
+  if (h->tape_space == SIM_TAPE_SHARED) return fail(h, SIM_EUNSUPPORTED, "tape does not fit in shared memory");
+  return SIM_OK;
+}
+
+template <class T, class DT>
+int launch_rollout(sim_handle* h, const void* q0, const void* qd0, const void* tau, int64_t T_,
+                   int k, void* ckpt, void* qT, void* qdT, void* traj, void* stream) {
+  DevModel<T> m = dev_model<T>(h);
+  size_t shm = 0;
+  int st = ST_GLOBAL;
+  int rc = SIM_OK;
+  auto kern = k_rollout<T, DT, ST_GLOBAL>;
+  if constexpr (sizeof(T) == 4) {  // on-chip modes: FP32 storage only
+    rc = choose_storage<T>(h, k_rollout<T, DT, ST_GLOBAL>, k_rollout<T, DT, ST_HYBRID>,
+                           k_rollout<T, DT, ST_SMEM>, false, &st, &shm);
+    if (st == ST_SMEM) kern = k_rollout<T, DT, ST_SMEM>;
+    if (st == ST_HYBRID) kern = k_rollout<T, DT, ST_HYBRID>;
+  }
+  if (rc != SIM_OK) return rc;
+  h->last_storage = st;
+  int grid = 0;
+  rc = launch_shape(h, kern, &grid, &m.persistent, shm, stream);
+  if (rc != SIM_OK) return rc;
+  kern<<<grid, h->block, shm, S(stream)>>>(m, (const T*)q0, (const T*)qd0, (const T*)tau, (long long)T_,
+                                           k, (T*)ckpt, (T*)qT, (T*)qdT, (T*)traj);
+  cudaError_t e = cudaGetLastError();
+  return e == cudaSuccess ? SIM_OK : cuda_fail(h, e, "rollout launch");
+}
+
+template <class T, class DT>
+int launch_backward(sim_handle* h, const void* ckpt, const void* tau, int64_t T_, int k,
+                    const void* gqT, const void* gqdT, const void* gtraj, void* gq0, void* gqd0,
+                    void* gtau, void* gmass, void* work, void* stream) {
+  DevModel<T> m = dev_model<T>(h);
+  size_t shm = 0;
+  int st = ST_GLOBAL;
+  int rc = SIM_OK;
+  auto kern = k_backward<T, DT, ST_GLOBAL>;
+  if constexpr (sizeof(T) == 4) {  // on-chip modes: FP32 storage only
+    rc = choose_storage<T>(h, k_backward<T, DT, ST_GLOBAL>, k_backward<T, DT, ST_HYBRID>,
+                           k_backward<T, DT, ST_SMEM>, true, &st, &shm);
+    if (st == ST_SMEM) kern = k_backward<T, DT, ST_SMEM>;
+    if (st == ST_HYBRID) kern = k_backward<T, DT, ST_HYBRID>;
+  }
+  if (rc != SIM_OK) return rc;
+  h->last_storage_bwd = st;
+  int grid = 0;
+  rc = launch_shape(h, kern, &grid, &m.persistent, shm, stream);
+  if (rc != SIM_OK) return rc;
+  kern<<<grid, h->block, shm, S(stream)>>>(m, (const T*)ckpt, (const T*)tau, (long long)T_, k,
+                                           (const T*)gqT, (const T*)gqdT, (const T*)gtraj, (T*)gq0,
+                                           (T*)gqd0, (T*)gtau, (T*)h->gm_acc, (T*)work);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return cuda_fail(h, e, "backward launch");
+  if (gmass) {
+    k_gather_mass_grad<T><<<(h->L_total + 255) / 256, 256, 0, S(stream)>>>(
+        (const T*)h->gm_acc, h->link_slot, h->L_total, (T*)gmass);
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return cuda_fail(h, e, "mass-gradient launch");
+  }
+  return SIM_OK;
+}
+
+
+// One step with the per-link tape at `tape`.
+template <class T, class DT>
+int launch_step_with_tape(sim_handle* h, const void* q, const void* qd, const void* tau, void* q_out,
+                          void* qd_out, void* tape, void* stream) {
+  DevModel<T> m = dev_model<T>(h);
+  m.tape = (T*)tape;
+  const int grid = (h->B + h->block - 1) / h->block;
+  k_rollout<T, DT, ST_GLOBAL><<<grid, h->block, 0, S(stream)>>>(m, (const T*)q, (const T*)qd, (const T*)tau,
+                                                                1LL, 1, (T*)nullptr, (T*)q_out, (T*)qd_out,
+                                                                (T*)nullptr);
+  cudaError_t e = cudaGetLastError();
+  return e == cudaSuccess ? SIM_OK : cuda_fail(h, e, "step launch");
+}
+
+template <class T>
+int launch_jvp(sim_handle* h, const void* q, const void* qd, const void* tau, const void* dq,
+               const void* dqd, const void* dtau, void* q_out, void* qd_out, void* dq_out,
+               void* dqd_out, void* work, void* stream) {
+  const int grid = (h->B + h->block - 1) / h->block;
+  k_step_jvp<T, T><<<grid, h->block, 0, S(stream)>>>(
+      dev_model<T>(h), (const T*)q, (const T*)qd, (const T*)tau, (const T*)dq, (const T*)dqd,
+      (const T*)dtau, (T*)q_out, (T*)qd_out, (T*)dq_out, (T*)dqd_out, (Dual<T>*)work);
+  cudaError_t e = cudaGetLastError();
+  return e == cudaSuccess ? SIM_OK : cuda_fail(h, e, "jvp launch");
+}
+
+template <class T>
+int launch_set_masses(sim_handle* h, const void* mass, void* stream) {
+  const int grid = (h->L_total + 255) / 256;
+  k_set_masses<T><<<grid, 256, 0, S(stream)>>>((T*)h->prm, h->link_slot, h->L_total, h->B, h->maxL,
+                                              (const T*)mass);
+  cudaError_t e = cudaGetLastError();
+  return e == cudaSuccess ? SIM_OK : cuda_fail(h, e, "set_masses launch");
+}
+
+}  // namespace host
+}  // namespace abasim
