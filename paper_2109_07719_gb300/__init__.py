@@ -23,7 +23,7 @@ import torch
 
 from . import build as _build
 
-__all__ = ["Simulator", "Rollout", "lib", "SimError", "PRECISIONS"]
+__all__ = ["Simulator", "Rollout", "RolloutTrajectory", "lib", "SimError", "PRECISIONS"]
 
 SIM_OK = 0
 SIM_ENONFINITE = -4
@@ -246,11 +246,11 @@ class Simulator:
         self._arg(dtau, (self.nv_max, B), "dtau")
         outs = [self.empty(self.nq_max, B), self.empty(self.nv_max, B), self.empty(self.nq_max, B),
                 self.empty(self.nv_max, B)]
-        wb = lib.sim_jvp_work_bytes(self._h)
         if work is None:
-            work = torch.empty(wb, dtype=torch.uint8, device=self.device)
+            work = torch.empty(lib.sim_jvp_work_bytes(self._h), dtype=torch.uint8, device=self.device)
+        have = work.numel() * work.element_size()
         self._check(lib.sim_step_jvp(self._h, _ptr(q), _ptr(qd), _ptr(tau), _ptr(dq), _ptr(dqd),
-                                     _ptr(dtau), *[_ptr(o) for o in outs], _ptr(work), wb, _stream()),
+                                     _ptr(dtau), *[_ptr(o) for o in outs], _ptr(work), have, _stream()),
                     "sim_step_jvp")
         return tuple(outs)
 
@@ -289,9 +289,10 @@ class Simulator:
         wb = self.work_bytes(k)
         if wb and work is None:
             work = torch.empty(wb, dtype=torch.uint8, device=self.device)
+        have = 0 if work is None else work.numel() * work.element_size()
         self._check(lib.sim_backward_rollout(
             self._h, _ptr(ckpt), _ptr(tau), T, k, _ptr(gqT), _ptr(gqdT), _ptr(g_traj), _ptr(gq0),
-            _ptr(gqd0), _ptr(gtau), _ptr(gm), _ptr(work), wb, _stream()), "sim_backward_rollout")
+            _ptr(gqd0), _ptr(gtau), _ptr(gm), _ptr(work), have, _stream()), "sim_backward_rollout")
         return gq0, gqd0, gtau, gm
 
     def status(self):
@@ -333,4 +334,36 @@ class Rollout(torch.autograd.Function):
         gqT = torch.zeros(sim.nq_max, sim.B, dtype=sim.dtype, device=sim.device) if gqT is None else gqT.contiguous()
         gqdT = torch.zeros(sim.nv_max, sim.B, dtype=sim.dtype, device=sim.device) if gqdT is None else gqdT.contiguous()
         gq0, gqd0, gtau, gm = sim.backward(ck, tau, gqT, gqdT, k=ctx.k, mass_grad=ctx.has_mass)
+        return None, gq0, gqd0, gtau, gm, None
+
+
+class RolloutTrajectory(torch.autograd.Function):
+    """(q0, qd0, tau, mass) -> every state x^0..x^T as [T+1, nq_max + nv_max, B].
+
+    For objectives over the whole trajectory (per-step costs, Sec. 2: Phi(x, u)):
+    the backward receives dPhi/dx^t for every t and passes it to
+    sim_backward_rollout as per-step seeds (g_traj), so the same one-step
+    recompute adjoint runs once for all terms.
+    """
+
+    @staticmethod
+    def forward(ctx, sim: Simulator, q0, qd0, tau, mass=None, k: int = 1):
+        q0, qd0, tau = q0.contiguous(), qd0.contiguous(), tau.contiguous()
+        if mass is not None:
+            sim.set_masses(mass.detach().contiguous())
+        _, _, ck, traj = sim.rollout(q0, qd0, tau, k=k, ckpt=True, traj=True)
+        ctx.sim, ctx.k, ctx.has_mass = sim, k, mass is not None
+        ctx.save_for_backward(ck, tau, mass.detach() if mass is not None else None)
+        return traj
+
+    @staticmethod
+    def backward(ctx, g_traj):
+        ck, tau, mass = ctx.saved_tensors
+        sim = ctx.sim
+        if mass is not None:
+            sim.set_masses(mass.contiguous())
+        zq = torch.zeros(sim.nq_max, sim.B, dtype=sim.dtype, device=sim.device)
+        zqd = torch.zeros(sim.nv_max, sim.B, dtype=sim.dtype, device=sim.device)
+        gq0, gqd0, gtau, gm = sim.backward(ck, tau, zq, zqd, k=ctx.k, g_traj=g_traj.contiguous(),
+                                           mass_grad=ctx.has_mass)
         return None, gq0, gqd0, gtau, gm, None

@@ -22,7 +22,7 @@ def groups(model, systems):
     return list(g.values())
 
 
-def oracle_forward(model, systems, q0, qd0, tau, integrator="semi"):
+def oracle_forward(model, systems, q0, qd0, tau, integrator="semi", fd="crba"):
     """Final states of the listed systems, padded SoA [nq_max, S], [nv_max, S]."""
     nqm, nvm = q0.shape[0], qd0.shape[0]
     S = len(systems)
@@ -35,14 +35,14 @@ def oracle_forward(model, systems, q0, qd0, tau, integrator="semi"):
         oqd = torch.tensor(qd0[:om.nv, grp].T)
         ot = torch.tensor(tau[:, :om.nv, grp]).permute(0, 2, 1).contiguous()
         with torch.no_grad():
-            a, b, _ = rollout(om, oq, oqd, ot, integrator, keep=False)
+            a, b, _ = rollout(om, oq, oqd, ot, integrator, fd, keep=False)
         for j, s in enumerate(grp):
             qT[:om.nq, col[s]] = a[j].numpy()
             qdT[:om.nv, col[s]] = b[j].numpy()
     return qT, qdT
 
 
-def oracle_backward(model, systems, q0, qd0, tau, gqT, gqdT, integrator="semi"):
+def oracle_backward(model, systems, q0, qd0, tau, gqT, gqdT, integrator="semi", fd="crba"):
     """Gradients of <gqT, q^T> + <gqdT, qd^T> for the listed systems."""
     nqm, nvm = q0.shape[0], qd0.shape[0]
     T = tau.shape[0]
@@ -55,7 +55,7 @@ def oracle_backward(model, systems, q0, qd0, tau, gqT, gqdT, integrator="semi"):
         oqd = torch.tensor(qd0[:om.nv, grp].T)
         ot = torch.tensor(tau[:, :om.nv, grp]).permute(0, 2, 1).contiguous()
         g = rollout_backward(om, oq, oqd, ot, torch.tensor(gqT[:om.nq, grp].T),
-                             torch.tensor(gqdT[:om.nv, grp].T), integrator=integrator)
+                             torch.tensor(gqdT[:om.nv, grp].T), integrator=integrator, fd=fd)
         for j, s in enumerate(grp):
             c = col[s]
             out["gq0"][:om.nq, c] = g[0][j].numpy()

@@ -310,3 +310,67 @@ def test_joint_damping_fp64(cfg):
     check("gtau", gtau.cpu().numpy()[:, :, sel], o["gtau"], 1e-6)
     gmd = mass_grad_of(work.model, gm.cpu().numpy(), sel)
     check("gmass", np.concatenate([gmd[s] for s in sel]), np.concatenate([o["gm"][s] for s in sel]), 1e-6)
+
+
+def test_trajectory_objective_through_autograd():
+    """A per-step cost sum_t |q^t|^2 + |qd^t|^2 through RolloutTrajectory equals
+    the oracle's gradient of the same objective (per-step seeds g_traj)."""
+    from paper_2109_07719_gb300 import RolloutTrajectory
+    B, T = 9, 40
+    work = _work(2, B, T)
+    sim = _sim(work)
+    (q0, qd0, tau), (hq, hqd, ht) = _inputs(work, sim, T)
+    q0.requires_grad_(True)
+    tau.requires_grad_(True)
+    mass = torch.tensor(work.model.mass, device=sim.device, requires_grad=True)
+    traj = RolloutTrajectory.apply(sim, q0, qd0, tau, mass, 1)
+    (traj ** 2).sum().backward()
+    from oracle.dynamics import OracleModel
+    from oracle.rollout import rollout, rollout_backward
+    om = OracleModel(work.model, list(range(B)))
+    oq = torch.tensor(hq[:om.nq].T)
+    oqd = torch.tensor(hqd[:om.nv].T)
+    ot = torch.tensor(ht).permute(0, 2, 1).contiguous()
+    with torch.no_grad():
+        _, _, otraj = rollout(om, oq, oqd, ot)
+    g_traj = [(2 * x[0], 2 * x[1]) for x in otraj]
+    g = rollout_backward(om, oq, oqd, ot, torch.zeros_like(oq), torch.zeros_like(oqd), g_traj=g_traj)
+    check("gq0", q0.grad.cpu().numpy()[:om.nq].T, g[0].numpy(), 1e-6)
+    check("gtau", tau.grad.cpu().numpy().transpose(0, 2, 1), g[2].numpy(), 1e-6)
+    gm = mass.grad.cpu().numpy().reshape(B, om.N)
+    check("gmass", gm, g[3].numpy(), 1e-6)
+
+
+def test_maximum_link_count():
+    """Systems at the 255-link limit (a serial chain), mixed with short ones."""
+    import numpy as np
+    work = wl.config(4, B=34, T=6, dof_lo=250, dof_hi=255, precision="fp64")
+    sim = _sim(work)
+    assert sim.n_links == int(np.diff(work.model.sys_link_offset).sum())
+    (q0, qd0, tau), (hq, hqd, ht) = _inputs(work, sim, 6)
+    qT, qdT, ck, _ = sim.rollout(q0, qd0, tau)
+    gq0, gqd0, gtau, gm = sim.backward(ck, tau, torch.ones_like(qT), torch.zeros_like(qdT))
+    sel = [0, 33]
+    oq, oqd = oracle_forward(work.model, sel, hq, hqd, ht, fd="aba")
+    check("qT", qT.cpu().numpy()[:, sel], oq, 1e-8)
+    check("qdT", qdT.cpu().numpy()[:, sel], oqd, 1e-8)
+    o = oracle_backward(work.model, sel[:1], hq, hqd, ht, np.ones_like(hq), np.zeros_like(hqd), fd="aba")
+    check("gtau", gtau.cpu().numpy()[:, :, sel[:1]], o["gtau"], 1e-6)
+
+
+def test_call_argument_errors_are_reported():
+    from paper_2109_07719_gb300 import SimError, lib
+    work = _work(2, 4, 3)
+    sim = _sim(work)
+    (q0, qd0, tau), _ = _inputs(work, sim, 3)
+    with pytest.raises(SimError):
+        sim.rollout(q0.float(), qd0, tau)                      # wrong dtype
+    with pytest.raises(SimError):
+        sim.step(q0, qd0, tau)                                  # wrong torque shape
+    assert lib.sim_rollout(sim._h, None, None, None, 3, 1, None, None, None, None, None) == -1
+    assert lib.sim_rollout(sim._h, q0.data_ptr(), qd0.data_ptr(), tau.data_ptr(), 3, 0, None,
+                           q0.data_ptr(), qd0.data_ptr(), None, None) == -1      # k < 1
+    assert b"k >= 1" in lib.sim_last_error(sim._h)
+    with pytest.raises(SimError, match="workspace"):
+        qT, qdT, ck, _ = sim.rollout(q0, qd0, tau, k=2)
+        sim.backward(ck, tau, qT, qdT, k=2, work=torch.empty(1, dtype=torch.uint8, device=sim.device))
