@@ -77,6 +77,19 @@ class OracleModel:
             qo += nq
             vo += nv
         self.nq, self.nv = qo, vo
+        # contact spheres (links whose radius is >= 0) and solver parameters
+        ct = getattr(desc, "contact", None)
+        cts = t(ct) if ct is not None else None
+        self.contact_links = [] if cts is None else [i for i in range(n) if float(cts[0, i, 3]) >= 0]
+        for r in range(self.B):
+            if cts is not None and [i for i in range(n) if float(cts[r, i, 3]) >= 0] != self.contact_links:
+                raise ValueError("systems do not share a topology")
+        if self.contact_links:
+            self.contact_p = cts[:, self.contact_links, :3]
+            self.contact_r = cts[:, self.contact_links, 3]
+        self.friction = float(getattr(desc, "friction", 0.8))
+        self.pgs_iterations = int(getattr(desc, "pgs_iterations", 20))
+        self.erp = float(getattr(desc, "erp", 0.2))
         # viscous damping per velocity coordinate (revolute joints only)
         self.damping = torch.zeros(self.B, vo, dtype=f64)
         for i, j in enumerate(self.jtype):

@@ -32,9 +32,15 @@ def qdd_of(model, q, qd, tau, fd="crba", mass=None):
 
 
 def step(model: OracleModel, q, qd, tau, integrator="semi", fd="crba", mass=None):
-    """One time step x^k -> x^{k+1}; joint forces are tau - b qd (viscous damping)."""
+    """One time step x^k -> x^{k+1}; joint forces are tau - b qd (viscous damping);
+    contact impulses (if the model has contact spheres) change the velocity by
+    M^-1 J^T lambda, applied as an extra acceleration over the step."""
     qdd = qdd_of(model, q, qd, tau - model.damping * qd, fd, mass)
     dt = model.dt
+    if model.contact_links:
+        from .contact import contact_velocity_change
+        dv, _ = contact_velocity_change(model, q, qd + dt * qdd, mass)
+        qdd = qdd + dv / dt
     qd_new = qd + dt * qdd
     qv = qd_new if integrator == "semi" else qd
     parts = []

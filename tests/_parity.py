@@ -17,7 +17,8 @@ def groups(model, systems):
     g = defaultdict(list)
     for s in systems:
         r = model.links(s)
-        key = (tuple(model.parent[r.start:r.stop]), tuple(model.joint_type[r.start:r.stop]))
+        ct = () if model.contact is None else tuple(model.contact[r.start:r.stop, 3] >= 0)
+        key = (tuple(model.parent[r.start:r.stop]), tuple(model.joint_type[r.start:r.stop]), ct)
         g[key].append(int(s))
     return list(g.values())
 

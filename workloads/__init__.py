@@ -19,6 +19,10 @@ links stored CSR by system, each system's links in topological order):
   com              f64  [L,3]    centre of mass in the link frame
   I_com            f64  [L,6]    rotational inertia about the COM: xx yy zz xy xz yz
   damping          f64  [L]      viscous joint damping b (joint force -b qd), or None
+  contact          f64  [L,4]    contact sphere of a link against the ground z = 0:
+                                 centre in the link frame (3), radius (< 0: none); or None
+  friction, pgs_iterations, erp  contact solver parameters (Coulomb coefficient,
+                                 Gauss-Seidel sweeps, penetration correction rate)
 
 State layout (structure of arrays, system index fastest, zero padded to the
 batch maximum): q [nq_max, B], qd [nv_max, B], tau [T, nv_max, B].
@@ -56,6 +60,10 @@ class ModelDesc:
     gravity: np.ndarray
     name: str = ""
     damping: np.ndarray = None
+    contact: np.ndarray = None
+    friction: float = 0.8
+    pgs_iterations: int = 20
+    erp: float = 0.2
 
     @property
     def n_systems(self) -> int:
@@ -96,7 +104,9 @@ class ModelDesc:
                          self.axis[idx].copy(), self.X_tree[idx].copy(), self.mass[idx].copy(),
                          self.com[idx].copy(), self.I_com[idx].copy(), self.dt,
                          self.gravity.copy(), self.name + "[subset]",
-                         None if self.damping is None else self.damping[idx].copy())
+                         None if self.damping is None else self.damping[idx].copy(),
+                         None if self.contact is None else self.contact[idx].copy(),
+                         self.friction, self.pgs_iterations, self.erp)
 
     def with_damping(self, seed: int, lo: float = 0.05, hi: float = 0.5) -> "ModelDesc":
         """A copy with viscous damping ~ U(lo, hi) on every revolute joint."""
@@ -239,7 +249,7 @@ def serial_chains(B: int = 4096, T: int = 1000, n: int = 7, seed: int = SEED_BAS
 
 
 def quadruped(B: int = 8192, T: int = 2000, seed: int = SEED_BASE + 3,
-              precision: str = "fp32_d64") -> Workload:
+              precision: str = "fp32_d64", contacts: bool = False) -> Workload:
     """Floating-base quadruped: 10 kg 0.5 x 0.3 x 0.15 m box base on a free joint,
     hips at (+-0.25, +-0.15, 0); each leg hip roll (x), hip pitch (y), knee pitch (y)
     with 0.2 m thigh and calf, leg link masses U(0.5, 1.5), inertia eigenvalues
@@ -268,6 +278,13 @@ def quadruped(B: int = 8192, T: int = 2000, seed: int = SEED_BASE + 3,
     jt = [FREE] + [REVOLUTE] * (nl - 1)
     model = _assemble([nl] * B, par1 * B, jt * B, ax1 * B, r1 * B, mass.reshape(-1),
                       com1 * B, Ic.reshape(-1, 6), 5e-4, (0.0, 0.0, -9.81), "quadruped")
+    if contacts:
+        # 2 cm foot spheres at the ends of the calves (the last link of each leg)
+        ct = np.full((nl, 4), -1.0)
+        for leg in range(4):
+            ct[3 + 3 * leg] = (0.0, 0.0, -0.2, 0.02)
+        model.contact = np.tile(ct, (B, 1))
+        model.name = "quadruped_contact"
     q0, qd0, mask = _state_arrays(model)
     q0[2, :] = 0.5
     q0[6, :] = 1.0
