@@ -42,7 +42,9 @@ class _Desc(ctypes.Structure):
                 ("sys_link_offset", ctypes.c_void_p), ("parent", ctypes.c_void_p),
                 ("joint_type", ctypes.c_void_p), ("axis", ctypes.c_void_p),
                 ("X_tree", ctypes.c_void_p), ("mass", ctypes.c_void_p), ("com", ctypes.c_void_p),
-                ("I_com", ctypes.c_void_p), ("damping", ctypes.c_void_p)]
+                ("I_com", ctypes.c_void_p), ("damping", ctypes.c_void_p),
+                ("contact", ctypes.c_void_p), ("friction", ctypes.c_double), ("erp", ctypes.c_double),
+                ("pgs_iterations", ctypes.c_int32), ("reserved2", ctypes.c_int32)]
 
 
 _P = ctypes.c_void_p
@@ -118,7 +120,12 @@ class Simulator:
             I_com=np.ascontiguousarray(model.I_com, np.float64))
         if getattr(model, "damping", None) is not None:
             keep["damping"] = np.ascontiguousarray(model.damping, np.float64)
+        if getattr(model, "contact", None) is not None:
+            keep["contact"] = np.ascontiguousarray(model.contact, np.float64)
         d = _Desc()
+        d.friction = float(getattr(model, "friction", 0.8))
+        d.erp = float(getattr(model, "erp", 0.2))
+        d.pgs_iterations = int(getattr(model, "pgs_iterations", 20))
         d.n_systems = len(keep["sys_link_offset"]) - 1
         d.precision = PRECISIONS[precision]
         d.integrator = INTEGRATORS[integrator]

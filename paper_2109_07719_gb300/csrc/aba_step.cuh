@@ -25,8 +25,11 @@ namespace abasim {
 enum JointType : int { J_REVOLUTE = 0, J_FREE = 1 };
 enum Integrator : int { I_SEMI_IMPLICIT = 0, I_EXPLICIT = 1 };
 
-// per-link model parameters, [link][field][system]
-enum : int { P_E = 0, P_R = 9, P_AX = 12, P_M = 15, P_C = 16, P_IC = 19, P_DAMP = 25, NPRM = 26 };
+// per-link model parameters, [link][field][system]; P_CP / P_CR: contact sphere
+// centre (link frame) and radius (< 0: the link has none)
+enum : int {
+  P_E = 0, P_R = 9, P_AX = 12, P_M = 15, P_C = 16, P_IC = 19, P_DAMP = 25, P_CP = 26, P_CR = 29, NPRM = 30
+};
 // per-link forward tape
 enum : int {
   T_E = 0, T_R = 9, T_V = 12, T_C = 18, T_H = 24, T_IA = 30, T_PA = 51, T_U = 57, T_D = 63,
@@ -37,6 +40,21 @@ enum : int {
 enum : int {
   G_A = 0, G_C = 6, G_E = 12, G_R = 21, G_U = 24, G_D = 30, G_u = 31, G_IA = 37, G_PA = 58,
   G_V = 64, G_M = 70, NADJ = 71
+};
+
+// per-link contact tape (models with contact spheres only), [link][field][system]:
+// world pose of the link (C_EW rotation world -> link, C_OW origin), link
+// velocities for the velocity after the unconstrained step (C_VS), one unit
+// test pass's articulated bias force, joint force and link acceleration (C_TP,
+// C_TU, C_TA), the contact velocity change per coordinate (C_DV), the adjoint
+// accumulators of a test pass (C_TAB, C_TPB, C_TUB), the adjoint of the
+// unconstrained qdd from the integrator (C_QDDB), and the adjoints the contact
+// solve hands to the step adjoint (B_*: U, 1/D, the free root's articulated
+// inertia, the link transform E and r, world pose, unconstrained qdd and qd).
+enum : int {
+  C_EW = 0, C_OW = 9, C_VS = 12, C_TP = 18, C_TA = 24, C_TU = 30, C_DV = 36, C_TAB = 42, C_TPB = 48,
+  C_TUB = 54, C_QDDB = 60, B_U = 66, B_DI = 72, B_IA = 73, B_E = 94, B_R = 103, B_EW = 106, B_OW = 115,
+  B_VS = 118, B_QDD = 124, B_QD = 130, NCT = 136
 };
 
 // meta word per link: parent+1 (8 bits) | joint type (1) | "has a child other than
@@ -79,6 +97,10 @@ template <class T> struct Col {
 // slots, [tile][link][field][lane], so a warp's 32 systems touch 32 consecutive
 // words and every field offset is a compile-time multiple of LANES.
 constexpr int LANES = 32;
+
+// contact-tape word of link l, field f (ct points at this system's lane)
+template <class T> SD T& ctw(T* ct, int l, int f) { return ct[(l * NCT + f) * LANES]; }
+template <class T> SD T ctr(const T* ct, int l, int f) { return ct[(l * NCT + f) * LANES]; }
 
 // The per-system view used by the step functions (pointers at this system's lane).
 // T is the arithmetic scalar, PT the stored type of the model constants (they
@@ -369,15 +391,17 @@ SD void aba_forward(const Sys<T, PT>& s, Col<const T> q, Col<const T> qd, Col<co
   }
 }
 
-// Integrates x -> x' in place from the qdd on the tape.
+// Integrates x -> x' in place from the qdd on the tape, plus the contact
+// velocity change C_DV of the contact tape ct when given.
 template <class T, class PT>
-SD void integrate(const Sys<T, PT>& s, Col<T> q, Col<T> qd, T dt, int integ) {
+SD void integrate(const Sys<T, PT>& s, Col<T> q, Col<T> qd, T dt, int integ, const T* ct = nullptr) {
   for (int l = 0; l < s.nl; ++l) {
     const int m = s.M(l);
     const int jt = meta_jtype(m), qo = meta_qoff(m), vo = meta_voff(m);
     if (jt == J_REVOLUTE) {
       T v0 = qd[vo];
       T v1 = v0 + dt * s.tp(l, T_QDD);
+      if (ct) v1 += ctr(ct, l, C_DV);
       qd[vo] = v1;
       q[qo] = q[qo] + dt * (integ == I_SEMI_IMPLICIT ? v1 : v0);
     } else {
@@ -385,6 +409,7 @@ SD void integrate(const Sys<T, PT>& s, Col<T> q, Col<T> qd, T dt, int integ) {
       for (int i = 0; i < 6; ++i) {
         T v0 = qd[vo + i];
         T v1 = v0 + dt * s.tp(l, T_QDD + i);
+        if (ct) v1 += ctr(ct, l, C_DV + i);
         qd[vo + i] = v1;
         nu[i] = integ == I_SEMI_IMPLICIT ? v1 : v0;
       }
@@ -410,7 +435,8 @@ SD void integrate(const Sys<T, PT>& s, Col<T> q, Col<T> qd, T dt, int integ) {
 // for this link's coordinates and returns the adjoint of its qdd in qddb[0..nv).
 template <class T, class PT>
 SD void integrator_adjoint(const Sys<T, PT>& s, int l, int jt, int qo, int vo, Col<const T> q,
-                           Col<const T> qd, Col<T> gq, Col<T> gqd, T dt, int integ, T* qddb) {
+                           Col<const T> qd, Col<T> gq, Col<T> gqd, T dt, int integ, T* qddb,
+                           const T* ct = nullptr) {
   const T half = T(0.5);
   if (jt == J_REVOLUTE) {
     const T qb = gq[qo], vb = gqd[vo];
@@ -427,7 +453,9 @@ SD void integrator_adjoint(const Sys<T, PT>& s, int l, int jt, int qo, int vo, C
   T nu[6], nub[6];
   for (int i = 0; i < 6; ++i) {
     const T v0 = qd[vo + i];
-    nu[i] = integ == I_SEMI_IMPLICIT ? v0 + dt * s.tp(l, T_QDD + i) : v0;
+    T v1 = v0 + dt * s.tp(l, T_QDD + i);
+    if (ct) v1 += ctr(ct, l, C_DV + i);
+    nu[i] = integ == I_SEMI_IMPLICIT ? v1 : v0;
     nub[i] = gqd[vo + i];
   }
   const T qt[4] = {q[qo + 3], q[qo + 4], q[qo + 5], q[qo + 6]};
@@ -481,11 +509,20 @@ SD void integrator_adjoint(const Sys<T, PT>& s, int l, int jt, int qo, int vo, C
 // Adjoints flowing between a link and its parent ride in registers when the
 // parent is the previous link; accumulators in the adjoint tape serve the other
 // (tree) children and are zeroed first only for links that have such children.
+// With a contact tape ct, the integrator adjoint has already run (its qdd
+// adjoint is in C_QDDB) and the contact adjoint's B_* terms are added in.
 template <class T, class DT, class PT>
 SD void step_adjoint(const Sys<T, PT>& s, Col<const T> q, Col<const T> qd, Col<T> gq, Col<T> gqd,
-                     Col<T> gtau, Col<T> gm, V3<T> grav, T dt, int integ) {
+                     Col<T> gtau, Col<T> gm, V3<T> grav, T dt, int integ, const T* ct = nullptr) {
   const int nl = s.nl;
   const T half = T(0.5);
+  if (ct) {
+    for (int l = 0; l < nl; ++l) {
+      const int m = s.M(l);
+      const int nvl = meta_jtype(m) == J_REVOLUTE ? 1 : 6;
+      for (int i = 0; i < nvl; ++i) gqd[meta_voff(m) + i] += ctr(ct, l, B_QD + i);
+    }
+  }
   for (int l = 0; l < nl; ++l) {
     if (meta_treechild(s.M(l))) {
       ad_sv(s, l, G_A, zeroSV<T>());
@@ -507,7 +544,11 @@ SD void step_adjoint(const Sys<T, PT>& s, Col<const T> q, Col<const T> qd, Col<T
       if (carry) ab += cab;
       carry = false;
       T qddb[6];
-      integrator_adjoint(s, l, jt, qo, vo, q, qd, gq, gqd, dt, integ, qddb);
+      if (ct) {
+        for (int i = 0; i < 6; ++i) qddb[i] = ctr(ct, l, C_QDDB + i) + ctr(ct, l, B_QDD + i);
+      } else {
+        integrator_adjoint(s, l, jt, qo, vo, q, qd, gq, gqd, dt, integ, qddb);
+      }
       SV<T> apb;
       if (jt == J_REVOLUTE) {
         const V3<T> ax = s.pv3(l, P_AX);
@@ -518,8 +559,15 @@ SD void step_adjoint(const Sys<T, PT>& s, Col<const T> q, Col<const T> qd, Col<T
         const T qb = qddb[0] + dot(ax, ab.w);
         const T wb = (T)((DT)qb * Di);
         apb = ab - wb * U;
-        ad_sv(s, l, G_U, zeroSV<T>() - wb * ap);
-        s.ad(l, G_D) = -wb * qdd;
+        SV<T> Ub = zeroSV<T>() - wb * ap;
+        T Db = -wb * qdd;
+        if (ct) {  // contact solve: U and 1/D adjoints (dD = -D^-2 d(1/D))
+          Ub += SV<T>{{ctr(ct, l, B_U), ctr(ct, l, B_U + 1), ctr(ct, l, B_U + 2)},
+                      {ctr(ct, l, B_U + 3), ctr(ct, l, B_U + 4), ctr(ct, l, B_U + 5)}};
+          Db -= (T)((DT)ctr(ct, l, B_DI) * Di * Di);
+        }
+        ad_sv(s, l, G_U, Ub);
+        s.ad(l, G_D) = Db;
         s.ad(l, G_u) = wb;
       } else {
         const SV<T> qb{{qddb[0], qddb[1], qddb[2]}, {qddb[3], qddb[4], qddb[5]}};
@@ -527,11 +575,25 @@ SD void step_adjoint(const Sys<T, PT>& s, Col<const T> q, Col<const T> qd, Col<T
         const SV<T> ub = spd_solve<T, DT>(tp_si(s, l, T_IA), ab + qb);
         apb = zeroSV<T>() - qb;
         ad_sv(s, l, G_u, ub);
-        ad_si(s, l, G_IA, scale(T(-1), sym_outer(ub, a)));
+        SI<T> IAb = scale(T(-1), sym_outer(ub, a));
+        if (ct) {
+          S3<T> A{ctr(ct, l, B_IA), ctr(ct, l, B_IA + 1), ctr(ct, l, B_IA + 2), ctr(ct, l, B_IA + 3),
+                  ctr(ct, l, B_IA + 4), ctr(ct, l, B_IA + 5)};
+          M3<T> Bm;
+          for (int i = 0; i < 9; ++i) Bm.a[i] = ctr(ct, l, B_IA + 6 + i);
+          S3<T> C{ctr(ct, l, B_IA + 15), ctr(ct, l, B_IA + 16), ctr(ct, l, B_IA + 17), ctr(ct, l, B_IA + 18),
+                  ctr(ct, l, B_IA + 19), ctr(ct, l, B_IA + 20)};
+          IAb += SI<T>{A, Bm, C};
+        }
+        ad_si(s, l, G_IA, IAb);
       }
       ad_sv(s, l, G_C, apb);
       M3<T> Eb = zeroM3<T>();
       V3<T> rb = zero3<T>();
+      if (ct) {
+        for (int i = 0; i < 9; ++i) Eb.a[i] = ctr(ct, l, B_E + i);
+        rb = V3<T>{ctr(ct, l, B_R), ctr(ct, l, B_R + 1), ctr(ct, l, B_R + 2)};
+      }
       SV<T> apar_b = zeroSV<T>();
       apply_adj(X, apar, apb, Eb, rb, par >= 0 ? &apar_b : (SV<T>*)nullptr);
       ad_m3(s, l, G_E, Eb);

@@ -11,6 +11,7 @@
 #include <string>
 #include <vector>
 
+#include "contact.cuh"
 #include "handle.h"
 
 using namespace abasim;
@@ -64,6 +65,7 @@ int validate(const sim_model_desc* d, std::string& why) {
       !d->com || !d->I_com)
     return bad("null model array");
   if (d->sys_link_offset[0] != 0) return bad("sys_link_offset[0] must be 0");
+  bool any_contact = false;
   for (int b = 0; b < d->n_systems; ++b) {
     const int o0 = d->sys_link_offset[b], o1 = d->sys_link_offset[b + 1];
     const int n = o1 - o0;
@@ -72,9 +74,15 @@ int validate(const sim_model_desc* d, std::string& why) {
       snprintf(buf, sizeof buf, "system %d has %d links (1..%d allowed)", b, n, kMaxLinks);
       return bad(buf);
     }
-    int nq = 0, nv = 0;
+    int nq = 0, nv = 0, ncs = 0;
     for (int l = 0; l < n; ++l) {
       const int i = o0 + l;
+      if (d->contact) {
+        const double* c = d->contact + 4 * i;
+        for (int x = 0; x < 4; ++x)
+          if (!std::isfinite(c[x])) return bad("non-finite contact sphere");
+        if (c[3] >= 0) ++ncs;
+      }
       const int p = d->parent[i], jt = d->joint_type[i];
       if (p < -1 || p >= l) {
         snprintf(buf, sizeof buf, "system %d link %d: parent %d not in [-1, %d)", b, l, p, l);
@@ -129,6 +137,18 @@ int validate(const sim_model_desc* d, std::string& why) {
       }
     }
     if (nq > kMaxCoords || nv > kMaxCoords) return bad("too many coordinates in one system");
+    if (ncs > SIM_MAX_CONTACTS) {
+      char buf[160];
+      snprintf(buf, sizeof buf, "system %d has %d contact spheres (at most %d)", b, ncs, SIM_MAX_CONTACTS);
+      return bad(buf);
+    }
+    any_contact |= ncs > 0;
+  }
+  if (any_contact) {
+    if (!(d->friction >= 0) || !std::isfinite(d->friction)) return bad("friction must be finite and >= 0");
+    if (!(d->erp >= 0 && d->erp <= 1)) return bad("erp must be in [0, 1]");
+    if (d->pgs_iterations < 1 || d->pgs_iterations > SIM_MAX_PGS_ITERATIONS)
+      return bad("pgs_iterations must be in [1, SIM_MAX_PGS_ITERATIONS]");
   }
   return SIM_OK;
 }
@@ -217,6 +237,7 @@ int sim_create(const sim_model_desc* d, sim_handle** out) {
   std::vector<int> nl(B), nqv(B);
   std::vector<double> prm((size_t)maxL * NPRM * Bpad, 0.0);
   std::vector<int> meta((size_t)maxL * Bpad, 0), slot(h->L_total);
+  bool any_contact = false;
   for (int sl = 0; sl < B; ++sl) {
     const int b = order[sl];
     nl[sl] = nl_sys[b];
@@ -234,6 +255,9 @@ int sim_create(const sim_model_desc* d, sim_handle** out) {
       P(P_M) = d->mass[i];
       for (int x = 0; x < 6; ++x) P(P_IC + x) = d->I_com[6 * i + x];
       P(P_DAMP) = (d->damping && jt == SIM_REVOLUTE) ? d->damping[i] : 0.0;
+      for (int x = 0; x < 3; ++x) P(P_CP + x) = d->contact ? d->contact[4 * i + x] : 0.0;
+      P(P_CR) = (d->contact && d->contact[4 * i + 3] >= 0) ? d->contact[4 * i + 3] : -1.0;
+      if (d->contact && d->contact[4 * i + 3] >= 0) any_contact = true;
       bool treechild = false;  // a child other than link l + 1
       for (int c = l + 2; c < nl[sl]; ++c)
         if (d->parent[d->sys_link_offset[b] + c] == l) treechild = true;
@@ -271,6 +295,13 @@ int sim_create(const sim_model_desc* d, sim_handle** out) {
   if (rc == SIM_OK) rc = alloc((void**)&h->sys_of_slot, B * sizeof(int), "slot order");
   if (rc == SIM_OK) rc = put(h->sys_of_slot, order.data(), B * sizeof(int));
   if (rc == SIM_OK) rc = alloc((void**)&h->counter, sizeof(unsigned), "work ticket");
+  if (any_contact) {
+    h->friction = d->friction;
+    h->erp = d->erp;
+    h->pgs_iterations = d->pgs_iterations;
+    if (rc == SIM_OK) rc = alloc(&h->ctape, (size_t)maxL * NCT * Bpad * h->scalar, "contact tape");
+    if (rc == SIM_OK) rc = alloc(&h->csys, (size_t)NCS * Bpad * h->scalar, "contact record");
+  }
   if (rc == SIM_OK) {
     cudaError_t e = cudaMemset(h->status, 0, B * sizeof(int));
     if (e != cudaSuccess) rc = cuda_fail(h, e, "status init");
@@ -287,7 +318,7 @@ int sim_create(const sim_model_desc* d, sim_handle** out) {
 void sim_destroy(sim_handle* h) {
   if (!h) return;
   void* ptrs[] = {h->prm, h->meta, h->nl, h->nqv, h->tape, h->adj, h->gm_acc, h->link_slot,
-                  h->status, h->sys_of_slot, h->counter};
+                  h->status, h->sys_of_slot, h->counter, h->ctape, h->csys};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   delete h;
@@ -372,6 +403,7 @@ int sim_step_jvp(sim_handle* h, const void* q, const void* qd, const void* tau, 
     return fail(h, SIM_EINVAL, "null state, torque or output pointer");
   if (!work || work_bytes < sim_jvp_work_bytes(h))
     return fail(h, SIM_ENOMEM, "workspace smaller than sim_jvp_work_bytes");
+  if (h->ctape) return fail(h, SIM_EUNSUPPORTED, "forward-mode step of a model with contact spheres");
   return is_fp64(h) ? launch_jvp<double>(h, q, qd, tau, dq, dqd, dtau, q_out, qd_out, dq_out, dqd_out, work, stream)
                     : launch_jvp<float>(h, q, qd, tau, dq, dqd, dtau, q_out, qd_out, dq_out, dqd_out, work, stream);
 }

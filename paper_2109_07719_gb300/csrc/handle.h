@@ -35,6 +35,10 @@ struct sim_handle {
   int* status = nullptr;     // [B] by system
   int* sys_of_slot = nullptr;  // [B]
   unsigned* counter = nullptr;  // work-unit ticket of persistent launches
+  void* ctape = nullptr;     // [maxL][NCT][B] scalar, models with contact spheres only
+  void* csys = nullptr;      // [NCS][B] scalar, models with contact spheres only
+  double friction = 0.8, erp = 0.2;
+  int pgs_iterations = 20;
   int schedule = SIM_SCHED_GRID;
   int tape_space = SIM_TAPE_AUTO;
   int replay = SIM_REPLAY_SEGMENT;

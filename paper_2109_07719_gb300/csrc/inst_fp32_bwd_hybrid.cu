@@ -1,0 +1,15 @@
+// Explicit instantiation of the adjoint kernel for storage float, D-solves float,
+// tape in global memory, state and input streams on chip (the units compile in parallel).
+#include "kernels.cuh"
+
+namespace abasim {
+namespace host {
+
+template <class T, class DT, int ST>
+BackwardKernel<T> backward_kernel() {
+  return k_backward<T, DT, ST>;
+}
+template BackwardKernel<float> backward_kernel<float, float, ST_HYBRID>();
+
+}  // namespace host
+}  // namespace abasim

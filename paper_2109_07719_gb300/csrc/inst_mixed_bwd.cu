@@ -1,9 +1,15 @@
-// Explicit instantiation of the batched kernels for storage float, D-solves double
-// (adjoint kernels; the units compile in parallel).
+// Explicit instantiation of the adjoint kernel for storage float, D-solves double,
+// tape in global memory, and its launcher (the units compile in parallel).
 #include "kernels.cuh"
 
 namespace abasim {
 namespace host {
+
+template <class T, class DT, int ST>
+BackwardKernel<T> backward_kernel() {
+  return k_backward<T, DT, ST>;
+}
+template BackwardKernel<float> backward_kernel<float, double, ST_GLOBAL>();
 
 template int launch_backward<float, double>(sim_handle*, const void*, const void*, int64_t, int, const void*,
                                        const void*, const void*, void*, void*, void*, void*, void*, void*);

@@ -6,6 +6,7 @@
 
 #include <algorithm>
 
+#include "contact.cuh"
 #include "dual.cuh"
 #include "handle.h"
 
@@ -31,13 +32,17 @@ template <class T> struct DevModel {
   int persistent;
   int smem;
   int quadratic;
+  T* ctape;  // per-link contact tape [tile][maxL][NCT][lane] (null: no contact spheres)
+  T* csys;   // per-system contact record [tile][NCS][lane]
+  ContactParams<T> cp;
 };
 
 template <class T> DevModel<T> dev_model(const sim_handle* h) {
   return DevModel<T>{(const T*)h->prm, h->meta, h->nl, h->nqv, (T*)h->tape, (T*)h->adj, h->status,
                      h->sys_of_slot, h->counter, (long long)h->B, h->maxL, h->nq_max, h->nv_max, (T)h->dt,
                      (T)h->g[0], (T)h->g[1], (T)h->g[2], h->integrator, 0, 0,
-                     h->replay == SIM_REPLAY_QUADRATIC};
+                     h->replay == SIM_REPLAY_QUADRATIC, (T*)h->ctape, (T*)h->csys,
+                     ContactParams<T>{(T)h->friction, (T)h->erp, h->pgs_iterations}};
 }
 
 extern __shared__ __align__(16) unsigned char g_smem[];
@@ -131,6 +136,54 @@ __device__ __forceinline__ Sys<T> sys_of(const DevModel<T>& m, int slot) {
 
 template <class T> __device__ __forceinline__ bool finite_t(T x) { return isfinite(x); }
 
+template <class T> __device__ __forceinline__ CView<T> cview_of(const DevModel<T>& m, int slot) {
+  const long long tile = slot / LANES, lane = slot % LANES;
+  return CView<T>{m.ctape + tile * m.maxL * NCT * LANES + lane, m.csys + tile * NCS * LANES + lane};
+}
+
+// One step x -> x' in place: ABA, the contact impulses (CT: the model has
+// contact spheres), integration.
+template <class T, class DT, bool CT>
+__device__ __forceinline__ void forward_step(const DevModel<T>& m, const Sys<T>& s, int slot, Col<T> q,
+                                             Col<T> qd, Col<const T> tau_t, V3<T> g) {
+  aba_forward<T, DT, false>(s, Col<const T>{q.p, q.B}, Col<const T>{qd.p, qd.B}, tau_t, g);
+  if constexpr (CT) {
+    const CView<T> cv = cview_of(m, slot);
+    const int nc = contact_forward<T, DT, T>(s, cv, Col<const T>{qd.p, qd.B}, m.dt, m.cp);
+    integrate<T>(s, q, qd, m.dt, m.integ, nc > 0 ? (const T*)cv.ct : nullptr);
+  } else {
+    integrate<T>(s, q, qd, m.dt, m.integ);
+  }
+}
+
+// Recomputes the step from x^t and pulls the state adjoint (gq, gqd) back
+// through it.  With active contacts the integrator adjoint runs first for every
+// link (the contact adjoint needs all of qdd's adjoint), then the contact
+// adjoint, then the ABA adjoint with the contact terms added.
+template <class T, class DT, bool CT>
+__device__ __forceinline__ void adjoint_step(const DevModel<T>& m, const Sys<T>& s, int slot, Col<const T> q,
+                                             Col<const T> qd, Col<const T> tau_t, Col<T> gq, Col<T> gqd,
+                                             Col<T> gt, Col<T> gm, V3<T> g) {
+  aba_forward<T, DT, true>(s, q, qd, tau_t, g);
+  if constexpr (CT) {
+    const CView<T> cv = cview_of(m, slot);
+    const int nc = contact_forward<T, DT, T>(s, cv, qd, m.dt, m.cp);
+    if (nc > 0) {
+      for (int l = 0; l < s.nl; ++l) {
+        const int mt = s.M(l);
+        T qb[6] = {0, 0, 0, 0, 0, 0};
+        integrator_adjoint(s, l, meta_jtype(mt), meta_qoff(mt), meta_voff(mt), q, qd, gq, gqd, m.dt, m.integ,
+                           qb, (const T*)cv.ct);
+        for (int i = 0; i < 6; ++i) cv.L(l, C_QDDB + i) = qb[i];
+      }
+      contact_adjoint<T, DT, T>(s, cv, m.dt, m.cp);
+      step_adjoint<T, DT>(s, q, qd, gq, gqd, gt, gm, g, m.dt, m.integ, (const T*)cv.ct);
+      return;
+    }
+  }
+  step_adjoint<T, DT>(s, q, qd, gq, gqd, gt, gm, g, m.dt, m.integ);
+}
+
 // ------------------------------------------------------------------ kernels
 // Thread i of the launch handles slot i.  Slots hold the systems sorted by link
 // count (longest first) so a warp's systems walk the same number of links; the
@@ -138,7 +191,7 @@ template <class T> __device__ __forceinline__ bool finite_t(T x) { return isfini
 
 // T steps of one system.  The working state lives in (qT, qdT); checkpoints every
 // k steps; optional full trajectory.
-template <class T, class DT, int ST>
+template <class T, class DT, int ST, bool CT>
 __device__ __forceinline__ void rollout_one(const DevModel<T>& m, int slot, const T* __restrict__ q0,
                                             const T* __restrict__ qd0, const T* __restrict__ tau,
                                             long long Tn, int k, T* ckpt, T* qT, T* qdT, T* traj) {
@@ -181,8 +234,7 @@ __device__ __forceinline__ void rollout_one(const DevModel<T>& m, int slot, cons
       cp_wait_all_but_newest();
       tau_t = Col<const T>{sbuf + (t & 1) * nvm * LANES, LANES};
     }
-    aba_forward<T, DT, false>(s, Col<const T>{q.p, q.B}, Col<const T>{qd.p, qd.B}, tau_t, g);
-    integrate<T>(s, q, qd, m.dt, m.integ);
+    forward_step<T, DT, CT>(m, s, slot, q, qd, tau_t, g);
     if (traj) {
       T* c = traj + (t + 1) * NX * B + b;
       for (int d = 0; d < nqm; ++d) c[d * B] = q[d];
@@ -202,7 +254,7 @@ __device__ __forceinline__ void rollout_one(const DevModel<T>& m, int slot, cons
 
 // Adjoint rollout of one system.  (gq0, gqd0) carry the running state adjoint
 // R^t = xbar^t.
-template <class T, class DT, int ST>
+template <class T, class DT, int ST, bool CT>
 __device__ __forceinline__ void backward_one(const DevModel<T>& m, int slot, const T* __restrict__ ckpt,
                                              const T* __restrict__ tau, long long Tn, int k,
                                              const T* __restrict__ gqT, const T* __restrict__ gqdT,
@@ -254,9 +306,8 @@ __device__ __forceinline__ void backward_one(const DevModel<T>& m, int slot, con
       cp_wait_all_but_newest();
       const T* xb = sbuf + (t & 1) * W * LANES;
       Col<const T> q{xb, LANES}, qd{xb + nqm * LANES, LANES};
-      aba_forward<T, DT, true>(s, q, qd, Col<const T>{xb + NX * LANES, LANES}, g);
       T* gt = gtau + t * nvm * B + b;
-      step_adjoint<T, DT>(s, q, qd, gq, gqd, Col<T>{gt, B}, gm, g, m.dt, m.integ);
+      adjoint_step<T, DT, CT>(m, s, slot, q, qd, Col<const T>{xb + NX * LANES, LANES}, gq, gqd, Col<T>{gt, B}, gm, g);
       for (int d = nv; d < nvm; ++d) gt[d * B] = T(0);
       if (gtraj) {
         const T* gx = gtraj + t * NX * B + b;
@@ -277,9 +328,8 @@ __device__ __forceinline__ void backward_one(const DevModel<T>& m, int slot, con
           const T* prev = ring + (j - 1) * NX * B + slot;
           T* cur = ring + j * NX * B + slot;
           for (int d = 0; d < NX; ++d) cur[d * B] = prev[d * B];
-          aba_forward<T, DT, false>(s, Col<const T>{cur, B}, Col<const T>{cur + nqm * B, B},
-                         Col<const T>{tau + (t0 + j - 1) * nvm * B + b, B}, g);
-          integrate<T>(s, Col<T>{cur, B}, Col<T>{cur + nqm * B, B}, m.dt, m.integ);
+          forward_step<T, DT, CT>(m, s, slot, Col<T>{cur, B}, Col<T>{cur + nqm * B, B},
+                              Col<const T>{tau + (t0 + j - 1) * nvm * B + b, B}, g);
         }
       }
       for (long long t = t1 - 1; t >= t0; --t) {
@@ -289,15 +339,14 @@ __device__ __forceinline__ void backward_one(const DevModel<T>& m, int slot, con
           x = cur;
           for (int d = 0; d < NX; ++d) cur[d * B] = xs[d * B];
           for (long long j = t0; j < t; ++j) {
-            aba_forward<T, DT, false>(s, Col<const T>{cur, B}, Col<const T>{cur + nqm * B, B},
-                                      Col<const T>{tau + j * nvm * B + b, B}, g);
-            integrate<T>(s, Col<T>{cur, B}, Col<T>{cur + nqm * B, B}, m.dt, m.integ);
+            forward_step<T, DT, CT>(m, s, slot, Col<T>{cur, B}, Col<T>{cur + nqm * B, B},
+                                Col<const T>{tau + j * nvm * B + b, B}, g);
           }
         }
         Col<const T> q{x, B}, qd{x + nqm * B, B};
-        aba_forward<T, DT, true>(s, q, qd, Col<const T>{tau + t * nvm * B + b, B}, g);
         T* gt = gtau + t * nvm * B + b;
-        step_adjoint<T, DT>(s, q, qd, gq, gqd, Col<T>{gt, B}, gm, g, m.dt, m.integ);
+        adjoint_step<T, DT, CT>(m, s, slot, q, qd, Col<const T>{tau + t * nvm * B + b, B}, gq, gqd, Col<T>{gt, B},
+                            gm, g);
         for (int d = nv; d < nvm; ++d) gt[d * B] = T(0);
         if (gtraj) {
           const T* gx = gtraj + t * NX * B + b;
@@ -341,21 +390,40 @@ __device__ __forceinline__ int next_unit(unsigned* counter) {
     unit = next_unit((m).counter);                                           \
   }
 
-template <class T, class DT, int ST>
+// CT: the model has contact spheres (a separate instantiation, so the kernels of
+// contact-free models carry none of the contact code).
+template <class T, class DT, int ST, bool CT = false>
 __global__ void k_rollout(DevModel<T> m, const T* __restrict__ q0, const T* __restrict__ qd0,
                           const T* __restrict__ tau, long long Tn, int k, T* ckpt, T* qT, T* qdT,
                           T* traj) {
-  ABASIM_FOR_EACH_SLOT(m, rollout_one<T, DT, ST>(m, slot, q0, qd0, tau, Tn, k, ckpt, qT, qdT, traj))
+  ABASIM_FOR_EACH_SLOT(m, rollout_one<T, DT, ST, CT>(m, slot, q0, qd0, tau, Tn, k, ckpt, qT, qdT, traj))
 }
 
-template <class T, class DT, int ST>
+template <class T, class DT, int ST, bool CT = false>
 __global__ void k_backward(DevModel<T> m, const T* __restrict__ ckpt, const T* __restrict__ tau,
                            long long Tn, int k, const T* __restrict__ gqT, const T* __restrict__ gqdT,
                            const T* __restrict__ gtraj, T* gq0, T* gqd0, T* gtau, T* gm_acc,
                            T* ring) {
-  ABASIM_FOR_EACH_SLOT(m, backward_one<T, DT, ST>(m, slot, ckpt, tau, Tn, k, gqT, gqdT, gtraj, gq0, gqd0,
-                                          gtau, gm_acc, ring))
+  ABASIM_FOR_EACH_SLOT(m, backward_one<T, DT, ST, CT>(m, slot, ckpt, tau, Tn, k, gqT, gqdT, gtraj, gq0, gqd0,
+                                              gtau, gm_acc, ring))
 }
+
+template <class T>
+using BackwardKernel = void (*)(DevModel<T>, const T*, const T*, long long, int, const T*, const T*, const T*,
+                                T*, T*, T*, T*, T*);
+
+template <class T>
+using RolloutKernel = void (*)(DevModel<T>, const T*, const T*, const T*, long long, int, T*, T*, T*, T*);
+
+// Declared here; defined and explicitly instantiated only in the unit of each
+// storage mode, so that the three adjoint-kernel variants compile in parallel.
+template <class T, class DT, int ST>
+BackwardKernel<T> backward_kernel();
+// The contact-model kernels (global storage), instantiated in their own units.
+template <class T, class DT>
+RolloutKernel<T> rollout_contact_kernel();
+template <class T, class DT>
+BackwardKernel<T> backward_contact_kernel();
 
 // One step with tangents: the state, torque and tape are dual numbers staged in
 // the caller's workspace [tile][...][lane]; model constants stay plain.
@@ -483,8 +551,10 @@ int launch_rollout(sim_handle* h, const void* q0, const void* qd0, const void* t
   size_t shm = 0;
   int st = ST_GLOBAL;
   int rc = SIM_OK;
-  auto kern = k_rollout<T, DT, ST_GLOBAL>;
-  if constexpr (sizeof(T) == 4) {  // on-chip modes: FP32 storage only
+  RolloutKernel<T> kern = k_rollout<T, DT, ST_GLOBAL>;
+  if (h->ctape) {
+    kern = rollout_contact_kernel<T, DT>();
+  } else if constexpr (sizeof(T) == 4) {  // on-chip modes: FP32 storage only
     rc = choose_storage<T>(h, k_rollout<T, DT, ST_GLOBAL>, k_rollout<T, DT, ST_HYBRID>,
                            k_rollout<T, DT, ST_SMEM>, false, &st, &shm);
     if (st == ST_SMEM) kern = k_rollout<T, DT, ST_SMEM>;
@@ -509,12 +579,15 @@ int launch_backward(sim_handle* h, const void* ckpt, const void* tau, int64_t T_
   size_t shm = 0;
   int st = ST_GLOBAL;
   int rc = SIM_OK;
-  auto kern = k_backward<T, DT, ST_GLOBAL>;
-  if constexpr (sizeof(T) == 4) {  // on-chip modes: FP32 storage only
-    rc = choose_storage<T>(h, k_backward<T, DT, ST_GLOBAL>, k_backward<T, DT, ST_HYBRID>,
-                           k_backward<T, DT, ST_SMEM>, true, &st, &shm);
-    if (st == ST_SMEM) kern = k_backward<T, DT, ST_SMEM>;
-    if (st == ST_HYBRID) kern = k_backward<T, DT, ST_HYBRID>;
+  BackwardKernel<T> kern = backward_kernel<T, DT, ST_GLOBAL>();
+  if (h->ctape) {
+    kern = backward_contact_kernel<T, DT>();
+  } else if constexpr (sizeof(T) == 4) {  // on-chip modes: FP32 storage only
+    const BackwardKernel<T> k_hyb = backward_kernel<T, DT, ST_HYBRID>();
+    const BackwardKernel<T> k_smem = backward_kernel<T, DT, ST_SMEM>();
+    rc = choose_storage<T>(h, kern, k_hyb, k_smem, true, &st, &shm);
+    if (st == ST_SMEM) kern = k_smem;
+    if (st == ST_HYBRID) kern = k_hyb;
   }
   if (rc != SIM_OK) return rc;
   h->last_storage_bwd = st;
@@ -543,9 +616,9 @@ int launch_step_with_tape(sim_handle* h, const void* q, const void* qd, const vo
   DevModel<T> m = dev_model<T>(h);
   m.tape = (T*)tape;
   const int grid = (h->B + h->block - 1) / h->block;
-  k_rollout<T, DT, ST_GLOBAL><<<grid, h->block, 0, S(stream)>>>(m, (const T*)q, (const T*)qd, (const T*)tau,
-                                                                1LL, 1, (T*)nullptr, (T*)q_out, (T*)qd_out,
-                                                                (T*)nullptr);
+  const RolloutKernel<T> kern = h->ctape ? rollout_contact_kernel<T, DT>() : k_rollout<T, DT, ST_GLOBAL>;
+  kern<<<grid, h->block, 0, S(stream)>>>(m, (const T*)q, (const T*)qd, (const T*)tau, 1LL, 1, (T*)nullptr,
+                                         (T*)q_out, (T*)qd_out, (T*)nullptr);
   cudaError_t e = cudaGetLastError();
   return e == cudaSuccess ? SIM_OK : cuda_fail(h, e, "step launch");
 }

@@ -40,13 +40,18 @@ def _desc(model, precision=0, integrator=0, **override):
     for k, v in override.items():
         if k in arrs:
             arrs[k] = np.ascontiguousarray(v, arrs[k].dtype)
-        elif k == "damping":
+        elif k in ("damping", "contact"):
             arrs[k] = np.ascontiguousarray(v, np.float64)
+    if "contact" not in override and getattr(model, "contact", None) is not None:
+        arrs["contact"] = np.ascontiguousarray(model.contact, np.float64)
     d = p._Desc()
     d.n_systems = override.get("n_systems", len(arrs["sys_link_offset"]) - 1)
     d.precision = precision
     d.integrator = integrator
     d.dt = override.get("dt", model.dt)
+    d.friction = override.get("friction", 0.8)
+    d.erp = override.get("erp", 0.2)
+    d.pgs_iterations = override.get("pgs_iterations", 20)
     for i in range(3):
         d.gravity[i] = model.gravity[i]
     for k, v in arrs.items():
@@ -74,6 +79,9 @@ def _bad_cases():
     jt2 = m.joint_type.copy(); jt2[0] = 7
     ic = m.I_com.copy(); ic[1, 0] = -0.5
     off = m.sys_link_offset.copy(); off[1] = 0
+    qc = wl.config(3, B=1, T=1, contacts=True).model
+    many = qc.contact.copy(); many[:5, 3] = 0.02                      # five spheres in one system
+    nan = qc.contact.copy(); nan[3, 0] = np.nan
     return [
         (m, dict(parent=par), "parent"),
         (m, dict(axis=ax), "axis"),
@@ -87,10 +95,17 @@ def _bad_cases():
         (m, dict(n_systems=0), "n_systems"),
         (m, dict(damping=-np.ones(m.n_links_total)), "damping"),
         (q, dict(), None),
+        (qc, dict(contact=many), "contact spheres"),
+        (qc, dict(contact=nan), "contact sphere"),
+        (qc, dict(friction=-0.1), "friction"),
+        (qc, dict(erp=1.5), "erp"),
+        (qc, dict(pgs_iterations=0), "pgs_iterations"),
+        (qc, dict(pgs_iterations=65), "pgs_iterations"),
+        (qc, dict(), None),
     ]
 
 
-@pytest.mark.parametrize("case", range(12))
+@pytest.mark.parametrize("case", range(19))
 def test_model_validation(case):
     model, over, needle = _bad_cases()[case]
     d, _keep = _desc(model, **over)
