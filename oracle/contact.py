@@ -1,6 +1,7 @@
-"""Contact resolution by a mixed linear complementarity problem solved with
-projected Gauss-Seidel (Sec. 3.1 "Collision resolution", Eq. 8; supplement
-Sec. D, Alg. 1), plain CPU FP64.
+"""Contact and joint-limit resolution by a mixed linear complementarity problem
+solved with projected Gauss-Seidel (Sec. 3.1 "Collision resolution", Eq. 8;
+supplement Sec. D, Alg. 1), plain CPU FP64.  Test infrastructure only: imported
+by the tests, the smoke check and the benchmark's CPU baseline.
 
 Reading (the paper names the MLCP a = A x + b, 0 <= a _|_ x >= 0, c- <= x <= c+,
 with A the inertial matrix and b the relative velocities, and gives no contact
@@ -8,16 +9,22 @@ model parameters):
 * contact candidates are spheres (centre p_c in a link's frame, radius r) against
   the ground plane z = 0; the gap is phi = y_z - r with y the sphere centre in the
   world; a candidate is active when phi < 0;
-* the unknowns x are contact impulses lambda (3 per contact: world x, y tangent,
-  z normal); A = J M^-1 J^T with J the world-frame velocity Jacobian of the
-  sphere centres; b = J v* + (erp/dt) min(phi, 0) e_z, where v* = qd + dt qdd is
-  the velocity after the unconstrained step;
+* joint limits (the paper lists them among the constraints the LCP handles) are
+  rows on revolute joints with limits lo < hi: the gap is phi = q - lo below the
+  range (row J = +e_j) or phi = hi - q above it (row J = -e_j), active when
+  phi < 0; the row's impulse is >= 0, like a normal row;
+* the unknowns x are impulses lambda: 3 per contact (world x, y tangent, z
+  normal), then one per limit row; A = J M^-1 J^T with J stacking the world-frame
+  velocity Jacobian of the sphere centres and the limit rows;
+  b = J v* + (erp/dt) min(phi, 0) on the normal and limit rows, where
+  v* = qd + dt qdd is the velocity after the unconstrained step;
 * the normal impulse is >= 0 and complementary to the normal velocity; the
   friction impulses are boxed by c-+ = -+mu lambda_n (the box uses the current
   normal impulse, as PGS does);
-* PGS runs a fixed number of sweeps over the active contacts, normal row first,
-  then x and y; the post-contact velocity is v* + M^-1 J^T lambda.
-The contact impulse folds into the step as an extra acceleration M^-1 J^T lambda / dt.
+* PGS runs a fixed number of sweeps: over the active contacts (normal row
+  first, then x and y), then over the active limit rows; the post-constraint
+  velocity is v* + M^-1 J^T lambda.
+The impulse folds into the step as an extra acceleration M^-1 J^T lambda / dt.
 """
 from __future__ import annotations
 
@@ -35,6 +42,18 @@ def contact_points(model, q):
         ys.append(o[:, l] + (E[:, l].transpose(-1, -2) @ p[..., None])[..., 0])
     y = torch.stack(ys, 1)
     return y, y[..., 2] - model.contact_r
+
+
+def limit_gaps(model, q):
+    """Per limited joint: the row sign s [B, K] (+1 below the range, -1 above it)
+    and the gap phi [B, K] = s (q - the violated limit), negative when violated."""
+    qj = torch.stack([q[:, model.qs[l].start] for l in model.limit_links], 1)
+    below = qj - model.limit_lo
+    above = model.limit_hi - qj
+    s = torch.where(below < 0, torch.ones_like(qj), torch.where(above < 0, -torch.ones_like(qj),
+                                                                torch.ones_like(qj)))
+    phi = torch.where(below < 0, below, torch.where(above < 0, above, torch.minimum(below, above)))
+    return s, phi
 
 
 def point_velocities(model, q, v):
@@ -65,38 +84,71 @@ def contact_jacobian(model, q):
     return torch.stack(cols, -1)
 
 
-def pgs(A, b, active, mu, iterations):
-    """Projected Gauss-Seidel on the boxed MLCP; A [B, 3C, 3C], b [B, 3C],
-    active [B, C].  Rows of contact c: 3c (x), 3c+1 (y) tangent, 3c+2 (z) normal."""
-    B, n = b.shape
-    C = n // 3
+def limit_jacobian(model, q):
+    """J [B, K, nv]: row k is s_k e_j for limited joint k (coordinate j)."""
+    s, _ = limit_gaps(model, q)
+    J = torch.zeros(q.shape[0], len(model.limit_links), model.nv, dtype=q.dtype)
+    for k, l in enumerate(model.limit_links):
+        J[:, k, model.vs[l].start] = s[:, k]
+    return J
+
+
+def pgs(A, b, active, mu, iterations, n_contacts):
+    """Projected Gauss-Seidel on the boxed MLCP; A [B, n, n], b [B, n], active
+    [B, C + K].  Rows 3c (x), 3c+1 (y) tangent and 3c+2 (z) normal of contact c,
+    then one row per limit (rows 3C..3C+K-1)."""
+    Bn, n = b.shape
+    C = n_contacts
     lam = torch.zeros_like(b)
     act = active.to(b.dtype)
+
+    def update(lam, r, lo, hi, on):
+        s = lam[:, r] - ((A[:, r] * lam).sum(-1) + b[:, r]) / A[:, r, r]
+        if hi is None:
+            new = torch.clamp(s, min=0.0) * on
+        else:
+            new = torch.maximum(torch.minimum(s, hi), lo) * on
+        return torch.cat([lam[:, :r], new[:, None], lam[:, r + 1:]], 1)
+
     for _ in range(iterations):
         for c in range(C):
             rn = 3 * c + 2
-            s = lam[:, rn] - ((A[:, rn] * lam).sum(-1) + b[:, rn]) / A[:, rn, rn]
-            ln = torch.clamp(s, min=0.0) * act[:, c]
-            lam = torch.cat([lam[:, :rn], ln[:, None], lam[:, rn + 1:]], 1)
+            lam = update(lam, rn, None, None, act[:, c])
             for rt in (3 * c, 3 * c + 1):
-                s = lam[:, rt] - ((A[:, rt] * lam).sum(-1) + b[:, rt]) / A[:, rt, rt]
                 hi = mu * lam[:, rn]
-                lt = torch.maximum(torch.minimum(s, hi), -hi) * act[:, c]
-                lam = torch.cat([lam[:, :rt], lt[:, None], lam[:, rt + 1:]], 1)
+                lam = update(lam, rt, -hi, hi, act[:, c])
+        for k in range(n - 3 * C):
+            lam = update(lam, 3 * C + k, None, None, act[:, C + k])
     return lam
 
 
 def contact_velocity_change(model, q, v_star, mass=None):
-    """M^-1 J^T lambda: the velocity change the contact impulses cause."""
-    y, phi = contact_points(model, q)
-    active = phi < 0
-    J = contact_jacobian(model, q)
+    """M^-1 J^T lambda: the velocity change the contact and limit impulses cause,
+    and lambda."""
+    B = q.shape[0]
+    Js, bs, phis = [], [], []
+    C = len(model.contact_links)
+    if C:
+        _, phi_c = contact_points(model, q)
+        Jc = contact_jacobian(model, q)
+        bc = (Jc @ v_star[..., None])[..., 0].clone()
+        bc[:, 2::3] = bc[:, 2::3] + (model.erp / model.dt) * torch.clamp(phi_c, max=0.0)
+        Js.append(Jc)
+        bs.append(bc)
+        phis.append(phi_c)
+    if model.limit_links:
+        _, phi_l = limit_gaps(model, q)
+        Jl = limit_jacobian(model, q)
+        bl = (Jl @ v_star[..., None])[..., 0] + (model.erp / model.dt) * torch.clamp(phi_l, max=0.0)
+        Js.append(Jl)
+        bs.append(bl)
+        phis.append(phi_l)
+    J = torch.cat(Js, 1)
+    b = torch.cat(bs, 1)
+    active = torch.cat(phis, 1) < 0
     M = crba(model, q, mass)
     L = torch.linalg.cholesky(M)
     W = torch.cholesky_solve(J.transpose(-1, -2), L)           # M^-1 J^T
     A = J @ W
-    b = (J @ v_star[..., None])[..., 0]
-    b = b.clone()
-    b[:, 2::3] = b[:, 2::3] + (model.erp / model.dt) * torch.clamp(phi, max=0.0)
-    lam = pgs(A, b, active, model.friction, model.pgs_iterations)
+    lam = pgs(A, b, active, model.friction, model.pgs_iterations, C)
     return (W @ lam[..., None])[..., 0], lam

@@ -87,6 +87,18 @@ class OracleModel:
         if self.contact_links:
             self.contact_p = cts[:, self.contact_links, :3]
             self.contact_r = cts[:, self.contact_links, 3]
+        # revolute joints with position limits (lo, hi; +-inf: none on that side)
+        lim = getattr(desc, "limits", None)
+        lims = t(lim) if lim is not None else None
+        fin = lambda r: [i for i in range(n) if self.jtype[i] == REVOLUTE  # noqa: E731
+                         and bool(torch.isfinite(lims[r, i]).any())]
+        self.limit_links = [] if lims is None else fin(0)
+        for r in range(self.B):
+            if lims is not None and fin(r) != self.limit_links:
+                raise ValueError("systems do not share a topology")
+        if self.limit_links:
+            self.limit_lo = lims[:, self.limit_links, 0]
+            self.limit_hi = lims[:, self.limit_links, 1]
         self.friction = float(getattr(desc, "friction", 0.8))
         self.pgs_iterations = int(getattr(desc, "pgs_iterations", 20))
         self.erp = float(getattr(desc, "erp", 0.2))

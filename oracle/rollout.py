@@ -33,11 +33,12 @@ def qdd_of(model, q, qd, tau, fd="crba", mass=None):
 
 def step(model: OracleModel, q, qd, tau, integrator="semi", fd="crba", mass=None):
     """One time step x^k -> x^{k+1}; joint forces are tau - b qd (viscous damping);
-    contact impulses (if the model has contact spheres) change the velocity by
-    M^-1 J^T lambda, applied as an extra acceleration over the step."""
+    contact and joint-limit impulses (if the model has contact spheres or limits)
+    change the velocity by M^-1 J^T lambda, applied as an extra acceleration over
+    the step."""
     qdd = qdd_of(model, q, qd, tau - model.damping * qd, fd, mass)
     dt = model.dt
-    if model.contact_links:
+    if model.contact_links or model.limit_links:
         from .contact import contact_velocity_change
         dv, _ = contact_velocity_change(model, q, qd + dt * qdd, mass)
         qdd = qdd + dv / dt

@@ -18,7 +18,9 @@ def groups(model, systems):
     for s in systems:
         r = model.links(s)
         ct = () if model.contact is None else tuple(model.contact[r.start:r.stop, 3] >= 0)
-        key = (tuple(model.parent[r.start:r.stop]), tuple(model.joint_type[r.start:r.stop]), ct)
+        lm = () if getattr(model, "limits", None) is None else \
+            tuple(np.isfinite(model.limits[r.start:r.stop]).any(1))
+        key = (tuple(model.parent[r.start:r.stop]), tuple(model.joint_type[r.start:r.stop]), ct, lm)
         g[key].append(int(s))
     return list(g.values())
 

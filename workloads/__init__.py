@@ -21,6 +21,7 @@ links stored CSR by system, each system's links in topological order):
   damping          f64  [L]      viscous joint damping b (joint force -b qd), or None
   contact          f64  [L,4]    contact sphere of a link against the ground z = 0:
                                  centre in the link frame (3), radius (< 0: none); or None
+  limits           f64  [L,2]    revolute joint position limits lo < hi (+-inf: none); or None
   friction, pgs_iterations, erp  contact solver parameters (Coulomb coefficient,
                                  Gauss-Seidel sweeps, penetration correction rate)
 
@@ -64,6 +65,7 @@ class ModelDesc:
     friction: float = 0.8
     pgs_iterations: int = 20
     erp: float = 0.2
+    limits: np.ndarray = None
 
     @property
     def n_systems(self) -> int:
@@ -106,7 +108,21 @@ class ModelDesc:
                          self.gravity.copy(), self.name + "[subset]",
                          None if self.damping is None else self.damping[idx].copy(),
                          None if self.contact is None else self.contact[idx].copy(),
-                         self.friction, self.pgs_iterations, self.erp)
+                         self.friction, self.pgs_iterations, self.erp,
+                         None if self.limits is None else self.limits[idx].copy())
+
+    def with_limits(self, lo: float, hi: float, every: int = 1) -> "ModelDesc":
+        """A copy with position limits [lo, hi] on every ``every``-th revolute joint
+        of each system (counting from its first link)."""
+        m = ModelDesc(**{k: getattr(self, k) for k in self.__dataclass_fields__})
+        lim = np.tile(np.array([[-np.inf, np.inf]]), (self.n_links_total, 1))
+        for b in range(self.n_systems):
+            for j, i in enumerate(self.links(b)):
+                if self.joint_type[i] == REVOLUTE and j % every == 0:
+                    lim[i] = (lo, hi)
+        m.limits = lim
+        m.name = self.name + "_limits"
+        return m
 
     def with_damping(self, seed: int, lo: float = 0.05, hi: float = 0.5) -> "ModelDesc":
         """A copy with viscous damping ~ U(lo, hi) on every revolute joint."""
