@@ -108,8 +108,11 @@ def _dist():
     return ws, rank
 
 
-def workload(cfg: int, precision: str, B=None, T=None, rank: int = 0, contacts: bool = False):
-    """The workload of this rank: ranks simulate disjoint batches (their own seed)."""
+def workload(cfg: int, precision: str, B=None, T=None, rank: int = 0, contacts: bool = False,
+             limits: bool = False):
+    """The workload of this rank: ranks simulate disjoint batches (their own seed).
+    ``limits``: every revolute joint limited to [-0.5, 0.5] rad (chains and the
+    quadruped, at most 12 limited joints per system)."""
     import workloads as wl
     kw = {"seed": wl.SEED_BASE + cfg + 1000 * rank}
     if contacts:
@@ -122,7 +125,12 @@ def workload(cfg: int, precision: str, B=None, T=None, rank: int = 0, contacts: 
         kw["T"] = T
     if cfg != 1:
         kw["precision"] = precision
-    return wl.config(cfg, **kw)
+    work = wl.config(cfg, **kw)
+    if limits:
+        if cfg not in (2, 3):
+            raise SystemExit("--limits applies to the chain and quadruped workloads (--config 2 or 3)")
+        work.model = work.model.with_limits(-0.5, 0.5)
+    return work
 
 
 def run_ours(args):
@@ -136,7 +144,7 @@ def run_ours(args):
     torch.cuda.set_device(local)
     if ws > 1:
         dist.init_process_group("nccl")
-    work = workload(args.config, args.precision, args.batch, args.horizon, rank, args.contacts)
+    work = workload(args.config, args.precision, args.batch, args.horizon, rank, args.contacts, args.limits)
     m = work.model
     T, k = work.T, args.k
     sim = Simulator(m, precision=args.precision)
@@ -244,7 +252,8 @@ def run_ours(args):
                    "parallelism": f"replicas x{ws}" if ws > 1 else "single GPU",
                    "block": sim.launch[0], "schedule": "persistent" if sim.launch[1] else "grid",
                    "tape": args.tape, "replay": args.replay,
-                   "cuda_graph": bool(args.graph), "contacts": bool(args.contacts)},
+                   "cuda_graph": bool(args.graph), "contacts": bool(args.contacts),
+                   "joint_limits": bool(args.limits)},
         "fwd_env_steps_per_s": B * T / (float(np.mean(fwd_ms)) / 1e3),
         "ms_fwd": float(np.mean(fwd_ms)), "ms_adj": float(np.mean(adj_ms)),
         "ms_per_step_cuda_graph": graph_ms,
@@ -252,7 +261,8 @@ def run_ours(args):
                      "unit": "TFLOP/s", "frac": achieved / peak["tflops"],
                      "traffic": measured_traffic("k_backward", m.name, B, T, args.precision, k),
                      "flops_per_system_step": {"fwd": f_fwd, "adj": f_adj}, "peak_note": peak["note"]
-                     + ("; the FLOP count covers the ABA step only, not the contact solve" if args.contacts else "")},
+                     + ("; the FLOP count covers the ABA step only, not the constraint solve"
+                        if args.contacts or args.limits else "")},
         "e2e": e2e,
         "gpu_launches": args.steps * 3,
         "clocks": clocks,
@@ -366,7 +376,8 @@ def cpu_baseline(args, budget_s: float = 15.0):
     from oracle.dynamics import OracleModel
     from oracle.rollout import rollout_backward
     threads = torch.get_num_threads()
-    work = workload(args.config, args.precision, 16, 20, contacts=getattr(args, "contacts", False))
+    work = workload(args.config, args.precision, 16, 20, contacts=getattr(args, "contacts", False),
+                    limits=getattr(args, "limits", False))
     m = work.model
     sys_ = list(range(min(16, m.n_systems)))
     done = 0
@@ -395,7 +406,8 @@ def run_reference(args):
             "n_gpus": ws, "steps": args.steps, "warmup": args.warmup, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "config": {"workload": workload(args.config, args.precision, 4, 1,
-                                            contacts=getattr(args, "contacts", False)).model.name,
+                                            contacts=getattr(args, "contacts", False),
+                                            limits=getattr(args, "limits", False)).model.name,
                        "note": "CPU FP64 oracle, bounded sample"},
             "cpu_baseline": cb,
             "e2e": {"value": cb["value"], "unit": "env-steps/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
@@ -469,6 +481,7 @@ def main():
     ap.add_argument("--graph", action="store_true", help="replay the step as one CUDA graph")
     ap.add_argument("--contacts", action="store_true",
                     help="quadruped with foot contact spheres (the contact solve runs every step)")
+    ap.add_argument("--limits", action="store_true", help="revolute joints limited to [-0.5, 0.5] rad")
     ap.add_argument("--memory-sweep", action="store_true")
     ap.add_argument("--horizons", default="1000,5000,10000,50000")
     args = ap.parse_args()

@@ -70,23 +70,33 @@ enum sim_joint { SIM_REVOLUTE = 0, SIM_FREE = 1 };
  *               tau - damping * qd (NULL: none; ignored for free joints)
  *   contact[4]  a contact sphere rigidly attached to the link: centre in the link
  *               frame (3) and radius (a negative radius: none).  NULL: no contacts.
+ *   limits[2]   position limits lo < hi of a revolute joint (-inf / +inf: no limit
+ *               on that side).  NULL: no limits.  Finite limits on a free joint are
+ *               rejected.
  * gravity[3] is the world-frame gravitational acceleration (e.g. 0 0 -9.81).
  *
- * Contacts (Sec. 3.1 "collision resolution", Eq. 8; the projected Gauss-Seidel
- * solver of the supplement, Alg. 1): each sphere is tested against the ground
- * plane z = 0 with gap phi = (world z of its centre) - radius; at most
- * SIM_MAX_CONTACTS spheres per system.  For the spheres with phi < 0, the
- * impulses lambda (world x, y friction, z normal per contact) solve the mixed
- * LCP a = A lambda + b, A = J M^-1 J^T (J: world velocity Jacobian of the sphere
- * centres), b = J (qd + dt qdd) + (erp / dt) phi e_z, lambda_z >= 0 complementary
- * to a_z, |lambda_x|, |lambda_y| <= friction * lambda_z, by pgs_iterations
- * Gauss-Seidel sweeps (normal row, then x, then y, per contact) from lambda = 0;
- * the velocity change M^-1 J^T lambda is added to the step's qd update.
+ * Contacts and joint limits (Sec. 3.1 "collision resolution", Eq. 8; the
+ * projected Gauss-Seidel solver of the supplement, Alg. 1): each sphere is
+ * tested against the ground plane z = 0 with gap phi = (world z of its centre) -
+ * radius; at most SIM_MAX_CONTACTS spheres per system.  Each limited joint is
+ * tested against its range: below it the row is J = +e_j with gap q - lo, above
+ * it J = -e_j with gap hi - q; at most SIM_MAX_LIMITS limited joints per system.
+ * For the rows with phi < 0, the impulses lambda (world x, y friction, z normal
+ * per contact, then one per limit row) solve the mixed LCP a = A lambda + b,
+ * A = J M^-1 J^T (J: world velocity Jacobian of the sphere centres, then the
+ * limit rows), b = J (qd + dt qdd) + (erp / dt) phi on the normal and limit rows,
+ * lambda_z >= 0 complementary to a_z, |lambda_x|, |lambda_y| <= friction *
+ * lambda_z, limit impulses >= 0 complementary to their rows, by pgs_iterations
+ * Gauss-Seidel sweeps (per contact the normal row, then x, then y; then the limit
+ * rows) from lambda = 0; the velocity change M^-1 J^T lambda is added to the
+ * step's qd update.
  * friction >= 0, erp in [0, 1], pgs_iterations in [1, SIM_MAX_PGS_ITERATIONS];
- * all three are ignored without contact spheres.  The adjoint differentiates
- * the solver's iterations exactly (the active set is held fixed).  sim_step_jvp
- * returns SIM_EUNSUPPORTED for models with contact spheres. */
+ * all three are ignored without contact spheres or limits.  The adjoint
+ * differentiates the solver's iterations exactly (the active set is held fixed).
+ * sim_step_jvp returns SIM_EUNSUPPORTED for models with contact spheres or
+ * limits. */
 #define SIM_MAX_CONTACTS 4
+#define SIM_MAX_LIMITS 12
 #define SIM_MAX_PGS_ITERATIONS 64
 typedef struct sim_model_desc {
   int32_t n_systems;
@@ -109,6 +119,7 @@ typedef struct sim_model_desc {
   double erp;             /* fraction of the penetration removed per step */
   int32_t pgs_iterations; /* Gauss-Seidel sweeps of the contact solver */
   int32_t reserved2;
+  const double* limits;   /* [2] per link or NULL: revolute joint position limits */
 } sim_model_desc;
 
 typedef struct sim_handle sim_handle;
@@ -160,8 +171,8 @@ int sim_step_batch(sim_handle* h, const void* q, const void* qd, const void* tau
  * contents (every word a step reads is written earlier in the same step, so
  * nothing needs clearing); calls whose kernels overlap on the GPU race on it,
  * so serialize them (one stream, or events).  For a model with contact spheres
- * the contact solver's per-system scratch is the handle's, allocated once by
- * sim_create.  Same layouts, ownership and error codes as sim_step_batch. */
+ * or joint limits the constraint solver's per-system scratch is the handle's,
+ * allocated once by sim_create.  Same layouts, ownership and error codes as sim_step_batch. */
 int sim_step_batch_static(sim_handle* h, const void* q, const void* qd, const void* tau,
                           void* q_out, void* qd_out, void* stream);
 
@@ -214,7 +225,7 @@ int sim_set_launch(sim_handle* h, int32_t threads, int32_t schedule);
  * memory when the block's tiles of 32 systems fit the per-block limit, else in
  * the handle's global scratch; SIM_TAPE_GLOBAL / SIM_TAPE_SHARED force one
  * (SHARED fails with SIM_EUNSUPPORTED at launch if it does not fit).  Models with
- * contact spheres always run with the tape in global memory.  Results do not
+ * contact spheres or joint limits always run with the tape in global memory.  Results do not
  * depend on it. */
 #define SIM_TAPE_AUTO 0
 #define SIM_TAPE_GLOBAL 1

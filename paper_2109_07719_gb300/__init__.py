@@ -44,7 +44,8 @@ class _Desc(ctypes.Structure):
                 ("X_tree", ctypes.c_void_p), ("mass", ctypes.c_void_p), ("com", ctypes.c_void_p),
                 ("I_com", ctypes.c_void_p), ("damping", ctypes.c_void_p),
                 ("contact", ctypes.c_void_p), ("friction", ctypes.c_double), ("erp", ctypes.c_double),
-                ("pgs_iterations", ctypes.c_int32), ("reserved2", ctypes.c_int32)]
+                ("pgs_iterations", ctypes.c_int32), ("reserved2", ctypes.c_int32),
+                ("limits", ctypes.c_void_p)]
 
 
 _P = ctypes.c_void_p
@@ -122,6 +123,8 @@ class Simulator:
             keep["damping"] = np.ascontiguousarray(model.damping, np.float64)
         if getattr(model, "contact", None) is not None:
             keep["contact"] = np.ascontiguousarray(model.contact, np.float64)
+        if getattr(model, "limits", None) is not None:
+            keep["limits"] = np.ascontiguousarray(model.limits, np.float64)
         d = _Desc()
         d.friction = float(getattr(model, "friction", 0.8))
         d.erp = float(getattr(model, "erp", 0.2))

@@ -26,9 +26,11 @@ enum JointType : int { J_REVOLUTE = 0, J_FREE = 1 };
 enum Integrator : int { I_SEMI_IMPLICIT = 0, I_EXPLICIT = 1 };
 
 // per-link model parameters, [link][field][system]; P_CP / P_CR: contact sphere
-// centre (link frame) and radius (< 0: the link has none)
+// centre (link frame) and radius (< 0: the link has none); P_LO / P_HI: revolute
+// joint position limits (-inf / +inf: none)
 enum : int {
-  P_E = 0, P_R = 9, P_AX = 12, P_M = 15, P_C = 16, P_IC = 19, P_DAMP = 25, P_CP = 26, P_CR = 29, NPRM = 30
+  P_E = 0, P_R = 9, P_AX = 12, P_M = 15, P_C = 16, P_IC = 19, P_DAMP = 25, P_CP = 26, P_CR = 29, P_LO = 30,
+  P_HI = 31, NPRM = 32
 };
 // per-link forward tape
 enum : int {
@@ -50,11 +52,13 @@ enum : int {
 // accumulators of a test pass (C_TAB, C_TPB, C_TUB), the adjoint of the
 // unconstrained qdd from the integrator (C_QDDB), and the adjoints the contact
 // solve hands to the step adjoint (B_*: U, 1/D, the free root's articulated
-// inertia, the link transform E and r, world pose, unconstrained qdd and qd).
+// inertia, the link transform E and r, world pose, unconstrained qdd, qd and, for
+// limited joints, q), then a test pass's joint accelerations and their adjoint
+// (C_TQ, C_TQB).
 enum : int {
   C_EW = 0, C_OW = 9, C_VS = 12, C_TP = 18, C_TA = 24, C_TU = 30, C_DV = 36, C_TAB = 42, C_TPB = 48,
   C_TUB = 54, C_QDDB = 60, B_U = 66, B_DI = 72, B_IA = 73, B_E = 94, B_R = 103, B_EW = 106, B_OW = 115,
-  B_VS = 118, B_QDD = 124, B_QD = 130, NCT = 136
+  B_VS = 118, B_QDD = 124, B_QD = 130, B_Q = 136, B_END = 137, C_TQ = 137, C_TQB = 143, NCT = 149
 };
 
 // meta word per link: parent+1 (8 bits) | joint type (1) | "has a child other than
@@ -519,8 +523,9 @@ SD void step_adjoint(const Sys<T, PT>& s, Col<const T> q, Col<const T> qd, Col<T
   if (ct) {
     for (int l = 0; l < nl; ++l) {
       const int m = s.M(l);
-      const int nvl = meta_jtype(m) == J_REVOLUTE ? 1 : 6;
-      for (int i = 0; i < nvl; ++i) gqd[meta_voff(m) + i] += ctr(ct, l, B_QD + i);
+      const bool rev = meta_jtype(m) == J_REVOLUTE;
+      for (int i = 0; i < (rev ? 1 : 6); ++i) gqd[meta_voff(m) + i] += ctr(ct, l, B_QD + i);
+      if (rev) gq[meta_qoff(m)] += ctr(ct, l, B_Q);
     }
   }
   for (int l = 0; l < nl; ++l) {

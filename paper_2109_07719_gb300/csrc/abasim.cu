@@ -74,9 +74,23 @@ int validate(const sim_model_desc* d, std::string& why) {
       snprintf(buf, sizeof buf, "system %d has %d links (1..%d allowed)", b, n, kMaxLinks);
       return bad(buf);
     }
-    int nq = 0, nv = 0, ncs = 0;
+    int nq = 0, nv = 0, ncs = 0, nlim = 0;
     for (int l = 0; l < n; ++l) {
       const int i = o0 + l;
+      if (d->limits) {
+        const double lo = d->limits[2 * i], hi = d->limits[2 * i + 1];
+        if (std::isnan(lo) || std::isnan(hi) || !(lo < hi) || lo == INFINITY || hi == -INFINITY) {
+          snprintf(buf, sizeof buf, "system %d link %d: joint limits need lo < hi", b, l);
+          return bad(buf);
+        }
+        if (std::isfinite(lo) || std::isfinite(hi)) {
+          if (d->joint_type[i] != SIM_REVOLUTE) {
+            snprintf(buf, sizeof buf, "system %d link %d: limits apply to revolute joints only", b, l);
+            return bad(buf);
+          }
+          ++nlim;
+        }
+      }
       if (d->contact) {
         const double* c = d->contact + 4 * i;
         for (int x = 0; x < 4; ++x)
@@ -138,11 +152,14 @@ int validate(const sim_model_desc* d, std::string& why) {
     }
     if (nq > kMaxCoords || nv > kMaxCoords) return bad("too many coordinates in one system");
     if (ncs > SIM_MAX_CONTACTS) {
-      char buf[160];
       snprintf(buf, sizeof buf, "system %d has %d contact spheres (at most %d)", b, ncs, SIM_MAX_CONTACTS);
       return bad(buf);
     }
-    any_contact |= ncs > 0;
+    if (nlim > SIM_MAX_LIMITS) {
+      snprintf(buf, sizeof buf, "system %d has %d limited joints (at most %d)", b, nlim, SIM_MAX_LIMITS);
+      return bad(buf);
+    }
+    any_contact |= ncs > 0 || nlim > 0;
   }
   if (any_contact) {
     if (!(d->friction >= 0) || !std::isfinite(d->friction)) return bad("friction must be finite and >= 0");
@@ -258,6 +275,10 @@ int sim_create(const sim_model_desc* d, sim_handle** out) {
       for (int x = 0; x < 3; ++x) P(P_CP + x) = d->contact ? d->contact[4 * i + x] : 0.0;
       P(P_CR) = (d->contact && d->contact[4 * i + 3] >= 0) ? d->contact[4 * i + 3] : -1.0;
       if (d->contact && d->contact[4 * i + 3] >= 0) any_contact = true;
+      const bool lim = d->limits && jt == SIM_REVOLUTE;
+      P(P_LO) = lim ? d->limits[2 * i] : -INFINITY;
+      P(P_HI) = lim ? d->limits[2 * i + 1] : INFINITY;
+      if (lim && (std::isfinite(d->limits[2 * i]) || std::isfinite(d->limits[2 * i + 1]))) any_contact = true;
       bool treechild = false;  // a child other than link l + 1
       for (int c = l + 2; c < nl[sl]; ++c)
         if (d->parent[d->sys_link_offset[b] + c] == l) treechild = true;
@@ -403,7 +424,7 @@ int sim_step_jvp(sim_handle* h, const void* q, const void* qd, const void* tau, 
     return fail(h, SIM_EINVAL, "null state, torque or output pointer");
   if (!work || work_bytes < sim_jvp_work_bytes(h))
     return fail(h, SIM_ENOMEM, "workspace smaller than sim_jvp_work_bytes");
-  if (h->ctape) return fail(h, SIM_EUNSUPPORTED, "forward-mode step of a model with contact spheres");
+  if (h->ctape) return fail(h, SIM_EUNSUPPORTED, "forward-mode step of a model with contact spheres or limits");
   return is_fp64(h) ? launch_jvp<double>(h, q, qd, tau, dq, dqd, dtau, q_out, qd_out, dq_out, dqd_out, work, stream)
                     : launch_jvp<float>(h, q, qd, tau, dq, dqd, dtau, q_out, qd_out, dq_out, dqd_out, work, stream);
 }

@@ -32,7 +32,7 @@ template <class T> struct DevModel {
   int persistent;
   int smem;
   int quadratic;
-  T* ctape;  // per-link contact tape [tile][maxL][NCT][lane] (null: no contact spheres)
+  T* ctape;  // per-link contact tape [tile][maxL][NCT][lane] (null: no contact spheres or limits)
   T* csys;   // per-system contact record [tile][NCS][lane]
   ContactParams<T> cp;
 };
@@ -141,15 +141,16 @@ template <class T> __device__ __forceinline__ CView<T> cview_of(const DevModel<T
   return CView<T>{m.ctape + tile * m.maxL * NCT * LANES + lane, m.csys + tile * NCS * LANES + lane};
 }
 
-// One step x -> x' in place: ABA, the contact impulses (CT: the model has
-// contact spheres), integration.
+// One step x -> x' in place: ABA, the contact and joint-limit impulses (CT: the
+// model has contact spheres or joint limits), integration.
 template <class T, class DT, bool CT>
 __device__ __forceinline__ void forward_step(const DevModel<T>& m, const Sys<T>& s, int slot, Col<T> q,
                                              Col<T> qd, Col<const T> tau_t, V3<T> g) {
   aba_forward<T, DT, false>(s, Col<const T>{q.p, q.B}, Col<const T>{qd.p, qd.B}, tau_t, g);
   if constexpr (CT) {
     const CView<T> cv = cview_of(m, slot);
-    const int nc = contact_forward<T, DT, T>(s, cv, Col<const T>{qd.p, qd.B}, m.dt, m.cp);
+    const int nc =
+        contact_forward<T, DT, T>(s, cv, Col<const T>{q.p, q.B}, Col<const T>{qd.p, qd.B}, m.dt, m.cp);
     integrate<T>(s, q, qd, m.dt, m.integ, nc > 0 ? (const T*)cv.ct : nullptr);
   } else {
     integrate<T>(s, q, qd, m.dt, m.integ);
@@ -157,9 +158,9 @@ __device__ __forceinline__ void forward_step(const DevModel<T>& m, const Sys<T>&
 }
 
 // Recomputes the step from x^t and pulls the state adjoint (gq, gqd) back
-// through it.  With active contacts the integrator adjoint runs first for every
-// link (the contact adjoint needs all of qdd's adjoint), then the contact
-// adjoint, then the ABA adjoint with the contact terms added.
+// through it.  With active contact or limit rows the integrator adjoint runs
+// first for every link (the constraint adjoint needs all of qdd's adjoint), then
+// the constraint adjoint, then the ABA adjoint with its terms added.
 template <class T, class DT, bool CT>
 __device__ __forceinline__ void adjoint_step(const DevModel<T>& m, const Sys<T>& s, int slot, Col<const T> q,
                                              Col<const T> qd, Col<const T> tau_t, Col<T> gq, Col<T> gqd,
@@ -167,7 +168,7 @@ __device__ __forceinline__ void adjoint_step(const DevModel<T>& m, const Sys<T>&
   aba_forward<T, DT, true>(s, q, qd, tau_t, g);
   if constexpr (CT) {
     const CView<T> cv = cview_of(m, slot);
-    const int nc = contact_forward<T, DT, T>(s, cv, qd, m.dt, m.cp);
+    const int nc = contact_forward<T, DT, T>(s, cv, q, qd, m.dt, m.cp);
     if (nc > 0) {
       for (int l = 0; l < s.nl; ++l) {
         const int mt = s.M(l);
@@ -390,8 +391,8 @@ __device__ __forceinline__ int next_unit(unsigned* counter) {
     unit = next_unit((m).counter);                                           \
   }
 
-// CT: the model has contact spheres (a separate instantiation, so the kernels of
-// contact-free models carry none of the contact code).
+// CT: the model has contact spheres or joint limits (a separate instantiation, so
+// the kernels of unconstrained models carry none of the constraint code).
 template <class T, class DT, int ST, bool CT = false>
 __global__ void k_rollout(DevModel<T> m, const T* __restrict__ q0, const T* __restrict__ qd0,
                           const T* __restrict__ tau, long long Tn, int k, T* ckpt, T* qT, T* qdT,

@@ -40,7 +40,7 @@ def _desc(model, precision=0, integrator=0, **override):
     for k, v in override.items():
         if k in arrs:
             arrs[k] = np.ascontiguousarray(v, arrs[k].dtype)
-        elif k in ("damping", "contact"):
+        elif k in ("damping", "contact", "limits"):
             arrs[k] = np.ascontiguousarray(v, np.float64)
     if "contact" not in override and getattr(model, "contact", None) is not None:
         arrs["contact"] = np.ascontiguousarray(model.contact, np.float64)
@@ -82,6 +82,12 @@ def _bad_cases():
     qc = wl.config(3, B=1, T=1, contacts=True).model
     many = qc.contact.copy(); many[:5, 3] = 0.02                      # five spheres in one system
     nan = qc.contact.copy(); nan[3, 0] = np.nan
+    inf2 = np.tile([[-np.inf, np.inf]], (q.n_links_total, 1))
+    lim_free = inf2.copy(); lim_free[0] = (-1.0, 1.0)                   # a limit on the floating base
+    lim_order = inf2.copy(); lim_order[2] = (0.5, -0.5)
+    lim_many = np.tile([[-1.0, 1.0]], (m.n_links_total, 1))
+    ch = wl.config(4, B=1, T=1, dof_lo=14, dof_hi=14).model            # 14 limited joints in one system
+    lim_14 = np.tile([[-1.0, 1.0]], (ch.n_links_total, 1))
     return [
         (m, dict(parent=par), "parent"),
         (m, dict(axis=ax), "axis"),
@@ -102,10 +108,14 @@ def _bad_cases():
         (qc, dict(pgs_iterations=0), "pgs_iterations"),
         (qc, dict(pgs_iterations=65), "pgs_iterations"),
         (qc, dict(), None),
+        (q, dict(limits=lim_free), "revolute joints only"),
+        (q, dict(limits=lim_order), "lo < hi"),
+        (ch, dict(limits=lim_14), "limited joints"),
+        (m, dict(limits=lim_many), None),
     ]
 
 
-@pytest.mark.parametrize("case", range(19))
+@pytest.mark.parametrize("case", range(23))
 def test_model_validation(case):
     model, over, needle = _bad_cases()[case]
     d, _keep = _desc(model, **over)

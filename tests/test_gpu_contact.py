@@ -1,12 +1,15 @@
-"""GPU parity of the contact path (sphere contacts against the ground plane,
-the MLCP of Sec. 3.1 Eq. 8 solved by projected Gauss-Seidel) and of its
-adjoint, through the C ABI, against the CPU FP64 oracle.
+"""GPU parity of the constraint path (sphere contacts against the ground plane
+and revolute joint limits, the MLCP of Sec. 3.1 Eq. 8 solved by projected
+Gauss-Seidel) and of its adjoint, through the C ABI, against the CPU FP64 oracle.
 
 Inputs: the floating-base quadruped (13 links, a 2 cm sphere on each foot) with
 straight legs, its base lowered so that in some systems the lowest foot starts
 4 mm inside the ground and in the others 2-9 mm above it, falling at 1 m/s, so
 contacts are active from step 0 in some systems and appear during the rollout
-in others.  The batch spans two 32-system blocks with a ragged tail.
+in others.  Joint limits: 7-DOF chains with every other joint limited to
+[-0.4, 0.4] and q0 ~ U(-1, 1), and the quadrupeds with knee and hip-pitch
+limits that the straight legs violate.  The batches span two 32-system blocks
+with a ragged tail.
 """
 import numpy as np
 import pytest
@@ -160,3 +163,89 @@ def test_jvp_of_contact_model_is_refused():
     dq0, dqd0, dtau = _dev(sim, q0, qd0, tau)
     with pytest.raises(SimError, match="contact"):
         sim.jvp(dq0, dqd0, dtau[0], dq=torch.ones_like(dq0))
+
+
+# ---------------------------------------------------------------- joint limits
+
+def _limited_chains(B=37, T=40, seed=8):
+    """7-DOF chains with every other joint limited to [-0.4, 0.4]: q0 ~ U(-1, 1)
+    starts many joints outside their range, qd0 ~ N(0, 0.5^2)."""
+    work = wl.config(2, B=B, T=T, precision="fp64")
+    work.model = work.model.with_limits(-0.4, 0.4, every=2)
+    g = np.random.default_rng(seed)
+    qd0 = 0.5 * g.standard_normal(work.qd0.shape)
+    return work, work.q0, qd0, work.tau().numpy()
+
+
+def _with_leg_limits(work):
+    """Knees limited to [-1, -0.02] (straight legs start above the range) and hip
+    pitch to [-0.05, 0.05]."""
+    md = work.model
+    lim = np.tile(np.array([[-np.inf, np.inf]]), (md.n_links_total, 1))
+    for b in range(md.n_systems):
+        for leg in range(4):
+            lim[md.sys_link_offset[b] + 3 + 3 * leg] = (-1.0, -0.02)
+            lim[md.sys_link_offset[b] + 2 + 3 * leg] = (-0.05, 0.05)
+    md.limits = lim
+    return work
+
+
+def _parity_fp64(work, q0, qd0, tau, sel, seed=13):
+    sim = _sim(work)
+    dq0, dqd0, dtau = _dev(sim, q0, qd0, tau)
+    qT, qdT, ck, _ = sim.rollout(dq0, dqd0, dtau, k=1)
+    g = torch.Generator().manual_seed(seed)
+    gqT = torch.randn(qT.shape, generator=g, dtype=torch.float64)
+    gqdT = torch.randn(qdT.shape, generator=g, dtype=torch.float64)
+    gq0, gqd0, gtau, gm = sim.backward(ck, dtau, gqT.to(sim.device), gqdT.to(sim.device), k=1)
+    torch.cuda.synchronize()
+    oq, oqd = oracle_forward(work.model, list(range(work.model.n_systems)), q0, qd0, tau)
+    check("qT", qT.cpu().numpy(), oq, 1e-8)
+    check("qdT", qdT.cpu().numpy(), oqd, 1e-8)
+    o = oracle_backward(work.model, sel, q0, qd0, tau, gqT.numpy(), gqdT.numpy())
+    check("gq0", gq0.cpu().numpy()[:, sel], o["gq0"], 1e-6)
+    check("gqd0", gqd0.cpu().numpy()[:, sel], o["gqd0"], 1e-6)
+    check("gtau", gtau.cpu().numpy()[:, :, sel], o["gtau"], 1e-6)
+    gmd = mass_grad_of(work.model, gm.cpu().numpy(), sel)
+    check("gmass", np.concatenate([gmd[s] for s in sel]), np.concatenate([o["gm"][s] for s in sel]), 1e-6)
+    assert sim.status().sum() == 0
+
+
+def test_joint_limits_fp64():
+    work, q0, qd0, tau = _limited_chains()
+    _parity_fp64(work, q0, qd0, tau, [0, 5, 31, 32, 36])
+
+
+def test_contacts_and_joint_limits_fp64():
+    work, q0, qd0, tau = _touching(B=37, T=25, seed=9)
+    work = _with_leg_limits(work)
+    _parity_fp64(work, q0, qd0, tau, [0, 1, 3, 33, 36])
+
+
+def test_joint_limits_checkpoint_replay():
+    work, q0, qd0, tau = _limited_chains(B=35, T=29, seed=10)
+    sim = _sim(work)
+    dq0, dqd0, dtau = _dev(sim, q0, qd0, tau)
+    qT, qdT, ck1, _ = sim.rollout(dq0, dqd0, dtau, k=1)
+    _, _, ckk, _ = sim.rollout(dq0, dqd0, dtau, k=6)
+    gqT, gqdT = torch.ones_like(qT), -torch.ones_like(qdT)
+    a = sim.backward(ck1, dtau, gqT, gqdT, k=1)
+    b = sim.backward(ckk, dtau, gqT, gqdT, k=6)
+    for name, x, y in zip(("gq0", "gqd0", "gtau", "gmass"), a, b):
+        check(name, y.cpu().numpy(), x.cpu().numpy(), 1e-10)
+
+
+def test_joint_limits_fp32():
+    work, q0, qd0, tau = _limited_chains(B=37, T=40, seed=12)
+    sim = _sim(work, "fp32")
+    dq0, dqd0, dtau = _dev(sim, q0, qd0, tau)
+    hq0, hqd0, htau = [x.double().cpu().numpy() for x in (dq0, dqd0, dtau)]
+    qT, qdT, ck, _ = sim.rollout(dq0, dqd0, dtau)
+    gq0, gqd0, gtau, gm = sim.backward(ck, dtau, torch.ones_like(qT), torch.ones_like(qdT))
+    oq, oqd = oracle_forward(work.model, list(range(37)), hq0, hqd0, htau)
+    check("qT", qT.cpu().numpy(), oq, 1e-3)
+    check("qdT", qdT.cpu().numpy(), oqd, 1e-3)
+    sel = [0, 9, 36]
+    o = oracle_backward(work.model, sel, hq0, hqd0, htau, np.ones_like(hq0), np.ones_like(hqd0))
+    check("gqd0", gqd0.cpu().numpy()[:, sel], o["gqd0"], 1e-2)
+    check("gtau", gtau.cpu().numpy()[:, :, sel], o["gtau"], 1e-2)
