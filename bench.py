@@ -479,12 +479,15 @@ def main():
     ap.add_argument("--no-plain", dest="plain", action="store_false")
     ap.add_argument("--no-e2e", dest="e2e", action="store_false")
     ap.add_argument("--graph", action="store_true", help="replay the step as one CUDA graph")
-    ap.add_argument("--contacts", action="store_true",
-                    help="quadruped with foot contact spheres (the contact solve runs every step)")
+    ap.add_argument("--contacts", action=argparse.BooleanOptionalAction, default=None,
+                    help="quadruped with foot contact spheres, the contact solve running every step "
+                         "(default: on for --config 3, whose specification includes foot contacts)")
     ap.add_argument("--limits", action="store_true", help="revolute joints limited to [-0.5, 0.5] rad")
     ap.add_argument("--memory-sweep", action="store_true")
     ap.add_argument("--horizons", default="1000,5000,10000,50000")
     args = ap.parse_args()
+    if args.contacts is None:
+        args.contacts = args.config == 3
     args.warmup = max(args.warmup, 3)
     if args.memory_sweep:
         memory_sweep(args)

@@ -125,27 +125,31 @@ def pgs(A, b, active, mu, iterations, n_contacts):
 def contact_velocity_change(model, q, v_star, mass=None):
     """M^-1 J^T lambda: the velocity change the contact and limit impulses cause,
     and lambda."""
-    B = q.shape[0]
-    Js, bs, phis = [], [], []
     C = len(model.contact_links)
+    phis = []
     if C:
-        _, phi_c = contact_points(model, q)
+        phis.append(contact_points(model, q)[1])
+    if model.limit_links:
+        phis.append(limit_gaps(model, q)[1])
+    phi = torch.cat(phis, 1)
+    active = phi < 0
+    n = 3 * C + len(model.limit_links)
+    if not bool(active.any()):       # no active row anywhere: lambda = 0 and M^-1 J^T lambda = 0
+        return torch.zeros_like(v_star), torch.zeros(q.shape[0], n, dtype=q.dtype)
+    Js, bs = [], []
+    k = model.erp / model.dt
+    if C:
         Jc = contact_jacobian(model, q)
         bc = (Jc @ v_star[..., None])[..., 0].clone()
-        bc[:, 2::3] = bc[:, 2::3] + (model.erp / model.dt) * torch.clamp(phi_c, max=0.0)
+        bc[:, 2::3] = bc[:, 2::3] + k * torch.clamp(phi[:, :C], max=0.0)
         Js.append(Jc)
         bs.append(bc)
-        phis.append(phi_c)
     if model.limit_links:
-        _, phi_l = limit_gaps(model, q)
         Jl = limit_jacobian(model, q)
-        bl = (Jl @ v_star[..., None])[..., 0] + (model.erp / model.dt) * torch.clamp(phi_l, max=0.0)
         Js.append(Jl)
-        bs.append(bl)
-        phis.append(phi_l)
+        bs.append((Jl @ v_star[..., None])[..., 0] + k * torch.clamp(phi[:, C:], max=0.0))
     J = torch.cat(Js, 1)
     b = torch.cat(bs, 1)
-    active = torch.cat(phis, 1) < 0
     M = crba(model, q, mass)
     L = torch.linalg.cholesky(M)
     W = torch.cholesky_solve(J.transpose(-1, -2), L)           # M^-1 J^T
