@@ -224,12 +224,18 @@ int sim_set_launch(sim_handle* h, int32_t threads, int32_t schedule);
 /* Where the per-step tape lives: SIM_TAPE_AUTO (default) puts it in shared
  * memory when the block's tiles of 32 systems fit the per-block limit, else in
  * the handle's global scratch; SIM_TAPE_GLOBAL / SIM_TAPE_SHARED force one
- * (SHARED fails with SIM_EUNSUPPORTED at launch if it does not fit).  Models with
- * contact spheres or joint limits always run with the tape in global memory.  Results do not
- * depend on it. */
+ * (SHARED fails with SIM_EUNSUPPORTED at launch if it does not fit).
+ * SIM_TAPE_PIPELINED runs the FP32 adjoint with checkpoint interval 1 as two
+ * warps per 32-system tile: one recomputes step t's forward intermediates (into a
+ * staging tape in the handle's global scratch) while the other differentiates
+ * step t + 1 from a shared-memory copy; AUTO picks it when it fits, and forcing
+ * it fails with SIM_EUNSUPPORTED for k > 1, FP64 or a tile too large for shared
+ * memory.  Models with contact spheres or joint limits always run with the tape
+ * in global memory.  Results do not depend on the choice beyond rounding. */
 #define SIM_TAPE_AUTO 0
 #define SIM_TAPE_GLOBAL 1
 #define SIM_TAPE_SHARED 2
+#define SIM_TAPE_PIPELINED 3
 int sim_set_tape_space(sim_handle* h, int32_t space);
 
 /* How sim_backward_rollout rebuilds the states inside a checkpoint segment when

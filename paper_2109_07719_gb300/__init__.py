@@ -196,8 +196,9 @@ class Simulator:
         self.launch = (int(threads) or 32, bool(persistent))
 
     def set_tape_space(self, space: str = "auto"):
-        """'auto' (shared memory when it fits), 'global' or 'shared'."""
-        code = {"auto": 0, "global": 1, "shared": 2}[space]
+        """'auto' (the pipelined adjoint or shared memory when they fit), 'global',
+        'shared' (one warp per tile, tape on chip) or 'pipelined' (two warps per tile)."""
+        code = {"auto": 0, "global": 1, "shared": 2, "pipelined": 3}[space]
         self._check(lib.sim_set_tape_space(self._h, code), "sim_set_tape_space")
 
     def set_replay(self, mode: str = "segment"):

@@ -1,5 +1,6 @@
-// Explicit instantiation of the adjoint kernel for storage float, D-solves float,
-// tape and model constants on chip (the units compile in parallel).
+// Explicit instantiation of the adjoint kernels for storage float, D-solves float,
+// tape and model constants on chip, and the pipelined two-warp variant (the units
+// compile in parallel).
 #include "kernels.cuh"
 
 namespace abasim {
@@ -10,6 +11,12 @@ BackwardKernel<T> backward_kernel() {
   return k_backward<T, DT, ST>;
 }
 template BackwardKernel<float> backward_kernel<float, float, ST_SMEM>();
+
+template <class T, class DT>
+BackwardKernel<T> backward_pipe_kernel() {
+  return k_backward_pipe<T, DT>;
+}
+template BackwardKernel<float> backward_pipe_kernel<float, float>();
 
 }  // namespace host
 }  // namespace abasim

@@ -49,8 +49,9 @@ extern __shared__ __align__(16) unsigned char g_smem[];
 
 // Storage modes of the batched kernels: everything per system in global memory
 // (ST_GLOBAL); tape and model constants global but the working state and the
-// prefetched input streams on chip (ST_HYBRID); everything on chip (ST_SMEM).
-enum : int { ST_GLOBAL = 0, ST_HYBRID = 1, ST_SMEM = 2 };
+// prefetched input streams on chip (ST_HYBRID); everything on chip (ST_SMEM);
+// the two-warp pipelined adjoint (ST_PIPE, k_backward_pipe).
+enum : int { ST_GLOBAL = 0, ST_HYBRID = 1, ST_SMEM = 2, ST_PIPE = 3 };
 
 // Scalars per tile (32 systems) a kernel keeps in dynamic shared memory when it
 // runs with on-chip storage: the tape (and, for the adjoint, its accumulators and
@@ -107,6 +108,11 @@ template <class T> __device__ __forceinline__ void cp_async(T* smem_dst, const T
     asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(dst), "l"(gsrc) : "memory");
   else
     asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(dst), "l"(gsrc) : "memory");
+}
+// 16-byte copy bypassing L1 (both addresses 16-byte aligned).
+__device__ __forceinline__ void cp_async16(void* smem_dst, const void* gsrc) {
+  const unsigned dst = (unsigned)__cvta_generic_to_shared(smem_dst);
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(dst), "l"(gsrc) : "memory");
 }
 __device__ __forceinline__ void cp_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
 __device__ __forceinline__ void cp_wait_all_but_newest() { asm volatile("cp.async.wait_group 1;\n" ::: "memory"); }
@@ -409,6 +415,139 @@ __global__ void k_backward(DevModel<T> m, const T* __restrict__ ckpt, const T* _
                                               gtau, gm_acc, ring))
 }
 
+// ------------------------------------------------------------------ pipelined adjoint
+// Two warps per 32-system tile (k = 1 only): the producer warp recomputes step
+// t's forward intermediates (the tape) from the checkpoint x^t into the tile's
+// staging tape in global memory (L2-resident: one tape per tile) while the
+// consumer warp runs the adjoint of step t + 1 from its own copy of the tape in
+// shared memory.  Step t's recompute does not depend on step t + 1's adjoint, so
+// the two overlap; the consumer copies the staged tape into shared memory with
+// 16-byte cp.async at the start of each step and then releases the staging tape.
+// Hand-off by two named barriers (hardware barriers: no spinning): FULL (the
+// producer arrives when the staging tape holds step t, the consumer waits) and
+// EMPTY (the consumer arrives once its copy is done, the producer waits before
+// overwriting).  Both warps execute every barrier the same number of times
+// whatever their systems (inactive lanes included): FULL Tn times, EMPTY Tn - 1
+// times per tile.
+enum : int { BAR_FULL = 1, BAR_EMPTY = 2 };
+__device__ __forceinline__ void pair_sync(int id) { asm volatile("bar.sync %0, 64;\n" ::"r"(id) : "memory"); }
+__device__ __forceinline__ void pair_arrive(int id) { asm volatile("bar.arrive %0, 64;\n" ::"r"(id) : "memory"); }
+
+// Shared memory of one pipelined block, in scalars per lane: tape, adjoint
+// accumulators, model constants, meta words, state adjoint, mass-gradient sums
+// and the consumer's copy of x^t.
+__host__ __device__ __forceinline__ long long pipe_smem_per_tile(int maxL, int nx) {
+  return (long long)maxL * (NTAPE + NADJ + NPRM + 1 + 1) + 2LL * nx;
+}
+
+template <class T, class DT>
+__global__ void __launch_bounds__(2 * LANES, 1)
+k_backward_pipe(DevModel<T> m, const T* __restrict__ ckpt, const T* __restrict__ tau, long long Tn, int k,
+                const T* __restrict__ gqT, const T* __restrict__ gqdT, const T* __restrict__ gtraj, T* gq0,
+                T* gqd0, T* gtau, T* gm_acc, T* ring) {
+  const int warp = threadIdx.x / LANES, lane = threadIdx.x % LANES;
+  const bool consumer = warp == 0;
+  const long long B = m.B;
+  const int nqm = m.nq_max, nvm = m.nv_max, NX = nqm + nvm;
+  const long long L = m.maxL;
+  const V3<T> g{m.g0, m.g1, m.g2};
+  constexpr int MS = (int)(sizeof(T) / sizeof(int));
+  T* s_tape = reinterpret_cast<T*>(g_smem);
+  T* s_adj = s_tape + L * NTAPE * LANES;
+  T* s_prm = s_adj + L * NADJ * LANES;
+  T* s_meta = s_prm + L * NPRM * LANES;
+  T* s_state = s_meta + L * LANES;
+  T* s_gm = s_state + (long long)NX * LANES;
+  T* s_x = s_gm + L * LANES;
+  int* meta_l = reinterpret_cast<int*>(s_meta + lane);
+  int unit = m.persistent ? next_unit(m.counter) : (int)blockIdx.x;
+  while ((long long)unit * LANES < B) {
+    const int slot = unit * LANES + lane;
+    const bool act = slot < B;
+    const int b = act ? m.sys_of_slot[slot] : 0;
+    const int nl = act ? m.nl[slot] : 0;
+    const int nq = act ? (m.nqv[slot] & 0xffff) : 0, nv = act ? (m.nqv[slot] >> 16) : 0;
+    const int tile_links = m.nl[unit * LANES];  // slots are sorted by link count: the tile's longest
+    T* stage = m.tape + (long long)unit * L * NTAPE * LANES;
+    if (consumer && act) {
+      const T* gprm = m.prm + (long long)unit * L * NPRM * LANES + lane;
+      const int* gmeta = m.meta + (long long)unit * L * LANES + lane;
+      for (int l = 0; l < nl; ++l) {
+        for (int f = 0; f < NPRM; ++f) s_prm[(l * NPRM + f) * LANES + lane] = gprm[(l * NPRM + f) * LANES];
+        meta_l[l * LANES * MS] = gmeta[l * LANES];
+      }
+    }
+    __syncthreads();
+    const Sys<T> sc{s_prm + lane, meta_l, s_tape + lane, s_adj + lane, nl, MS};
+    const Sys<T> sp{s_prm + lane, meta_l, stage + lane, nullptr, nl, MS};
+    Col<T> gq{s_state + lane, LANES}, gqd{s_state + nqm * LANES + lane, LANES}, gm{s_gm + lane, LANES};
+    if (consumer && act) {
+      for (int d = 0; d < nqm; ++d) {
+        T v = d < nq ? gqT[d * B + b] : T(0);
+        if (gtraj && d < nq) v += gtraj[(Tn * NX + d) * B + b];
+        gq[d] = v;
+      }
+      for (int d = 0; d < nvm; ++d) {
+        T v = d < nv ? gqdT[d * B + b] : T(0);
+        if (gtraj && d < nv) v += gtraj[(Tn * NX + nqm + d) * B + b];
+        gqd[d] = v;
+      }
+      for (int l = 0; l < nl; ++l) gm[l] = T(0);
+    }
+    for (long long t = Tn - 1; t >= 0; --t) {
+      if (!consumer) {  // producer: recompute step t into the staging tape
+        __syncwarp();
+        if (t < Tn - 1) pair_sync(BAR_EMPTY);
+        if (act) {
+          const T* x = ckpt + t * NX * B + b;
+          aba_forward<T, DT, true>(sp, Col<const T>{x, B}, Col<const T>{x + nqm * B, B},
+                                   Col<const T>{tau + t * nvm * B + b, B}, g);
+        }
+        __threadfence();
+        __syncwarp();
+        pair_arrive(BAR_FULL);
+      } else {  // consumer: the adjoint of step t from a shared-memory copy of its tape
+        if (act)
+          for (int d = 0; d < NX; ++d) cp_async(s_x + d * LANES + lane, ckpt + (t * NX + d) * B + b);
+        __syncwarp();
+        pair_sync(BAR_FULL);
+        const int chunks = (int)((long long)tile_links * NTAPE * LANES * sizeof(T) / 16);
+        for (int i = lane; i < chunks; i += LANES)
+          cp_async16(reinterpret_cast<char*>(s_tape) + 16LL * i, reinterpret_cast<const char*>(stage) + 16LL * i);
+        cp_commit();
+        cp_wait_all();
+        __syncwarp();
+        if (t > 0) pair_arrive(BAR_EMPTY);
+        if (act) {
+          Col<const T> q{s_x + lane, LANES}, qd{s_x + nqm * LANES + lane, LANES};
+          T* gt = gtau + t * nvm * B + b;
+          step_adjoint<T, DT>(sc, q, qd, gq, gqd, Col<T>{gt, B}, gm, g, m.dt, m.integ);
+          for (int d = nv; d < nvm; ++d) gt[d * B] = T(0);
+          if (gtraj) {
+            const T* gx = gtraj + t * NX * B + b;
+            for (int d = 0; d < nq; ++d) gq[d] += gx[d * B];
+            for (int d = 0; d < nv; ++d) gqd[d] += gx[(nqm + d) * B];
+          }
+        }
+        __syncwarp();
+      }
+    }
+    if (consumer && act) {
+      bool ok = true;
+      for (int d = 0; d < nq; ++d) ok &= finite_t(gq[d]);
+      for (int d = 0; d < nv; ++d) ok &= finite_t(gqd[d]);
+      for (int l = 0; l < nl; ++l) ok &= finite_t(gm[l]);
+      if (!ok) m.status[b] |= 1;
+      for (int d = 0; d < nqm; ++d) gq0[d * B + b] = gq[d];
+      for (int d = 0; d < nvm; ++d) gqd0[d * B + b] = gqd[d];
+      for (int l = 0; l < nl; ++l) gm_acc[l * B + slot] = gm[l];
+    }
+    __syncthreads();  // shared memory is reused by the next unit
+    if (!m.persistent) break;
+    unit = next_unit(m.counter);
+  }
+}
+
 template <class T>
 using BackwardKernel = void (*)(DevModel<T>, const T*, const T*, long long, int, const T*, const T*, const T*,
                                 T*, T*, T*, T*, T*);
@@ -425,6 +564,8 @@ template <class T, class DT>
 RolloutKernel<T> rollout_contact_kernel();
 template <class T, class DT>
 BackwardKernel<T> backward_contact_kernel();
+template <class T, class DT>
+BackwardKernel<T> backward_pipe_kernel();
 
 // One step with tangents: the state, torque and tape are dual numbers staged in
 // the caller's workspace [tile][...][lane]; model constants stay plain.
@@ -491,14 +632,20 @@ __global__ void k_set_masses(T* prm, const int* __restrict__ link_slot, int L, l
 
 
 // Grid size and mode of a batched launch; resets the ticket of persistent launches.
+// A work unit is one block of `threads` (default h->block) threads covering
+// `slots` slots (default: one per thread; the pipelined adjoint runs two warps
+// on one 32-slot tile).
 template <class K>
-int launch_shape(sim_handle* h, K kernel, int* grid, int* persistent, size_t shm, void* stream) {
-  const int units = (h->B + h->block - 1) / h->block;
+int launch_shape(sim_handle* h, K kernel, int* grid, int* persistent, size_t shm, void* stream, int threads = 0,
+                 int slots = 0) {
+  if (threads == 0) threads = h->block;
+  if (slots == 0) slots = threads;
+  const int units = (h->B + slots - 1) / slots;
   *grid = units;
   *persistent = 0;
   if (h->schedule != SIM_SCHED_PERSISTENT) return SIM_OK;
   int per_sm = 0;
-  cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, h->block, shm);
+  cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, threads, shm);
   if (e != cudaSuccess) return cuda_fail(h, e, "occupancy query");
   const int cap = std::max(1, per_sm) * std::max(1, h->sms);
   *grid = std::min(units, cap);
@@ -581,21 +728,43 @@ int launch_backward(sim_handle* h, const void* ckpt, const void* tau, int64_t T_
   int st = ST_GLOBAL;
   int rc = SIM_OK;
   BackwardKernel<T> kern = backward_kernel<T, DT, ST_GLOBAL>();
+  int threads = h->block;
   if (h->ctape) {
     kern = backward_contact_kernel<T, DT>();
   } else if constexpr (sizeof(T) == 4) {  // on-chip modes: FP32 storage only
-    const BackwardKernel<T> k_hyb = backward_kernel<T, DT, ST_HYBRID>();
-    const BackwardKernel<T> k_smem = backward_kernel<T, DT, ST_SMEM>();
-    rc = choose_storage<T>(h, kern, k_hyb, k_smem, true, &st, &shm);
-    if (st == ST_SMEM) kern = k_smem;
-    if (st == ST_HYBRID) kern = k_hyb;
+    bool piped = false;
+    if (k == 1 && T_ > 0 && (h->tape_space == SIM_TAPE_AUTO || h->tape_space == SIM_TAPE_PIPELINED)) {
+      // the pipelined two-warp adjoint, when its shared memory fits one block
+      int limit = 0;
+      cudaError_t e = cudaDeviceGetAttribute(&limit, cudaDevAttrMaxSharedMemoryPerBlockOptin, h->device);
+      if (e != cudaSuccess) return cuda_fail(h, e, "shared-memory limit query");
+      const size_t need = (size_t)pipe_smem_per_tile(h->maxL, h->nq_max + h->nv_max) * LANES * sizeof(T);
+      if (need <= (size_t)limit) {
+        kern = backward_pipe_kernel<T, DT>();
+        e = cudaFuncSetAttribute((const void*)kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)need);
+        if (e != cudaSuccess) return cuda_fail(h, e, "shared-memory opt-in");
+        st = ST_PIPE;
+        shm = need;
+        threads = 2 * LANES;
+        piped = true;
+      }
+    }
+    if (!piped && h->tape_space == SIM_TAPE_PIPELINED)
+      return fail(h, SIM_EUNSUPPORTED, "the pipelined adjoint needs k = 1 and a tile that fits in shared memory");
+    if (!piped) {
+      const BackwardKernel<T> k_hyb = backward_kernel<T, DT, ST_HYBRID>();
+      const BackwardKernel<T> k_smem = backward_kernel<T, DT, ST_SMEM>();
+      rc = choose_storage<T>(h, kern, k_hyb, k_smem, true, &st, &shm);
+      if (st == ST_SMEM) kern = k_smem;
+      if (st == ST_HYBRID) kern = k_hyb;
+    }
   }
   if (rc != SIM_OK) return rc;
   h->last_storage_bwd = st;
   int grid = 0;
-  rc = launch_shape(h, kern, &grid, &m.persistent, shm, stream);
+  rc = launch_shape(h, kern, &grid, &m.persistent, shm, stream, threads, st == ST_PIPE ? LANES : threads);
   if (rc != SIM_OK) return rc;
-  kern<<<grid, h->block, shm, S(stream)>>>(m, (const T*)ckpt, (const T*)tau, (long long)T_, k,
+  kern<<<grid, threads, shm, S(stream)>>>(m, (const T*)ckpt, (const T*)tau, (long long)T_, k,
                                            (const T*)gqT, (const T*)gqdT, (const T*)gtraj, (T*)gq0,
                                            (T*)gqd0, (T*)gtau, (T*)h->gm_acc, (T*)work);
   cudaError_t e = cudaGetLastError();

@@ -1,0 +1,85 @@
+"""The pipelined two-warp adjoint (one warp recomputes step t while the other
+differentiates step t + 1) against the single-warp adjoint and the FP64 oracle,
+through the C ABI: ragged batches, horizons of 1 and 2 steps, persistent
+scheduling, per-step objective terms and the FP32 + FP64 D-solve mode."""
+import numpy as np
+import pytest
+import torch
+
+import workloads as wl
+from tests._parity import oracle_backward, check
+
+pytestmark = pytest.mark.gpu
+
+
+def _run(sim, space, q0, qd0, tau, gqT, gqdT, g_traj=None, persistent=False):
+    sim.set_tape_space(space)
+    sim.set_launch(32, persistent)
+    qT, qdT, ck, _ = sim.rollout(q0, qd0, tau, k=1)
+    out = sim.backward(ck, tau, gqT, gqdT, k=1, g_traj=g_traj)
+    torch.cuda.synchronize()
+    return out
+
+
+def _setup(B, T, precision="fp32", seed=3):
+    from paper_2109_07719_gb300 import Simulator
+    work = wl.config(2, B=B, T=T, precision=precision, seed=wl.SEED_BASE + seed)
+    sim = Simulator(work.model, precision=precision)
+    dt, dev = sim.dtype, sim.device
+    q0 = torch.tensor(work.q0, dtype=dt, device=dev)
+    g = torch.Generator().manual_seed(seed)
+    qd0 = (0.5 * torch.randn(work.qd0.shape, generator=g, dtype=torch.float64)).to(dt).to(dev)
+    tau = work.tau(device=dev, dtype=dt)
+    gqT = torch.randn(q0.shape, generator=g, dtype=torch.float64).to(dt).to(dev)
+    gqdT = torch.randn(qd0.shape, generator=g, dtype=torch.float64).to(dt).to(dev)
+    return work, sim, q0, qd0, tau, gqT, gqdT
+
+
+@pytest.mark.parametrize("B,T", [(100, 37), (32, 1), (33, 2), (4096, 20)])
+@pytest.mark.parametrize("precision", ["fp32", "fp32_d64"])
+def test_pipelined_matches_single_warp(B, T, precision):
+    work, sim, q0, qd0, tau, gqT, gqdT = _setup(B, T, precision)
+    a = _run(sim, "shared", q0, qd0, tau, gqT, gqdT)
+    b = _run(sim, "pipelined", q0, qd0, tau, gqT, gqdT)
+    for name, x, y in zip(("gq0", "gqd0", "gtau", "gmass"), a, b):
+        check(name, y.cpu().numpy(), x.cpu().numpy(), 1e-5)
+    assert sim.status().sum() == 0
+
+
+def test_pipelined_persistent_equals_grid():
+    work, sim, q0, qd0, tau, gqT, gqdT = _setup(300, 25)
+    a = _run(sim, "pipelined", q0, qd0, tau, gqT, gqdT, persistent=False)
+    b = _run(sim, "pipelined", q0, qd0, tau, gqT, gqdT, persistent=True)
+    for x, y in zip(a, b):
+        assert torch.equal(x, y)
+
+
+def test_pipelined_per_step_objective():
+    work, sim, q0, qd0, tau, gqT, gqdT = _setup(70, 15)
+    g = torch.Generator().manual_seed(9)
+    gtraj = torch.randn((16, sim.nx, sim.B), generator=g, dtype=torch.float64).to(sim.dtype).to(sim.device)
+    a = _run(sim, "shared", q0, qd0, tau, gqT, gqdT, g_traj=gtraj)
+    b = _run(sim, "pipelined", q0, qd0, tau, gqT, gqdT, g_traj=gtraj)
+    for name, x, y in zip(("gq0", "gqd0", "gtau", "gmass"), a, b):
+        check(name, y.cpu().numpy(), x.cpu().numpy(), 1e-5)
+
+
+def test_pipelined_against_oracle():
+    """FP32 pipelined gradients against the FP64 oracle within the FP32 bound (1e-2)."""
+    work, sim, q0, qd0, tau, gqT, gqdT = _setup(64, 60, seed=5)
+    gq0, gqd0, gtau, gm = _run(sim, "pipelined", q0, qd0, tau, gqT, gqdT)
+    sel = [0, 31, 63]
+    h = [x.double().cpu().numpy() for x in (q0, qd0, tau, gqT, gqdT)]
+    o = oracle_backward(work.model, sel, h[0], h[1], h[2], h[3], h[4])
+    check("gq0", gq0.cpu().numpy()[:, sel], o["gq0"], 1e-2)
+    check("gqd0", gqd0.cpu().numpy()[:, sel], o["gqd0"], 1e-2)
+    check("gtau", gtau.cpu().numpy()[:, :, sel], o["gtau"], 1e-2)
+
+
+def test_pipelined_refuses_what_it_cannot_run():
+    from paper_2109_07719_gb300 import SimError
+    work, sim, q0, qd0, tau, gqT, gqdT = _setup(40, 12)
+    sim.set_tape_space("pipelined")
+    qT, qdT, ck, _ = sim.rollout(q0, qd0, tau, k=3)
+    with pytest.raises(SimError, match="pipelined"):
+        sim.backward(ck, tau, gqT, gqdT, k=3)
