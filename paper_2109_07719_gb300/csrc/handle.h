@@ -29,6 +29,7 @@ struct sim_handle {
   int* nl = nullptr;         // [B]
   int* nqv = nullptr;        // [B]  nq | nv << 16
   void* tape = nullptr;      // [maxL][NTAPE][B] scalar
+  void* tape2 = nullptr;     // second staging tape of the pipelined adjoint (FP32 storage, small trees)
   void* adj = nullptr;       // [maxL][NADJ][B] scalar
   void* gm_acc = nullptr;    // [maxL][B] scalar
   int* link_slot = nullptr;  // [L_total] -> l * B + slot

@@ -417,25 +417,28 @@ __global__ void k_backward(DevModel<T> m, const T* __restrict__ ckpt, const T* _
 
 // ------------------------------------------------------------------ pipelined adjoint
 // Two warps per 32-system tile (k = 1 only): the producer warp recomputes step
-// t's forward intermediates (the tape) from the checkpoint x^t into the tile's
-// staging tape in global memory (L2-resident: one tape per tile) while the
-// consumer warp runs the adjoint of step t + 1 from its own copy of the tape in
-// shared memory.  Step t's recompute does not depend on step t + 1's adjoint, so
-// the two overlap; the consumer copies the staged tape into shared memory with
-// 16-byte cp.async at the start of each step and then releases the staging tape.
-// Hand-off by two named barriers (hardware barriers: no spinning): FULL (the
-// producer arrives when the staging tape holds step t, the consumer waits) and
-// EMPTY (the consumer arrives once its copy is done, the producer waits before
-// overwriting).  Both warps execute every barrier the same number of times
-// whatever their systems (inactive lanes included): FULL Tn times, EMPTY Tn - 1
-// times per tile.
-enum : int { BAR_FULL = 1, BAR_EMPTY = 2 };
+// t's forward intermediates (the tape) from the checkpoint x^t in its own
+// shared-memory tape, then copies it out (16-byte vector moves) to one of two
+// staging tapes of the tile in global memory (L2-resident); meanwhile the
+// consumer warp runs the adjoint of step t + 1 reading its tape from the other
+// staging buffer, with its adjoint accumulators, state adjoint and mass-gradient
+// sums in shared memory.  Step t's recompute does not depend on step t + 1's
+// adjoint, so the two overlap.  Hand-off by named barriers (hardware barriers:
+// no spinning), one pair per staging buffer b: FULL(b) (the producer arrives
+// when buffer b holds its step, the consumer waits) and EMPTY(b) (the consumer
+// arrives when it has finished a step from buffer b that the producer will
+// reuse, the producer waits before overwriting).  Per tile and buffer both warps
+// execute the same number of operations whatever their systems (inactive lanes
+// included), and a warp never arrives twice at a barrier before its partner's
+// matching wait: the producer's next arrival at FULL(b) comes after its wait on
+// EMPTY(b), which follows the consumer's wait on FULL(b), and vice versa.
+enum : int { BAR_FULL0 = 1, BAR_FULL1 = 2, BAR_EMPTY0 = 3, BAR_EMPTY1 = 4 };
 __device__ __forceinline__ void pair_sync(int id) { asm volatile("bar.sync %0, 64;\n" ::"r"(id) : "memory"); }
 __device__ __forceinline__ void pair_arrive(int id) { asm volatile("bar.arrive %0, 64;\n" ::"r"(id) : "memory"); }
 
-// Shared memory of one pipelined block, in scalars per lane: tape, adjoint
-// accumulators, model constants, meta words, state adjoint, mass-gradient sums
-// and the consumer's copy of x^t.
+// Shared memory of one pipelined block, in scalars per lane: the producer's tape,
+// the consumer's adjoint accumulators, model constants, meta words, state
+// adjoint, mass-gradient sums and the consumer's copy of x^t.
 __host__ __device__ __forceinline__ long long pipe_smem_per_tile(int maxL, int nx) {
   return (long long)maxL * (NTAPE + NADJ + NPRM + 1 + 1) + 2LL * nx;
 }
@@ -444,7 +447,7 @@ template <class T, class DT>
 __global__ void __launch_bounds__(2 * LANES, 1)
 k_backward_pipe(DevModel<T> m, const T* __restrict__ ckpt, const T* __restrict__ tau, long long Tn, int k,
                 const T* __restrict__ gqT, const T* __restrict__ gqdT, const T* __restrict__ gtraj, T* gq0,
-                T* gqd0, T* gtau, T* gm_acc, T* ring) {
+                T* gqd0, T* gtau, T* gm_acc, T* stage2) {
   const int warp = threadIdx.x / LANES, lane = threadIdx.x % LANES;
   const bool consumer = warp == 0;
   const long long B = m.B;
@@ -468,7 +471,7 @@ k_backward_pipe(DevModel<T> m, const T* __restrict__ ckpt, const T* __restrict__
     const int nl = act ? m.nl[slot] : 0;
     const int nq = act ? (m.nqv[slot] & 0xffff) : 0, nv = act ? (m.nqv[slot] >> 16) : 0;
     const int tile_links = m.nl[unit * LANES];  // slots are sorted by link count: the tile's longest
-    T* stage = m.tape + (long long)unit * L * NTAPE * LANES;
+    T* stage[2] = {m.tape + (long long)unit * L * NTAPE * LANES, stage2 + (long long)unit * L * NTAPE * LANES};
     if (consumer && act) {
       const T* gprm = m.prm + (long long)unit * L * NPRM * LANES + lane;
       const int* gmeta = m.meta + (long long)unit * L * LANES + lane;
@@ -478,8 +481,6 @@ k_backward_pipe(DevModel<T> m, const T* __restrict__ ckpt, const T* __restrict__
       }
     }
     __syncthreads();
-    const Sys<T> sc{s_prm + lane, meta_l, s_tape + lane, s_adj + lane, nl, MS};
-    const Sys<T> sp{s_prm + lane, meta_l, stage + lane, nullptr, nl, MS};
     Col<T> gq{s_state + lane, LANES}, gqd{s_state + nqm * LANES + lane, LANES}, gm{s_gm + lane, LANES};
     if (consumer && act) {
       for (int d = 0; d < nqm; ++d) {
@@ -494,31 +495,34 @@ k_backward_pipe(DevModel<T> m, const T* __restrict__ ckpt, const T* __restrict__
       }
       for (int l = 0; l < nl; ++l) gm[l] = T(0);
     }
+    const int chunks = (int)((long long)tile_links * NTAPE * LANES * sizeof(T) / 16);
     for (long long t = Tn - 1; t >= 0; --t) {
-      if (!consumer) {  // producer: recompute step t into the staging tape
+      const int buf = (int)(t & 1);
+      if (!consumer) {  // producer: recompute step t on chip, then stage it
         __syncwarp();
-        if (t < Tn - 1) pair_sync(BAR_EMPTY);
+        if (t < Tn - 2) pair_sync(buf ? BAR_EMPTY1 : BAR_EMPTY0);
         if (act) {
+          const Sys<T> sp{s_prm + lane, meta_l, s_tape + lane, nullptr, nl, MS};
           const T* x = ckpt + t * NX * B + b;
           aba_forward<T, DT, true>(sp, Col<const T>{x, B}, Col<const T>{x + nqm * B, B},
                                    Col<const T>{tau + t * nvm * B + b, B}, g);
         }
+        __syncwarp();
+        const uint4* src = reinterpret_cast<const uint4*>(s_tape);
+        uint4* dst = reinterpret_cast<uint4*>(stage[buf]);
+        for (int i = lane; i < chunks; i += LANES) dst[i] = src[i];
         __threadfence();
         __syncwarp();
-        pair_arrive(BAR_FULL);
-      } else {  // consumer: the adjoint of step t from a shared-memory copy of its tape
+        pair_arrive(buf ? BAR_FULL1 : BAR_FULL0);
+      } else {  // consumer: the adjoint of step t, its tape read from staging buffer t & 1
         if (act)
           for (int d = 0; d < NX; ++d) cp_async(s_x + d * LANES + lane, ckpt + (t * NX + d) * B + b);
-        __syncwarp();
-        pair_sync(BAR_FULL);
-        const int chunks = (int)((long long)tile_links * NTAPE * LANES * sizeof(T) / 16);
-        for (int i = lane; i < chunks; i += LANES)
-          cp_async16(reinterpret_cast<char*>(s_tape) + 16LL * i, reinterpret_cast<const char*>(stage) + 16LL * i);
         cp_commit();
-        cp_wait_all();
         __syncwarp();
-        if (t > 0) pair_arrive(BAR_EMPTY);
+        pair_sync(buf ? BAR_FULL1 : BAR_FULL0);
+        cp_wait_all();
         if (act) {
+          const Sys<T> sc{s_prm + lane, meta_l, stage[buf] + lane, s_adj + lane, nl, MS};
           Col<const T> q{s_x + lane, LANES}, qd{s_x + nqm * LANES + lane, LANES};
           T* gt = gtau + t * nvm * B + b;
           step_adjoint<T, DT>(sc, q, qd, gq, gqd, Col<T>{gt, B}, gm, g, m.dt, m.integ);
@@ -530,6 +534,7 @@ k_backward_pipe(DevModel<T> m, const T* __restrict__ ckpt, const T* __restrict__
           }
         }
         __syncwarp();
+        if (t >= 2) pair_arrive(buf ? BAR_EMPTY1 : BAR_EMPTY0);
       }
     }
     if (consumer && act) {
@@ -733,7 +738,8 @@ int launch_backward(sim_handle* h, const void* ckpt, const void* tau, int64_t T_
     kern = backward_contact_kernel<T, DT>();
   } else if constexpr (sizeof(T) == 4) {  // on-chip modes: FP32 storage only
     bool piped = false;
-    if (k == 1 && T_ > 0 && (h->tape_space == SIM_TAPE_AUTO || h->tape_space == SIM_TAPE_PIPELINED)) {
+    if (k == 1 && T_ > 0 && h->tape2 &&
+        (h->tape_space == SIM_TAPE_AUTO || h->tape_space == SIM_TAPE_PIPELINED)) {
       // the pipelined two-warp adjoint, when its shared memory fits one block
       int limit = 0;
       cudaError_t e = cudaDeviceGetAttribute(&limit, cudaDevAttrMaxSharedMemoryPerBlockOptin, h->device);
@@ -766,7 +772,8 @@ int launch_backward(sim_handle* h, const void* ckpt, const void* tau, int64_t T_
   if (rc != SIM_OK) return rc;
   kern<<<grid, threads, shm, S(stream)>>>(m, (const T*)ckpt, (const T*)tau, (long long)T_, k,
                                            (const T*)gqT, (const T*)gqdT, (const T*)gtraj, (T*)gq0,
-                                           (T*)gqd0, (T*)gtau, (T*)h->gm_acc, (T*)work);
+                                           (T*)gqd0, (T*)gtau, (T*)h->gm_acc,
+                                           st == ST_PIPE ? (T*)h->tape2 : (T*)work);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return cuda_fail(h, e, "backward launch");
   if (gmass) {
