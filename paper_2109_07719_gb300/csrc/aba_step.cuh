@@ -18,6 +18,10 @@
 // quat' = normalize(quat + dt/2 quat (x) (w, 0)).
 #pragma once
 
+#if defined(ABASIM_HOST_CHECKS)
+#include <cstdlib>
+#endif
+
 #include "spatial.cuh"
 
 namespace abasim {
@@ -90,6 +94,60 @@ template <> SD void sincos_t<double>(double x, double* s, double* c) {
 }
 template <class T> SD T sqrt_t(T x) { return sqrt(x); }
 
+// Tape and adjoint layouts.  LAY_FULL holds every field (any tree, any joint).
+// The pipelined adjoint of serial chains of revolute joints uses two compact
+// layouts: LAY_CONS, the 81 tape fields and 33 adjoint fields the adjoint step
+// reads for such links, and LAY_PROD, the same 81 tape fields first (so one
+// contiguous copy per link hands them over) followed by the forward pass's own
+// scratch (rigid-body inertia and bias force, T_IA and T_PA).  Fields a compact
+// layout lacks are never touched for chain links; host builds with
+// ABASIM_HOST_CHECKS abort if one is.
+enum : int { LAY_FULL = 0, LAY_PROD = 1, LAY_CONS = 2 };
+constexpr int NTAPE_CONS = 81, NTAPE_PROD = 108, NADJ_CONS = 33;
+SD constexpr int cons_field(int f) {
+  return f < T_IA                      ? f
+         : f >= T_U && f < T_U + 6     ? 30 + (f - T_U)
+         : f == T_DI                   ? 36
+         : f == T_DI2                  ? 37
+         : f == T_u                    ? 38
+         : f >= T_Ia && f < T_Ia + 21  ? 39 + (f - T_Ia)
+         : f >= T_pa && f < T_pa + 6   ? 60 + (f - T_pa)
+         : f >= T_AP && f < T_AP + 6   ? 66 + (f - T_AP)
+         : f >= T_A && f < T_A + 6     ? 72 + (f - T_A)
+         : f == T_QDD                  ? 78
+         : f >= T_SC && f < T_SC + 2   ? 79 + (f - T_SC)
+                                       : -1;
+}
+SD constexpr int prod_field(int f) {
+  return cons_field(f) >= 0            ? cons_field(f)
+         : f >= T_IA && f < T_IA + 21  ? 81 + (f - T_IA)
+         : f >= T_PA && f < T_PA + 6   ? 102 + (f - T_PA)
+                                       : -1;
+}
+SD constexpr int cons_adj(int f) {
+  return f >= G_C && f < G_C + 6       ? f - G_C
+         : f >= G_E && f < G_E + 9     ? 6 + (f - G_E)
+         : f >= G_R && f < G_R + 3     ? 15 + (f - G_R)
+         : f >= G_U && f < G_U + 6     ? 18 + (f - G_U)
+         : f == G_D                    ? 24
+         : f == G_u                    ? 25
+         : f >= G_PA && f < G_PA + 6   ? 26 + (f - G_PA)
+         : f == G_M                    ? 32
+                                       : -1;
+}
+template <int TL> SD constexpr int tape_stride() { return TL == LAY_FULL ? NTAPE : TL == LAY_PROD ? NTAPE_PROD : NTAPE_CONS; }
+template <int AL> SD constexpr int adj_stride() { return AL == LAY_CONS ? NADJ_CONS : NADJ; }
+SD int lay_checked(int i) {
+#if defined(ABASIM_HOST_CHECKS) && !defined(__CUDA_ARCH__)
+  if (i < 0) abort();
+#endif
+  return i < 0 ? 0 : i;
+}
+template <int TL> SD int tape_field(int f) {
+  return TL == LAY_FULL ? f : lay_checked(TL == LAY_PROD ? prod_field(f) : cons_field(f));
+}
+template <int AL> SD int adj_field(int f) { return AL == LAY_CONS ? lay_checked(cons_adj(f)) : f; }
+
 // Strided column of one system: element d lives at p[d * B].
 template <class T> struct Col {
   T* p;
@@ -109,17 +167,17 @@ template <class T> SD T ctr(const T* ct, int l, int f) { return ct[(l * NCT + f)
 // The per-system view used by the step functions (pointers at this system's lane).
 // T is the arithmetic scalar, PT the stored type of the model constants (they
 // differ when T carries derivatives, e.g. a dual number for forward mode).
-template <class T, class PT = T> struct Sys {
+template <class T, class PT = T, int TL = LAY_FULL, int AL = LAY_FULL> struct Sys {
   const PT* prm;    // [maxL][NPRM][LANES] of this tile
   const int* meta;  // [maxL][LANES] (ints spaced mstride apart)
-  T* tape;          // [maxL][NTAPE][LANES]
-  T* adj;           // [maxL][NADJ][LANES]
+  T* tape;          // [maxL][tape_stride<TL>][LANES]
+  T* adj;           // [maxL][adj_stride<AL>][LANES]
   int nl;
   int mstride = 1;
   SD T P(int l, int f) const { return T(prm[(l * NPRM + f) * LANES]); }
   SD int M(int l) const { return meta[l * LANES * mstride]; }
-  SD T& tp(int l, int f) const { return tape[(l * NTAPE + f) * LANES]; }
-  SD T& ad(int l, int f) const { return adj[(l * NADJ + f) * LANES]; }
+  SD T& tp(int l, int f) const { return tape[(l * tape_stride<TL>() + tape_field<TL>(f)) * LANES]; }
+  SD T& ad(int l, int f) const { return adj[(l * adj_stride<AL>() + adj_field<AL>(f)) * LANES]; }
 
   // ---- field helpers
   SD V3<T> pv3(int l, int f) const { return {P(l, f), P(l, f + 1), P(l, f + 2)}; }
@@ -128,41 +186,41 @@ template <class T, class PT = T> struct Sys {
 };
 
 #define ABASIM_FIELD_IO(NAME, ACC)                                                                   \
-  template <class T, class PT> SD V3<T> NAME##_v3(const Sys<T, PT>& s, int l, int f) {                              \
+  template <class T, class PT, int TL, int AL> SD V3<T> NAME##_v3(const Sys<T, PT, TL, AL>& s, int l, int f) {                              \
     return {s.ACC(l, f), s.ACC(l, f + 1), s.ACC(l, f + 2)};                                           \
   }                                                                                                  \
-  template <class T, class PT> SD void NAME##_v3(const Sys<T, PT>& s, int l, int f, V3<T> v) {                      \
+  template <class T, class PT, int TL, int AL> SD void NAME##_v3(const Sys<T, PT, TL, AL>& s, int l, int f, V3<T> v) {                      \
     s.ACC(l, f) = v.x; s.ACC(l, f + 1) = v.y; s.ACC(l, f + 2) = v.z;                                  \
   }                                                                                                  \
-  template <class T, class PT> SD SV<T> NAME##_sv(const Sys<T, PT>& s, int l, int f) {                              \
+  template <class T, class PT, int TL, int AL> SD SV<T> NAME##_sv(const Sys<T, PT, TL, AL>& s, int l, int f) {                              \
     return {NAME##_v3(s, l, f), NAME##_v3(s, l, f + 3)};                                              \
   }                                                                                                  \
-  template <class T, class PT> SD void NAME##_sv(const Sys<T, PT>& s, int l, int f, SV<T> v) {                      \
+  template <class T, class PT, int TL, int AL> SD void NAME##_sv(const Sys<T, PT, TL, AL>& s, int l, int f, SV<T> v) {                      \
     NAME##_v3(s, l, f, v.w); NAME##_v3(s, l, f + 3, v.v);                                             \
   }                                                                                                  \
-  template <class T, class PT> SD M3<T> NAME##_m3(const Sys<T, PT>& s, int l, int f) {                              \
+  template <class T, class PT, int TL, int AL> SD M3<T> NAME##_m3(const Sys<T, PT, TL, AL>& s, int l, int f) {                              \
     M3<T> m; for (int i = 0; i < 9; ++i) m.a[i] = s.ACC(l, f + i); return m;                          \
   }                                                                                                  \
-  template <class T, class PT> SD void NAME##_m3(const Sys<T, PT>& s, int l, int f, const M3<T>& m) {               \
+  template <class T, class PT, int TL, int AL> SD void NAME##_m3(const Sys<T, PT, TL, AL>& s, int l, int f, const M3<T>& m) {               \
     for (int i = 0; i < 9; ++i) s.ACC(l, f + i) = m.a[i];                                             \
   }                                                                                                  \
-  template <class T, class PT> SD S3<T> NAME##_s3(const Sys<T, PT>& s, int l, int f) {                              \
+  template <class T, class PT, int TL, int AL> SD S3<T> NAME##_s3(const Sys<T, PT, TL, AL>& s, int l, int f) {                              \
     return {s.ACC(l, f), s.ACC(l, f + 1), s.ACC(l, f + 2), s.ACC(l, f + 3), s.ACC(l, f + 4), s.ACC(l, f + 5)}; \
   }                                                                                                  \
-  template <class T, class PT> SD void NAME##_s3(const Sys<T, PT>& s, int l, int f, const S3<T>& v) {               \
+  template <class T, class PT, int TL, int AL> SD void NAME##_s3(const Sys<T, PT, TL, AL>& s, int l, int f, const S3<T>& v) {               \
     s.ACC(l, f) = v.xx; s.ACC(l, f + 1) = v.yy; s.ACC(l, f + 2) = v.zz;                               \
     s.ACC(l, f + 3) = v.xy; s.ACC(l, f + 4) = v.xz; s.ACC(l, f + 5) = v.yz;                           \
   }                                                                                                  \
-  template <class T, class PT> SD SI<T> NAME##_si(const Sys<T, PT>& s, int l, int f) {                              \
+  template <class T, class PT, int TL, int AL> SD SI<T> NAME##_si(const Sys<T, PT, TL, AL>& s, int l, int f) {                              \
     return {NAME##_s3(s, l, f), NAME##_m3(s, l, f + 6), NAME##_s3(s, l, f + 15)};                     \
   }                                                                                                  \
-  template <class T, class PT> SD void NAME##_si(const Sys<T, PT>& s, int l, int f, const SI<T>& v) {               \
+  template <class T, class PT, int TL, int AL> SD void NAME##_si(const Sys<T, PT, TL, AL>& s, int l, int f, const SI<T>& v) {               \
     NAME##_s3(s, l, f, v.A); NAME##_m3(s, l, f + 6, v.B); NAME##_s3(s, l, f + 15, v.C);               \
   }                                                                                                  \
-  template <class T, class PT> SD XF<T> NAME##_xf(const Sys<T, PT>& s, int l, int f) {                              \
+  template <class T, class PT, int TL, int AL> SD XF<T> NAME##_xf(const Sys<T, PT, TL, AL>& s, int l, int f) {                              \
     return {NAME##_m3(s, l, f), NAME##_v3(s, l, f + 9)};                                              \
   }                                                                                                  \
-  template <class T, class PT> SD void NAME##_xf(const Sys<T, PT>& s, int l, int f, const XF<T>& v) {               \
+  template <class T, class PT, int TL, int AL> SD void NAME##_xf(const Sys<T, PT, TL, AL>& s, int l, int f, const XF<T>& v) {               \
     NAME##_m3(s, l, f, v.E); NAME##_v3(s, l, f + 9, v.r);                                             \
   }
 
@@ -214,12 +272,12 @@ template <class T> SD SV<T> chol6_solve(const T* L, SV<T> b) {
 // The articulated-inertia solves (D = S^T I^A S, 1/D, U D^-1 U^T, the free root's
 // 6x6 solve) run in the scalar DT: the storage type T, or double in the mixed
 // FP32 + FP64 mode.  1/D is kept on the tape as a hi/lo pair of T words.
-template <class T, class DT, class PT> SD void put_di(const Sys<T, PT>& s, int l, DT di) {
+template <class T, class DT, class PT, int TL, int AL> SD void put_di(const Sys<T, PT, TL, AL>& s, int l, DT di) {
   const T hi = (T)di;
   s.tp(l, T_DI) = hi;
   s.tp(l, T_DI2) = (T)(di - (DT)hi);
 }
-template <class T, class DT, class PT> SD DT get_di(const Sys<T, PT>& s, int l) {
+template <class T, class DT, class PT, int TL, int AL> SD DT get_di(const Sys<T, PT, TL, AL>& s, int l) {
   return (DT)s.tp(l, T_DI) + (DT)s.tp(l, T_DI2);
 }
 template <class DT, class T> SD SI<DT> si_cast(const SI<T>& I) {
@@ -258,8 +316,8 @@ template <class T, class DT> SD SV<T> spd_solve(const SI<T>& IA, SV<T> b) {
 // link and its parent ride in registers when the parent is the previous link (the
 // whole of a serial chain); other parents go through the tape.  Each iteration
 // loads what it needs before it stores anything, so the loads overlap.
-template <class T, class DT, bool ADJ = true, class PT>
-SD void aba_forward(const Sys<T, PT>& s, Col<const T> q, Col<const T> qd, Col<const T> tau, V3<T> grav) {
+template <class T, class DT, bool ADJ = true, class PT, int TL, int AL>
+SD void aba_forward(const Sys<T, PT, TL, AL>& s, Col<const T> q, Col<const T> qd, Col<const T> tau, V3<T> grav) {
   const int nl = s.nl;
   // jcalc + pass 1 (root -> leaves)
   SV<T> v_prev = zeroSV<T>();
@@ -397,8 +455,8 @@ SD void aba_forward(const Sys<T, PT>& s, Col<const T> q, Col<const T> qd, Col<co
 
 // Integrates x -> x' in place from the qdd on the tape, plus the contact
 // velocity change C_DV of the contact tape ct when given.
-template <class T, class PT>
-SD void integrate(const Sys<T, PT>& s, Col<T> q, Col<T> qd, T dt, int integ, const T* ct = nullptr) {
+template <class T, class PT, int TL, int AL>
+SD void integrate(const Sys<T, PT, TL, AL>& s, Col<T> q, Col<T> qd, T dt, int integ, const T* ct = nullptr) {
   for (int l = 0; l < s.nl; ++l) {
     const int m = s.M(l);
     const int jt = meta_jtype(m), qo = meta_qoff(m), vo = meta_voff(m);
@@ -437,8 +495,8 @@ SD void integrate(const Sys<T, PT>& s, Col<T> q, Col<T> qd, T dt, int integ, con
 // Integrator adjoint of one link (folded into the pass-3 adjoint loop): turns the
 // adjoint of x^{k+1} held in (gq, gqd) into the direct part of the adjoint of x^k
 // for this link's coordinates and returns the adjoint of its qdd in qddb[0..nv).
-template <class T, class PT>
-SD void integrator_adjoint(const Sys<T, PT>& s, int l, int jt, int qo, int vo, Col<const T> q,
+template <class T, class PT, int TL, int AL>
+SD void integrator_adjoint(const Sys<T, PT, TL, AL>& s, int l, int jt, int qo, int vo, Col<const T> q,
                            Col<const T> qd, Col<T> gq, Col<T> gqd, T dt, int integ, T* qddb,
                            const T* ct = nullptr) {
   const T half = T(0.5);
@@ -515,8 +573,8 @@ SD void integrator_adjoint(const Sys<T, PT>& s, int l, int jt, int qo, int vo, C
 // (tree) children and are zeroed first only for links that have such children.
 // With a contact tape ct, the integrator adjoint has already run (its qdd
 // adjoint is in C_QDDB) and the contact adjoint's B_* terms are added in.
-template <class T, class DT, class PT>
-SD void step_adjoint(const Sys<T, PT>& s, Col<const T> q, Col<const T> qd, Col<T> gq, Col<T> gqd,
+template <class T, class DT, class PT, int TL, int AL>
+SD void step_adjoint(const Sys<T, PT, TL, AL>& s, Col<const T> q, Col<const T> qd, Col<T> gq, Col<T> gqd,
                      Col<T> gtau, Col<T> gm, V3<T> grav, T dt, int integ, const T* ct = nullptr) {
   const int nl = s.nl;
   const T half = T(0.5);

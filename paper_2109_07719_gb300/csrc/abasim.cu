@@ -292,6 +292,12 @@ int sim_create(const sim_model_desc* d, sim_handle** out) {
     h->nv_max = std::max(h->nv_max, vo);
   }
   cudaDeviceGetAttribute(&h->sms, cudaDevAttrMultiProcessorCount, h->device);
+  h->all_chains = !any_contact;
+  for (int b = 0; b < B && h->all_chains; ++b)
+    for (int l = 0; l < nl_sys[b]; ++l) {
+      const int i = d->sys_link_offset[b] + l;
+      if (d->joint_type[i] != SIM_REVOLUTE || d->parent[i] != l - 1) h->all_chains = false;
+    }
   int rc = h->precision == SIM_FP64 ? upload<double>(h, prm) : upload<float>(h, prm);
   auto alloc = [&](void** p, size_t bytes, const char* what) -> int {
     cudaError_t e = cudaMalloc(p, bytes);
@@ -311,14 +317,6 @@ int sim_create(const sim_model_desc* d, sim_handle** out) {
   if (rc == SIM_OK) rc = put(h->link_slot, slot.data(), slot.size() * sizeof(int));
   if (rc == SIM_OK) rc = alloc(&h->tape, (size_t)maxL * NTAPE * Bpad * h->scalar, "tape");
   if (rc == SIM_OK) rc = alloc(&h->adj, (size_t)maxL * NADJ * Bpad * h->scalar, "adjoint tape");
-  if (rc == SIM_OK && h->precision != SIM_FP64 && !any_contact) {
-    // the pipelined adjoint's second staging tape, when its block fits in shared memory
-    int limit = 0;
-    cudaDeviceGetAttribute(&limit, cudaDevAttrMaxSharedMemoryPerBlockOptin, h->device);
-    const size_t pipe = ((size_t)maxL * (NTAPE + NADJ + NPRM + 2) + 2 * (size_t)(h->nq_max + h->nv_max)) *
-                        LANES * sizeof(float);
-    if (pipe <= (size_t)limit) rc = alloc(&h->tape2, (size_t)maxL * NTAPE * Bpad * h->scalar, "staging tape");
-  }
   if (rc == SIM_OK) rc = alloc(&h->gm_acc, (size_t)maxL * B * h->scalar, "mass-gradient buffer");
   if (rc == SIM_OK) rc = alloc((void**)&h->status, B * sizeof(int), "status");
   if (rc == SIM_OK) rc = alloc((void**)&h->sys_of_slot, B * sizeof(int), "slot order");
@@ -346,7 +344,7 @@ int sim_create(const sim_model_desc* d, sim_handle** out) {
 
 void sim_destroy(sim_handle* h) {
   if (!h) return;
-  void* ptrs[] = {h->prm, h->meta, h->nl, h->nqv, h->tape, h->tape2, h->adj, h->gm_acc, h->link_slot,
+  void* ptrs[] = {h->prm, h->meta, h->nl, h->nqv, h->tape, h->adj, h->gm_acc, h->link_slot,
                   h->status, h->sys_of_slot, h->counter, h->ctape, h->csys};
   for (void* p : ptrs)
     if (p) cudaFree(p);

@@ -29,7 +29,6 @@ struct sim_handle {
   int* nl = nullptr;         // [B]
   int* nqv = nullptr;        // [B]  nq | nv << 16
   void* tape = nullptr;      // [maxL][NTAPE][B] scalar
-  void* tape2 = nullptr;     // second staging tape of the pipelined adjoint (FP32 storage, small trees)
   void* adj = nullptr;       // [maxL][NADJ][B] scalar
   void* gm_acc = nullptr;    // [maxL][B] scalar
   int* link_slot = nullptr;  // [L_total] -> l * B + slot
@@ -45,6 +44,7 @@ struct sim_handle {
   int replay = SIM_REPLAY_SEGMENT;
   int last_storage = 0, last_storage_bwd = 0;
   int sms = 0;
+  bool all_chains = false;   // every system a serial chain of revolute joints (the pipelined adjoint)
   std::vector<int> h_sys_of_slot;
   std::string err;
 };

@@ -416,38 +416,41 @@ __global__ void k_backward(DevModel<T> m, const T* __restrict__ ckpt, const T* _
 }
 
 // ------------------------------------------------------------------ pipelined adjoint
-// Two warps per 32-system tile (k = 1 only): the producer warp recomputes step
-// t's forward intermediates (the tape) from the checkpoint x^t in its own
-// shared-memory tape, then copies it out (16-byte vector moves) to one of two
-// staging tapes of the tile in global memory (L2-resident); meanwhile the
-// consumer warp runs the adjoint of step t + 1 reading its tape from the other
-// staging buffer, with its adjoint accumulators, state adjoint and mass-gradient
-// sums in shared memory.  Step t's recompute does not depend on step t + 1's
-// adjoint, so the two overlap.  Hand-off by named barriers (hardware barriers:
-// no spinning), one pair per staging buffer b: FULL(b) (the producer arrives
-// when buffer b holds its step, the consumer waits) and EMPTY(b) (the consumer
-// arrives when it has finished a step from buffer b that the producer will
-// reuse, the producer waits before overwriting).  Per tile and buffer both warps
-// execute the same number of operations whatever their systems (inactive lanes
-// included), and a warp never arrives twice at a barrier before its partner's
-// matching wait: the producer's next arrival at FULL(b) comes after its wait on
-// EMPTY(b), which follows the consumer's wait on FULL(b), and vice versa.
-enum : int { BAR_FULL0 = 1, BAR_FULL1 = 2, BAR_EMPTY0 = 3, BAR_EMPTY1 = 4 };
-__device__ __forceinline__ void pair_sync(int id) { asm volatile("bar.sync %0, 64;\n" ::"r"(id) : "memory"); }
-__device__ __forceinline__ void pair_arrive(int id) { asm volatile("bar.arrive %0, 64;\n" ::"r"(id) : "memory"); }
+// Two warps per 32-system tile, for batches of serial revolute chains with a
+// checkpoint every step: the producer warp recomputes step t's forward
+// intermediates from the checkpoint x^t into its shared-memory tape (compact
+// layout LAY_PROD) while the consumer warp runs the adjoint of step t + 1 from
+// its own shared-memory tape (LAY_CONS) with compact adjoint accumulators.  Step
+// t's recompute does not depend on step t + 1's adjoint, so the two overlap.  At
+// each step the consumer copies the 81 fields per link it reads out of the
+// producer's tape (one contiguous block per link, 16-byte moves) and releases it.
+// Hand-off by two named barriers (hardware barriers: no spinning): FULL (the
+// producer arrives when its tape holds step t, the consumer waits) and EMPTY (the
+// consumer arrives once its copy is done, the producer waits before computing
+// the next step).  Per tile both warps execute FULL Tn times and EMPTY Tn - 1
+// times whatever their systems (inactive lanes included), and neither arrives
+// twice before the other's matching wait: the producer's next FULL arrival
+// follows its EMPTY wait, which follows the consumer's FULL wait, and the
+// consumer's next EMPTY arrival follows its FULL wait, which follows the
+// producer's EMPTY wait.
+enum : int { BAR_FULL = 1, BAR_EMPTY = 2 };
+__device__ __forceinline__ void pair_sync_full() { asm volatile("bar.sync 1, 64;\n" ::: "memory"); }
+__device__ __forceinline__ void pair_arrive_full() { asm volatile("bar.arrive 1, 64;\n" ::: "memory"); }
+__device__ __forceinline__ void pair_sync_empty() { asm volatile("bar.sync 2, 64;\n" ::: "memory"); }
+__device__ __forceinline__ void pair_arrive_empty() { asm volatile("bar.arrive 2, 64;\n" ::: "memory"); }
 
-// Shared memory of one pipelined block, in scalars per lane: the producer's tape,
-// the consumer's adjoint accumulators, model constants, meta words, state
-// adjoint, mass-gradient sums and the consumer's copy of x^t.
+// Shared memory of one pipelined block, in scalars per lane: the producer's and
+// the consumer's tapes, the adjoint accumulators, meta words, the state adjoint,
+// the mass-gradient sums and the consumer's copy of x^t.
 __host__ __device__ __forceinline__ long long pipe_smem_per_tile(int maxL, int nx) {
-  return (long long)maxL * (NTAPE + NADJ + NPRM + 1 + 1) + 2LL * nx;
+  return (long long)maxL * (NTAPE_PROD + NTAPE_CONS + NADJ_CONS + 1 + 1) + 2LL * nx;
 }
 
 template <class T, class DT>
 __global__ void __launch_bounds__(2 * LANES, 1)
 k_backward_pipe(DevModel<T> m, const T* __restrict__ ckpt, const T* __restrict__ tau, long long Tn, int k,
                 const T* __restrict__ gqT, const T* __restrict__ gqdT, const T* __restrict__ gtraj, T* gq0,
-                T* gqd0, T* gtau, T* gm_acc, T* stage2) {
+                T* gqd0, T* gtau, T* gm_acc, T* ring) {
   const int warp = threadIdx.x / LANES, lane = threadIdx.x % LANES;
   const bool consumer = warp == 0;
   const long long B = m.B;
@@ -455,10 +458,10 @@ k_backward_pipe(DevModel<T> m, const T* __restrict__ ckpt, const T* __restrict__
   const long long L = m.maxL;
   const V3<T> g{m.g0, m.g1, m.g2};
   constexpr int MS = (int)(sizeof(T) / sizeof(int));
-  T* s_tape = reinterpret_cast<T*>(g_smem);
-  T* s_adj = s_tape + L * NTAPE * LANES;
-  T* s_prm = s_adj + L * NADJ * LANES;
-  T* s_meta = s_prm + L * NPRM * LANES;
+  T* s_ptape = reinterpret_cast<T*>(g_smem);
+  T* s_ctape = s_ptape + L * NTAPE_PROD * LANES;
+  T* s_adj = s_ctape + L * NTAPE_CONS * LANES;
+  T* s_meta = s_adj + L * NADJ_CONS * LANES;
   T* s_state = s_meta + L * LANES;
   T* s_gm = s_state + (long long)NX * LANES;
   T* s_x = s_gm + L * LANES;
@@ -471,14 +474,10 @@ k_backward_pipe(DevModel<T> m, const T* __restrict__ ckpt, const T* __restrict__
     const int nl = act ? m.nl[slot] : 0;
     const int nq = act ? (m.nqv[slot] & 0xffff) : 0, nv = act ? (m.nqv[slot] >> 16) : 0;
     const int tile_links = m.nl[unit * LANES];  // slots are sorted by link count: the tile's longest
-    T* stage[2] = {m.tape + (long long)unit * L * NTAPE * LANES, stage2 + (long long)unit * L * NTAPE * LANES};
+    const T* gprm = m.prm + (long long)unit * L * NPRM * LANES + lane;
     if (consumer && act) {
-      const T* gprm = m.prm + (long long)unit * L * NPRM * LANES + lane;
       const int* gmeta = m.meta + (long long)unit * L * LANES + lane;
-      for (int l = 0; l < nl; ++l) {
-        for (int f = 0; f < NPRM; ++f) s_prm[(l * NPRM + f) * LANES + lane] = gprm[(l * NPRM + f) * LANES];
-        meta_l[l * LANES * MS] = gmeta[l * LANES];
-      }
+      for (int l = 0; l < nl; ++l) meta_l[l * LANES * MS] = gmeta[l * LANES];
     }
     __syncthreads();
     Col<T> gq{s_state + lane, LANES}, gqd{s_state + nqm * LANES + lane, LANES}, gm{s_gm + lane, LANES};
@@ -495,34 +494,36 @@ k_backward_pipe(DevModel<T> m, const T* __restrict__ ckpt, const T* __restrict__
       }
       for (int l = 0; l < nl; ++l) gm[l] = T(0);
     }
-    const int chunks = (int)((long long)tile_links * NTAPE * LANES * sizeof(T) / 16);
+    constexpr int CH = NTAPE_CONS * LANES * (int)sizeof(T) / 16;  // 16-byte chunks of one link's fields
     for (long long t = Tn - 1; t >= 0; --t) {
-      const int buf = (int)(t & 1);
-      if (!consumer) {  // producer: recompute step t on chip, then stage it
+      if (!consumer) {  // producer: recompute step t on chip
         __syncwarp();
-        if (t < Tn - 2) pair_sync(buf ? BAR_EMPTY1 : BAR_EMPTY0);
+        if (t < Tn - 1) pair_sync_empty();
         if (act) {
-          const Sys<T> sp{s_prm + lane, meta_l, s_tape + lane, nullptr, nl, MS};
+          const Sys<T, T, LAY_PROD, LAY_FULL> sp{gprm, meta_l, s_ptape + lane, nullptr, nl, MS};
           const T* x = ckpt + t * NX * B + b;
           aba_forward<T, DT, true>(sp, Col<const T>{x, B}, Col<const T>{x + nqm * B, B},
                                    Col<const T>{tau + t * nvm * B + b, B}, g);
         }
+        __threadfence_block();
         __syncwarp();
-        const uint4* src = reinterpret_cast<const uint4*>(s_tape);
-        uint4* dst = reinterpret_cast<uint4*>(stage[buf]);
-        for (int i = lane; i < chunks; i += LANES) dst[i] = src[i];
-        __threadfence();
-        __syncwarp();
-        pair_arrive(buf ? BAR_FULL1 : BAR_FULL0);
-      } else {  // consumer: the adjoint of step t, its tape read from staging buffer t & 1
+        pair_arrive_full();
+      } else {  // consumer: copy step t's fields out of the producer's tape, then its adjoint
         if (act)
           for (int d = 0; d < NX; ++d) cp_async(s_x + d * LANES + lane, ckpt + (t * NX + d) * B + b);
         cp_commit();
         __syncwarp();
-        pair_sync(buf ? BAR_FULL1 : BAR_FULL0);
+        pair_sync_full();
+        for (int i = lane; i < tile_links * CH; i += LANES) {
+          const int l = i / CH, c = i - l * CH;
+          reinterpret_cast<uint4*>(s_ctape + (long long)l * NTAPE_CONS * LANES)[c] =
+              reinterpret_cast<const uint4*>(s_ptape + (long long)l * NTAPE_PROD * LANES)[c];
+        }
+        __syncwarp();
+        if (t > 0) pair_arrive_empty();
         cp_wait_all();
         if (act) {
-          const Sys<T> sc{s_prm + lane, meta_l, stage[buf] + lane, s_adj + lane, nl, MS};
+          const Sys<T, T, LAY_CONS, LAY_CONS> sc{gprm, meta_l, s_ctape + lane, s_adj + lane, nl, MS};
           Col<const T> q{s_x + lane, LANES}, qd{s_x + nqm * LANES + lane, LANES};
           T* gt = gtau + t * nvm * B + b;
           step_adjoint<T, DT>(sc, q, qd, gq, gqd, Col<T>{gt, B}, gm, g, m.dt, m.integ);
@@ -534,7 +535,6 @@ k_backward_pipe(DevModel<T> m, const T* __restrict__ ckpt, const T* __restrict__
           }
         }
         __syncwarp();
-        if (t >= 2) pair_arrive(buf ? BAR_EMPTY1 : BAR_EMPTY0);
       }
     }
     if (consumer && act) {
@@ -738,7 +738,7 @@ int launch_backward(sim_handle* h, const void* ckpt, const void* tau, int64_t T_
     kern = backward_contact_kernel<T, DT>();
   } else if constexpr (sizeof(T) == 4) {  // on-chip modes: FP32 storage only
     bool piped = false;
-    if (k == 1 && T_ > 0 && h->tape2 &&
+    if (k == 1 && T_ > 0 && h->all_chains &&
         (h->tape_space == SIM_TAPE_AUTO || h->tape_space == SIM_TAPE_PIPELINED)) {
       // the pipelined two-warp adjoint, when its shared memory fits one block
       int limit = 0;
@@ -756,7 +756,8 @@ int launch_backward(sim_handle* h, const void* ckpt, const void* tau, int64_t T_
       }
     }
     if (!piped && h->tape_space == SIM_TAPE_PIPELINED)
-      return fail(h, SIM_EUNSUPPORTED, "the pipelined adjoint needs k = 1 and a tile that fits in shared memory");
+      return fail(h, SIM_EUNSUPPORTED,
+                  "the pipelined adjoint needs k = 1, serial revolute chains and a tile that fits in shared memory");
     if (!piped) {
       const BackwardKernel<T> k_hyb = backward_kernel<T, DT, ST_HYBRID>();
       const BackwardKernel<T> k_smem = backward_kernel<T, DT, ST_SMEM>();
@@ -772,8 +773,7 @@ int launch_backward(sim_handle* h, const void* ckpt, const void* tau, int64_t T_
   if (rc != SIM_OK) return rc;
   kern<<<grid, threads, shm, S(stream)>>>(m, (const T*)ckpt, (const T*)tau, (long long)T_, k,
                                            (const T*)gqT, (const T*)gqdT, (const T*)gtraj, (T*)gq0,
-                                           (T*)gqd0, (T*)gtau, (T*)h->gm_acc,
-                                           st == ST_PIPE ? (T*)h->tape2 : (T*)work);
+                                           (T*)gqd0, (T*)gtau, (T*)h->gm_acc, (T*)work);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return cuda_fail(h, e, "backward launch");
   if (gmass) {
