@@ -99,11 +99,13 @@ template <class T> SD T sqrt_t(T x) { return sqrt(x); }
 // layouts: LAY_CONS, the 81 tape fields and 33 adjoint fields the adjoint step
 // reads for such links, and LAY_PROD, the same 81 tape fields first (so one
 // contiguous copy per link hands them over) followed by the forward pass's own
-// scratch (rigid-body inertia and bias force, T_IA and T_PA).  Fields a compact
+// scratch, the bias force T_PA (in LAY_PROD the inward pass recomputes each
+// link's rigid-body inertia from the model constants instead of storing it).
+// Fields a compact
 // layout lacks are never touched for chain links; host builds with
 // ABASIM_HOST_CHECKS abort if one is.
 enum : int { LAY_FULL = 0, LAY_PROD = 1, LAY_CONS = 2 };
-constexpr int NTAPE_CONS = 81, NTAPE_PROD = 108, NADJ_CONS = 33;
+constexpr int NTAPE_CONS = 81, NTAPE_PROD = 87, NADJ_CONS = 33;
 SD constexpr int cons_field(int f) {
   return f < T_IA                      ? f
          : f >= T_U && f < T_U + 6     ? 30 + (f - T_U)
@@ -120,8 +122,7 @@ SD constexpr int cons_field(int f) {
 }
 SD constexpr int prod_field(int f) {
   return cons_field(f) >= 0            ? cons_field(f)
-         : f >= T_IA && f < T_IA + 21  ? 81 + (f - T_IA)
-         : f >= T_PA && f < T_PA + 6   ? 102 + (f - T_PA)
+         : f >= T_PA && f < T_PA + 6   ? 81 + (f - T_PA)
                                        : -1;
 }
 SD constexpr int cons_adj(int f) {
@@ -355,7 +356,7 @@ SD void aba_forward(const Sys<T, PT, TL, AL>& s, Col<const T> q, Col<const T> qd
     tp_sv(s, l, T_V, v);
     tp_sv(s, l, T_C, c);
     if (ADJ) tp_sv(s, l, T_H, h);
-    tp_si(s, l, T_IA, I);
+    if (TL != LAY_PROD) tp_si(s, l, T_IA, I);
     tp_sv(s, l, T_PA, crossf(v, h));
     if (ADJ && jt == J_REVOLUTE) {
       s.tp(l, T_SC) = sn;
@@ -370,7 +371,7 @@ SD void aba_forward(const Sys<T, PT, TL, AL>& s, Col<const T> q, Col<const T> qd
   for (int l = nl - 1; l >= 0; --l) {
     const int m = s.M(l);
     const int par = meta_parent(m), jt = meta_jtype(m), vo = meta_voff(m);
-    SI<T> IA = tp_si(s, l, T_IA);
+    SI<T> IA = TL == LAY_PROD ? rbi(s.P(l, P_M), s.pv3(l, P_C), s.ps3(l, P_IC)) : tp_si(s, l, T_IA);
     SV<T> pA = tp_sv(s, l, T_PA);
     if (carry) {
       IA += cI;

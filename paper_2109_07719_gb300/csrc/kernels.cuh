@@ -440,10 +440,11 @@ __device__ __forceinline__ void pair_sync_empty() { asm volatile("bar.sync 2, 64
 __device__ __forceinline__ void pair_arrive_empty() { asm volatile("bar.arrive 2, 64;\n" ::: "memory"); }
 
 // Shared memory of one pipelined block, in scalars per lane: the producer's and
-// the consumer's tapes, the adjoint accumulators, meta words, the state adjoint,
-// the mass-gradient sums and the consumer's copy of x^t.
-__host__ __device__ __forceinline__ long long pipe_smem_per_tile(int maxL, int nx) {
-  return (long long)maxL * (NTAPE_PROD + NTAPE_CONS + NADJ_CONS + 1 + 1) + 2LL * nx;
+// the consumer's tapes, the adjoint accumulators, model constants, meta words,
+// the state adjoint, the mass-gradient sums, the consumer's copy of x^t and the
+// producer's double-buffered (x^t, tau^t) fetched one step ahead.
+__host__ __device__ __forceinline__ long long pipe_smem_per_tile(int maxL, int nx, int nv) {
+  return (long long)maxL * (NTAPE_PROD + NTAPE_CONS + NADJ_CONS + NPRM + 1 + 1) + 2LL * nx + 2LL * (nx + nv);
 }
 
 template <class T, class DT>
@@ -461,10 +462,13 @@ k_backward_pipe(DevModel<T> m, const T* __restrict__ ckpt, const T* __restrict__
   T* s_ptape = reinterpret_cast<T*>(g_smem);
   T* s_ctape = s_ptape + L * NTAPE_PROD * LANES;
   T* s_adj = s_ctape + L * NTAPE_CONS * LANES;
-  T* s_meta = s_adj + L * NADJ_CONS * LANES;
+  T* s_prm = s_adj + L * NADJ_CONS * LANES;
+  T* s_meta = s_prm + L * NPRM * LANES;
   T* s_state = s_meta + L * LANES;
   T* s_gm = s_state + (long long)NX * LANES;
   T* s_x = s_gm + L * LANES;
+  T* s_in = s_x + (long long)NX * LANES;  // [2][NX + nvm][LANES]
+  const int W = NX + nvm;
   int* meta_l = reinterpret_cast<int*>(s_meta + lane);
   int unit = m.persistent ? next_unit(m.counter) : (int)blockIdx.x;
   while ((long long)unit * LANES < B) {
@@ -474,12 +478,26 @@ k_backward_pipe(DevModel<T> m, const T* __restrict__ ckpt, const T* __restrict__
     const int nl = act ? m.nl[slot] : 0;
     const int nq = act ? (m.nqv[slot] & 0xffff) : 0, nv = act ? (m.nqv[slot] >> 16) : 0;
     const int tile_links = m.nl[unit * LANES];  // slots are sorted by link count: the tile's longest
-    const T* gprm = m.prm + (long long)unit * L * NPRM * LANES + lane;
     if (consumer && act) {
+      const T* gprm = m.prm + (long long)unit * L * NPRM * LANES + lane;
       const int* gmeta = m.meta + (long long)unit * L * LANES + lane;
-      for (int l = 0; l < nl; ++l) meta_l[l * LANES * MS] = gmeta[l * LANES];
+      for (int l = 0; l < nl; ++l) {
+        for (int f = 0; f < NPRM; ++f) s_prm[(l * NPRM + f) * LANES + lane] = gprm[(l * NPRM + f) * LANES];
+        meta_l[l * LANES * MS] = gmeta[l * LANES];
+      }
     }
     __syncthreads();
+    const T* sprm = s_prm + lane;
+    // the producer's inputs of step t: x^t and tau^t, fetched one step ahead
+    auto fetch = [&](long long t, int buf) {
+      T* dst = s_in + buf * W * LANES + lane;
+      for (int d = 0; d < NX; ++d) cp_async(dst + d * LANES, ckpt + (t * NX + d) * B + b);
+      for (int d = 0; d < nvm; ++d) cp_async(dst + (NX + d) * LANES, tau + (t * nvm + d) * B + b);
+    };
+    if (!consumer) {
+      if (act && Tn > 0) fetch(Tn - 1, (int)((Tn - 1) & 1));
+      cp_commit();
+    }
     Col<T> gq{s_state + lane, LANES}, gqd{s_state + nqm * LANES + lane, LANES}, gm{s_gm + lane, LANES};
     if (consumer && act) {
       for (int d = 0; d < nqm; ++d) {
@@ -497,13 +515,16 @@ k_backward_pipe(DevModel<T> m, const T* __restrict__ ckpt, const T* __restrict__
     constexpr int CH = NTAPE_CONS * LANES * (int)sizeof(T) / 16;  // 16-byte chunks of one link's fields
     for (long long t = Tn - 1; t >= 0; --t) {
       if (!consumer) {  // producer: recompute step t on chip
+        if (act && t > 0) fetch(t - 1, (int)((t - 1) & 1));
+        cp_commit();
+        cp_wait_all_but_newest();
         __syncwarp();
         if (t < Tn - 1) pair_sync_empty();
         if (act) {
-          const Sys<T, T, LAY_PROD, LAY_FULL> sp{gprm, meta_l, s_ptape + lane, nullptr, nl, MS};
-          const T* x = ckpt + t * NX * B + b;
-          aba_forward<T, DT, true>(sp, Col<const T>{x, B}, Col<const T>{x + nqm * B, B},
-                                   Col<const T>{tau + t * nvm * B + b, B}, g);
+          const Sys<T, T, LAY_PROD, LAY_FULL> sp{sprm, meta_l, s_ptape + lane, nullptr, nl, MS};
+          const T* x = s_in + (t & 1) * W * LANES + lane;
+          aba_forward<T, DT, true>(sp, Col<const T>{x, LANES}, Col<const T>{x + nqm * LANES, LANES},
+                                   Col<const T>{x + NX * LANES, LANES}, g);
         }
         __threadfence_block();
         __syncwarp();
@@ -523,7 +544,7 @@ k_backward_pipe(DevModel<T> m, const T* __restrict__ ckpt, const T* __restrict__
         if (t > 0) pair_arrive_empty();
         cp_wait_all();
         if (act) {
-          const Sys<T, T, LAY_CONS, LAY_CONS> sc{gprm, meta_l, s_ctape + lane, s_adj + lane, nl, MS};
+          const Sys<T, T, LAY_CONS, LAY_CONS> sc{sprm, meta_l, s_ctape + lane, s_adj + lane, nl, MS};
           Col<const T> q{s_x + lane, LANES}, qd{s_x + nqm * LANES + lane, LANES};
           T* gt = gtau + t * nvm * B + b;
           step_adjoint<T, DT>(sc, q, qd, gq, gqd, Col<T>{gt, B}, gm, g, m.dt, m.integ);
@@ -537,6 +558,7 @@ k_backward_pipe(DevModel<T> m, const T* __restrict__ ckpt, const T* __restrict__
         __syncwarp();
       }
     }
+    if (!consumer) cp_wait_all();
     if (consumer && act) {
       bool ok = true;
       for (int d = 0; d < nq; ++d) ok &= finite_t(gq[d]);
@@ -744,7 +766,8 @@ int launch_backward(sim_handle* h, const void* ckpt, const void* tau, int64_t T_
       int limit = 0;
       cudaError_t e = cudaDeviceGetAttribute(&limit, cudaDevAttrMaxSharedMemoryPerBlockOptin, h->device);
       if (e != cudaSuccess) return cuda_fail(h, e, "shared-memory limit query");
-      const size_t need = (size_t)pipe_smem_per_tile(h->maxL, h->nq_max + h->nv_max) * LANES * sizeof(T);
+      const size_t need =
+          (size_t)pipe_smem_per_tile(h->maxL, h->nq_max + h->nv_max, h->nv_max) * LANES * sizeof(T);
       if (need <= (size_t)limit) {
         kern = backward_pipe_kernel<T, DT>();
         e = cudaFuncSetAttribute((const void*)kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)need);
