@@ -97,9 +97,9 @@ template <class T> SD T sqrt_t(T x) { return sqrt(x); }
 // Tape and adjoint layouts.  LAY_FULL holds every field (any tree, any joint).
 // The pipelined adjoint of serial chains of revolute joints uses two compact
 // layouts: LAY_CONS, the 81 tape fields and 33 adjoint fields the adjoint step
-// reads for such links, and LAY_PROD, the same 81 tape fields first (so one
-// contiguous copy per link hands them over) followed by the forward pass's own
-// scratch, the bias force T_PA (in LAY_PROD the inward pass recomputes each
+// reads for such links, and LAY_PROD, the same 81 tape fields at the same places
+// (so the adjoint reads a LAY_PROD tape directly) followed by the forward pass's
+// own scratch, the bias force T_PA (in LAY_PROD the inward pass recomputes each
 // link's rigid-body inertia from the model constants instead of storing it).
 // Fields a compact
 // layout lacks are never touched for chain links; host builds with

@@ -418,33 +418,42 @@ __global__ void k_backward(DevModel<T> m, const T* __restrict__ ckpt, const T* _
 // ------------------------------------------------------------------ pipelined adjoint
 // Two warps per 32-system tile, for batches of serial revolute chains with a
 // checkpoint every step: the producer warp recomputes step t's forward
-// intermediates from the checkpoint x^t into its shared-memory tape (compact
-// layout LAY_PROD) while the consumer warp runs the adjoint of step t + 1 from
-// its own shared-memory tape (LAY_CONS) with compact adjoint accumulators.  Step
-// t's recompute does not depend on step t + 1's adjoint, so the two overlap.  At
-// each step the consumer copies the 81 fields per link it reads out of the
-// producer's tape (one contiguous block per link, 16-byte moves) and releases it.
-// Hand-off by two named barriers (hardware barriers: no spinning): FULL (the
-// producer arrives when its tape holds step t, the consumer waits) and EMPTY (the
-// consumer arrives once its copy is done, the producer waits before computing
-// the next step).  Per tile both warps execute FULL Tn times and EMPTY Tn - 1
-// times whatever their systems (inactive lanes included), and neither arrives
-// twice before the other's matching wait: the producer's next FULL arrival
-// follows its EMPTY wait, which follows the consumer's FULL wait, and the
-// consumer's next EMPTY arrival follows its FULL wait, which follows the
-// producer's EMPTY wait.
-enum : int { BAR_FULL = 1, BAR_EMPTY = 2 };
-__device__ __forceinline__ void pair_sync_full() { asm volatile("bar.sync 1, 64;\n" ::: "memory"); }
-__device__ __forceinline__ void pair_arrive_full() { asm volatile("bar.arrive 1, 64;\n" ::: "memory"); }
-__device__ __forceinline__ void pair_sync_empty() { asm volatile("bar.sync 2, 64;\n" ::: "memory"); }
-__device__ __forceinline__ void pair_arrive_empty() { asm volatile("bar.arrive 2, 64;\n" ::: "memory"); }
+// intermediates from the checkpoint x^t into one of two shared-memory tapes
+// (compact layout LAY_PROD) while the consumer warp runs the adjoint of step t + 1
+// from the other one, with compact adjoint accumulators (LAY_CONS).  Step t's
+// recompute does not depend on step t + 1's adjoint, so the two overlap.  Tape b
+// holds the steps of parity b.  Hand-off by named barriers (hardware barriers: no
+// spinning), one pair per tape: FULL(b) (the producer arrives when tape b holds
+// its step, the consumer waits) and EMPTY(b) (the consumer arrives when it has
+// finished a step from tape b that the producer will reuse, the producer waits
+// before overwriting).  Per tile and tape both warps execute the same number of
+// operations whatever their systems (inactive lanes included), and neither
+// arrives twice at a barrier before the other's matching wait: the producer's
+// next arrival at FULL(b) follows its wait on EMPTY(b), which follows the
+// consumer's wait on FULL(b), and vice versa.
+__device__ __forceinline__ void pair_sync_full(int b) {
+  if (b) asm volatile("bar.sync 2, 64;\n" ::: "memory");
+  else asm volatile("bar.sync 1, 64;\n" ::: "memory");
+}
+__device__ __forceinline__ void pair_arrive_full(int b) {
+  if (b) asm volatile("bar.arrive 2, 64;\n" ::: "memory");
+  else asm volatile("bar.arrive 1, 64;\n" ::: "memory");
+}
+__device__ __forceinline__ void pair_sync_empty(int b) {
+  if (b) asm volatile("bar.sync 4, 64;\n" ::: "memory");
+  else asm volatile("bar.sync 3, 64;\n" ::: "memory");
+}
+__device__ __forceinline__ void pair_arrive_empty(int b) {
+  if (b) asm volatile("bar.arrive 4, 64;\n" ::: "memory");
+  else asm volatile("bar.arrive 3, 64;\n" ::: "memory");
+}
 
-// Shared memory of one pipelined block, in scalars per lane: the producer's and
-// the consumer's tapes, the adjoint accumulators, model constants, meta words,
-// the state adjoint, the mass-gradient sums, the consumer's copy of x^t and the
-// producer's double-buffered (x^t, tau^t) fetched one step ahead.
+// Shared memory of one pipelined block, in scalars per lane: the two tapes, the
+// adjoint accumulators, model constants, meta words, the state adjoint, the
+// mass-gradient sums, the consumer's copy of x^t and the producer's
+// double-buffered (x^t, tau^t) fetched one step ahead.
 __host__ __device__ __forceinline__ long long pipe_smem_per_tile(int maxL, int nx, int nv) {
-  return (long long)maxL * (NTAPE_PROD + NTAPE_CONS + NADJ_CONS + NPRM + 1 + 1) + 2LL * nx + 2LL * (nx + nv);
+  return (long long)maxL * (2 * NTAPE_PROD + NADJ_CONS + NPRM + 1 + 1) + 2LL * nx + 2LL * (nx + nv);
 }
 
 template <class T, class DT>
@@ -459,9 +468,8 @@ k_backward_pipe(DevModel<T> m, const T* __restrict__ ckpt, const T* __restrict__
   const long long L = m.maxL;
   const V3<T> g{m.g0, m.g1, m.g2};
   constexpr int MS = (int)(sizeof(T) / sizeof(int));
-  T* s_ptape = reinterpret_cast<T*>(g_smem);
-  T* s_ctape = s_ptape + L * NTAPE_PROD * LANES;
-  T* s_adj = s_ctape + L * NTAPE_CONS * LANES;
+  T* s_tape = reinterpret_cast<T*>(g_smem);  // [2][L][NTAPE_PROD][LANES]
+  T* s_adj = s_tape + 2 * L * NTAPE_PROD * LANES;
   T* s_prm = s_adj + L * NADJ_CONS * LANES;
   T* s_meta = s_prm + L * NPRM * LANES;
   T* s_state = s_meta + L * LANES;
@@ -477,7 +485,6 @@ k_backward_pipe(DevModel<T> m, const T* __restrict__ ckpt, const T* __restrict__
     const int b = act ? m.sys_of_slot[slot] : 0;
     const int nl = act ? m.nl[slot] : 0;
     const int nq = act ? (m.nqv[slot] & 0xffff) : 0, nv = act ? (m.nqv[slot] >> 16) : 0;
-    const int tile_links = m.nl[unit * LANES];  // slots are sorted by link count: the tile's longest
     if (consumer && act) {
       const T* gprm = m.prm + (long long)unit * L * NPRM * LANES + lane;
       const int* gmeta = m.meta + (long long)unit * L * LANES + lane;
@@ -512,39 +519,33 @@ k_backward_pipe(DevModel<T> m, const T* __restrict__ ckpt, const T* __restrict__
       }
       for (int l = 0; l < nl; ++l) gm[l] = T(0);
     }
-    constexpr int CH = NTAPE_CONS * LANES * (int)sizeof(T) / 16;  // 16-byte chunks of one link's fields
     for (long long t = Tn - 1; t >= 0; --t) {
-      if (!consumer) {  // producer: recompute step t on chip
+      const int buf = (int)(t & 1);
+      T* tape_b = s_tape + buf * L * NTAPE_PROD * LANES;
+      if (!consumer) {  // producer: recompute step t into tape t & 1
         if (act && t > 0) fetch(t - 1, (int)((t - 1) & 1));
         cp_commit();
         cp_wait_all_but_newest();
         __syncwarp();
-        if (t < Tn - 1) pair_sync_empty();
+        if (t < Tn - 2) pair_sync_empty(buf);
         if (act) {
-          const Sys<T, T, LAY_PROD, LAY_FULL> sp{sprm, meta_l, s_ptape + lane, nullptr, nl, MS};
-          const T* x = s_in + (t & 1) * W * LANES + lane;
+          const Sys<T, T, LAY_PROD, LAY_FULL> sp{sprm, meta_l, tape_b + lane, nullptr, nl, MS};
+          const T* x = s_in + buf * W * LANES + lane;
           aba_forward<T, DT, true>(sp, Col<const T>{x, LANES}, Col<const T>{x + nqm * LANES, LANES},
                                    Col<const T>{x + NX * LANES, LANES}, g);
         }
         __threadfence_block();
         __syncwarp();
-        pair_arrive_full();
-      } else {  // consumer: copy step t's fields out of the producer's tape, then its adjoint
+        pair_arrive_full(buf);
+      } else {  // consumer: the adjoint of step t from tape t & 1
         if (act)
           for (int d = 0; d < NX; ++d) cp_async(s_x + d * LANES + lane, ckpt + (t * NX + d) * B + b);
         cp_commit();
         __syncwarp();
-        pair_sync_full();
-        for (int i = lane; i < tile_links * CH; i += LANES) {
-          const int l = i / CH, c = i - l * CH;
-          reinterpret_cast<uint4*>(s_ctape + (long long)l * NTAPE_CONS * LANES)[c] =
-              reinterpret_cast<const uint4*>(s_ptape + (long long)l * NTAPE_PROD * LANES)[c];
-        }
-        __syncwarp();
-        if (t > 0) pair_arrive_empty();
+        pair_sync_full(buf);
         cp_wait_all();
         if (act) {
-          const Sys<T, T, LAY_CONS, LAY_CONS> sc{sprm, meta_l, s_ctape + lane, s_adj + lane, nl, MS};
+          const Sys<T, T, LAY_PROD, LAY_CONS> sc{sprm, meta_l, tape_b + lane, s_adj + lane, nl, MS};
           Col<const T> q{s_x + lane, LANES}, qd{s_x + nqm * LANES + lane, LANES};
           T* gt = gtau + t * nvm * B + b;
           step_adjoint<T, DT>(sc, q, qd, gq, gqd, Col<T>{gt, B}, gm, g, m.dt, m.integ);
@@ -556,6 +557,7 @@ k_backward_pipe(DevModel<T> m, const T* __restrict__ ckpt, const T* __restrict__
           }
         }
         __syncwarp();
+        if (t >= 2) pair_arrive_empty(buf);
       }
     }
     if (!consumer) cp_wait_all();
