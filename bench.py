@@ -235,6 +235,8 @@ def run_ours(args):
                       qd0.cpu().pin_memory())
     if rank != 0:
         return None
+    storage = sim.last_storage()
+    kname = "k_backward_pipe" if storage[1] == "pipelined" else "k_backward"
     f_fwd = flops_per_system_step(m, "fwd")
     f_adj = flops_per_system_step(m, "adj")
     adj_flops = B * T * (f_fwd + f_adj)
@@ -251,15 +253,15 @@ def run_ours(args):
                    "precision": args.precision, "l2": "flushed between steps (256 MB write)",
                    "parallelism": f"replicas x{ws}" if ws > 1 else "single GPU",
                    "block": sim.launch[0], "schedule": "persistent" if sim.launch[1] else "grid",
-                   "tape": args.tape, "replay": args.replay,
+                   "tape": args.tape, "replay": args.replay, "storage": {"rollout": storage[0], "adjoint": storage[1]},
                    "cuda_graph": bool(args.graph), "contacts": bool(args.contacts),
                    "joint_limits": bool(args.limits)},
         "fwd_env_steps_per_s": B * T / (float(np.mean(fwd_ms)) / 1e3),
         "ms_fwd": float(np.mean(fwd_ms)), "ms_adj": float(np.mean(adj_ms)),
         "ms_per_step_cuda_graph": graph_ms,
-        "roofline": {"bound": "alu", "kernel": "k_backward", "achieved": achieved, "peak": peak["tflops"],
+        "roofline": {"bound": "alu", "kernel": kname, "achieved": achieved, "peak": peak["tflops"],
                      "unit": "TFLOP/s", "frac": achieved / peak["tflops"],
-                     "traffic": measured_traffic("k_backward", m.name, B, T, args.precision, k),
+                     "traffic": measured_traffic(kname, m.name, B, T, args.precision, k),
                      "flops_per_system_step": {"fwd": f_fwd, "adj": f_adj}, "peak_note": peak["note"]
                      + ("; the FLOP count covers the ABA step only, not the constraint solve"
                         if args.contacts or args.limits else "")},
@@ -473,7 +475,7 @@ def main():
     ap.add_argument("--block", type=int, default=0)
     ap.add_argument("--persistent", action="store_true")
     ap.add_argument("--autotune", action="store_true")
-    ap.add_argument("--tape", default="auto", choices=["auto", "global", "shared"])
+    ap.add_argument("--tape", default="auto", choices=["auto", "global", "shared", "pipelined"])
     ap.add_argument("--replay", default="segment", choices=["segment", "quadratic"])
     ap.add_argument("--no-cpu-baseline", dest="cpu_baseline", action="store_false")
     ap.add_argument("--no-plain", dest="plain", action="store_false")

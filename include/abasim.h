@@ -238,6 +238,12 @@ int sim_set_launch(sim_handle* h, int32_t threads, int32_t schedule);
 #define SIM_TAPE_PIPELINED 3
 int sim_set_tape_space(sim_handle* h, int32_t space);
 
+/* The storage mode the last sim_rollout (or step) and sim_backward_rollout
+ * launches of this handle ran with: 0 tape in global memory, 1 tape global with
+ * state and input streams on chip, 2 tape on chip, 3 the pipelined two-warp
+ * adjoint.  Either pointer may be NULL.  No device work. */
+int sim_last_storage(const sim_handle* h, int32_t* rollout_mode, int32_t* backward_mode);
+
 /* How sim_backward_rollout rebuilds the states inside a checkpoint segment when
  * k > 1.  SIM_REPLAY_SEGMENT (default): replay the segment once into the caller
  * workspace, then differentiate it backwards (≈ one extra forward step per step).

@@ -56,6 +56,7 @@ _SIGS = {
     "sim_ckpt_bytes": (ctypes.c_size_t, [_P, ctypes.c_int64, ctypes.c_int32]),
     "sim_work_bytes": (ctypes.c_size_t, [_P, ctypes.c_int32]),
     "sim_set_masses": (ctypes.c_int, [_P, _P, _P]),
+    "sim_last_storage": (ctypes.c_int, [_P, ctypes.POINTER(ctypes.c_int32), ctypes.POINTER(ctypes.c_int32)]),
     "sim_step_batch": (ctypes.c_int, [_P] * 7),
     "sim_step_batch_static": (ctypes.c_int, [_P] * 7),
     "sim_rollout": (ctypes.c_int, [_P, _P, _P, _P, ctypes.c_int64, ctypes.c_int32, _P, _P, _P, _P, _P]),
@@ -200,6 +201,15 @@ class Simulator:
         'shared' (one warp per tile, tape on chip) or 'pipelined' (two warps per tile)."""
         code = {"auto": 0, "global": 1, "shared": 2, "pipelined": 3}[space]
         self._check(lib.sim_set_tape_space(self._h, code), "sim_set_tape_space")
+
+    STORAGE = ("global", "hybrid", "shared", "pipelined")
+
+    def last_storage(self):
+        """(rollout, backward) storage modes of the last launches: 'global', 'hybrid',
+        'shared' or 'pipelined'."""
+        f, b = ctypes.c_int32(), ctypes.c_int32()
+        self._check(lib.sim_last_storage(self._h, ctypes.byref(f), ctypes.byref(b)), "sim_last_storage")
+        return self.STORAGE[f.value], self.STORAGE[b.value]
 
     def set_replay(self, mode: str = "segment"):
         """k > 1 state rebuild: 'segment' (replay once) or 'quadratic' (from the checkpoint)."""

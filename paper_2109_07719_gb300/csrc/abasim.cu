@@ -494,6 +494,13 @@ int sim_set_tape_space(sim_handle* h, int32_t space) {
   return SIM_OK;
 }
 
+int sim_last_storage(const sim_handle* h, int32_t* rollout_mode, int32_t* backward_mode) {
+  if (!h) return SIM_EINVAL;
+  if (rollout_mode) *rollout_mode = h->last_storage;
+  if (backward_mode) *backward_mode = h->last_storage_bwd;
+  return SIM_OK;
+}
+
 int sim_set_replay(sim_handle* h, int32_t mode) {
   if (!h) return SIM_EINVAL;
   if (mode != SIM_REPLAY_SEGMENT && mode != SIM_REPLAY_QUADRATIC) return fail(h, SIM_EINVAL, "unknown replay mode");
