@@ -454,6 +454,145 @@ SD void aba_forward(const Sys<T, PT, TL, AL>& s, Col<const T> q, Col<const T> qd
   }
 }
 
+// ------------------------------------------------------------------ split forward
+// The ABA forward of a serial chain of revolute joints (parent of link l is
+// l - 1) split into the part that depends on q alone (the articulated-inertia
+// recursion) and the rest (velocities, bias forces, accelerations), so two
+// warps can run them side by side.  Same formulas and operation order as
+// aba_forward.  Exchange record per link, [link][EX_N][LANES]: U, 1/D (hi/lo
+// pair) and I^a; the bias half's own scratch, [link][BS_N][LANES]: X, c, p^A, u.
+enum : int { EX_U = 0, EX_DI = 6, EX_Ia = 8, EX_N = 29 };
+enum : int { BS_E = 0, BS_C = 12, BS_PA = 18, BS_u = 24, BS_N = 25 };
+
+template <class T> SD T& exw(T* base, int l, int f) { return base[(l * EX_N + f) * LANES]; }
+template <class T> SD T& bsw(T* base, int l, int f) { return base[(l * BS_N + f) * LANES]; }
+
+// Inertia half, leaves -> root; ready(l) runs after link l's record is written.
+template <class T, class DT, class PT, class F>
+SD void chain_inertia(const Sys<T, PT>& s, Col<const T> q, T* ex, F&& ready, int links) {
+  SI<T> cI = zeroSI<T>();
+  for (int l = links - 1; l >= 0; --l) {
+    if (l < s.nl) {
+      const int m = s.M(l);
+      const V3<T> a = s.pv3(l, P_AX);
+      T sn, cs;
+      sincos_t(q[meta_qoff(m)], &sn, &cs);
+      const XF<T> X{mm(rot_axis_T(a, sn, cs), s.pm3(l, P_E)), s.pv3(l, P_R)};
+      SI<T> IA = rbi(s.P(l, P_M), s.pv3(l, P_C), s.ps3(l, P_IC));
+      if (l < s.nl - 1) IA += cI;
+      const SV<T> U{mul(IA.A, a), mulT(IA.B, a)};
+      const DT D = (DT)a.x * (DT)U.w.x + (DT)a.y * (DT)U.w.y + (DT)a.z * (DT)U.w.z;
+      const DT Di = DT(1) / D;
+      const T hi = (T)Di;
+      const T u6[6] = {U.w.x, U.w.y, U.w.z, U.v.x, U.v.y, U.v.z};
+      for (int i = 0; i < 6; ++i) exw(ex, l, EX_U + i) = u6[i];
+      exw(ex, l, EX_DI) = hi;
+      exw(ex, l, EX_DI + 1) = (T)(Di - (DT)hi);
+      if (l > 0) {
+        const SI<T> Ia = minus_scaled_outer<T, DT>(IA, Di, U);
+        const T ia[21] = {Ia.A.xx, Ia.A.yy, Ia.A.zz, Ia.A.xy, Ia.A.xz, Ia.A.yz, Ia.B.a[0], Ia.B.a[1], Ia.B.a[2],
+                          Ia.B.a[3], Ia.B.a[4], Ia.B.a[5], Ia.B.a[6], Ia.B.a[7], Ia.B.a[8], Ia.C.xx, Ia.C.yy,
+                          Ia.C.zz, Ia.C.xy, Ia.C.xz, Ia.C.yz};
+        for (int i = 0; i < 21; ++i) exw(ex, l, EX_Ia + i) = ia[i];
+        cI = congruence(X, Ia);
+      }
+    }
+    ready(l);
+  }
+}
+
+// Bias half, pass 1 (root -> leaves): X, v, c, p^A into the scratch.
+template <class T, class PT>
+SD void chain_bias_out(const Sys<T, PT>& s, Col<const T> q, Col<const T> qd, T* bs) {
+  SV<T> v_prev = zeroSV<T>();
+  for (int l = 0; l < s.nl; ++l) {
+    const int m = s.M(l);
+    const V3<T> a = s.pv3(l, P_AX);
+    T sn, cs;
+    sincos_t(q[meta_qoff(m)], &sn, &cs);
+    const XF<T> X{mm(rot_axis_T(a, sn, cs), s.pm3(l, P_E)), s.pv3(l, P_R)};
+    const SV<T> vJ{qd[meta_voff(m)] * a, zero3<T>()};
+    SV<T> v = vJ;
+    if (l > 0) v += apply(X, v_prev);
+    const SV<T> c = crossm(v, vJ);
+    const SV<T> h = mul(rbi(s.P(l, P_M), s.pv3(l, P_C), s.ps3(l, P_IC)), v);
+    const SV<T> pA = crossf(v, h);
+    for (int i = 0; i < 9; ++i) bsw(bs, l, BS_E + i) = X.E.a[i];
+    bsw(bs, l, BS_E + 9) = X.r.x;
+    bsw(bs, l, BS_E + 10) = X.r.y;
+    bsw(bs, l, BS_E + 11) = X.r.z;
+    const T cc[6] = {c.w.x, c.w.y, c.w.z, c.v.x, c.v.y, c.v.z};
+    const T pp[6] = {pA.w.x, pA.w.y, pA.w.z, pA.v.x, pA.v.y, pA.v.z};
+    for (int i = 0; i < 6; ++i) {
+      bsw(bs, l, BS_C + i) = cc[i];
+      bsw(bs, l, BS_PA + i) = pp[i];
+    }
+    v_prev = v;
+  }
+}
+
+template <class T> SD XF<T> bs_xf(T* bs, int l) {
+  XF<T> X;
+  for (int i = 0; i < 9; ++i) X.E.a[i] = bsw(bs, l, BS_E + i);
+  X.r = V3<T>{bsw(bs, l, BS_E + 9), bsw(bs, l, BS_E + 10), bsw(bs, l, BS_E + 11)};
+  return X;
+}
+template <class T> SD SV<T> rd_sv(T* base, int l, int f, int n) {
+  return SV<T>{{base[(l * n + f) * LANES], base[(l * n + f + 1) * LANES], base[(l * n + f + 2) * LANES]},
+               {base[(l * n + f + 3) * LANES], base[(l * n + f + 4) * LANES], base[(l * n + f + 5) * LANES]}};
+}
+
+// Bias half, pass 2 (leaves -> root) and pass 3 (root -> leaves), then the
+// integrator: wait(l) runs before link l's exchange record is read.
+template <class T, class DT, class PT, class F>
+SD void chain_bias_in(const Sys<T, PT>& s, Col<T> q, Col<T> qd, Col<const T> tau, V3<T> grav, T* ex, T* bs,
+                      F&& wait, int links, T dt, int integ) {
+  SV<T> cp = zeroSV<T>();
+  for (int l = links - 1; l >= 0; --l) {
+    wait(l);
+    if (l >= s.nl) continue;
+    const int m = s.M(l);
+    const int vo = meta_voff(m);
+    const V3<T> a = s.pv3(l, P_AX);
+    SV<T> pA = rd_sv(bs, l, BS_PA, BS_N);
+    if (l < s.nl - 1) pA += cp;
+    const T tl = tau[vo] - s.P(l, P_DAMP) * qd[vo];
+    const T u = tl - dot(a, pA.w);
+    bsw(bs, l, BS_u) = u;
+    if (l > 0) {
+      const SV<T> U = rd_sv(ex, l, EX_U, EX_N);
+      const DT Di = (DT)exw(ex, l, EX_DI) + (DT)exw(ex, l, EX_DI + 1);
+      SI<T> Ia;
+      Ia.A = S3<T>{exw(ex, l, EX_Ia), exw(ex, l, EX_Ia + 1), exw(ex, l, EX_Ia + 2), exw(ex, l, EX_Ia + 3),
+                   exw(ex, l, EX_Ia + 4), exw(ex, l, EX_Ia + 5)};
+      for (int i = 0; i < 9; ++i) Ia.B.a[i] = exw(ex, l, EX_Ia + 6 + i);
+      Ia.C = S3<T>{exw(ex, l, EX_Ia + 15), exw(ex, l, EX_Ia + 16), exw(ex, l, EX_Ia + 17),
+                   exw(ex, l, EX_Ia + 18), exw(ex, l, EX_Ia + 19), exw(ex, l, EX_Ia + 20)};
+      const SV<T> c = rd_sv(bs, l, BS_C, BS_N);
+      const SV<T> pa = pA + mul(Ia, c) + (T)((DT)u * Di) * U;
+      cp = applyT(bs_xf(bs, l), pa);
+    }
+  }
+  const SV<T> a0{zero3<T>(), -grav};
+  SV<T> a_prev = a0;
+  for (int l = 0; l < s.nl; ++l) {
+    const int m = s.M(l);
+    const V3<T> ax = s.pv3(l, P_AX);
+    const SV<T> U = rd_sv(ex, l, EX_U, EX_N);
+    const DT Di = (DT)exw(ex, l, EX_DI) + (DT)exw(ex, l, EX_DI + 1);
+    const SV<T> ap = apply(bs_xf(bs, l), a_prev) + rd_sv(bs, l, BS_C, BS_N);
+    const T qdd = (T)(((DT)bsw(bs, l, BS_u) - (DT)dot(U, ap)) * Di);
+    SV<T> a = ap;
+    a.w += qdd * ax;
+    a_prev = a;
+    const int qo = meta_qoff(m), vo = meta_voff(m);
+    const T v0 = qd[vo];
+    const T v1 = v0 + dt * qdd;
+    qd[vo] = v1;
+    q[qo] = q[qo] + dt * (integ == I_SEMI_IMPLICIT ? v1 : v0);
+  }
+}
+
 // Integrates x -> x' in place from the qdd on the tape, plus the contact
 // velocity change C_DV of the contact tape ct when given.
 template <class T, class PT, int TL, int AL>

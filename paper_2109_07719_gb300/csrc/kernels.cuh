@@ -577,6 +577,140 @@ k_backward_pipe(DevModel<T> m, const T* __restrict__ ckpt, const T* __restrict__
   }
 }
 
+// ------------------------------------------------------------------ pipelined rollout
+// Two warps per 32-system tile for batches of serial revolute chains: the
+// inertia warp runs the q-only articulated-inertia recursion of each step
+// (chain_inertia) while the bias warp runs the velocity / bias-force pass, then
+// follows the inertia warp link by link through the inward pass, then the
+// acceleration pass and the integrator (chain_bias_out / chain_bias_in).  Named
+// barriers: LINK(l) = 1 + l (the inertia warp arrives when link l's record is
+// written, the bias warp waits before reading it) and Q = 15 (the bias warp
+// arrives when the state of the next step is in place, the inertia warp waits).
+// Per tile both warps execute Q Tn times and every LINK(l), l < the tile's
+// longest chain, once per step, whatever their systems; an arrival at LINK(l)
+// for step t + 1 follows the Q wait that follows the bias warp's LINK(l) wait of
+// step t, and the bias warp's next Q arrival follows LINK waits that follow the
+// inertia warp's Q wait.  Chains of up to 14 links.
+constexpr int PIPE_MAX_LINKS = 14;
+__device__ __forceinline__ void bar_sync_id(int id) { asm volatile("bar.sync %0, 64;\n" ::"r"(id) : "memory"); }
+__device__ __forceinline__ void bar_arrive_id(int id) { asm volatile("bar.arrive %0, 64;\n" ::"r"(id) : "memory"); }
+
+__host__ __device__ __forceinline__ long long pipe_fwd_smem_per_tile(int maxL, int nx, int nv) {
+  return (long long)maxL * (NPRM + 1 + EX_N + BS_N) + nx + 2LL * nv;
+}
+
+template <class T, class DT>
+__global__ void __launch_bounds__(2 * LANES, 1)
+k_rollout_pipe(DevModel<T> m, const T* __restrict__ q0, const T* __restrict__ qd0, const T* __restrict__ tau,
+               long long Tn, int k, T* ckpt, T* qT, T* qdT, T* traj) {
+  const int warp = threadIdx.x / LANES, lane = threadIdx.x % LANES;
+  const bool bias = warp == 0;
+  const long long B = m.B;
+  const int nqm = m.nq_max, nvm = m.nv_max, NX = nqm + nvm;
+  const long long L = m.maxL;
+  const V3<T> g{m.g0, m.g1, m.g2};
+  constexpr int MS = (int)(sizeof(T) / sizeof(int));
+  constexpr int BAR_Q = 15;
+  T* s_prm = reinterpret_cast<T*>(g_smem);
+  T* s_meta = s_prm + L * NPRM * LANES;
+  T* s_ex = s_meta + L * LANES;
+  T* s_bs = s_ex + L * EX_N * LANES;
+  T* s_state = s_bs + L * BS_N * LANES;
+  T* s_tau = s_state + (long long)NX * LANES;  // [2][nvm][LANES]
+  int* meta_l = reinterpret_cast<int*>(s_meta + lane);
+  int unit = m.persistent ? next_unit(m.counter) : (int)blockIdx.x;
+  while ((long long)unit * LANES < B) {
+    const int slot = unit * LANES + lane;
+    const bool act = slot < B;
+    const int b = act ? m.sys_of_slot[slot] : 0;
+    const int nl = act ? m.nl[slot] : 0;
+    const int links = m.nl[unit * LANES];  // slots are sorted by link count: the tile's longest
+    if (bias && act) {
+      const T* gprm = m.prm + (long long)unit * L * NPRM * LANES + lane;
+      const int* gmeta = m.meta + (long long)unit * L * LANES + lane;
+      for (int l = 0; l < nl; ++l) {
+        for (int f = 0; f < NPRM; ++f) s_prm[(l * NPRM + f) * LANES + lane] = gprm[(l * NPRM + f) * LANES];
+        meta_l[l * LANES * MS] = gmeta[l * LANES];
+      }
+    }
+    __syncthreads();
+    const Sys<T> s{s_prm + lane, meta_l, nullptr, nullptr, nl, MS};
+    Col<T> q{s_state + lane, LANES}, qd{s_state + nqm * LANES + lane, LANES};
+    T* ex = s_ex + lane;
+    T* bs = s_bs + lane;
+    if (bias) {
+      if (act) {
+        if (Tn > 0)
+          for (int d = 0; d < nvm; ++d) cp_async(s_tau + d * LANES + lane, tau + (long long)d * B + b);
+        for (int d = 0; d < nqm; ++d) q[d] = q0[d * B + b];
+        for (int d = 0; d < nvm; ++d) qd[d] = qd0[d * B + b];
+        if (traj) {
+          for (int d = 0; d < nqm; ++d) traj[d * B + b] = q[d];
+          for (int d = 0; d < nvm; ++d) traj[(nqm + d) * B + b] = qd[d];
+        }
+      }
+      cp_commit();
+      __threadfence_block();
+      __syncwarp();
+      if (Tn > 0) bar_arrive_id(BAR_Q);
+    }
+    for (long long t = 0; t < Tn; ++t) {
+      if (!bias) {  // inertia warp
+        __syncwarp();
+        bar_sync_id(BAR_Q);
+        chain_inertia<T, DT>(s, Col<const T>{q.p, LANES}, ex,
+                             [&](int l) {
+                               __threadfence_block();
+                               __syncwarp();
+                               bar_arrive_id(1 + l);
+                             },
+                             links);
+      } else {  // bias warp
+        if (act && ckpt && t % k == 0) {
+          T* c = ckpt + (t / k) * NX * B + b;
+          for (int d = 0; d < nqm; ++d) c[d * B] = q[d];
+          for (int d = 0; d < nvm; ++d) c[(nqm + d) * B] = qd[d];
+        }
+        if (act && t + 1 < Tn) {
+          T* nb = s_tau + ((t + 1) & 1) * nvm * LANES + lane;
+          for (int d = 0; d < nvm; ++d) cp_async(nb + d * LANES, tau + ((t + 1) * nvm + d) * B + b);
+        }
+        cp_commit();
+        cp_wait_all_but_newest();
+        if (act) chain_bias_out(s, Col<const T>{q.p, LANES}, Col<const T>{qd.p, LANES}, bs);
+        chain_bias_in<T, DT>(s, q, qd, Col<const T>{s_tau + (t & 1) * nvm * LANES + lane, LANES}, g, ex, bs,
+                             [&](int l) {
+                               __syncwarp();
+                               bar_sync_id(1 + l);
+                             },
+                             links, m.dt, m.integ);
+        if (act && traj) {
+          T* c = traj + (t + 1) * NX * B + b;
+          for (int d = 0; d < nqm; ++d) c[d * B] = q[d];
+          for (int d = 0; d < nvm; ++d) c[(nqm + d) * B] = qd[d];
+        }
+        __threadfence_block();
+        __syncwarp();
+        if (t + 1 < Tn) bar_arrive_id(BAR_Q);
+      }
+    }
+    if (bias) {
+      cp_wait_all();
+      if (act) {
+        bool ok = true;
+        for (int d = 0; d < nqm; ++d) ok &= finite_t(q[d]);
+        for (int d = 0; d < nvm; ++d) ok &= finite_t(qd[d]);
+        if (!ok) m.status[b] |= 1;
+        for (int d = 0; d < nqm; ++d) qT[d * B + b] = q[d];
+        for (int d = 0; d < nvm; ++d) qdT[d * B + b] = qd[d];
+      }
+    }
+    __syncthreads();  // shared memory is reused by the next unit
+    if (!m.persistent) break;
+    unit = next_unit(m.counter);
+  }
+}
+
 template <class T>
 using BackwardKernel = void (*)(DevModel<T>, const T*, const T*, long long, int, const T*, const T*, const T*,
                                 T*, T*, T*, T*, T*);
@@ -729,20 +863,43 @@ int launch_rollout(sim_handle* h, const void* q0, const void* qd0, const void* t
   int st = ST_GLOBAL;
   int rc = SIM_OK;
   RolloutKernel<T> kern = k_rollout<T, DT, ST_GLOBAL>;
+  int threads = h->block;
   if (h->ctape) {
     kern = rollout_contact_kernel<T, DT>();
   } else if constexpr (sizeof(T) == 4) {  // on-chip modes: FP32 storage only
-    rc = choose_storage<T>(h, k_rollout<T, DT, ST_GLOBAL>, k_rollout<T, DT, ST_HYBRID>,
-                           k_rollout<T, DT, ST_SMEM>, false, &st, &shm);
-    if (st == ST_SMEM) kern = k_rollout<T, DT, ST_SMEM>;
-    if (st == ST_HYBRID) kern = k_rollout<T, DT, ST_HYBRID>;
+    bool piped = false;
+    if (h->all_chains && h->maxL <= PIPE_MAX_LINKS &&
+        (h->tape_space == SIM_TAPE_AUTO || h->tape_space == SIM_TAPE_PIPELINED)) {
+      const size_t need =
+          (size_t)pipe_fwd_smem_per_tile(h->maxL, h->nq_max + h->nv_max, h->nv_max) * LANES * sizeof(T);
+      int limit = 0;
+      cudaError_t e = cudaDeviceGetAttribute(&limit, cudaDevAttrMaxSharedMemoryPerBlockOptin, h->device);
+      if (e != cudaSuccess) return cuda_fail(h, e, "shared-memory limit query");
+      if (need <= (size_t)limit) {
+        kern = k_rollout_pipe<T, DT>;
+        e = cudaFuncSetAttribute((const void*)kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)need);
+        if (e != cudaSuccess) return cuda_fail(h, e, "shared-memory opt-in");
+        st = ST_PIPE;
+        shm = need;
+        threads = 2 * LANES;
+        piped = true;
+      }
+    }
+    if (!piped && h->tape_space == SIM_TAPE_PIPELINED)
+      return fail(h, SIM_EUNSUPPORTED, "the pipelined rollout needs serial revolute chains of at most 14 links");
+    if (!piped) {
+      rc = choose_storage<T>(h, k_rollout<T, DT, ST_GLOBAL>, k_rollout<T, DT, ST_HYBRID>,
+                             k_rollout<T, DT, ST_SMEM>, false, &st, &shm);
+      if (st == ST_SMEM) kern = k_rollout<T, DT, ST_SMEM>;
+      if (st == ST_HYBRID) kern = k_rollout<T, DT, ST_HYBRID>;
+    }
   }
   if (rc != SIM_OK) return rc;
   h->last_storage = st;
   int grid = 0;
-  rc = launch_shape(h, kern, &grid, &m.persistent, shm, stream);
+  rc = launch_shape(h, kern, &grid, &m.persistent, shm, stream, threads, st == ST_PIPE ? LANES : threads);
   if (rc != SIM_OK) return rc;
-  kern<<<grid, h->block, shm, S(stream)>>>(m, (const T*)q0, (const T*)qd0, (const T*)tau, (long long)T_,
+  kern<<<grid, threads, shm, S(stream)>>>(m, (const T*)q0, (const T*)qd0, (const T*)tau, (long long)T_,
                                            k, (T*)ckpt, (T*)qT, (T*)qdT, (T*)traj);
   cudaError_t e = cudaGetLastError();
   return e == cudaSuccess ? SIM_OK : cuda_fail(h, e, "rollout launch");

@@ -83,3 +83,58 @@ def test_pipelined_refuses_what_it_cannot_run():
     qT, qdT, ck, _ = sim.rollout(q0, qd0, tau, k=3)
     with pytest.raises(SimError, match="pipelined"):
         sim.backward(ck, tau, gqT, gqdT, k=3)
+
+
+# ---------------------------------------------------------------- pipelined rollout
+
+@pytest.mark.parametrize("B,T", [(100, 37), (32, 1), (33, 2)])
+@pytest.mark.parametrize("precision", ["fp32", "fp32_d64"])
+def test_pipelined_rollout_matches_single_warp(B, T, precision):
+    """Forward rollout split over an inertia warp and a bias warp against the
+    one-warp rollout: final state, checkpoints and trajectory."""
+    work, sim, q0, qd0, tau, gqT, gqdT = _setup(B, T, precision)
+    outs = {}
+    for space in ("shared", "pipelined"):
+        sim.set_tape_space(space)
+        outs[space] = sim.rollout(q0, qd0, tau, k=1, traj=True)
+        torch.cuda.synchronize()
+        assert sim.last_storage()[0] == space
+    for name, x, y in zip(("qT", "qdT", "ckpt", "traj"), outs["shared"], outs["pipelined"]):
+        check(name, y.cpu().numpy(), x.cpu().numpy(), 1e-5)
+
+
+def test_pipelined_rollout_persistent_and_interval():
+    work, sim, q0, qd0, tau, gqT, gqdT = _setup(300, 23)
+    sim.set_tape_space("pipelined")
+    sim.set_launch(32, False)
+    a = sim.rollout(q0, qd0, tau, k=5)
+    sim.set_launch(32, True)
+    b = sim.rollout(q0, qd0, tau, k=5)
+    torch.cuda.synchronize()
+    for x, y in zip(a[:3], b[:3]):
+        assert torch.equal(x, y)
+    sim.set_launch(32, False)
+    c = sim.rollout(q0, qd0, tau, k=1)
+    assert torch.equal(a[2], c[2][::5])
+
+
+@pytest.mark.parametrize("n,expect", [(14, "pipelined"), (15, None)])
+def test_pipelined_rollout_chain_length_limit(n, expect):
+    from paper_2109_07719_gb300 import Simulator
+    work = wl.serial_chains(B=40, T=12, n=n, precision="fp32")
+    sim = Simulator(work.model, precision="fp32")
+    dev = sim.device
+    q0 = torch.tensor(work.q0, dtype=torch.float32, device=dev)
+    qd0 = torch.tensor(work.qd0, dtype=torch.float32, device=dev)
+    tau = work.tau(device=dev, dtype=torch.float32)
+    a = sim.rollout(q0, qd0, tau)
+    torch.cuda.synchronize()
+    mode = sim.last_storage()[0]
+    if expect:
+        assert mode == expect
+        sim.set_tape_space("shared")
+        b = sim.rollout(q0, qd0, tau)
+        for x, y in zip(a[:2], b[:2]):
+            check("state", x.cpu().numpy(), y.cpu().numpy(), 1e-5)
+    else:
+        assert mode != "pipelined"
