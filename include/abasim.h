@@ -225,12 +225,14 @@ int sim_set_launch(sim_handle* h, int32_t threads, int32_t schedule);
  * memory when the block's tiles of 32 systems fit the per-block limit, else in
  * the handle's global scratch; SIM_TAPE_GLOBAL / SIM_TAPE_SHARED force one
  * (SHARED fails with SIM_EUNSUPPORTED at launch if it does not fit).
- * SIM_TAPE_PIPELINED runs the FP32 adjoint with checkpoint interval 1 as two
- * warps per 32-system tile: one recomputes step t's forward intermediates (into a
- * staging tape in the handle's global scratch) while the other differentiates
- * step t + 1 from a shared-memory copy; AUTO picks it when it fits, and forcing
- * it fails with SIM_EUNSUPPORTED for k > 1, FP64 or a tile too large for shared
- * memory.  Models with contact spheres or joint limits always run with the tape
+ * SIM_TAPE_PIPELINED runs batches of serial revolute chains (FP32 storage) with
+ * two warps per 32-system tile: in the rollout one warp runs the articulated-
+ * inertia recursion of each step while the other runs the velocity, bias-force
+ * and acceleration passes (chains of at most 14 links); in the adjoint with
+ * checkpoint interval 1 one warp recomputes step t's forward intermediates into
+ * one of two shared-memory tapes while the other differentiates step t + 1 from
+ * the other tape (when the two tapes fit, about 7 links).  AUTO picks each when it
+ * applies; forcing it fails with SIM_EUNSUPPORTED where it does not.  Models with contact spheres or joint limits always run with the tape
  * in global memory.  Results do not depend on the choice beyond rounding. */
 #define SIM_TAPE_AUTO 0
 #define SIM_TAPE_GLOBAL 1
