@@ -48,21 +48,20 @@ enum : int {
   G_V = 64, G_M = 70, NADJ = 71
 };
 
-// per-link contact tape (models with contact spheres only), [link][field][system]:
-// world pose of the link (C_EW rotation world -> link, C_OW origin), link
-// velocities for the velocity after the unconstrained step (C_VS), one unit
-// test pass's articulated bias force, joint force and link acceleration (C_TP,
-// C_TU, C_TA), the contact velocity change per coordinate (C_DV), the adjoint
-// accumulators of a test pass (C_TAB, C_TPB, C_TUB), the adjoint of the
-// unconstrained qdd from the integrator (C_QDDB), and the adjoints the contact
-// solve hands to the step adjoint (B_*: U, 1/D, the free root's articulated
-// inertia, the link transform E and r, world pose, unconstrained qdd, qd and, for
-// limited joints, q), then a test pass's joint accelerations and their adjoint
-// (C_TQ, C_TQB).
+// per-link contact tape (models with contact spheres or joint limits only),
+// [link][field][system]: world pose of the link (C_EW rotation world -> link,
+// C_OW origin), link velocities for the velocity after the unconstrained step
+// (C_VS), the constraint velocity change per coordinate (C_DV), the adjoint of
+// the unconstrained qdd from the integrator (C_QDDB), the adjoints the
+// constraint solve hands to the step adjoint (B_*: U, 1/D, the free root's
+// articulated inertia, the link transform E and r, world pose, unconstrained
+// qdd, qd and, for limited joints, q), then a test pass's bias forces, link
+// accelerations, joint forces, their adjoints and its joint accelerations and
+// their adjoint, 6 words per right-hand side for up to 3 right-hand sides.
 enum : int {
-  C_EW = 0, C_OW = 9, C_VS = 12, C_TP = 18, C_TA = 24, C_TU = 30, C_DV = 36, C_TAB = 42, C_TPB = 48,
-  C_TUB = 54, C_QDDB = 60, B_U = 66, B_DI = 72, B_IA = 73, B_E = 94, B_R = 103, B_EW = 106, B_OW = 115,
-  B_VS = 118, B_QDD = 124, B_QD = 130, B_Q = 136, B_END = 137, C_TQ = 137, C_TQB = 143, NCT = 149
+  C_EW = 0, C_OW = 9, C_VS = 12, C_DV = 18, C_QDDB = 24, B_U = 30, B_DI = 36, B_IA = 37, B_E = 58, B_R = 67,
+  B_EW = 70, B_OW = 79, B_VS = 82, B_QDD = 88, B_QD = 94, B_Q = 100, B_END = 101, C_TP = 101, C_TA = 119,
+  C_TU = 137, C_TAB = 155, C_TPB = 173, C_TUB = 191, C_TQ = 209, C_TQB = 227, NCT = 245
 };
 
 // meta word per link: parent+1 (8 bits) | joint type (1) | "has a child other than

@@ -127,143 +127,224 @@ template <class T, class PT> SD void world_poses(const Sys<T, PT>& s, const CVie
 }
 
 // ------------------------------------------------------------------ test pass
-// Response of the articulated system at rest (no velocity or gravity) to
-// external spatial forces fv[i] (link coordinates, at the link origin) on links
-// fl[i] and joint impulses jv[i] on revolute joints jl[i]: the ABA's bias-force
-// pass and acceleration pass with the step's U, 1/D, X and root articulated
-// inertia.  Leaves the articulated bias forces (C_TP), joint forces (C_TU) and
-// link accelerations (C_TA) on the contact tape, and the joint accelerations
-// M^-1 (sum J_i^T f_i + sum e_j jv) in field qf (if qf >= 0).
-template <class T, class DT, class PT>
-CD void test_pass(Sys<T, PT> s, CView<T> cv, const int* fl, const SV<T>* fv, int nf, const int* jl, const T* jv,
-                  int nj, int qf) {
+// Inputs of a test pass: n entries, each a spatial force (link coordinates, at
+// the link origin) on a link or an impulse on a revolute joint (f.w.x), for one
+// of the pass's right-hand sides.
+constexpr int MAXIN = MAXC + MAXL;
+template <class T> struct TPIn {
+  int n = 0;
+  int link[MAXIN];
+  int rhs[MAXIN];
+  bool joint[MAXIN];
+  SV<T> f[MAXIN];
+  SD void force(int l, int r, SV<T> v) { link[n] = l; rhs[n] = r; joint[n] = false; f[n++] = v; }
+  SD void impulse(int l, int r, T v) {
+    link[n] = l; rhs[n] = r; joint[n] = true;
+    f[n++] = SV<T>{{v, T(0), T(0)}, zero3<T>()};
+  }
+};
+
+// Free-root solves of several right-hand sides sharing one Cholesky factor (the
+// same operations as spd_solve).
+template <class T, class DT, int NR>
+SD void spd_solve_n(const SI<T>& IA, const SV<T>* b, SV<T>* x) {
+  DT L[21];
+  chol6(si_cast<DT>(IA), L);
+  for (int r = 0; r < NR; ++r) {
+    const SV<DT> y = chol6_solve(L, sv_cast<DT>(b[r]));
+    x[r] = SV<T>{{(T)y.w.x, (T)y.w.y, (T)y.w.z}, {(T)y.v.x, (T)y.v.y, (T)y.v.z}};
+  }
+}
+
+// Response of the articulated system at rest (no velocity or gravity) to the
+// inputs, for NR right-hand sides at once: the ABA's bias-force pass and
+// acceleration pass with the step's U, 1/D, X and root articulated inertia.
+// Leaves, per right-hand side r (fields + 6 r), the articulated bias forces
+// (C_TP), joint forces (C_TU) and link accelerations (C_TA) on the contact tape,
+// and the joint accelerations M^-1 (sum J_i^T f_i + sum e_j impulse) in field
+// qf + 6 r (if qf >= 0).
+template <class T, class DT, class PT, int NR>
+CD void test_pass(Sys<T, PT> s, CView<T> cv, TPIn<T> in, int qf) {
   const int nl = s.nl;
-  for (int l = 0; l < nl; ++l) cputv(cv, l, C_TP, zeroSV<T>());
+  for (int l = 0; l < nl; ++l)
+    for (int r = 0; r < NR; ++r) cputv(cv, l, C_TP + 6 * r, zeroSV<T>());
   for (int l = nl - 1; l >= 0; --l) {
     const int m = s.M(l);
     const int par = meta_parent(m);
-    SV<T> pA = cgetv(cv, l, C_TP);
-    for (int i = 0; i < nf; ++i)
-      if (fl[i] == l) pA -= fv[i];
-    cputv(cv, l, C_TP, pA);
+    SV<T> pA[NR];
+    T jadd[NR];
+    for (int r = 0; r < NR; ++r) {
+      pA[r] = cgetv(cv, l, C_TP + 6 * r);
+      jadd[r] = T(0);
+    }
+    for (int i = 0; i < in.n; ++i)
+      if (in.link[i] == l) {
+        for (int r = 0; r < NR; ++r)
+          if (in.rhs[i] == r) {
+            if (in.joint[i]) jadd[r] += in.f[i].w.x;
+            else pA[r] -= in.f[i];
+          }
+      }
+    for (int r = 0; r < NR; ++r) cputv(cv, l, C_TP + 6 * r, pA[r]);
     if (meta_jtype(m) == J_REVOLUTE) {
       const V3<T> ax = s.pv3(l, P_AX);
-      T u = -dot(ax, pA.w);
-      for (int i = 0; i < nj; ++i)
-        if (jl[i] == l) u += jv[i];
-      cv.L(l, C_TU) = u;
+      T u[NR];
+      for (int r = 0; r < NR; ++r) {
+        u[r] = -dot(ax, pA[r].w) + jadd[r];
+        cv.L(l, C_TU + 6 * r) = u[r];
+      }
       if (par >= 0) {
         const DT Di = get_di<T, DT, PT>(s, l);
-        const SV<T> pa = pA + (T)((DT)u * Di) * tp_sv(s, l, T_U);
-        caddv(cv, par, C_TP, applyT(tp_xf(s, l, T_E), pa));
+        const SV<T> U = tp_sv(s, l, T_U);
+        const XF<T> X = tp_xf(s, l, T_E);
+        for (int r = 0; r < NR; ++r) {
+          const SV<T> pa = pA[r] + (T)((DT)u[r] * Di) * U;
+          caddv(cv, par, C_TP + 6 * r, applyT(X, pa));
+        }
       }
     } else {
-      cputv(cv, l, C_TU, zeroSV<T>() - pA);
+      for (int r = 0; r < NR; ++r) cputv(cv, l, C_TU + 6 * r, zeroSV<T>() - pA[r]);
     }
   }
   for (int l = 0; l < nl; ++l) {
     const int m = s.M(l);
     const int par = meta_parent(m);
-    SV<T> a;
+    const XF<T> X = tp_xf(s, l, T_E);
     if (meta_jtype(m) == J_REVOLUTE) {
       const V3<T> ax = s.pv3(l, P_AX);
-      const SV<T> ap = par >= 0 ? apply(tp_xf(s, l, T_E), cgetv(cv, par, C_TA)) : zeroSV<T>();
       const DT Di = get_di<T, DT, PT>(s, l);
-      const T qdd = (T)(((DT)cv.L(l, C_TU) - (DT)dot(tp_sv(s, l, T_U), ap)) * Di);
-      a = ap;
-      a.w += qdd * ax;
-      if (qf >= 0) cv.L(l, qf) = qdd;
+      const SV<T> U = tp_sv(s, l, T_U);
+      for (int r = 0; r < NR; ++r) {
+        const SV<T> ap = par >= 0 ? apply(X, cgetv(cv, par, C_TA + 6 * r)) : zeroSV<T>();
+        const T qdd = (T)(((DT)cv.L(l, C_TU + 6 * r) - (DT)dot(U, ap)) * Di);
+        SV<T> a = ap;
+        a.w += qdd * ax;
+        if (qf >= 0) cv.L(l, qf + 6 * r) = qdd;
+        cputv(cv, l, C_TA + 6 * r, a);
+      }
     } else {  // free root: a = (I^A)^-1 u, qdd = a (its parent acceleration is 0)
-      a = spd_solve<T, DT>(tp_si(s, l, T_IA), cgetv(cv, l, C_TU));
-      if (qf >= 0) cputv(cv, l, qf, a);
+      SV<T> u[NR], a[NR];
+      for (int r = 0; r < NR; ++r) u[r] = cgetv(cv, l, C_TU + 6 * r);
+      spd_solve_n<T, DT, NR>(tp_si(s, l, T_IA), u, a);
+      for (int r = 0; r < NR; ++r) {
+        if (qf >= 0) cputv(cv, l, qf + 6 * r, a[r]);
+        cputv(cv, l, C_TA + 6 * r, a[r]);
+      }
     }
-    cputv(cv, l, C_TA, a);
   }
 }
 
 // Reverse of test_pass (which must have just run with the same inputs): the
-// caller has put the adjoints of the link accelerations in C_TAB; field qbf
-// (scaled by qbs; qbf < 0: none) holds the adjoint of the joint accelerations.
-// Adds the adjoints of U, 1/D, X and the root articulated inertia to B_U, B_DI,
-// B_E / B_R and B_IA, returns the adjoint of each applied force in fvb and
-// leaves the adjoint of each revolute joint's force (that of a joint impulse on
-// it) in C_TUB.
-template <class T, class DT, class PT>
-CD void test_pass_reverse(Sys<T, PT> s, CView<T> cv, int qbf, T qbs, const int* fl, int nf, SV<T>* fvb) {
+// caller has put the adjoints of the link accelerations in C_TAB + 6 r; field
+// qbf + 6 r (scaled by qbs; qbf < 0: none) holds the adjoint of the joint
+// accelerations.  Adds the adjoints of U, 1/D, X and the root articulated
+// inertia to B_U, B_DI, B_E / B_R and B_IA and returns the adjoint of each input
+// in fvb (a force's spatial adjoint; a joint impulse's adjoint in w.x).
+template <class T, class DT, class PT, int NR>
+CD void test_pass_reverse(Sys<T, PT> s, CView<T> cv, int qbf, T qbs, TPIn<T> in, SV<T>* fvb) {
   const int nl = s.nl;
   for (int l = nl - 1; l >= 0; --l) {  // acceleration pass, leaves -> root
     const int m = s.M(l);
     const int par = meta_parent(m);
     const XF<T> X = tp_xf(s, l, T_E);
-    const SV<T> ab = cgetv(cv, l, C_TAB);
-    const SV<T> apar = par >= 0 ? cgetv(cv, par, C_TA) : zeroSV<T>();
-    SV<T> apb;
+    SV<T> apb[NR], apar[NR];
+    for (int r = 0; r < NR; ++r) apar[r] = par >= 0 ? cgetv(cv, par, C_TA + 6 * r) : zeroSV<T>();
     if (meta_jtype(m) == J_REVOLUTE) {
       const V3<T> ax = s.pv3(l, P_AX);
       const SV<T> U = tp_sv(s, l, T_U);
       const DT Di = get_di<T, DT, PT>(s, l);
-      const T u = cv.L(l, C_TU);
-      const SV<T> ap = par >= 0 ? apply(X, apar) : zeroSV<T>();
-      T qb = dot(ax, ab.w);
-      if (qbf >= 0) qb += qbs * cv.L(l, qbf);
-      const T w = (T)((DT)qb * Di);  // qdd = (u - U.ap) / D
-      cv.L(l, C_TUB) = w;
-      caddv(cv, l, B_U, zeroSV<T>() - w * ap);
-      cv.L(l, B_DI) += (T)((DT)qb * ((DT)u - (DT)dot(U, ap)));
-      apb = ab - w * U;
+      SV<T> Ub = zeroSV<T>();
+      T Dib = T(0);
+      for (int r = 0; r < NR; ++r) {
+        const SV<T> ab = cgetv(cv, l, C_TAB + 6 * r);
+        const T u = cv.L(l, C_TU + 6 * r);
+        const SV<T> ap = par >= 0 ? apply(X, apar[r]) : zeroSV<T>();
+        T qb = dot(ax, ab.w);
+        if (qbf >= 0) qb += qbs * cv.L(l, qbf + 6 * r);
+        const T w = (T)((DT)qb * Di);  // qdd = (u - U.ap) / D
+        cv.L(l, C_TUB + 6 * r) = w;
+        Ub -= w * ap;
+        Dib += (T)((DT)qb * ((DT)u - (DT)dot(U, ap)));
+        apb[r] = ab - w * U;
+      }
+      caddv(cv, l, B_U, Ub);
+      cv.L(l, B_DI) += Dib;
     } else {
-      SV<T> qb = zeroSV<T>();
-      if (qbf >= 0) qb = qbs * cgetv(cv, l, qbf);
-      const SV<T> a = cgetv(cv, l, C_TA);
-      const SV<T> ub = spd_solve<T, DT>(tp_si(s, l, T_IA), ab + qb);
-      cputv(cv, l, C_TUB, ub);
-      caddsi(cv, l, B_IA, scale(T(-1), sym_outer(ub, a)));
-      apb = zeroSV<T>() - qb;
+      SV<T> rhs[NR], ub[NR];
+      for (int r = 0; r < NR; ++r) {
+        SV<T> qb = zeroSV<T>();
+        if (qbf >= 0) qb = qbs * cgetv(cv, l, qbf + 6 * r);
+        rhs[r] = cgetv(cv, l, C_TAB + 6 * r) + qb;
+        apb[r] = zeroSV<T>() - qb;
+      }
+      spd_solve_n<T, DT, NR>(tp_si(s, l, T_IA), rhs, ub);
+      for (int r = 0; r < NR; ++r) {
+        cputv(cv, l, C_TUB + 6 * r, ub[r]);
+        caddsi(cv, l, B_IA, scale(T(-1), sym_outer(ub[r], cgetv(cv, l, C_TA + 6 * r))));
+      }
     }
     if (par >= 0) {
       M3<T> Eb = zeroM3<T>();
       V3<T> rb = zero3<T>();
-      SV<T> aparb = zeroSV<T>();
-      apply_adj(X, apar, apb, Eb, rb, &aparb);
+      for (int r = 0; r < NR; ++r) {
+        SV<T> aparb = zeroSV<T>();
+        apply_adj(X, apar[r], apb[r], Eb, rb, &aparb);
+        caddv(cv, par, C_TAB + 6 * r, aparb);
+      }
       caddm(cv, l, B_E, Eb);
       cadd3(cv, l, B_R, rb);
-      caddv(cv, par, C_TAB, aparb);
     }
   }
   for (int l = 0; l < nl; ++l) {  // bias-force pass, root -> leaves
     const int m = s.M(l);
     const int par = meta_parent(m);
-    SV<T> pAb = zeroSV<T>();
     if (meta_jtype(m) == J_REVOLUTE) {
       const V3<T> ax = s.pv3(l, P_AX);
-      T ub = cv.L(l, C_TUB);
       if (par >= 0) {
         const XF<T> X = tp_xf(s, l, T_E);
         const SV<T> U = tp_sv(s, l, T_U);
         const DT Di = get_di<T, DT, PT>(s, l);
-        const T u = cv.L(l, C_TU);
-        const T uDi = (T)((DT)u * Di);
-        const SV<T> pa = cgetv(cv, l, C_TP) + uDi * U;
         M3<T> Eb = zeroM3<T>();
         V3<T> rb = zero3<T>();
-        SV<T> pab = zeroSV<T>();
-        applyT_adj(X, pa, cgetv(cv, par, C_TPB), Eb, rb, &pab);
+        SV<T> Ub = zeroSV<T>();
+        T Dib = T(0);
+        for (int r = 0; r < NR; ++r) {
+          T ub = cv.L(l, C_TUB + 6 * r);
+          const T u = cv.L(l, C_TU + 6 * r);
+          const T uDi = (T)((DT)u * Di);
+          const SV<T> pa = cgetv(cv, l, C_TP + 6 * r) + uDi * U;
+          SV<T> pab = zeroSV<T>();
+          applyT_adj(X, pa, cgetv(cv, par, C_TPB + 6 * r), Eb, rb, &pab);
+          SV<T> pAb = pab;  // pa = pA + U (u / D)
+          Ub += uDi * pab;
+          const T gb = dot(U, pab);
+          ub += (T)((DT)gb * Di);
+          Dib += (T)((DT)gb * (DT)u);
+          pAb.w -= ub * ax;  // u = -a . pA_w (+ joint impulse)
+          cv.L(l, C_TUB + 6 * r) = ub;
+          cputv(cv, l, C_TPB + 6 * r, pAb);
+        }
         caddm(cv, l, B_E, Eb);
         cadd3(cv, l, B_R, rb);
-        pAb += pab;  // pa = pA + U (u / D)
-        caddv(cv, l, B_U, uDi * pab);
-        const T gb = dot(U, pab);
-        ub += (T)((DT)gb * Di);
-        cv.L(l, B_DI) += (T)((DT)gb * (DT)u);
+        caddv(cv, l, B_U, Ub);
+        cv.L(l, B_DI) += Dib;
+      } else {
+        for (int r = 0; r < NR; ++r) {
+          const T ub = cv.L(l, C_TUB + 6 * r);
+          SV<T> pAb = zeroSV<T>();
+          pAb.w -= ub * ax;
+          cputv(cv, l, C_TPB + 6 * r, pAb);
+        }
       }
-      pAb.w -= ub * ax;  // u = -a . pA_w (+ joint impulse)
-      cv.L(l, C_TUB) = ub;
     } else {
-      pAb = zeroSV<T>() - cgetv(cv, l, C_TUB);  // u = -pA
+      for (int r = 0; r < NR; ++r) cputv(cv, l, C_TPB + 6 * r, zeroSV<T>() - cgetv(cv, l, C_TUB + 6 * r));  // u = -pA
     }
-    cputv(cv, l, C_TPB, pAb);
   }
-  for (int i = 0; i < nf; ++i) fvb[i] = zeroSV<T>() - cgetv(cv, fl[i], C_TPB);  // pA = (children) - f
+  for (int i = 0; i < in.n; ++i) {
+    const int l = in.link[i], r = in.rhs[i];
+    if (in.joint[i]) fvb[i] = SV<T>{{cv.L(l, C_TUB + 6 * r), T(0), T(0)}, zero3<T>()};
+    else fvb[i] = zeroSV<T>() - cgetv(cv, l, C_TPB + 6 * r);  // pA = (children) - f
+  }
 }
 
 // ------------------------------------------------------------------ forward
@@ -287,6 +368,42 @@ SD void gs_update(const CView<T>& cv, int r, int nr, bool box, T hi) {
     ln = ln > -hi ? ln : -hi;
   }
   cv.S(S_LF + r) = ln;
+}
+
+// Test-pass inputs of rows j0, j0 + 1, j0 + 2 (one right-hand side each): the unit
+// world force E_w e_k at a contact point (rows 3c + k) or the unit impulse s on a
+// limited joint (rows 3 nc + k).
+template <class T>
+SD TPIn<T> unit_inputs(const CView<T>& cv, int nc, int nr, int j0, const int* link, const V3<T>* pc,
+                       const int* llink, const T* lsg) {
+  TPIn<T> in;
+  for (int r = 0; r < 3 && j0 + r < nr; ++r) {
+    const int j = j0 + r;
+    if (j < 3 * nc) {
+      const int c = j / 3, k = j % 3;
+      const M3<T> Ew = cgetm(cv, link[c], C_EW);
+      const V3<T> f{Ew.a[k], Ew.a[3 + k], Ew.a[6 + k]};
+      in.force(link[c], r, SV<T>{cross(pc[c], f), f});
+    } else {
+      in.impulse(llink[j - 3 * nc], r, lsg[j - 3 * nc]);
+    }
+  }
+  return in;
+}
+
+// Test-pass inputs of the impulses lambda (one right-hand side): f = E_w lambda_c
+// at each contact point, s lambda on each limited joint.
+template <class T>
+SD TPIn<T> impulse_inputs(const CView<T>& cv, int nc, int nlr, const int* link, const V3<T>* pc,
+                          const int* llink, const T* lsg) {
+  TPIn<T> in;
+  for (int c = 0; c < nc; ++c) {
+    const V3<T> lam{cv.S(S_LF + 3 * c), cv.S(S_LF + 3 * c + 1), cv.S(S_LF + 3 * c + 2)};
+    const V3<T> f = mul(cgetm(cv, link[c], C_EW), lam);
+    in.force(link[c], 0, SV<T>{cross(pc[c], f), f});
+  }
+  for (int k = 0; k < nlr; ++k) in.impulse(llink[k], 0, lsg[k] * cv.S(S_LF + 3 * nc + k));
+  return in;
 }
 
 // Contact and limit impulses of one step; requires aba_forward to have filled the
@@ -373,26 +490,22 @@ CD int contact_forward(Sys<T, PT> s, CView<T> cv, Col<const T> q, Col<const T> q
     const T vstar = qd[meta_voff(s.M(l))] + dt * s.tp(l, T_QDD);
     cv.S(S_B + 3 * nc + k) = lsg[k] * vstar + kphi * cv.S(S_PHI + MAXC + k);
   }
-  // A, one column per active row
-  for (int j = 0; j < nr; ++j) {
-    if (j < 3 * nc) {
-      const int c = j / 3, k = j % 3;
-      const M3<T> Ew = cgetm(cv, link[c], C_EW);
-      const V3<T> f{Ew.a[k], Ew.a[3 + k], Ew.a[6 + k]};  // E_w e_k
-      const SV<T> fv{cross(pc[c], f), f};
-      test_pass<T, DT, PT>(s, cv, &link[c], &fv, 1, nullptr, nullptr, 0, C_TQ);
-    } else {
-      const int k = j - 3 * nc;
-      test_pass<T, DT, PT>(s, cv, nullptr, nullptr, 0, &llink[k], &lsg[k], 1, C_TQ);
+  // A, three columns (right-hand sides) per test pass
+  for (int j0 = 0; j0 < nr; j0 += 3) {
+    const TPIn<T> in = unit_inputs(cv, nc, nr, j0, link, pc, llink, lsg);
+    test_pass<T, DT, PT, 3>(s, cv, in, C_TQ);
+    for (int r = 0; r < 3 && j0 + r < nr; ++r) {
+      const int j = j0 + r;
+      for (int c2 = 0; c2 < nc; ++c2) {
+        const SV<T> a = cgetv(cv, link[c2], C_TA + 6 * r);
+        const V3<T> pa = mulT(cgetm(cv, link[c2], C_EW), a.v + cross(a.w, pc[c2]));
+        cv.S(S_A + (3 * c2) * NROW + j) = pa.x;
+        cv.S(S_A + (3 * c2 + 1) * NROW + j) = pa.y;
+        cv.S(S_A + (3 * c2 + 2) * NROW + j) = pa.z;
+      }
+      for (int k2 = 0; k2 < nlr; ++k2)
+        cv.S(S_A + (3 * nc + k2) * NROW + j) = lsg[k2] * cv.L(llink[k2], C_TQ + 6 * r);
     }
-    for (int c2 = 0; c2 < nc; ++c2) {
-      const SV<T> a = cgetv(cv, link[c2], C_TA);
-      const V3<T> pa = mulT(cgetm(cv, link[c2], C_EW), a.v + cross(a.w, pc[c2]));
-      cv.S(S_A + (3 * c2) * NROW + j) = pa.x;
-      cv.S(S_A + (3 * c2 + 1) * NROW + j) = pa.y;
-      cv.S(S_A + (3 * c2 + 2) * NROW + j) = pa.z;
-    }
-    for (int k2 = 0; k2 < nlr; ++k2) cv.S(S_A + (3 * nc + k2) * NROW + j) = lsg[k2] * cv.L(llink[k2], C_TQ);
   }
   // projected Gauss-Seidel
   for (int r = 0; r < nr; ++r) cv.S(S_LF + r) = T(0);
@@ -411,15 +524,7 @@ CD int contact_forward(Sys<T, PT> s, CView<T> cv, Col<const T> q, Col<const T> q
     }
   }
   // velocity change M^-1 J^T lambda
-  SV<T> fv[MAXC];
-  for (int c = 0; c < nc; ++c) {
-    const V3<T> lam{cv.S(S_LF + 3 * c), cv.S(S_LF + 3 * c + 1), cv.S(S_LF + 3 * c + 2)};
-    const V3<T> f = mul(cgetm(cv, link[c], C_EW), lam);
-    fv[c] = SV<T>{cross(pc[c], f), f};
-  }
-  T jv[MAXL];
-  for (int k = 0; k < nlr; ++k) jv[k] = lsg[k] * cv.S(S_LF + 3 * nc + k);
-  test_pass<T, DT, PT>(s, cv, link, fv, nc, llink, jv, nlr, C_DV);
+  test_pass<T, DT, PT, 1>(s, cv, impulse_inputs(cv, nc, nlr, link, pc, llink, lsg), C_DV);
   return nr;
 }
 
@@ -486,27 +591,21 @@ CD void contact_adjoint(Sys<T, PT> s, CView<T> cv, T dt, ContactParams<T> cp) {
   }
   // 1. the velocity change dv = M^-1 J^T lambda; dv enters qd' directly
   {
-    SV<T> fv[MAXC], fvb[MAXC];
-    V3<T> lam[MAXC];
-    T jv[MAXL];
-    for (int c = 0; c < nc; ++c) {
-      lam[c] = V3<T>{cv.S(S_LF + 3 * c), cv.S(S_LF + 3 * c + 1), cv.S(S_LF + 3 * c + 2)};
-      const V3<T> f = mul(cgetm(cv, link[c], C_EW), lam[c]);
-      fv[c] = SV<T>{cross(pc[c], f), f};
-    }
-    for (int k = 0; k < nlr; ++k) jv[k] = lsg[k] * cv.S(S_LF + 3 * nc + k);
-    test_pass<T, DT, PT>(s, cv, link, fv, nc, llink, jv, nlr, -1);
+    const TPIn<T> in = impulse_inputs(cv, nc, nlr, link, pc, llink, lsg);
+    SV<T> fvb[MAXIN];
+    test_pass<T, DT, PT, 1>(s, cv, in, -1);
     for (int l = 0; l < nl; ++l) cputv(cv, l, C_TAB, zeroSV<T>());
-    test_pass_reverse<T, DT, PT>(s, cv, C_QDDB, T(1) / dt, link, nc, fvb);
-    for (int c = 0; c < nc; ++c) {
+    test_pass_reverse<T, DT, PT, 1>(s, cv, C_QDDB, T(1) / dt, in, fvb);
+    for (int c = 0; c < nc; ++c) {  // entries 0 .. nc - 1 are the contact forces
+      const V3<T> lam{cv.S(S_LF + 3 * c), cv.S(S_LF + 3 * c + 1), cv.S(S_LF + 3 * c + 2)};
       const V3<T> flb = fvb[c].v + cross(fvb[c].w, pc[c]);  // f = E_w lambda, n = p x f
       const V3<T> lb = mulT(cgetm(cv, link[c], C_EW), flb);
       cv.S(S_LB + 3 * c) = lb.x;
       cv.S(S_LB + 3 * c + 1) = lb.y;
       cv.S(S_LB + 3 * c + 2) = lb.z;
-      caddm(cv, link[c], B_EW, outer(flb, lam[c]));
+      caddm(cv, link[c], B_EW, outer(flb, lam));
     }
-    for (int k = 0; k < nlr; ++k) cv.S(S_LB + 3 * nc + k) = lsg[k] * cv.L(llink[k], C_TUB);
+    for (int k = 0; k < nlr; ++k) cv.S(S_LB + 3 * nc + k) = lsg[k] * fvb[nc + k].w.x;  // then the impulses
   }
   // 2. the Gauss-Seidel sweeps, last update first
   for (int r = 0; r < nr; ++r) {
@@ -518,39 +617,37 @@ CD void contact_adjoint(Sys<T, PT> s, CView<T> cv, T dt, ContactParams<T> cp) {
     for (int c = nc - 1; c >= 0; --c)
       for (int qq = 2; qq >= 0; --qq) gs_update_reverse(cv, it, contact_row(c, qq), nr, qq != 0, 3 * c + 2, cp.mu);
   }
-  // 3. the columns of A
-  for (int j = 0; j < nr; ++j) {
-    const bool is_contact = j < 3 * nc;
-    const int c = j / 3, k = j % 3;
-    SV<T> fv;
-    if (is_contact) {
-      const M3<T> Ew = cgetm(cv, link[c], C_EW);
-      const V3<T> f{Ew.a[k], Ew.a[3 + k], Ew.a[6 + k]};
-      fv = SV<T>{cross(pc[c], f), f};
-      test_pass<T, DT, PT>(s, cv, &link[c], &fv, 1, nullptr, nullptr, 0, -1);
-    } else {
-      test_pass<T, DT, PT>(s, cv, nullptr, nullptr, 0, &llink[j - 3 * nc], &lsg[j - 3 * nc], 1, -1);
+  // 3. the columns of A, three per test pass
+  for (int j0 = 0; j0 < nr; j0 += 3) {
+    const TPIn<T> in = unit_inputs(cv, nc, nr, j0, link, pc, llink, lsg);
+    test_pass<T, DT, PT, 3>(s, cv, in, -1);
+    for (int l = 0; l < nl; ++l)
+      for (int r = 0; r < 3; ++r) {
+        cputv(cv, l, C_TAB + 6 * r, zeroSV<T>());
+        cputv(cv, l, C_TQB + 6 * r, zeroSV<T>());
+      }
+    for (int r = 0; r < 3 && j0 + r < nr; ++r) {
+      const int j = j0 + r;
+      for (int c2 = 0; c2 < nc; ++c2) {  // A_{., j} = E_w^T (a_v + a_w x p)
+        const int l2 = link[c2];
+        const V3<T> yb{cv.S(S_AB + (3 * c2) * NROW + j), cv.S(S_AB + (3 * c2 + 1) * NROW + j),
+                       cv.S(S_AB + (3 * c2 + 2) * NROW + j)};
+        const SV<T> a = cgetv(cv, l2, C_TA + 6 * r);
+        const V3<T> z = a.v + cross(a.w, pc[c2]);
+        caddm(cv, l2, B_EW, outer(z, yb));
+        const V3<T> zb = mul(cgetm(cv, l2, C_EW), yb);
+        caddv(cv, l2, C_TAB + 6 * r, SV<T>{cross(pc[c2], zb), zb});
+      }
+      for (int k2 = 0; k2 < nlr; ++k2)  // A_{limit k2, j} = s qdd_j
+        cv.L(llink[k2], C_TQB + 6 * r) += lsg[k2] * cv.S(S_AB + (3 * nc + k2) * NROW + j);
     }
-    for (int l = 0; l < nl; ++l) {
-      cputv(cv, l, C_TAB, zeroSV<T>());
-      cputv(cv, l, C_TQB, zeroSV<T>());
-    }
-    for (int c2 = 0; c2 < nc; ++c2) {  // A_{., j} = E_w^T (a_v + a_w x p)
-      const int l2 = link[c2];
-      const V3<T> yb{cv.S(S_AB + (3 * c2) * NROW + j), cv.S(S_AB + (3 * c2 + 1) * NROW + j),
-                     cv.S(S_AB + (3 * c2 + 2) * NROW + j)};
-      const SV<T> a = cgetv(cv, l2, C_TA);
-      const V3<T> z = a.v + cross(a.w, pc[c2]);
-      caddm(cv, l2, B_EW, outer(z, yb));
-      const V3<T> zb = mul(cgetm(cv, l2, C_EW), yb);
-      caddv(cv, l2, C_TAB, SV<T>{cross(pc[c2], zb), zb});
-    }
-    for (int k2 = 0; k2 < nlr; ++k2)  // A_{limit k2, j} = s qdd_j
-      cv.L(llink[k2], C_TQB) += lsg[k2] * cv.S(S_AB + (3 * nc + k2) * NROW + j);
-    SV<T> fvb;
-    test_pass_reverse<T, DT, PT>(s, cv, C_TQB, T(1), is_contact ? &link[c] : link, is_contact ? 1 : 0, &fvb);
-    if (is_contact) {
-      const V3<T> flb = fvb.v + cross(fvb.w, pc[c]);  // f = E_w e_k
+    SV<T> fvb[MAXIN];
+    test_pass_reverse<T, DT, PT, 3>(s, cv, C_TQB, T(1), in, fvb);
+    for (int i = 0; i < in.n; ++i) {
+      const int j = j0 + in.rhs[i];
+      if (in.joint[i] || j >= 3 * nc) continue;  // a unit impulse is a constant
+      const int c = j / 3, k = j % 3;
+      const V3<T> flb = fvb[i].v + cross(fvb[i].w, pc[c]);  // f = E_w e_k
       V3<T> ek = zero3<T>();
       if (k == 0) ek.x = T(1);
       else if (k == 1) ek.y = T(1);
