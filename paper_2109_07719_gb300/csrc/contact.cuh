@@ -6,9 +6,7 @@
 // solved by projected Gauss-Seidel (the supplement's Alg. 1).  Here, per system
 // and step, after the unconstrained ABA step:
 //   * every contact sphere (centre p in its link's frame, radius r) is tested
-//     against z = 0: gap phi = y_z - r, y = world centre; active when phi < 0
-//     (every sphere and limited joint keeps its rows in every step; an inactive
-//     row's impulse is held at 0, so a warp's systems take one path);
+//     against z = 0: gap phi = y_z - r, y = world centre; active when phi < 0;
 //   * every limited revolute joint is tested against [lo, hi]: below the range
 //     it gives a row J = +e_j with gap q - lo, above it J = -e_j with gap hi - q;
 //     a limit row's impulse is >= 0, like a normal row;
@@ -56,12 +54,11 @@ enum : int {
   S_B = S_A + NROW * NROW,       // b
   S_LAM = S_B + NROW,            // the impulse each Gauss-Seidel update overwrote, [sweep][row]
   S_LF = S_LAM + MAXPGS * NROW,  // lambda (final after the forward solve)
-  S_PHI = S_LF + NROW,           // gap of each contact sphere [MAXC], then of each limited joint [MAXL]
-  S_LINK = S_PHI + MAXC + MAXL,  // link of each contact sphere, then of each limited joint
-  S_SGN = S_LINK + MAXC + MAXL,  // sign s of each limit row (J = s e_j)
-  S_ACT = S_SGN + MAXL,          // 1 if the sphere / limit row is active (gap < 0), else 0
-  S_NC = S_ACT + MAXC + MAXL,    // number of contact spheres
-  S_NL = S_NC + 1,               // number of limited joints
+  S_PHI = S_LF + NROW,           // gap of each active contact [MAXC], then of each active limit [MAXL]
+  S_LINK = S_PHI + MAXC + MAXL,  // link of each active contact, then of each active limit
+  S_SGN = S_LINK + MAXC + MAXL,  // sign s of each active limit row (J = s e_j)
+  S_NC = S_SGN + MAXL,           // number of active contacts
+  S_NL = S_NC + 1,               // number of active limit rows
   S_AB = S_NL + 1,               // adjoint of A
   S_BB = S_AB + NROW * NROW,     // adjoint of b
   S_LB = S_BB + NROW,            // adjoint of lambda
@@ -358,7 +355,7 @@ SD int contact_row(int c, int q) { return q == 0 ? 3 * c + 2 : 3 * c + q - 1; }
 // One Gauss-Seidel update of row r: lambda_r <- project(lambda_r - (A_r . lambda + b_r) / A_rr),
 // onto [lo, hi] (box) or [0, inf) (box false).
 template <class T>
-SD void gs_update(const CView<T>& cv, int r, int nr, bool box, T hi, T act) {
+SD void gs_update(const CView<T>& cv, int r, int nr, bool box, T hi) {
   const T lr = cv.S(S_LF + r);
   T res = cv.S(S_B + r);
   for (int k = 0; k < nr; ++k) res += cv.S(S_A + r * NROW + k) * cv.S(S_LF + k);
@@ -370,7 +367,7 @@ SD void gs_update(const CView<T>& cv, int r, int nr, bool box, T hi, T act) {
     ln = sv < hi ? sv : hi;
     ln = ln > -hi ? ln : -hi;
   }
-  cv.S(S_LF + r) = ln * act;
+  cv.S(S_LF + r) = ln;
 }
 
 // Test-pass inputs of rows j0, j0 + 1, j0 + 2 (one right-hand side each): the unit
@@ -411,15 +408,12 @@ SD TPIn<T> impulse_inputs(const CView<T>& cv, int nc, int nlr, const int* link, 
 
 // Contact and limit impulses of one step; requires aba_forward to have filled the
 // tape (unconstrained qdd included).  Leaves the velocity change in C_DV of every
-// link and returns the number of rows (3 per contact sphere, 1 per limited joint;
-// 0: C_DV is not written and the step has no constraint term).
+// link and returns the number of active rows (0: C_DV is not written and the step
+// has no constraint term).
 template <class T, class DT, class PT>
 CD int contact_forward(Sys<T, PT> s, CView<T> cv, Col<const T> q, Col<const T> qd, T dt, ContactParams<T> cp) {
   const int nl = s.nl;
   world_poses(s, cv);
-  // every contact sphere and every limited joint has its rows in every step, active
-  // or not, so that all systems of a warp (one topology) take the same path; an
-  // inactive row's impulse is held at 0 (the activity flag multiplies each update)
   int nc = 0;
   int link[MAXC];
   V3<T> pc[MAXC];
@@ -429,12 +423,13 @@ CD int contact_forward(Sys<T, PT> s, CView<T> cv, Col<const T> q, Col<const T> q
     const V3<T> p = s.pv3(l, P_CP);
     const V3<T> y = cget3(cv, l, C_OW) + mulT(cgetm(cv, l, C_EW), p);
     const T phi = y.z - r;
-    link[nc] = l;
-    pc[nc] = p;
-    cv.S(S_LINK + nc) = (T)l;
-    cv.S(S_PHI + nc) = phi;
-    cv.S(S_ACT + nc) = phi < T(0) ? T(1) : T(0);
-    ++nc;
+    if (phi < T(0)) {
+      link[nc] = l;
+      pc[nc] = p;
+      cv.S(S_LINK + nc) = (T)l;
+      cv.S(S_PHI + nc) = phi;
+      ++nc;
+    }
   }
   int nlr = 0;
   int llink[MAXL];
@@ -442,25 +437,23 @@ CD int contact_forward(Sys<T, PT> s, CView<T> cv, Col<const T> q, Col<const T> q
   for (int l = 0; l < nl && nlr < MAXL; ++l) {
     const int m = s.M(l);
     if (meta_jtype(m) != J_REVOLUTE) continue;
-    const T lo = s.P(l, P_LO), hi = s.P(l, P_HI);
-    if (!(lo > T(-1e30) || hi < T(1e30))) continue;  // no finite limit
     const T ql = q[meta_qoff(m)];
-    const T below = ql - lo, above = hi - ql;
-    T sg = T(1), phi;
+    const T below = ql - s.P(l, P_LO), above = s.P(l, P_HI) - ql;
+    T sg, phi;
     if (below < T(0)) {
+      sg = T(1);
       phi = below;
     } else if (above < T(0)) {
       sg = T(-1);
       phi = above;
     } else {
-      phi = below < above ? below : above;
+      continue;
     }
     llink[nlr] = l;
     lsg[nlr] = sg;
     cv.S(S_LINK + MAXC + nlr) = (T)l;
     cv.S(S_PHI + MAXC + nlr) = phi;
     cv.S(S_SGN + nlr) = sg;
-    cv.S(S_ACT + MAXC + nlr) = phi < T(0) ? T(1) : T(0);
     ++nlr;
   }
   cv.S(S_NC) = (T)nc;
@@ -490,14 +483,12 @@ CD int contact_forward(Sys<T, PT> s, CView<T> cv, Col<const T> q, Col<const T> q
     const V3<T> pv = mulT(cgetm(cv, l, C_EW), V.v + cross(V.w, pc[c]));
     cv.S(S_B + 3 * c) = pv.x;
     cv.S(S_B + 3 * c + 1) = pv.y;
-    const T phi = cv.S(S_PHI + c);
-    cv.S(S_B + 3 * c + 2) = pv.z + kphi * (phi < T(0) ? phi : T(0));
+    cv.S(S_B + 3 * c + 2) = pv.z + kphi * cv.S(S_PHI + c);
   }
   for (int k = 0; k < nlr; ++k) {
     const int l = llink[k];
     const T vstar = qd[meta_voff(s.M(l))] + dt * s.tp(l, T_QDD);
-    const T phi = cv.S(S_PHI + MAXC + k);
-    cv.S(S_B + 3 * nc + k) = lsg[k] * vstar + kphi * (phi < T(0) ? phi : T(0));
+    cv.S(S_B + 3 * nc + k) = lsg[k] * vstar + kphi * cv.S(S_PHI + MAXC + k);
   }
   // A, three columns (right-hand sides) per test pass
   for (int j0 = 0; j0 < nr; j0 += 3) {
@@ -523,13 +514,13 @@ CD int contact_forward(Sys<T, PT> s, CView<T> cv, Col<const T> q, Col<const T> q
       for (int qq = 0; qq < 3; ++qq) {
         const int r = contact_row(c, qq);
         cv.S(S_LAM + it * NROW + r) = cv.S(S_LF + r);
-        gs_update(cv, r, nr, qq != 0, cp.mu * cv.S(S_LF + 3 * c + 2), cv.S(S_ACT + c));
+        gs_update(cv, r, nr, qq != 0, cp.mu * cv.S(S_LF + 3 * c + 2));
       }
     }
     for (int k = 0; k < nlr; ++k) {
       const int r = 3 * nc + k;
       cv.S(S_LAM + it * NROW + r) = cv.S(S_LF + r);
-      gs_update(cv, r, nr, false, T(0), cv.S(S_ACT + MAXC + k));
+      gs_update(cv, r, nr, false, T(0));
     }
   }
   // velocity change M^-1 J^T lambda
@@ -543,7 +534,7 @@ CD int contact_forward(Sys<T, PT> s, CView<T> cv, Col<const T> q, Col<const T> q
 // new lambda_r in S_LB onto lambda (S_LB), A (S_AB) and b (S_BB).  For a box row
 // the bound's adjoint goes to the normal impulse of contact c.
 template <class T>
-SD void gs_update_reverse(const CView<T>& cv, int it, int r, int nr, bool box, int rn, T mu, T act) {
+SD void gs_update_reverse(const CView<T>& cv, int it, int r, int nr, bool box, int rn, T mu) {
   const T lnb = cv.S(S_LB + r);
   const T lr = cv.S(S_LAM + it * NROW + r);
   cv.S(S_LF + r) = lr;  // the vector as the update saw it
@@ -553,9 +544,7 @@ SD void gs_update_reverse(const CView<T>& cv, int it, int r, int nr, bool box, i
   for (int k = 0; k < nr; ++k) res += cv.S(S_A + r * NROW + k) * cv.S(S_LF + k);
   const T sv = lr - res / Arr;
   T sb = T(0);
-  if (act == T(0)) {
-    // the impulse of an inactive row is held at 0: nothing flows back
-  } else if (!box) {
+  if (!box) {
     if (sv >= T(0)) sb = lnb;
   } else {
     const T hi = mu * cv.S(S_LF + rn);
@@ -624,11 +613,9 @@ CD void contact_adjoint(Sys<T, PT> s, CView<T> cv, T dt, ContactParams<T> cp) {
     for (int k = 0; k < nr; ++k) cv.S(S_AB + r * NROW + k) = T(0);
   }
   for (int it = cp.iters - 1; it >= 0; --it) {
-    for (int k = nlr - 1; k >= 0; --k)
-      gs_update_reverse(cv, it, 3 * nc + k, nr, false, 0, cp.mu, cv.S(S_ACT + MAXC + k));
+    for (int k = nlr - 1; k >= 0; --k) gs_update_reverse(cv, it, 3 * nc + k, nr, false, 0, cp.mu);
     for (int c = nc - 1; c >= 0; --c)
-      for (int qq = 2; qq >= 0; --qq)
-        gs_update_reverse(cv, it, contact_row(c, qq), nr, qq != 0, 3 * c + 2, cp.mu, cv.S(S_ACT + c));
+      for (int qq = 2; qq >= 0; --qq) gs_update_reverse(cv, it, contact_row(c, qq), nr, qq != 0, 3 * c + 2, cp.mu);
   }
   // 3. the columns of A, three per test pass
   for (int j0 = 0; j0 < nr; j0 += 3) {
