@@ -450,10 +450,10 @@ __device__ __forceinline__ void pair_arrive_empty(int b) {
 
 // Shared memory of one pipelined block, in scalars per lane: the two tapes, the
 // adjoint accumulators, model constants, meta words, the state adjoint, the
-// mass-gradient sums, the consumer's double-buffered x^t and the producer's
-// double-buffered (x^t, tau^t), both fetched one step ahead.
+// mass-gradient sums, the consumer's copy of x^t and the producer's
+// double-buffered (x^t, tau^t) fetched one step ahead.
 __host__ __device__ __forceinline__ long long pipe_smem_per_tile(int maxL, int nx, int nv) {
-  return (long long)maxL * (2 * NTAPE_PROD + NADJ_CONS + NPRM + 1 + 1) + nx + 2LL * nx + 2LL * (nx + nv);
+  return (long long)maxL * (2 * NTAPE_PROD + NADJ_CONS + NPRM + 1 + 1) + 2LL * nx + 2LL * (nx + nv);
 }
 
 template <class T, class DT>
@@ -474,8 +474,8 @@ k_backward_pipe(DevModel<T> m, const T* __restrict__ ckpt, const T* __restrict__
   T* s_meta = s_prm + L * NPRM * LANES;
   T* s_state = s_meta + L * LANES;
   T* s_gm = s_state + (long long)NX * LANES;
-  T* s_x = s_gm + L * LANES;               // [2][NX][LANES]
-  T* s_in = s_x + 2LL * NX * LANES;        // [2][NX + nvm][LANES]
+  T* s_x = s_gm + L * LANES;
+  T* s_in = s_x + (long long)NX * LANES;  // [2][NX + nvm][LANES]
   const int W = NX + nvm;
   int* meta_l = reinterpret_cast<int*>(s_meta + lane);
   int unit = m.persistent ? next_unit(m.counter) : (int)blockIdx.x;
@@ -485,11 +485,6 @@ k_backward_pipe(DevModel<T> m, const T* __restrict__ ckpt, const T* __restrict__
     const int b = act ? m.sys_of_slot[slot] : 0;
     const int nl = act ? m.nl[slot] : 0;
     const int nq = act ? (m.nqv[slot] & 0xffff) : 0, nv = act ? (m.nqv[slot] >> 16) : 0;
-    // the consumer's x^t, fetched one step ahead
-    auto fetch_x = [&](long long t) {
-      T* dst = s_x + (t & 1) * NX * LANES + lane;
-      for (int d = 0; d < NX; ++d) cp_async(dst + d * LANES, ckpt + (t * NX + d) * B + b);
-    };
     if (consumer && act) {
       const T* gprm = m.prm + (long long)unit * L * NPRM * LANES + lane;
       const int* gmeta = m.meta + (long long)unit * L * LANES + lane;
@@ -508,9 +503,6 @@ k_backward_pipe(DevModel<T> m, const T* __restrict__ ckpt, const T* __restrict__
     };
     if (!consumer) {
       if (act && Tn > 0) fetch(Tn - 1, (int)((Tn - 1) & 1));
-      cp_commit();
-    } else {
-      if (act && Tn > 0) fetch_x(Tn - 1);
       cp_commit();
     }
     Col<T> gq{s_state + lane, LANES}, gqd{s_state + nqm * LANES + lane, LANES}, gm{s_gm + lane, LANES};
@@ -546,15 +538,15 @@ k_backward_pipe(DevModel<T> m, const T* __restrict__ ckpt, const T* __restrict__
         __syncwarp();
         pair_arrive_full(buf);
       } else {  // consumer: the adjoint of step t from tape t & 1
-        if (act && t > 0) fetch_x(t - 1);
+        if (act)
+          for (int d = 0; d < NX; ++d) cp_async(s_x + d * LANES + lane, ckpt + (t * NX + d) * B + b);
         cp_commit();
-        cp_wait_all_but_newest();
         __syncwarp();
         pair_sync_full(buf);
+        cp_wait_all();
         if (act) {
           const Sys<T, T, LAY_PROD, LAY_CONS> sc{sprm, meta_l, tape_b + lane, s_adj + lane, nl, MS};
-          const T* xs = s_x + (t & 1) * NX * LANES + lane;
-          Col<const T> q{xs, LANES}, qd{xs + nqm * LANES, LANES};
+          Col<const T> q{s_x + lane, LANES}, qd{s_x + nqm * LANES + lane, LANES};
           T* gt = gtau + t * nvm * B + b;
           step_adjoint<T, DT>(sc, q, qd, gq, gqd, Col<T>{gt, B}, gm, g, m.dt, m.integ);
           for (int d = nv; d < nvm; ++d) gt[d * B] = T(0);
@@ -568,7 +560,7 @@ k_backward_pipe(DevModel<T> m, const T* __restrict__ ckpt, const T* __restrict__
         if (t >= 2) pair_arrive_empty(buf);
       }
     }
-    cp_wait_all();
+    if (!consumer) cp_wait_all();
     if (consumer && act) {
       bool ok = true;
       for (int d = 0; d < nq; ++d) ok &= finite_t(gq[d]);
