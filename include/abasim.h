@@ -225,11 +225,11 @@ int sim_set_launch(sim_handle* h, int32_t threads, int32_t schedule);
  * memory when the block's tiles of 32 systems fit the per-block limit, else in
  * the handle's global scratch; SIM_TAPE_GLOBAL / SIM_TAPE_SHARED force one
  * (SHARED fails with SIM_EUNSUPPORTED at launch if it does not fit).
- * SIM_TAPE_PIPELINED runs batches of serial revolute chains (FP32 storage) with
- * two warps per 32-system tile: in the rollout one warp runs the articulated-
- * inertia recursion of each step while the other runs the velocity, bias-force
- * and acceleration passes (chains of at most 14 links); in the adjoint with
- * checkpoint interval 1 one warp recomputes step t's forward intermediates into
+ * SIM_TAPE_PIPELINED runs batches of serial revolute chains with two warps per
+ * 32-system tile: in the rollout (any precision, chains of at most 14 links) one
+ * warp runs the articulated-inertia recursion of each step while the other runs
+ * the velocity, bias-force and acceleration passes; in the adjoint (FP32 storage,
+ * checkpoint interval 1) one warp recomputes step t's forward intermediates into
  * one of two shared-memory tapes while the other differentiates step t + 1 from
  * the other tape (when the two tapes fit, about 7 links).  AUTO picks each when it
  * applies; forcing it fails with SIM_EUNSUPPORTED where it does not.  Models with contact spheres or joint limits always run with the tape

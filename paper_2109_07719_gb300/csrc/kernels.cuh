@@ -866,8 +866,8 @@ int launch_rollout(sim_handle* h, const void* q0, const void* qd0, const void* t
   int threads = h->block;
   if (h->ctape) {
     kern = rollout_contact_kernel<T, DT>();
-  } else if constexpr (sizeof(T) == 4) {  // on-chip modes: FP32 storage only
-    bool piped = false;
+  } else {
+    bool piped = false;  // the pipelined rollout, any precision
     if (h->all_chains && h->maxL <= PIPE_MAX_LINKS &&
         (h->tape_space == SIM_TAPE_AUTO || h->tape_space == SIM_TAPE_PIPELINED)) {
       const size_t need =
@@ -887,11 +887,13 @@ int launch_rollout(sim_handle* h, const void* q0, const void* qd0, const void* t
     }
     if (!piped && h->tape_space == SIM_TAPE_PIPELINED)
       return fail(h, SIM_EUNSUPPORTED, "the pipelined rollout needs serial revolute chains of at most 14 links");
-    if (!piped) {
-      rc = choose_storage<T>(h, k_rollout<T, DT, ST_GLOBAL>, k_rollout<T, DT, ST_HYBRID>,
-                             k_rollout<T, DT, ST_SMEM>, false, &st, &shm);
-      if (st == ST_SMEM) kern = k_rollout<T, DT, ST_SMEM>;
-      if (st == ST_HYBRID) kern = k_rollout<T, DT, ST_HYBRID>;
+    if constexpr (sizeof(T) == 4) {  // the other on-chip modes: FP32 storage only
+      if (!piped) {
+        rc = choose_storage<T>(h, k_rollout<T, DT, ST_GLOBAL>, k_rollout<T, DT, ST_HYBRID>,
+                               k_rollout<T, DT, ST_SMEM>, false, &st, &shm);
+        if (st == ST_SMEM) kern = k_rollout<T, DT, ST_SMEM>;
+        if (st == ST_HYBRID) kern = k_rollout<T, DT, ST_HYBRID>;
+      }
     }
   }
   if (rc != SIM_OK) return rc;
