@@ -138,3 +138,45 @@ def test_pipelined_rollout_chain_length_limit(n, expect):
             check("state", x.cpu().numpy(), y.cpu().numpy(), 1e-5)
     else:
         assert mode != "pipelined"
+
+
+def _mixed_chains(B3=37, B7=30, T=21):
+    """A batch of 3-link and 7-link serial chains (tiles mixing both lengths after
+    slot packing): the model descriptions concatenated system by system."""
+    a = wl.serial_chains(B=B3, T=T, n=3, precision="fp32")
+    c = wl.serial_chains(B=B7, T=T, n=7, precision="fp32", seed=wl.SEED_BASE + 11)
+    ma, mc = a.model, c.model
+    off = np.concatenate([ma.sys_link_offset, ma.sys_link_offset[-1] + mc.sys_link_offset[1:]]).astype(np.int32)
+    cat = lambda f: np.concatenate([getattr(ma, f), getattr(mc, f)])  # noqa: E731
+    m = wl.ModelDesc(off, cat("parent"), cat("joint_type"), cat("axis"), cat("X_tree"), cat("mass"), cat("com"),
+                     cat("I_com"), ma.dt, ma.gravity, "mixed_chains")
+    q0 = np.zeros((7, B3 + B7))
+    q0[:3, :B3] = a.q0
+    q0[:, B3:] = c.q0
+    return m, q0, np.zeros((7, B3 + B7))
+
+
+def test_pipelined_kernels_with_mixed_chain_lengths():
+    from paper_2109_07719_gb300 import Simulator
+    m, q0h, qd0h = _mixed_chains()
+    sim = Simulator(m, precision="fp32")
+    dev = sim.device
+    g = torch.Generator().manual_seed(21)
+    q0 = torch.tensor(q0h, dtype=torch.float32, device=dev)
+    qd0 = torch.tensor(0.3 * np.random.default_rng(4).standard_normal(qd0h.shape), dtype=torch.float32, device=dev)
+    nv = torch.tensor(m.nv_per_system())
+    mask = (torch.arange(7)[:, None] < nv[None, :]).float().to(dev)
+    qd0 = qd0 * mask
+    tau = torch.randn((21, 7, sim.B), generator=g).float().to(dev) * mask
+    gqT, gqdT = torch.ones_like(q0) * mask, torch.ones_like(qd0) * mask
+    outs = {}
+    for space in ("global", "pipelined"):
+        sim.set_tape_space(space)
+        qT, qdT, ck, _ = sim.rollout(q0, qd0, tau)
+        gr = sim.backward(ck, tau, gqT, gqdT)
+        torch.cuda.synchronize()
+        outs[space] = (qT, qdT) + tuple(gr)
+        assert sim.last_storage() == ((space, space) if space == "pipelined" else ("global", "global"))
+    for name, x, y in zip(("qT", "qdT", "gq0", "gqd0", "gtau", "gmass"), outs["global"], outs["pipelined"]):
+        check(name, y.cpu().numpy(), x.cpu().numpy(), 1e-5)
+    assert sim.status().sum() == 0
