@@ -1,6 +1,6 @@
 """Build the CUDA library in-tree: ``csrc/*.cu`` -> ``_lib/libabasim.so``.
 
-Fourteen translation units (the host side of the C ABI; kernel instantiation
+Thirteen translation units (the host side of the C ABI; kernel instantiation
 units per precision, direction and adjoint storage mode; the kernels of models
 with contact spheres per precision), compiled by nvcc for sm_103a only, in
 parallel, then linked.  Called by ``__graft_entry__.build()`` and, lazily, by
@@ -21,7 +21,7 @@ INCLUDE = os.path.join(os.path.dirname(HERE), "include")
 SOURCES = ["abasim.cu", "inst_fp32_fwd.cu", "inst_fp32_bwd.cu", "inst_fp32_bwd_hybrid.cu",
            "inst_fp32_bwd_smem.cu", "inst_mixed_fwd.cu", "inst_mixed_bwd.cu", "inst_mixed_bwd_hybrid.cu",
            "inst_mixed_bwd_smem.cu", "inst_fp64.cu", "inst_fp32_contact.cu", "inst_mixed_contact.cu",
-           "inst_fp64_contact.cu", "inst_fp64_bwd_onchip.cu"]
+           "inst_fp64_contact.cu"]
 DEPS = SOURCES + ["aba_step.cuh", "contact.cuh", "spatial.cuh", "dual.cuh", "kernels.cuh", "handle.h"]
 
 NVCC_FLAGS = ["-gencode", "arch=compute_103a,code=sm_103a", "-lineinfo", "-O3", "-std=c++17",

@@ -824,7 +824,7 @@ template <class T, class K0, class K1, class K2>
 int choose_storage(sim_handle* h, K0 k_global, K1 k_hybrid, K2 k_smem, bool bwd, int* st, size_t* bytes) {
   *st = ST_GLOBAL;
   *bytes = 0;
-  if (h->tape_space == SIM_TAPE_GLOBAL) return SIM_OK;
+  if (h->tape_space == SIM_TAPE_GLOBAL || sizeof(T) != 4) return SIM_OK;
   int limit = 0;
   cudaError_t e = cudaDeviceGetAttribute(&limit, cudaDevAttrMaxSharedMemoryPerBlockOptin, h->device);
   if (e != cudaSuccess) return cuda_fail(h, e, "shared-memory limit query");
@@ -887,11 +887,13 @@ int launch_rollout(sim_handle* h, const void* q0, const void* qd0, const void* t
     }
     if (!piped && h->tape_space == SIM_TAPE_PIPELINED)
       return fail(h, SIM_EUNSUPPORTED, "the pipelined rollout needs serial revolute chains of at most 14 links");
-    if (!piped) {  // the other on-chip modes, when they fit
-      rc = choose_storage<T>(h, k_rollout<T, DT, ST_GLOBAL>, k_rollout<T, DT, ST_HYBRID>,
-                             k_rollout<T, DT, ST_SMEM>, false, &st, &shm);
-      if (st == ST_SMEM) kern = k_rollout<T, DT, ST_SMEM>;
-      if (st == ST_HYBRID) kern = k_rollout<T, DT, ST_HYBRID>;
+    if constexpr (sizeof(T) == 4) {  // the other on-chip modes: FP32 storage only
+      if (!piped) {
+        rc = choose_storage<T>(h, k_rollout<T, DT, ST_GLOBAL>, k_rollout<T, DT, ST_HYBRID>,
+                               k_rollout<T, DT, ST_SMEM>, false, &st, &shm);
+        if (st == ST_SMEM) kern = k_rollout<T, DT, ST_SMEM>;
+        if (st == ST_HYBRID) kern = k_rollout<T, DT, ST_HYBRID>;
+      }
     }
   }
   if (rc != SIM_OK) return rc;
@@ -917,32 +919,29 @@ int launch_backward(sim_handle* h, const void* ckpt, const void* tau, int64_t T_
   int threads = h->block;
   if (h->ctape) {
     kern = backward_contact_kernel<T, DT>();
-  } else {
+  } else if constexpr (sizeof(T) == 4) {  // on-chip modes: FP32 storage only
     bool piped = false;
-    if constexpr (sizeof(T) == 4) {  // the pipelined two-warp adjoint: FP32 storage, k = 1, serial chains
-      if (k == 1 && T_ > 0 && h->all_chains &&
-          (h->tape_space == SIM_TAPE_AUTO || h->tape_space == SIM_TAPE_PIPELINED)) {
-        // when its shared memory fits one block
-        int limit = 0;
-        cudaError_t e = cudaDeviceGetAttribute(&limit, cudaDevAttrMaxSharedMemoryPerBlockOptin, h->device);
-        if (e != cudaSuccess) return cuda_fail(h, e, "shared-memory limit query");
-        const size_t need =
-            (size_t)pipe_smem_per_tile(h->maxL, h->nq_max + h->nv_max, h->nv_max) * LANES * sizeof(T);
-        if (need <= (size_t)limit) {
-          kern = backward_pipe_kernel<T, DT>();
-          e = cudaFuncSetAttribute((const void*)kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)need);
-          if (e != cudaSuccess) return cuda_fail(h, e, "shared-memory opt-in");
-          st = ST_PIPE;
-          shm = need;
-          threads = 2 * LANES;
-          piped = true;
-        }
+    if (k == 1 && T_ > 0 && h->all_chains &&
+        (h->tape_space == SIM_TAPE_AUTO || h->tape_space == SIM_TAPE_PIPELINED)) {
+      // the pipelined two-warp adjoint, when its shared memory fits one block
+      int limit = 0;
+      cudaError_t e = cudaDeviceGetAttribute(&limit, cudaDevAttrMaxSharedMemoryPerBlockOptin, h->device);
+      if (e != cudaSuccess) return cuda_fail(h, e, "shared-memory limit query");
+      const size_t need =
+          (size_t)pipe_smem_per_tile(h->maxL, h->nq_max + h->nv_max, h->nv_max) * LANES * sizeof(T);
+      if (need <= (size_t)limit) {
+        kern = backward_pipe_kernel<T, DT>();
+        e = cudaFuncSetAttribute((const void*)kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)need);
+        if (e != cudaSuccess) return cuda_fail(h, e, "shared-memory opt-in");
+        st = ST_PIPE;
+        shm = need;
+        threads = 2 * LANES;
+        piped = true;
       }
     }
     if (!piped && h->tape_space == SIM_TAPE_PIPELINED)
       return fail(h, SIM_EUNSUPPORTED,
-                  "the pipelined adjoint needs FP32 storage, k = 1, serial revolute chains and a tile that fits "
-                  "in shared memory");
+                  "the pipelined adjoint needs k = 1, serial revolute chains and a tile that fits in shared memory");
     if (!piped) {
       const BackwardKernel<T> k_hyb = backward_kernel<T, DT, ST_HYBRID>();
       const BackwardKernel<T> k_smem = backward_kernel<T, DT, ST_SMEM>();
