@@ -232,12 +232,15 @@ int sim_set_launch(sim_handle* h, int32_t threads, int32_t schedule);
  * checkpoint interval 1) one warp recomputes step t's forward intermediates into
  * one of two shared-memory tapes while the other differentiates step t + 1 from
  * the other tape (when the two tapes fit, about 7 links).  AUTO picks each when it
- * applies; forcing it fails with SIM_EUNSUPPORTED where it does not.  Models with contact spheres or joint limits always run with the tape
+ * applies; forcing it fails with SIM_EUNSUPPORTED where it does not.
+ * SIM_TAPE_ONE_WARP chooses like AUTO among the one-warp-per-tile kernels only
+ * (the autotuner times both, as one or two lanes per system).  Models with contact spheres or joint limits always run with the tape
  * in global memory.  Results do not depend on the choice beyond rounding. */
 #define SIM_TAPE_AUTO 0
 #define SIM_TAPE_GLOBAL 1
 #define SIM_TAPE_SHARED 2
 #define SIM_TAPE_PIPELINED 3
+#define SIM_TAPE_ONE_WARP 4  /* as SIM_TAPE_AUTO, without the pipelined kernels */
 int sim_set_tape_space(sim_handle* h, int32_t space);
 
 /* The storage mode the last sim_rollout (or step) and sim_backward_rollout

@@ -197,9 +197,10 @@ class Simulator:
         self.launch = (int(threads) or 32, bool(persistent))
 
     def set_tape_space(self, space: str = "auto"):
-        """'auto' (the pipelined adjoint or shared memory when they fit), 'global',
-        'shared' (one warp per tile, tape on chip) or 'pipelined' (two warps per tile)."""
-        code = {"auto": 0, "global": 1, "shared": 2, "pipelined": 3}[space]
+        """'auto' (the pipelined kernels or shared memory when they fit), 'global',
+        'shared' (one warp per tile, tape on chip), 'pipelined' (two warps per tile)
+        or 'one_warp' (as 'auto' without the pipelined kernels)."""
+        code = {"auto": 0, "global": 1, "shared": 2, "pipelined": 3, "one_warp": 4}[space]
         self._check(lib.sim_set_tape_space(self._h, code), "sim_set_tape_space")
 
     STORAGE = ("global", "hybrid", "shared", "pipelined")

@@ -1,16 +1,23 @@
 """Launch-shape autotuner for the batched rollout kernels.
 
-Times a short forward + adjoint rollout for each candidate (threads per block,
-grid or persistent schedule) and keeps the fastest.  Results are cached in a
-JSON file keyed by the batch signature (systems, padded sizes, links, precision,
-link-count histogram) and the GPU name, so a model is tuned once per device type.
+Times a short forward + adjoint rollout for each candidate — lanes per system
+(one warp per 32-system tile, or the pipelined kernels' two wherever they
+apply), threads per block (systems per block with one lane) and grid or
+persistent schedule — and keeps the fastest.  A two-lane candidate is dropped
+when neither direction ran pipelined (the model is not a batch of short serial
+chains, or the checkpoint interval is above 1).  Results are cached in a JSON file keyed by the batch signature
+(systems, padded sizes, links, precision, link-count histogram) and the GPU
+name, so a model is tuned once per device type.
 """
 from __future__ import annotations
 
 import json
 import os
 
-CANDIDATES = [(32, False), (64, False), (128, False), (32, True), (64, True), (128, True)]
+# (threads per block, persistent schedule, lanes per system)
+CANDIDATES = [(32, False, 1), (64, False, 1), (128, False, 1), (32, True, 1), (64, True, 1), (128, True, 1),
+              (32, False, 2), (32, True, 2)]
+TAPE_SPACE = {1: "one_warp", 2: "auto"}
 
 
 def cache_path() -> str:
@@ -52,32 +59,43 @@ def choose(times: dict):
     return best
 
 
+def apply(sim, cand):
+    threads, persistent, lanes = cand
+    sim.set_tape_space(TAPE_SPACE[lanes])
+    sim.set_launch(threads, persistent)
+
+
 def autotune(sim, q0, qd0, T_probe: int = 16, reps: int = 3, k: int = 1, use_cache: bool = True,
              timer=None, device_name: str | None = None):
-    """Select and apply the fastest launch shape for ``sim``; returns (threads, persistent).
+    """Select and apply the fastest candidate for ``sim``; returns (threads, persistent, lanes).
 
-    ``timer(sim, cand)`` may replace the GPU measurement (it returns seconds)."""
+    ``timer(sim, cand)`` may replace the GPU measurement; it returns seconds."""
     import torch
     name = device_name or torch.cuda.get_device_name(sim.device)
     key = cache_key(sim.signature, name)
     table = load_cache() if use_cache else {}
     if key in table:
-        threads, persistent = table[key]["threads"], table[key]["persistent"]
-        sim.set_launch(threads, persistent)
-        return threads, persistent
+        e = table[key]
+        best = (e["threads"], e["persistent"], e.get("lanes", 1))
+        apply(sim, best)
+        return best
     if timer is None:
         timer = _gpu_timer(q0, qd0, T_probe, reps, k)
     times = {}
     for cand in CANDIDATES:
-        if cand[0] > 32 and cand[0] // 2 >= sim.B:
+        if cand[2] == 1 and cand[0] > 32 and cand[0] // 2 >= sim.B:
             continue
-        sim.set_launch(*cand)
-        times[cand] = timer(sim, cand)
+        apply(sim, cand)
+        t = timer(sim, cand)
+        if cand[2] == 2 and "pipelined" not in sim.last_storage():
+            continue                                   # ran as one lane: a repeat of another candidate
+        times[cand] = t
     best = choose(times)
-    sim.set_launch(*best)
+    apply(sim, best)
     if use_cache:
-        table[key] = {"threads": best[0], "persistent": best[1],
-                      "seconds": {f"{c[0]}/{'persistent' if c[1] else 'grid'}": t for c, t in times.items()}}
+        table[key] = {"threads": best[0], "persistent": best[1], "lanes": best[2],
+                      "seconds": {f"{c[0]}/{'persistent' if c[1] else 'grid'}/{c[2]} lane(s)": t
+                                  for c, t in times.items()}}
         save_cache(table)
     return best
 

@@ -488,7 +488,7 @@ int sim_set_launch(sim_handle* h, int32_t threads, int32_t schedule) {
 int sim_set_tape_space(sim_handle* h, int32_t space) {
   if (!h) return SIM_EINVAL;
   if (space != SIM_TAPE_AUTO && space != SIM_TAPE_GLOBAL && space != SIM_TAPE_SHARED &&
-      space != SIM_TAPE_PIPELINED)
+      space != SIM_TAPE_PIPELINED && space != SIM_TAPE_ONE_WARP)
     return fail(h, SIM_EINVAL, "unknown tape space");
   h->tape_space = space;
   return SIM_OK;

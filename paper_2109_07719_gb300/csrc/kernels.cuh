@@ -845,7 +845,8 @@ int choose_storage(sim_handle* h, K0 k_global, K1 k_hybrid, K2 k_smem, bool bwd,
     int per_sm = 0;
     e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, h->block, need);
     if (e != cudaSuccess) return cuda_fail(h, e, "occupancy query");
-    if (h->tape_space == SIM_TAPE_AUTO && waves(per_sm) > waves(per_sm_g)) continue;
+    const bool automatic = h->tape_space == SIM_TAPE_AUTO || h->tape_space == SIM_TAPE_ONE_WARP;
+    if (automatic && waves(per_sm) > waves(per_sm_g)) continue;
     if (h->tape_space == SIM_TAPE_SHARED && mode != ST_SMEM) break;
     *st = mode;
     *bytes = need;

@@ -7,19 +7,31 @@ from paper_2109_07719_gb300 import autotune as at
 
 
 class FakeSim:
-    def __init__(self, B=4096):
+    """Records the launch controls; ``pipelines`` says whether the model's shape
+    lets the two-lane kernels run (what ``last_storage`` then reports)."""
+
+    def __init__(self, B=4096, pipelines=True):
         self.B = B
         self.signature = (B, 7, 7, 7 * B, "fp32", "abc")
         self.calls = []
+        self.pipelines = pipelines
+        self.space = "auto"
 
     def set_launch(self, threads=0, persistent=False):
-        self.calls.append((threads, persistent))
+        self.calls.append((threads, persistent, self.space))
         self.launch = (threads, persistent)
+
+    def set_tape_space(self, space="auto"):
+        self.space = space
+
+    def last_storage(self):
+        mode = "pipelined" if self.space == "auto" and self.pipelines else "shared"
+        return mode, mode
 
 
 def test_choose_picks_fastest_and_breaks_ties_by_order():
-    times = {(32, False): 2.0, (64, False): 1.0, (128, True): 1.0}
-    assert at.choose(times) == (64, False)
+    times = {(32, False, 1): 2.0, (64, False, 1): 1.0, (128, True, 1): 1.0, (32, True, 2): 1.0}
+    assert at.choose(times) == (64, False, 1)
     with pytest.raises(ValueError):
         at.choose({})
 
@@ -27,8 +39,8 @@ def test_choose_picks_fastest_and_breaks_ties_by_order():
 def test_autotune_times_candidates_and_caches(tmp_path, monkeypatch):
     monkeypatch.setenv("ABASIM_TUNE_CACHE", str(tmp_path / "tune.json"))
     sim = FakeSim()
-    cost = {(32, False): 3.0, (64, False): 2.0, (128, False): 2.5, (32, True): 1.5,
-            (64, True): 4.0, (128, True): 5.0}
+    cost = {(32, False, 1): 3.0, (64, False, 1): 2.0, (128, False, 1): 2.5, (32, True, 1): 1.5,
+            (64, True, 1): 4.0, (128, True, 1): 5.0, (32, False, 2): 1.6, (32, True, 2): 1.7}
     seen = []
 
     def timer(s, cand):
@@ -36,8 +48,8 @@ def test_autotune_times_candidates_and_caches(tmp_path, monkeypatch):
         return cost[cand]
 
     best = at.autotune(sim, None, None, timer=timer, device_name="GB300")
-    assert best == (32, True)
-    assert sim.launch == (32, True)
+    assert best == (32, True, 1)
+    assert sim.launch == (32, True) and sim.space == "one_warp"
     assert sorted(seen) == sorted(cost)
     table = json.load(open(tmp_path / "tune.json"))
     assert len(table) == 1
@@ -45,7 +57,7 @@ def test_autotune_times_candidates_and_caches(tmp_path, monkeypatch):
     sim2 = FakeSim()
     best2 = at.autotune(sim2, None, None, timer=lambda s, c: pytest.fail("timed again"),
                         device_name="GB300")
-    assert best2 == (32, True) and sim2.calls == [(32, True)]
+    assert best2 == (32, True, 1) and sim2.calls == [(32, True, "one_warp")]
     # another GPU name is another key
     sim3 = FakeSim()
     at.autotune(sim3, None, None, timer=timer, device_name="other")
@@ -59,3 +71,33 @@ def test_small_batches_skip_oversized_blocks(tmp_path, monkeypatch):
     at.autotune(sim, None, None, timer=lambda s, c: seen.append(c) or 1.0, device_name="x",
                 use_cache=False)
     assert all(c[0] == 32 for c in seen)
+
+
+def test_two_lanes_win_where_the_model_pipelines(tmp_path, monkeypatch):
+    monkeypatch.setenv("ABASIM_TUNE_CACHE", str(tmp_path / "tune.json"))
+    cost = lambda s, c: 1.0 if c[2] == 2 else 2.0          # noqa: E731
+    sim = FakeSim()
+    assert at.autotune(sim, None, None, timer=cost, device_name="x") == (32, False, 2)
+    assert sim.space == "auto"
+    assert json.load(open(tmp_path / "tune.json")).popitem()[1]["lanes"] == 2
+    # the cache entry restores the tape mode too
+    sim2 = FakeSim()
+    at.autotune(sim2, None, None, timer=lambda s, c: pytest.fail("timed again"), device_name="x")
+    assert sim2.space == "auto" and sim2.launch == (32, False)
+
+
+def test_two_lane_candidates_dropped_when_nothing_pipelines(tmp_path, monkeypatch):
+    """A model the pipelined kernels cannot run: 'auto' falls back to one lane,
+    so its timing repeats a one-lane candidate and is not kept."""
+    monkeypatch.setenv("ABASIM_TUNE_CACHE", str(tmp_path / "tune.json"))
+    sim = FakeSim(pipelines=False)
+    best = at.autotune(sim, None, None, timer=lambda s, c: 1.0 if c[2] == 2 else 2.0, device_name="x")
+    assert best[2] == 1 and sim.space == "one_warp"
+
+
+def test_old_cache_entries_without_lanes_mean_one_lane(tmp_path, monkeypatch):
+    monkeypatch.setenv("ABASIM_TUNE_CACHE", str(tmp_path / "tune.json"))
+    sim = FakeSim()
+    at.save_cache({at.cache_key(sim.signature, "x"): {"threads": 64, "persistent": False}})
+    assert at.autotune(sim, None, None, timer=None, device_name="x") == (64, False, 1)
+    assert sim.space == "one_warp"

@@ -84,10 +84,29 @@ def test_autotune_keeps_results(tmp_path, monkeypatch):
     work, sim, q0, qd0, tau = _setup()
     ref = _run(sim, q0, qd0, tau)
     best = sim.autotune(q0, qd0, T_probe=4, reps=1)
-    assert best in [(32, False), (64, False), (128, False), (32, True), (64, True), (128, True)]
+    assert best in [(32, False, 1), (64, False, 1), (128, False, 1), (32, True, 1), (64, True, 1), (128, True, 1)]
     out = _run(sim, q0, qd0, tau)
     for a, b in zip(ref, out):
         assert torch.equal(a, b)
+
+
+def test_autotune_lanes_on_chains(tmp_path, monkeypatch):
+    """Serial chains: both lane counts are timed; the pick runs with the matching
+    kernels and gives the results of the one-lane path (to FP32 round-off)."""
+    from paper_2109_07719_gb300 import autotune as at
+    monkeypatch.setenv("ABASIM_TUNE_CACHE", str(tmp_path / "tune.json"))
+    work, sim, q0, qd0, tau = _setup(cfg=2, B=256, T=20)
+    sim.set_tape_space("one_warp")
+    ref = _run(sim, q0, qd0, tau)
+    assert "pipelined" not in sim.last_storage()
+    best = sim.autotune(q0, qd0, T_probe=4, reps=1)
+    out = _run(sim, q0, qd0, tau)
+    assert ("pipelined" in sim.last_storage()) == (best[2] == 2)
+    entry = next(iter(at.load_cache().values()))
+    assert any(key.endswith("/2 lane(s)") for key in entry["seconds"])
+    for a, b in zip(ref, out):
+        err = float((a - b).abs().max() / (b.abs().max() + 1e-30))
+        assert err < 1e-5
 
 
 @pytest.mark.parametrize("cfg", [2, 3, 4])
