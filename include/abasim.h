@@ -60,7 +60,9 @@ enum sim_joint { SIM_REVOLUTE = 0, SIM_FREE = 1 };
  * they are in topological order: parent[l] is the parent's index inside the
  * same system and must be < l, or -1 for the world.  A SIM_FREE joint is allowed
  * only on a system's first link (the floating base).  Per link:
- *   axis[3]     unit rotation axis in the link frame (revolute)
+ *   axis[3]     unit rotation axis in the link frame (revolute); sim_create
+ *               re-expresses each revolute link in a frame whose z axis is this
+ *               axis (no state, input or gradient depends on the link frames)
  *   X_tree[12]  parent frame -> joint frame: rotation E (row major, 9) then the
  *               joint origin r in parent coordinates (3); motion vectors map as
  *               [E w; E (v - r x w)] (the supplement's st_apply)

@@ -29,7 +29,9 @@ namespace abasim {
 enum JointType : int { J_REVOLUTE = 0, J_FREE = 1 };
 enum Integrator : int { I_SEMI_IMPLICIT = 0, I_EXPLICIT = 1 };
 
-// per-link model parameters, [link][field][system]; P_CP / P_CR: contact sphere
+// per-link model parameters, [link][field][system], in the frames sim_create
+// chooses (a revolute link's z axis is its joint axis, so P_AX is e_z there and
+// the kernels use S = [e_z; 0] without reading it); P_CP / P_CR: contact sphere
 // centre (link frame) and radius (< 0: the link has none); P_LO / P_HI: revolute
 // joint position limits (-inf / +inf: none)
 enum : int {
@@ -332,23 +334,28 @@ SD void aba_forward(const Sys<T, PT, TL, AL>& s, Col<const T> q, Col<const T> qd
     SV<T> vpar = zeroSV<T>();
     if (par >= 0) vpar = (par == l - 1) ? v_prev : tp_sv(s, par, T_V);
     XF<T> X;
-    SV<T> vJ;
+    SV<T> v, c;
     T sn = 0, cs = 1;
-    if (jt == J_REVOLUTE) {
-      const V3<T> a = s.pv3(l, P_AX);
+    if (jt == J_REVOLUTE) {  // about the link's z axis: vJ = [qd e_z; 0]
       const T ql = q[qo], vl = qd[vo];
       sincos_t(ql, &sn, &cs);
-      X = XF<T>{mm(rot_axis_T(a, sn, cs), Et), rt};
-      vJ = SV<T>{vl * a, zero3<T>()};
+      X = XF<T>{rotz_T_mm(sn, cs, Et), rt};
+      if (par >= 0) {
+        v = apply(X, vpar);
+        v.w.z += vl;
+      } else {
+        v = SV<T>{{T(0), T(0), vl}, zero3<T>()};
+      }
+      c = crossm_z(v, vl);
     } else {
       const V3<T> p{q[qo], q[qo + 1], q[qo + 2]};
       const M3<T> EJ = transpose(quat_R(q[qo + 3], q[qo + 4], q[qo + 5], q[qo + 6]));
       X = compose(EJ, p, Et, rt);
-      vJ = SV<T>{{qd[vo], qd[vo + 1], qd[vo + 2]}, {qd[vo + 3], qd[vo + 4], qd[vo + 5]}};
+      const SV<T> vJ{{qd[vo], qd[vo + 1], qd[vo + 2]}, {qd[vo + 3], qd[vo + 4], qd[vo + 5]}};
+      v = vJ;
+      if (par >= 0) v += apply(X, vpar);
+      c = crossm(v, vJ);
     }
-    SV<T> v = vJ;
-    if (par >= 0) v += apply(X, vpar);
-    const SV<T> c = crossm(v, vJ);
     const SI<T> I = rbi(mass, com, Ic);
     const SV<T> h = mul(I, v);
     tp_xf(s, l, T_E, X);
@@ -378,7 +385,6 @@ SD void aba_forward(const Sys<T, PT, TL, AL>& s, Col<const T> q, Col<const T> qd
     }
     carry = false;
     if (jt == J_REVOLUTE) {
-      const V3<T> a = s.pv3(l, P_AX);
       const T tl = tau[vo] - s.P(l, P_DAMP) * qd[vo];  // viscous damping: joint force -b qd
       SV<T> c = zeroSV<T>();
       XF<T> X;
@@ -386,10 +392,9 @@ SD void aba_forward(const Sys<T, PT, TL, AL>& s, Col<const T> q, Col<const T> qd
         c = tp_sv(s, l, T_C);
         X = tp_xf(s, l, T_E);
       }
-      const SV<T> U{mul(IA.A, a), mulT(IA.B, a)};
-      const DT D = (DT)a.x * (DT)U.w.x + (DT)a.y * (DT)U.w.y + (DT)a.z * (DT)U.w.z;
-      const DT Di = DT(1) / D;
-      const T u = tl - dot(a, pA.w);
+      const SV<T> U = col_z(IA);  // U = I^A S, D = S^T U, u = tau - S^T p^A with S = [e_z; 0]
+      const DT Di = DT(1) / (DT)U.w.z;
+      const T u = tl - pA.w.z;
       tp_sv(s, l, T_U, U);
       put_di<T, DT, PT>(s, l, Di);
       s.tp(l, T_u) = u;
@@ -430,7 +435,6 @@ SD void aba_forward(const Sys<T, PT, TL, AL>& s, Col<const T> q, Col<const T> qd
     if (par >= 0) apar = (par == l - 1) ? a_prev : tp_sv(s, par, T_A);
     SV<T> a;
     if (jt == J_REVOLUTE) {
-      const V3<T> ax = s.pv3(l, P_AX);
       const SV<T> U = tp_sv(s, l, T_U);
       const T u = s.tp(l, T_u);
       const DT Di = get_di<T, DT, PT>(s, l);
@@ -438,7 +442,7 @@ SD void aba_forward(const Sys<T, PT, TL, AL>& s, Col<const T> q, Col<const T> qd
       const T qdd = (T)(((DT)u - (DT)dot(U, ap)) * Di);
       s.tp(l, T_QDD) = qdd;
       a = ap;
-      a.w += qdd * ax;
+      a.w.z += qdd;
       if (ADJ) tp_sv(s, l, T_AP, ap);
     } else {
       const SI<T> IA = tp_si(s, l, T_IA);
@@ -473,15 +477,13 @@ SD void chain_inertia(const Sys<T, PT>& s, Col<const T> q, T* ex, F&& ready, int
   for (int l = links - 1; l >= 0; --l) {
     if (l < s.nl) {
       const int m = s.M(l);
-      const V3<T> a = s.pv3(l, P_AX);
       T sn, cs;
       sincos_t(q[meta_qoff(m)], &sn, &cs);
-      const XF<T> X{mm(rot_axis_T(a, sn, cs), s.pm3(l, P_E)), s.pv3(l, P_R)};
+      const XF<T> X{rotz_T_mm(sn, cs, s.pm3(l, P_E)), s.pv3(l, P_R)};
       SI<T> IA = rbi(s.P(l, P_M), s.pv3(l, P_C), s.ps3(l, P_IC));
       if (l < s.nl - 1) IA += cI;
-      const SV<T> U{mul(IA.A, a), mulT(IA.B, a)};
-      const DT D = (DT)a.x * (DT)U.w.x + (DT)a.y * (DT)U.w.y + (DT)a.z * (DT)U.w.z;
-      const DT Di = DT(1) / D;
+      const SV<T> U = col_z(IA);
+      const DT Di = DT(1) / (DT)U.w.z;
       const T hi = (T)Di;
       const T u6[6] = {U.w.x, U.w.y, U.w.z, U.v.x, U.v.y, U.v.z};
       for (int i = 0; i < 6; ++i) exw(ex, l, EX_U + i) = u6[i];
@@ -506,14 +508,16 @@ SD void chain_bias_out(const Sys<T, PT>& s, Col<const T> q, Col<const T> qd, T* 
   SV<T> v_prev = zeroSV<T>();
   for (int l = 0; l < s.nl; ++l) {
     const int m = s.M(l);
-    const V3<T> a = s.pv3(l, P_AX);
     T sn, cs;
     sincos_t(q[meta_qoff(m)], &sn, &cs);
-    const XF<T> X{mm(rot_axis_T(a, sn, cs), s.pm3(l, P_E)), s.pv3(l, P_R)};
-    const SV<T> vJ{qd[meta_voff(m)] * a, zero3<T>()};
-    SV<T> v = vJ;
-    if (l > 0) v += apply(X, v_prev);
-    const SV<T> c = crossm(v, vJ);
+    const XF<T> X{rotz_T_mm(sn, cs, s.pm3(l, P_E)), s.pv3(l, P_R)};
+    const T vl = qd[meta_voff(m)];
+    SV<T> v{{T(0), T(0), vl}, zero3<T>()};
+    if (l > 0) {
+      v = apply(X, v_prev);
+      v.w.z += vl;
+    }
+    const SV<T> c = crossm_z(v, vl);
     const SV<T> h = mul(rbi(s.P(l, P_M), s.pv3(l, P_C), s.ps3(l, P_IC)), v);
     const SV<T> pA = crossf(v, h);
     for (int i = 0; i < 9; ++i) bsw(bs, l, BS_E + i) = X.E.a[i];
@@ -552,11 +556,10 @@ SD void chain_bias_in(const Sys<T, PT>& s, Col<T> q, Col<T> qd, Col<const T> tau
     if (l >= s.nl) continue;
     const int m = s.M(l);
     const int vo = meta_voff(m);
-    const V3<T> a = s.pv3(l, P_AX);
     SV<T> pA = rd_sv(bs, l, BS_PA, BS_N);
     if (l < s.nl - 1) pA += cp;
     const T tl = tau[vo] - s.P(l, P_DAMP) * qd[vo];
-    const T u = tl - dot(a, pA.w);
+    const T u = tl - pA.w.z;
     bsw(bs, l, BS_u) = u;
     if (l > 0) {
       const SV<T> U = rd_sv(ex, l, EX_U, EX_N);
@@ -576,13 +579,12 @@ SD void chain_bias_in(const Sys<T, PT>& s, Col<T> q, Col<T> qd, Col<const T> tau
   SV<T> a_prev = a0;
   for (int l = 0; l < s.nl; ++l) {
     const int m = s.M(l);
-    const V3<T> ax = s.pv3(l, P_AX);
     const SV<T> U = rd_sv(ex, l, EX_U, EX_N);
     const DT Di = (DT)exw(ex, l, EX_DI) + (DT)exw(ex, l, EX_DI + 1);
     const SV<T> ap = apply(bs_xf(bs, l), a_prev) + rd_sv(bs, l, BS_C, BS_N);
     const T qdd = (T)(((DT)bsw(bs, l, BS_u) - (DT)dot(U, ap)) * Di);
     SV<T> a = ap;
-    a.w += qdd * ax;
+    a.w.z += qdd;
     a_prev = a;
     const int qo = meta_qoff(m), vo = meta_voff(m);
     const T v0 = qd[vo];
@@ -753,12 +755,11 @@ SD void step_adjoint(const Sys<T, PT, TL, AL>& s, Col<const T> q, Col<const T> q
       }
       SV<T> apb;
       if (jt == J_REVOLUTE) {
-        const V3<T> ax = s.pv3(l, P_AX);
         const SV<T> U = tp_sv(s, l, T_U);
         const SV<T> ap = tp_sv(s, l, T_AP);
         const DT Di = get_di<T, DT, PT>(s, l);
         const T qdd = s.tp(l, T_QDD);
-        const T qb = qddb[0] + dot(ax, ab.w);
+        const T qb = qddb[0] + ab.w.z;
         const T wb = (T)((DT)qb * Di);
         apb = ab - wb * U;
         SV<T> Ub = zeroSV<T>() - wb * ap;
@@ -820,7 +821,6 @@ SD void step_adjoint(const Sys<T, PT, TL, AL>& s, Col<const T> q, Col<const T> q
       SV<T> pAb = zeroSV<T>();
       SI<T> IAb;
       if (jt == J_REVOLUTE) {
-        const V3<T> ax = s.pv3(l, P_AX);
         SV<T> Ub = ad_sv(s, l, G_U);
         T Db = s.ad(l, G_D);
         T ub = s.ad(l, G_u);
@@ -866,13 +866,18 @@ SD void step_adjoint(const Sys<T, PT, TL, AL>& s, Col<const T> q, Col<const T> q
           Ub -= (T)(DT(2) * Di) * IbU;
           Db += (T)(Di * Di * (DT)dot(U, IbU));
         }
-        // u = tau - b qd - S^T pA,  D = S^T U,  U = IA S
+        // u = tau - b qd - S^T pA,  D = S^T U,  U = IA S with S = [e_z; 0]:
+        // IAb += sym_outer(Ub.w, e_z) and outer(e_z, Ub.v) / 2 (third column / row)
         gtau[vo] = ub;
         gqd[vo] -= s.P(l, P_DAMP) * ub;
-        pAb.w -= ub * ax;
-        Ub.w += Db * ax;
-        IAb.A += sym_outer(Ub.w, ax);
-        IAb.B += scale(half, outer(ax, Ub.v));
+        pAb.w.z -= ub;
+        Ub.w.z += Db;
+        IAb.A.zz += Ub.w.z;
+        IAb.A.xz += half * Ub.w.x;
+        IAb.A.yz += half * Ub.w.y;
+        IAb.B.a[6] += half * Ub.v.x;
+        IAb.B.a[7] += half * Ub.v.y;
+        IAb.B.a[8] += half * Ub.v.z;
       } else {
         const SV<T> ub = ad_sv(s, l, G_u);
         IAb = ad_si(s, l, G_IA);
@@ -920,11 +925,14 @@ SD void step_adjoint(const Sys<T, PT, TL, AL>& s, Col<const T> q, Col<const T> q
       const SI<T> I = rbi(mass, com, Ic);
       gml += rbi_dmass_bilinear(hb, v, com);
       vb += mul(I, hb);
-      SV<T> vJ;
-      if (jt == J_REVOLUTE) vJ = SV<T>{qd[vo] * s.pv3(l, P_AX), zero3<T>()};
-      else vJ = SV<T>{{qd[vo], qd[vo + 1], qd[vo + 2]}, {qd[vo + 3], qd[vo + 4], qd[vo + 5]}};
       SV<T> vJb = zeroSV<T>();
-      crossm_adj(v, vJ, cb, vb, vJb);
+      T qdb = T(0);  // revolute: the qd adjoint through c = v x [qd e_z; 0]
+      if (jt == J_REVOLUTE) {
+        qdb = crossm_z_adj(v, qd[vo], cb, vb);
+      } else {
+        const SV<T> vJ{{qd[vo], qd[vo + 1], qd[vo + 2]}, {qd[vo + 3], qd[vo + 4], qd[vo + 5]}};
+        crossm_adj(v, vJ, cb, vb, vJb);
+      }
       vJb += vb;
       if (par >= 0) {
         SV<T> vpb = zeroSV<T>();
@@ -936,12 +944,11 @@ SD void step_adjoint(const Sys<T, PT, TL, AL>& s, Col<const T> q, Col<const T> q
           ad_sv(s, par, G_V, ad_sv(s, par, G_V) + vpb);
         }
       }
-      const M3<T> EJb = mmT(Eb, Et);  // E = E_J E_t
       if (jt == J_REVOLUTE) {
-        const V3<T> ax = s.pv3(l, P_AX);
-        gqd[vo] += dot(ax, vJb.w);
-        gq[qo] += rot_axis_T_dq(ax, s.tp(l, T_SC), s.tp(l, T_SC + 1), EJb);
+        gqd[vo] += qdb + vJb.w.z;
+        gq[qo] += rotz_T_dq(s.tp(l, T_SC), s.tp(l, T_SC + 1), Eb, Et);  // E = E_J E_t
       } else {
+        const M3<T> EJb = mmT(Eb, Et);
         const T vv[6] = {vJb.w.x, vJb.w.y, vJb.w.z, vJb.v.x, vJb.v.y, vJb.v.z};
         for (int i = 0; i < 6; ++i) gqd[vo + i] += vv[i];
         const V3<T> pb = mul(Et, rb);  // r = r_t + E_t^T p

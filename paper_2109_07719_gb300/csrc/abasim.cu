@@ -4,6 +4,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <array>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
@@ -50,6 +51,43 @@ bool is_fp64(const sim_handle* h) { return h->precision == SIM_FP64; }
 // ------------------------------------------------------------------ validation
 
 bool near(double a, double b, double tol) { return std::fabs(a - b) <= tol; }
+
+// ------------------------------------------------------------------ joint frames
+// The kernels take every revolute joint about its link's z axis.  Each revolute
+// link is re-expressed in the frame x' = R x with R a = e_z (a the model's
+// axis); a free link keeps its frame.  Row-major 3x3 helpers, double precision.
+using M9 = std::array<double, 9>;
+
+M9 mat_mul(const M9& a, const M9& b) {
+  M9 o{};
+  for (int i = 0; i < 3; ++i)
+    for (int j = 0; j < 3; ++j) o[3 * i + j] = a[3 * i] * b[j] + a[3 * i + 1] * b[3 + j] + a[3 * i + 2] * b[6 + j];
+  return o;
+}
+M9 mat_T(const M9& a) { return M9{a[0], a[3], a[6], a[1], a[4], a[7], a[2], a[5], a[8]}; }
+void mat_vec(const M9& a, const double* x, double* y) {
+  for (int i = 0; i < 3; ++i) y[i] = a[3 * i] * x[0] + a[3 * i + 1] * x[1] + a[3 * i + 2] * x[2];
+}
+
+// A rotation R with R n = e_z for the unit vector n = a / |a|: Rodrigues' rotation
+// about n x e_z, R = 1 + K + K^2 / (1 + n.z) with K = skew(n x e_z).  For n.z < 0
+// n is first turned by pi about x (diag(1, -1, -1)), which keeps 1 + n.z away from 0.
+M9 rotation_to_z(const double* a) {
+  const double len = std::sqrt(a[0] * a[0] + a[1] * a[1] + a[2] * a[2]);
+  double n[3] = {a[0] / len, a[1] / len, a[2] / len};
+  const bool flip = n[2] < 0;
+  if (flip) {
+    n[1] = -n[1];
+    n[2] = -n[2];
+  }
+  const double vx = n[1], vy = -n[0];  // n x e_z = (n.y, -n.x, 0)
+  const double k = 1.0 / (1.0 + n[2]);
+  const M9 K{0, 0, vy, 0, 0, -vx, -vy, vx, 0};
+  const M9 K2 = mat_mul(K, K);
+  M9 R{};
+  for (int i = 0; i < 9; ++i) R[i] = (i % 4 == 0 ? 1.0 : 0.0) + K[i] + k * K2[i];
+  return flip ? mat_mul(R, M9{1, 0, 0, 0, -1, 0, 0, 0, -1}) : R;
+}
 
 int validate(const sim_model_desc* d, std::string& why) {
   auto bad = [&](const std::string& s) { why = s; return SIM_EINVAL; };
@@ -254,6 +292,14 @@ int sim_create(const sim_model_desc* d, sim_handle** out) {
   std::vector<int> nl(B), nqv(B);
   std::vector<double> prm((size_t)maxL * NPRM * Bpad, 0.0);
   std::vector<int> meta((size_t)maxL * Bpad, 0), slot(h->L_total);
+  // per link: the frame change R (x' = R x) that puts a revolute axis on z.  With
+  // R_p the parent's (identity for the world): X_tree' = (R E_t R_p^T, R_p r_t),
+  // com' = R com, I_com' = R I_com R^T, sphere centre' = R p.  States, inputs and
+  // every gradient are in joint coordinates, so none of them changes.
+  const M9 eye{1, 0, 0, 0, 1, 0, 0, 0, 1};
+  std::vector<M9> Rl(h->L_total, eye);
+  for (int i = 0; i < h->L_total; ++i)
+    if (d->joint_type[i] == SIM_REVOLUTE) Rl[i] = rotation_to_z(d->axis + 3 * i);
   bool any_contact = false;
   for (int sl = 0; sl < B; ++sl) {
     const int b = order[sl];
@@ -264,15 +310,28 @@ int sim_create(const sim_model_desc* d, sim_handle** out) {
       const int jt = d->joint_type[i];
       const size_t tile = sl / LANES, lane = sl % LANES;
       auto P = [&](int f) -> double& { return prm[((tile * maxL + l) * NPRM + f) * LANES + lane]; };
-      for (int x = 0; x < 12; ++x) P(P_E + x) = d->X_tree[12 * i + x];
+      const M9& R = Rl[i];
+      const M9& Rp = d->parent[i] >= 0 ? Rl[d->sys_link_offset[b] + d->parent[i]] : eye;
+      M9 Et;
+      for (int x = 0; x < 9; ++x) Et[x] = d->X_tree[12 * i + x];
+      const M9 Et2 = mat_mul(mat_mul(R, Et), mat_T(Rp));
+      double rt[3], com[3], cp[3] = {0, 0, 0};
+      mat_vec(Rp, d->X_tree + 12 * i + 9, rt);
+      mat_vec(R, d->com + 3 * i, com);
+      if (d->contact) mat_vec(R, d->contact + 4 * i, cp);
+      const double* ic = d->I_com + 6 * i;  // xx yy zz xy xz yz
+      const M9 Ic2 = mat_mul(mat_mul(R, M9{ic[0], ic[3], ic[4], ic[3], ic[1], ic[5], ic[4], ic[5], ic[2]}), mat_T(R));
+      for (int x = 0; x < 9; ++x) P(P_E + x) = Et2[x];
       for (int x = 0; x < 3; ++x) {
-        P(P_AX + x) = jt == SIM_REVOLUTE ? d->axis[3 * i + x] : 0.0;
-        P(P_C + x) = d->com[3 * i + x];
+        P(P_R + x) = rt[x];
+        P(P_AX + x) = (jt == SIM_REVOLUTE && x == 2) ? 1.0 : 0.0;
+        P(P_C + x) = com[x];
+        P(P_CP + x) = cp[x];
       }
       P(P_M) = d->mass[i];
-      for (int x = 0; x < 6; ++x) P(P_IC + x) = d->I_com[6 * i + x];
+      const double ic2[6] = {Ic2[0], Ic2[4], Ic2[8], Ic2[1], Ic2[2], Ic2[5]};
+      for (int x = 0; x < 6; ++x) P(P_IC + x) = ic2[x];
       P(P_DAMP) = (d->damping && jt == SIM_REVOLUTE) ? d->damping[i] : 0.0;
-      for (int x = 0; x < 3; ++x) P(P_CP + x) = d->contact ? d->contact[4 * i + x] : 0.0;
       P(P_CR) = (d->contact && d->contact[4 * i + 3] >= 0) ? d->contact[4 * i + 3] : -1.0;
       if (d->contact && d->contact[4 * i + 3] >= 0) any_contact = true;
       const bool lim = d->limits && jt == SIM_REVOLUTE;

@@ -187,7 +187,7 @@ CD void test_pass(Sys<T, PT> s, CView<T> cv, TPIn<T> in, int qf) {
       }
     for (int r = 0; r < NR; ++r) cputv(cv, l, C_TP + 6 * r, pA[r]);
     if (meta_jtype(m) == J_REVOLUTE) {
-      const V3<T> ax = s.pv3(l, P_AX);
+      const V3<T> ax = zaxis<T>();
       T u[NR];
       for (int r = 0; r < NR; ++r) {
         u[r] = -dot(ax, pA[r].w) + jadd[r];
@@ -211,7 +211,7 @@ CD void test_pass(Sys<T, PT> s, CView<T> cv, TPIn<T> in, int qf) {
     const int par = meta_parent(m);
     const XF<T> X = tp_xf(s, l, T_E);
     if (meta_jtype(m) == J_REVOLUTE) {
-      const V3<T> ax = s.pv3(l, P_AX);
+      const V3<T> ax = zaxis<T>();
       const DT Di = get_di<T, DT, PT>(s, l);
       const SV<T> U = tp_sv(s, l, T_U);
       for (int r = 0; r < NR; ++r) {
@@ -250,7 +250,7 @@ CD void test_pass_reverse(Sys<T, PT> s, CView<T> cv, int qbf, T qbs, TPIn<T> in,
     SV<T> apb[NR], apar[NR];
     for (int r = 0; r < NR; ++r) apar[r] = par >= 0 ? cgetv(cv, par, C_TA + 6 * r) : zeroSV<T>();
     if (meta_jtype(m) == J_REVOLUTE) {
-      const V3<T> ax = s.pv3(l, P_AX);
+      const V3<T> ax = zaxis<T>();
       const SV<T> U = tp_sv(s, l, T_U);
       const DT Di = get_di<T, DT, PT>(s, l);
       SV<T> Ub = zeroSV<T>();
@@ -299,7 +299,7 @@ CD void test_pass_reverse(Sys<T, PT> s, CView<T> cv, int qbf, T qbs, TPIn<T> in,
     const int m = s.M(l);
     const int par = meta_parent(m);
     if (meta_jtype(m) == J_REVOLUTE) {
-      const V3<T> ax = s.pv3(l, P_AX);
+      const V3<T> ax = zaxis<T>();
       if (par >= 0) {
         const XF<T> X = tp_xf(s, l, T_E);
         const SV<T> U = tp_sv(s, l, T_U);
@@ -466,7 +466,7 @@ CD int contact_forward(Sys<T, PT> s, CView<T> cv, Col<const T> q, Col<const T> q
     const int par = meta_parent(m), vo = meta_voff(m);
     SV<T> vJ;
     if (meta_jtype(m) == J_REVOLUTE) {
-      vJ = SV<T>{(qd[vo] + dt * s.tp(l, T_QDD)) * s.pv3(l, P_AX), zero3<T>()};
+      vJ = SV<T>{(qd[vo] + dt * s.tp(l, T_QDD)) * zaxis<T>(), zero3<T>()};
     } else {
       T w[6];
       for (int i = 0; i < 6; ++i) w[i] = qd[vo + i] + dt * s.tp(l, T_QDD + i);
@@ -685,7 +685,7 @@ CD void contact_adjoint(Sys<T, PT> s, CView<T> cv, T dt, ContactParams<T> cp) {
     const int par = meta_parent(m);
     const SV<T> Vb = cgetv(cv, l, B_VS);
     if (meta_jtype(m) == J_REVOLUTE) {
-      const T vb = dot(s.pv3(l, P_AX), Vb.w);
+      const T vb = dot(zaxis<T>(), Vb.w);
       cv.L(l, B_QD) += vb;
       cv.L(l, B_QDD) += dt * vb;
     } else {

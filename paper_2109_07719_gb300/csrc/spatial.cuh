@@ -296,6 +296,46 @@ template <class T> SD T rot_axis_T_dq(V3<T> a, T s, T c, const M3<T>& Gb) {
   const V3<T> Ga = mul(Gb, a);
   return -s * tr - c * gk + s * dot(a, Ga);
 }
+// ------------------------------------------------------------------ revolute joints about z
+// sim_create expresses every revolute link in a frame whose z axis is the joint
+// axis, so S = [e_z; 0] and E_J = R(e_z, q)^T.  The helpers below are the general
+// formulas above with a = e_z written out: without fast-math the compiler keeps
+// products with constant zeros, so the saving has to be spelled out.
+template <class T> SD V3<T> zaxis() { return V3<T>{T(0), T(0), T(1)}; }
+// R(e_z, q)^T Et: rows 0 and 1 of Et rotated, row 2 kept
+template <class T> SD M3<T> rotz_T_mm(T s, T c, const M3<T>& Et) {
+  const T* e = Et.a;
+  return M3<T>{{c * e[0] + s * e[3], c * e[1] + s * e[4], c * e[2] + s * e[5],
+                c * e[3] - s * e[0], c * e[4] - s * e[1], c * e[5] - s * e[2], e[6], e[7], e[8]}};
+}
+// <Eb Et^T, dE_J/dq> for E = E_J Et (rot_axis_T_dq at a = e_z: -s (g0 + g4) - c (g3 - g1)
+// with G = Eb Et^T; only those four entries are formed)
+template <class T> SD T rotz_T_dq(T s, T c, const M3<T>& Eb, const M3<T>& Et) {
+  const T* b = Eb.a;
+  const T* e = Et.a;
+  const T g0 = b[0] * e[0] + b[1] * e[1] + b[2] * e[2];
+  const T g1 = b[0] * e[3] + b[1] * e[4] + b[2] * e[5];
+  const T g3 = b[3] * e[0] + b[4] * e[1] + b[5] * e[2];
+  const T g4 = b[3] * e[3] + b[4] * e[4] + b[5] * e[5];
+  return -s * (g0 + g4) - c * (g3 - g1);
+}
+// I [e_z; 0]: the third column of a symmetric 6x6 (U = I^A S of a revolute link)
+template <class T> SD SV<T> col_z(const SI<T>& I) {
+  return SV<T>{{I.A.xz, I.A.yz, I.A.zz}, {I.B.a[6], I.B.a[7], I.B.a[8]}};
+}
+// m x [qd e_z; 0] (the velocity-product term c of a revolute link)
+template <class T> SD SV<T> crossm_z(SV<T> m, T qd) {
+  return SV<T>{{m.w.y * qd, -m.w.x * qd, T(0)}, {m.v.y * qd, -m.v.x * qd, T(0)}};
+}
+// adjoint of y = m x [qd e_z; 0]: mb += ..., returns the qd adjoint
+template <class T> SD T crossm_z_adj(SV<T> m, T qd, SV<T> yb, SV<T>& mb) {
+  mb.w.x -= qd * yb.w.y;
+  mb.w.y += qd * yb.w.x;
+  mb.v.x -= qd * yb.v.y;
+  mb.v.y += qd * yb.v.x;
+  return yb.w.x * m.w.y - yb.w.y * m.w.x + yb.v.x * m.v.y - yb.v.y * m.v.x;
+}
+
 // body -> world rotation of the unit quaternion (x, y, z, w)
 template <class T> SD M3<T> quat_R(T x, T y, T z, T w) {
   return M3<T>{{T(1) - T(2) * (y * y + z * z), T(2) * (x * y - z * w), T(2) * (x * z + y * w),
