@@ -261,6 +261,20 @@ int sim_last_storage(const sim_handle* h, int32_t* rollout_mode, int32_t* backwa
 #define SIM_REPLAY_QUADRATIC 1
 int sim_set_replay(sim_handle* h, int32_t mode);
 
+/* Running-state precision of sim_rollout in SIM_FP32_D64 mode (the mixed mode's
+ * FP64 D-solves leave the step-to-step state sums in FP32; the paper does not say
+ * which).  fp64 = 1: sim_rollout keeps q and qd in FP64 (device memory the handle
+ * allocates here, (nq_max + nv_max) * n_systems doubles) and accumulates the
+ * integrator's sums there; every step's dynamics read the FP32 rounding of that
+ * state, and the checkpoints, trajectory and final state are stored as FP32.
+ * fp64 = 0 (default): the state is FP32 throughout.  The backward's segment
+ * replay (k > 1) and sim_step_batch start from FP32 states and sum in FP32; with
+ * k = 1 the adjoint recomputes every step from exactly the FP32 state the
+ * rollout evaluated.  Rollouts then use the one-warp kernels.  Returns
+ * SIM_EUNSUPPORTED for the other precisions and SIM_ECUDA if the buffer cannot
+ * be allocated.  Not thread-safe with a rollout in flight on the handle. */
+int sim_set_state_accumulation(sim_handle* h, int32_t fp64);
+
 /* The packing of systems into slots (thread order): sys_of_slot[n_systems]
  * (host memory) receives the system index run by each slot.  Systems are sorted
  * by link count, longest first, so the systems of a warp walk equally many links

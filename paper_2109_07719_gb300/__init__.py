@@ -68,6 +68,7 @@ _SIGS = {
     "sim_slot_order": (ctypes.c_int, [_P, _P]),
     "sim_set_tape_space": (ctypes.c_int, [_P, ctypes.c_int32]),
     "sim_set_replay": (ctypes.c_int, [_P, ctypes.c_int32]),
+    "sim_set_state_accumulation": (ctypes.c_int, [_P, ctypes.c_int32]),
     "sim_jvp_work_bytes": (ctypes.c_size_t, [_P]),
     "sim_step_jvp": (ctypes.c_int, [_P] * 11 + [_P, ctypes.c_size_t, _P]),
     "sim_last_error": (ctypes.c_char_p, [_P]),
@@ -216,6 +217,12 @@ class Simulator:
         """k > 1 state rebuild: 'segment' (replay once) or 'quadratic' (from the checkpoint)."""
         code = {"segment": 0, "quadratic": 1}[mode]
         self._check(lib.sim_set_replay(self._h, code), "sim_set_replay")
+
+    def set_state_accumulation(self, precision: str = "fp32"):
+        """Running-state precision of rollouts in the 'fp32_d64' mode: 'fp64' sums q
+        and qd in FP64 between steps (stored as FP32), 'fp32' (default) does not."""
+        code = {"fp32": 0, "fp64": 1}[precision]
+        self._check(lib.sim_set_state_accumulation(self._h, code), "sim_set_state_accumulation")
 
     def slot_order(self):
         """System index run by each slot (thread), longest systems first."""

@@ -595,41 +595,47 @@ SD void chain_bias_in(const Sys<T, PT>& s, Col<T> q, Col<T> qd, Col<const T> tau
 }
 
 // Integrates x -> x' in place from the qdd on the tape, plus the contact
-// velocity change C_DV of the contact tape ct when given.
-template <class T, class PT, int TL, int AL>
-SD void integrate(const Sys<T, PT, TL, AL>& s, Col<T> q, Col<T> qd, T dt, int integ, const T* ct = nullptr) {
+// velocity change C_DV of the contact tape ct when given.  The state columns may
+// be wider than the step's scalar (A = double with T = float: the running state
+// accumulated in FP64 while the dynamics run in FP32).
+template <class A, class T, class PT, int TL, int AL>
+SD void integrate_in(const Sys<T, PT, TL, AL>& s, Col<A> q, Col<A> qd, A dt, int integ, const T* ct) {
   for (int l = 0; l < s.nl; ++l) {
     const int m = s.M(l);
     const int jt = meta_jtype(m), qo = meta_qoff(m), vo = meta_voff(m);
     if (jt == J_REVOLUTE) {
-      T v0 = qd[vo];
-      T v1 = v0 + dt * s.tp(l, T_QDD);
-      if (ct) v1 += ctr(ct, l, C_DV);
+      A v0 = qd[vo];
+      A v1 = v0 + dt * (A)s.tp(l, T_QDD);
+      if (ct) v1 += (A)ctr(ct, l, C_DV);
       qd[vo] = v1;
       q[qo] = q[qo] + dt * (integ == I_SEMI_IMPLICIT ? v1 : v0);
     } else {
-      T nu[6];
+      A nu[6];
       for (int i = 0; i < 6; ++i) {
-        T v0 = qd[vo + i];
-        T v1 = v0 + dt * s.tp(l, T_QDD + i);
-        if (ct) v1 += ctr(ct, l, C_DV + i);
+        A v0 = qd[vo + i];
+        A v1 = v0 + dt * (A)s.tp(l, T_QDD + i);
+        if (ct) v1 += (A)ctr(ct, l, C_DV + i);
         qd[vo + i] = v1;
         nu[i] = integ == I_SEMI_IMPLICIT ? v1 : v0;
       }
-      T qt[4] = {q[qo + 3], q[qo + 4], q[qo + 5], q[qo + 6]};
-      V3<T> dp = mul(quat_R(qt[0], qt[1], qt[2], qt[3]), V3<T>{nu[3], nu[4], nu[5]});
+      A qt[4] = {q[qo + 3], q[qo + 4], q[qo + 5], q[qo + 6]};
+      V3<A> dp = mul(quat_R(qt[0], qt[1], qt[2], qt[3]), V3<A>{nu[3], nu[4], nu[5]});
       q[qo] = q[qo] + dt * dp.x;
       q[qo + 1] = q[qo + 1] + dt * dp.y;
       q[qo + 2] = q[qo + 2] + dt * dp.z;
-      T wq[4] = {nu[0], nu[1], nu[2], T(0)};
-      T r[4];
+      A wq[4] = {nu[0], nu[1], nu[2], A(0)};
+      A r[4];
       quat_mul(qt, wq, r);
-      T raw[4];
-      for (int i = 0; i < 4; ++i) raw[i] = qt[i] + T(0.5) * dt * r[i];
-      T n = sqrt_t(raw[0] * raw[0] + raw[1] * raw[1] + raw[2] * raw[2] + raw[3] * raw[3]);
+      A raw[4];
+      for (int i = 0; i < 4; ++i) raw[i] = qt[i] + A(0.5) * dt * r[i];
+      A n = sqrt_t(raw[0] * raw[0] + raw[1] * raw[1] + raw[2] * raw[2] + raw[3] * raw[3]);
       for (int i = 0; i < 4; ++i) q[qo + 3 + i] = raw[i] / n;
     }
   }
+}
+template <class T, class PT, int TL, int AL>
+SD void integrate(const Sys<T, PT, TL, AL>& s, Col<T> q, Col<T> qd, T dt, int integ, const T* ct = nullptr) {
+  integrate_in<T>(s, q, qd, dt, integ, ct);
 }
 
 // ------------------------------------------------------------------ adjoint

@@ -404,7 +404,7 @@ int sim_create(const sim_model_desc* d, sim_handle** out) {
 void sim_destroy(sim_handle* h) {
   if (!h) return;
   void* ptrs[] = {h->prm, h->meta, h->nl, h->nqv, h->tape, h->adj, h->gm_acc, h->link_slot,
-                  h->status, h->sys_of_slot, h->counter, h->ctape, h->csys};
+                  h->status, h->sys_of_slot, h->counter, h->ctape, h->csys, h->x64};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   delete h;
@@ -564,6 +564,22 @@ int sim_set_replay(sim_handle* h, int32_t mode) {
   if (!h) return SIM_EINVAL;
   if (mode != SIM_REPLAY_SEGMENT && mode != SIM_REPLAY_QUADRATIC) return fail(h, SIM_EINVAL, "unknown replay mode");
   h->replay = mode;
+  return SIM_OK;
+}
+
+int sim_set_state_accumulation(sim_handle* h, int32_t fp64) {
+  if (!h) return SIM_EINVAL;
+  if (fp64 != 0 && fp64 != 1) return fail(h, SIM_EINVAL, "state accumulation flag must be 0 or 1");
+  if (fp64 && h->precision != SIM_FP32_D64)
+    return fail(h, SIM_EUNSUPPORTED, "FP64 state accumulation applies to the FP32 + FP64 D-solve mode");
+  if (fp64 && !h->x64) {
+    cudaError_t e = cudaMalloc(&h->x64, (size_t)(h->nq_max + h->nv_max) * h->B * sizeof(double));
+    if (e != cudaSuccess) {
+      h->x64 = nullptr;
+      return cuda_fail(h, e, "FP64 state buffer");
+    }
+  }
+  h->state64 = fp64 != 0;
   return SIM_OK;
 }
 

@@ -5,6 +5,7 @@
 #pragma once
 
 #include <algorithm>
+#include <type_traits>
 
 #include "contact.cuh"
 #include "dual.cuh"
@@ -35,6 +36,8 @@ template <class T> struct DevModel {
   T* ctape;  // per-link contact tape [tile][maxL][NCT][lane] (null: no contact spheres or limits)
   T* csys;   // per-system contact record [tile][NCS][lane]
   ContactParams<T> cp;
+  double dt64;   // the time step in FP64
+  double* x64;   // FP64 running state [nq_max + nv_max][B] of the rollout (null: off; FP32 + FP64 D only)
 };
 
 template <class T> DevModel<T> dev_model(const sim_handle* h) {
@@ -42,7 +45,8 @@ template <class T> DevModel<T> dev_model(const sim_handle* h) {
                      h->sys_of_slot, h->counter, (long long)h->B, h->maxL, h->nq_max, h->nv_max, (T)h->dt,
                      (T)h->g[0], (T)h->g[1], (T)h->g[2], h->integrator, 0, 0,
                      h->replay == SIM_REPLAY_QUADRATIC, (T*)h->ctape, (T*)h->csys,
-                     ContactParams<T>{(T)h->friction, (T)h->erp, h->pgs_iterations}};
+                     ContactParams<T>{(T)h->friction, (T)h->erp, h->pgs_iterations}, h->dt,
+                     h->state64 ? (double*)h->x64 : nullptr};
 }
 
 extern __shared__ __align__(16) unsigned char g_smem[];
@@ -151,16 +155,26 @@ template <class T> __device__ __forceinline__ CView<T> cview_of(const DevModel<T
 // model has contact spheres or joint limits), integration.
 template <class T, class DT, bool CT>
 __device__ __forceinline__ void forward_step(const DevModel<T>& m, const Sys<T>& s, int slot, Col<T> q,
-                                             Col<T> qd, Col<const T> tau_t, V3<T> g) {
+                                             Col<T> qd, Col<const T> tau_t, V3<T> g,
+                                             Col<double> xw = Col<double>{nullptr, 0}) {
   aba_forward<T, DT, false>(s, Col<const T>{q.p, q.B}, Col<const T>{qd.p, qd.B}, tau_t, g);
+  const T* ct = nullptr;
   if constexpr (CT) {
     const CView<T> cv = cview_of(m, slot);
     const int nc =
         contact_forward<T, DT, T>(s, cv, Col<const T>{q.p, q.B}, Col<const T>{qd.p, qd.B}, m.dt, m.cp);
-    integrate<T>(s, q, qd, m.dt, m.integ, nc > 0 ? (const T*)cv.ct : nullptr);
-  } else {
-    integrate<T>(s, q, qd, m.dt, m.integ);
+    if (nc > 0) ct = cv.ct;
   }
+  if constexpr (!std::is_same<T, DT>::value) {
+    if (xw.p) {  // the running state in FP64 (xw); the dynamics read its FP32 rounding
+      const Col<double> xq = xw, xqd{xw.p + (long long)m.nq_max * xw.B, xw.B};
+      integrate_in<double>(s, xq, xqd, m.dt64, m.integ, ct);
+      for (int d = 0; d < m.nq_max; ++d) q[d] = (T)xq[d];
+      for (int d = 0; d < m.nv_max; ++d) qd[d] = (T)xqd[d];
+      return;
+    }
+  }
+  integrate<T>(s, q, qd, m.dt, m.integ, ct);
 }
 
 // Recomputes the step from x^t and pulls the state adjoint (gq, gqd) back
@@ -221,6 +235,14 @@ __device__ __forceinline__ void rollout_one(const DevModel<T>& m, int slot, cons
   }
   for (int d = 0; d < nqm; ++d) q[d] = q0[d * B + b];
   for (int d = 0; d < nvm; ++d) qd[d] = qd0[d * B + b];
+  Col<double> xw{nullptr, 0};
+  if constexpr (!std::is_same<T, DT>::value) {
+    if (m.x64) {  // FP64 state accumulation, started from the FP32 initial state
+      xw = Col<double>{m.x64 + b, B};
+      for (int d = 0; d < nqm; ++d) xw[d] = (double)q[d];
+      for (int d = 0; d < nvm; ++d) xw[nqm + d] = (double)qd[d];
+    }
+  }
   if (traj) {
     for (int d = 0; d < nqm; ++d) traj[d * B + b] = q[d];
     for (int d = 0; d < nvm; ++d) traj[(nqm + d) * B + b] = qd[d];
@@ -241,7 +263,7 @@ __device__ __forceinline__ void rollout_one(const DevModel<T>& m, int slot, cons
       cp_wait_all_but_newest();
       tau_t = Col<const T>{sbuf + (t & 1) * nvm * LANES, LANES};
     }
-    forward_step<T, DT, CT>(m, s, slot, q, qd, tau_t, g);
+    forward_step<T, DT, CT>(m, s, slot, q, qd, tau_t, g, xw);
     if (traj) {
       T* c = traj + (t + 1) * NX * B + b;
       for (int d = 0; d < nqm; ++d) c[d * B] = q[d];
@@ -869,7 +891,7 @@ int launch_rollout(sim_handle* h, const void* q0, const void* qd0, const void* t
     kern = rollout_contact_kernel<T, DT>();
   } else {
     bool piped = false;  // the pipelined rollout, any precision
-    if (h->all_chains && h->maxL <= PIPE_MAX_LINKS &&
+    if (h->all_chains && h->maxL <= PIPE_MAX_LINKS && !h->state64 &&
         (h->tape_space == SIM_TAPE_AUTO || h->tape_space == SIM_TAPE_PIPELINED)) {
       const size_t need =
           (size_t)pipe_fwd_smem_per_tile(h->maxL, h->nq_max + h->nv_max, h->nv_max) * LANES * sizeof(T);
@@ -887,7 +909,8 @@ int launch_rollout(sim_handle* h, const void* q0, const void* qd0, const void* t
       }
     }
     if (!piped && h->tape_space == SIM_TAPE_PIPELINED)
-      return fail(h, SIM_EUNSUPPORTED, "the pipelined rollout needs serial revolute chains of at most 14 links");
+      return fail(h, SIM_EUNSUPPORTED,
+                  "the pipelined rollout needs serial revolute chains of at most 14 links and FP32 state accumulation");
     if constexpr (sizeof(T) == 4) {  // the other on-chip modes: FP32 storage only
       if (!piped) {
         rc = choose_storage<T>(h, k_rollout<T, DT, ST_GLOBAL>, k_rollout<T, DT, ST_HYBRID>,
