@@ -1,0 +1,31 @@
+"""The kernels' per-operation adjoint rules (a host build of csrc/spatial.cuh and
+csrc/aba_step.cuh in FP64, tests/adjoint_rules.cpp) against central differences,
+and the closed forms of a joint about e_z against the general formulas.  These
+pins do not involve the oracle."""
+import os
+import shutil
+import subprocess
+
+import pytest
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+
+RULES = {"crossm_adj", "crossf_adj", "apply_adj", "applyT_adj", "congruence_adj", "rbi_dmass",
+         "rbi_dmass_bilinear", "rot_axis_T_dq", "rotz_T_dq", "crossm_z_adj", "quat_R_adj", "spd_solve_adj"}
+IDENTITIES = {"rotz_T_mm_equals_general", "rotz_T_dq_equals_general", "crossm_z_col_z_equal_general"}
+
+
+def test_adjoint_rules_match_central_differences(tmp_path):
+    cxx = shutil.which("g++")
+    if cxx is None:
+        pytest.skip("no host C++ compiler")
+    exe = tmp_path / "adjoint_rules"
+    subprocess.run([cxx, "-O1", "-std=c++17", "-o", str(exe), os.path.join(HERE, "adjoint_rules.cpp")],
+                   check=True)
+    out = subprocess.run([str(exe)], check=True, capture_output=True, text=True).stdout
+    res = {line.split()[0]: float(line.split()[1]) for line in out.strip().splitlines()}
+    assert set(res) == RULES | IDENTITIES
+    for name in RULES:
+        assert res[name] < 1e-7, (name, res[name])          # O(h^2) central differences, h = 1e-6
+    for name in IDENTITIES:
+        assert res[name] < 1e-14, (name, res[name])
