@@ -1,7 +1,8 @@
-"""The kernels' per-operation adjoint rules (a host build of csrc/spatial.cuh and
-csrc/aba_step.cuh in FP64, tests/adjoint_rules.cpp) against central differences,
-and the closed forms of a joint about e_z against the general formulas.  These
-pins do not involve the oracle."""
+"""The kernels' per-operation adjoint rules (tests/adjoint_rules.cpp) and their
+whole adjoint step (tests/step_adjoint.cpp), built for the host in FP64 from
+csrc/spatial.cuh and csrc/aba_step.cuh, against central differences; and the
+closed forms of a joint about e_z against the general formulas.  These pins do
+not involve the oracle."""
 import os
 import shutil
 import subprocess
@@ -29,3 +30,20 @@ def test_adjoint_rules_match_central_differences(tmp_path):
         assert res[name] < 1e-7, (name, res[name])          # O(h^2) central differences, h = 1e-6
     for name in IDENTITIES:
         assert res[name] < 1e-14, (name, res[name])
+
+
+def test_whole_adjoint_step_matches_central_differences(tmp_path):
+    """step_adjoint of the kernels (host build, FP64) against central differences of
+    their own forward step with respect to q, qd, tau and the link masses: a
+    floating base with a branched revolute tree, a damped chain, a revolute tree
+    with explicit Euler and a lone free body."""
+    cxx = shutil.which("g++")
+    if cxx is None:
+        pytest.skip("no host C++ compiler")
+    exe = tmp_path / "step_adjoint"
+    subprocess.run([cxx, "-O1", "-std=c++17", "-o", str(exe), os.path.join(HERE, "step_adjoint.cpp")], check=True)
+    out = subprocess.run([str(exe)], check=True, capture_output=True, text=True).stdout
+    res = {line.split()[0]: float(line.split()[1]) for line in out.strip().splitlines()}
+    assert set(res) == {"floating_base_tree", "damped_chain", "revolute_tree_explicit", "free_body_explicit"}
+    for name, err in res.items():
+        assert err < 1e-7, (name, err)       # a 0.1 % error in one gradient block shows as ~1e-5
