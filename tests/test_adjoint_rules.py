@@ -1,6 +1,8 @@
-"""The kernels' per-operation adjoint rules (tests/adjoint_rules.cpp) and their
-whole adjoint step (tests/step_adjoint.cpp), built for the host in FP64 from
-csrc/spatial.cuh and csrc/aba_step.cuh, against central differences; and the
+"""The kernels' per-operation adjoint rules (tests/adjoint_rules.cpp), their whole
+adjoint step (tests/step_adjoint.cpp) and their constrained step with contacts
+and limits (tests/contact_adjoint.cpp), built for the host in FP64 from
+csrc/spatial.cuh, csrc/aba_step.cuh and csrc/contact.cuh, against central
+differences; and the
 closed forms of a joint about e_z against the general formulas.  These pins do
 not involve the oracle."""
 import os
@@ -47,3 +49,22 @@ def test_whole_adjoint_step_matches_central_differences(tmp_path):
     assert set(res) == {"floating_base_tree", "damped_chain", "revolute_tree_explicit", "free_body_explicit"}
     for name, err in res.items():
         assert err < 1e-7, (name, err)       # a 0.1 % error in one gradient block shows as ~1e-5
+
+
+def test_constrained_step_adjoint_matches_central_differences(tmp_path):
+    """The contact + joint-limit step (sphere-ground MLCP by projected Gauss-Seidel)
+    and its adjoint, in the order the adjoint kernels run it, against central
+    differences: a floating base on four penetrating feet with two knees past a
+    limit (14 active rows), both integrators."""
+    cxx = shutil.which("g++")
+    if cxx is None:
+        pytest.skip("no host C++ compiler")
+    exe = tmp_path / "contact_adjoint"
+    subprocess.run([cxx, "-O1", "-std=c++17", "-o", str(exe), os.path.join(HERE, "contact_adjoint.cpp")],
+                   check=True)
+    out = subprocess.run([str(exe)], check=True, capture_output=True, text=True).stdout
+    res = {line.split()[0]: (float(line.split()[1]), int(line.split()[2])) for line in out.strip().splitlines()}
+    assert set(res) == {"contacts_limits_semi_implicit", "contacts_limits_explicit"}
+    for name, (err, rows) in res.items():
+        assert rows == 14, (name, rows)          # 4 contacts x 3 rows + 2 limit rows active in every trial
+        assert err < 1e-6, (name, err)           # a 0.1 % error in the constraint path shows as ~1e-3
