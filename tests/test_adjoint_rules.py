@@ -2,7 +2,8 @@
 adjoint step (tests/step_adjoint.cpp) and their constrained step with contacts
 and limits (tests/contact_adjoint.cpp), built for the host in FP64 from
 csrc/spatial.cuh, csrc/aba_step.cuh and csrc/contact.cuh, against central
-differences; and the
+differences; the pipelined kernels' compact tapes and split forward step against
+the one-warp formulation (tests/layout_parity.cpp); and the
 closed forms of a joint about e_z against the general formulas.  These pins do
 not involve the oracle."""
 import os
@@ -68,3 +69,20 @@ def test_constrained_step_adjoint_matches_central_differences(tmp_path):
     for name, (err, rows) in res.items():
         assert rows == 14, (name, rows)          # 4 contacts x 3 rows + 2 limit rows active in every trial
         assert err < 1e-6, (name, err)           # a 0.1 % error in the constraint path shows as ~1e-3
+
+
+def test_pipelined_layouts_and_split_forward_are_bit_identical(tmp_path):
+    """What the two-warp kernels compute differently (compact producer/consumer
+    tapes; the forward step split into an inertia half and a bias half) equals the
+    one-warp formulation bit for bit on chains of 1 to 7 links (host FP64 build with
+    the field checks on)."""
+    cxx = shutil.which("g++")
+    if cxx is None:
+        pytest.skip("no host C++ compiler")
+    exe = tmp_path / "layout_parity"
+    subprocess.run([cxx, "-O1", "-std=c++17", "-o", str(exe), os.path.join(HERE, "layout_parity.cpp")], check=True)
+    r = subprocess.run([str(exe)], capture_output=True, text=True)
+    assert r.returncode == 0, r.stdout + r.stderr
+    lines = r.stdout.strip().splitlines()
+    assert len(lines) == 21
+    assert all(" adjoint_diff 0 forward_diff 0 " in line for line in lines)
