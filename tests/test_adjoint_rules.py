@@ -3,7 +3,8 @@ adjoint step (tests/step_adjoint.cpp) and their constrained step with contacts
 and limits (tests/contact_adjoint.cpp), built for the host in FP64 from
 csrc/spatial.cuh, csrc/aba_step.cuh and csrc/contact.cuh, against central
 differences; the pipelined kernels' compact tapes and split forward step against
-the one-warp formulation (tests/layout_parity.cpp); and the
+the one-warp formulation (tests/layout_parity.cpp); the dot-product test of the
+forward-mode JVP against the adjoint (tests/jvp_dot.cpp); and the
 closed forms of a joint about e_z against the general formulas.  These pins do
 not involve the oracle."""
 import os
@@ -86,3 +87,19 @@ def test_pipelined_layouts_and_split_forward_are_bit_identical(tmp_path):
     lines = r.stdout.strip().splitlines()
     assert len(lines) == 21
     assert all(" adjoint_diff 0 forward_diff 0 " in line for line in lines)
+
+
+def test_jvp_and_adjoint_are_transposes(tmp_path):
+    """Dot-product test: the forward-mode JVP (the step on dual numbers) and
+    step_adjoint satisfy <ybar, J xdot> = <J^T ybar, xdot> to round-off on a
+    floating-base tree and a damped chain, both integrators."""
+    cxx = shutil.which("g++")
+    if cxx is None:
+        pytest.skip("no host C++ compiler")
+    exe = tmp_path / "jvp_dot"
+    subprocess.run([cxx, "-O1", "-std=c++17", "-o", str(exe), os.path.join(HERE, "jvp_dot.cpp")], check=True)
+    out = subprocess.run([str(exe)], check=True, capture_output=True, text=True).stdout
+    res = {line.split()[0]: float(line.split()[1]) for line in out.strip().splitlines()}
+    assert len(res) == 4
+    for name, err in res.items():
+        assert err < 1e-12, (name, err)
