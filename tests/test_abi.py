@@ -141,3 +141,7 @@ def test_null_arguments():
     assert p.lib.sim_work_bytes(None, 10) == 0
     assert p.lib.sim_rollout(None, None, None, None, 1, 1, None, None, None, None, None) == -1
     assert p.lib.sim_create(None, None) == -1
+    # the launch and precision controls refuse a null handle before touching it
+    assert p.lib.sim_set_state_accumulation(None, 1) == -1
+    assert p.lib.sim_set_tape_space(None, 4) == -1
+    assert p.lib.sim_set_replay(None, 0) == -1
