@@ -276,6 +276,8 @@ def run_ours(args):
         line["vs_plain_per_system"] = value / pl["value"]
     if args.cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(args)
+        one = cpu_baseline(args, budget_s=8.0, threads=1)
+        line["cpu_baseline"]["one_core"] = {"value": one["value"], "unit": one["unit"], "cores": 1}
     return line
 
 
@@ -408,33 +410,93 @@ def run_e2e(sim, work, k, steps, tau_h, q0_h, qd0_h):
             "copies": "per step, on a second stream overlapped with the neighbouring steps' compute"}
 
 
-def cpu_baseline(args, budget_s: float = 15.0):
-    """The FP64 oracle (forward + adjoint, one-step recompute) on a bounded sample:
-    a few systems of the workload over a short horizon, scaled to env-steps/s."""
-    import numpy as np
+ORACLE_SAMPLE = (16, 20)  # systems, steps of one oracle rollout of the CPU baseline
+
+
+def _oracle_sample(config, precision, contacts, limits):
+    """The CPU baseline's unit of work: forward + adjoint of 16 systems of the
+    workload over 20 steps through the FP64 oracle (CRBA + RNEA forward, per-step
+    recompute + reverse-mode step adjoint)."""
     import torch
     from oracle.dynamics import OracleModel
     from oracle.rollout import rollout_backward
-    threads = torch.get_num_threads()
-    work = workload(args.config, args.precision, 16, 20, contacts=getattr(args, "contacts", False),
-                    limits=getattr(args, "limits", False))
+    nsys, T = ORACLE_SAMPLE
+    work = workload(config, precision, nsys, T, contacts=contacts, limits=limits)
     m = work.model
-    sys_ = list(range(min(16, m.n_systems)))
-    done = 0
-    t0 = time.perf_counter()
-    T = 20
+    sys_ = list(range(min(nsys, m.n_systems)))
     tau = work.tau(T=T)
-    while time.perf_counter() - t0 < budget_s:
+
+    def once():
         om = OracleModel(m, sys_)
         q0 = torch.tensor(work.q0[:om.nq, sys_].T)
         qd0 = torch.tensor(work.qd0[:om.nv, sys_].T)
         ot = tau[:, :om.nv, sys_].permute(0, 2, 1).contiguous()
         rollout_backward(om, q0, qd0, ot, torch.ones_like(q0), torch.zeros_like(qd0))
-        done += len(sys_) * T
-    el = time.perf_counter() - t0
-    return {"value": done / el, "unit": "env-steps/s", "cores": threads, "kind": "oracle",
-            "sample": f"{len(sys_)} systems x {T} steps of the same workload, repeated for {el:.1f} s "
-                      f"(FP64 CRBA+RNEA forward, per-step recompute + reverse-mode step adjoint)"}
+        return len(sys_) * T
+
+    return once
+
+
+def _oracle_worker(config, precision, contacts, limits, budget_s, barrier, results):
+    """One single-threaded process of the all-core baseline: waits for the others,
+    then counts the env-steps it completes in budget_s."""
+    import torch
+    torch.set_num_threads(1)
+    once = _oracle_sample(config, precision, contacts, limits)
+    barrier.wait(timeout=600)
+    done, t0 = 0, time.perf_counter()
+    while time.perf_counter() - t0 < budget_s:
+        done += once()
+    results.put((done, time.perf_counter() - t0))
+
+
+def cpu_baseline(args, budget_s: float = 15.0, threads: int | None = None):
+    """The FP64 oracle on a bounded sample of the workload, scaled to env-steps/s:
+    one process on one thread (threads=1), or one single-threaded process per host
+    core, parallel over copies of the sample (the oracle batches its systems in
+    small tensors, which intra-op threads barely speed up).  The process pool is
+    started with spawn (this process may already hold a CUDA context)."""
+    contacts, limits = getattr(args, "contacts", False), getattr(args, "limits", False)
+    nsys, T = ORACLE_SAMPLE
+    what = (f"{nsys} systems x {T} steps of the same workload, repeated for {budget_s:.0f} s "
+            f"(FP64 CRBA+RNEA forward, per-step recompute + reverse-mode step adjoint)")
+    if threads == 1:
+        import torch
+        prev = torch.get_num_threads()
+        torch.set_num_threads(1)
+        try:
+            once = _oracle_sample(args.config, args.precision, contacts, limits)
+            done, t0 = 0, time.perf_counter()
+            while time.perf_counter() - t0 < budget_s:
+                done += once()
+            el = time.perf_counter() - t0
+        finally:
+            torch.set_num_threads(prev)
+        return {"value": done / el, "unit": "env-steps/s", "cores": 1, "kind": "oracle",
+                "sample": what + ", one process"}
+    import multiprocessing as mp
+    n = len(os.sched_getaffinity(0)) if hasattr(os, "sched_getaffinity") else (os.cpu_count() or 1)
+    ctx = mp.get_context("spawn")
+    barrier, results = ctx.Barrier(n + 1), ctx.Queue()
+    procs = [ctx.Process(target=_oracle_worker, daemon=True,
+                         args=(args.config, args.precision, contacts, limits, budget_s, barrier, results))
+             for _ in range(n)]
+    try:
+        for p in procs:
+            p.start()
+        barrier.wait(timeout=600)
+        got = [results.get(timeout=budget_s + 300) for _ in range(n)]
+    except Exception as e:  # a worker that failed to start or finish: report one process instead
+        for p in procs:
+            if p.is_alive():
+                p.terminate()
+        one = cpu_baseline(args, budget_s, threads=1)
+        one["sample"] += f" (process pool unavailable: {type(e).__name__})"
+        return one
+    for p in procs:
+        p.join(timeout=30)
+    return {"value": sum(d / el for d, el in got), "unit": "env-steps/s", "cores": n, "kind": "oracle",
+            "sample": what + f", in each of {n} single-threaded processes at once"}
 
 
 def run_reference(args):
