@@ -132,6 +132,44 @@ def test_oblique_joint_axes(precision):
     assert sim.status().sum() == 0
 
 
+def test_headline_configuration_full_size_sampled():
+    """The benchmark's own configuration at full size -- 4096 serial 7-DOF chains,
+    T = 1000, FP32, k = 1, automatic storage (the pipelined rollout and adjoint) --
+    against the FP64 oracle on sampled systems: the final state of every 64th system
+    and the last, and the gradients of the first, a middle and the last system (first
+    tile, a middle tile, the ragged end of the slot order)."""
+    from paper_2109_07719_gb300 import Simulator
+    work = wl.config(2)
+    B, T = work.model.n_systems, work.T
+    assert (B, T) == (4096, 1000)
+    sim = Simulator(work.model, precision="fp32")
+    dev = sim.device
+    q0 = torch.tensor(work.q0, dtype=torch.float32)
+    qd0 = torch.tensor(work.qd0, dtype=torch.float32)
+    tau = work.tau().float()
+    g = torch.Generator().manual_seed(41)
+    gqT = torch.randn(q0.shape, generator=g, dtype=torch.float64).float()
+    gqdT = torch.randn(qd0.shape, generator=g, dtype=torch.float64).float()
+    qT, qdT, ck, _ = sim.rollout(q0.to(dev), qd0.to(dev), tau.to(dev), k=1)
+    gq0, gqd0, gtau, gm = sim.backward(ck, tau.to(dev), gqT.to(dev), gqdT.to(dev), k=1)
+    torch.cuda.synchronize()
+    assert sim.last_storage() == ("pipelined", "pipelined")
+    assert sim.status().sum() == 0
+    h = [x.double().numpy() for x in (q0, qd0, tau, gqT, gqdT)]
+    ts, tg = TOL["fp32"]
+    sel = list(range(0, B, 64)) + [B - 1]
+    oq, oqd = oracle_forward(work.model, sel, h[0], h[1], h[2])
+    check("qT", qT.cpu().numpy()[:, sel], oq, ts)
+    check("qdT", qdT.cpu().numpy()[:, sel], oqd, ts)
+    gsel = [0, B // 2 - 1, B - 1]
+    o = oracle_backward(work.model, gsel, h[0], h[1], h[2], h[3], h[4])
+    check("gq0", gq0.cpu().numpy()[:, gsel], o["gq0"], tg)
+    check("gqd0", gqd0.cpu().numpy()[:, gsel], o["gqd0"], tg)
+    check("gtau", gtau.cpu().numpy()[:, :, gsel], o["gtau"], tg)
+    gmd = mass_grad_of(work.model, gm.cpu().numpy(), gsel)
+    check("gmass", np.concatenate([gmd[s] for s in gsel]), np.concatenate([o["gm"][s] for s in gsel]), tg)
+
+
 @pytest.mark.parametrize("cfg", [2, 3])
 def test_explicit_euler_fp64(cfg):
     B, T = 33, 50
