@@ -3,7 +3,8 @@
 Each test ties the oracle to something other than its own code: an independent
 algorithm (CRBA+RNEA vs ABA), a textbook closed form (compound and double
 pendulum), a conservation law (power balance, momentum), a small-angle period,
-finite differences, and the paper's printed adjoint rule of its worked example
+finite differences, forward-mode AD of the rollout (the dot-product test of the
+adjoint recurrence), and the paper's printed adjoint rule of its worked example
 (Sec. 3.1, Eq. 5-6).
 """
 import math
@@ -338,3 +339,34 @@ def test_quaternion_mul_vec_matches_supplement():
     expect = torch.stack([w * v[0] + y * v[2] - z * v[1], w * v[1] + z * v[0] - x * v[2],
                           w * v[2] + x * v[1] - y * v[0], -x * v[0] - y * v[1] - z * v[2]])
     assert torch.allclose(r, expect)
+
+
+@pytest.mark.parametrize("cfg,T,integrator", [(1, 30, "semi"), (2, 10, "semi"), (2, 8, "explicit"),
+                                              (3, 6, "semi"), (5, 4, "semi")])
+def test_adjoint_dot_product_with_forward_mode(cfg, T, integrator):
+    """The oracle's adjoint recurrence against forward-mode AD of its own rollout
+    (torch.func.jvp, a differentiation mode the recurrence does not use):
+    <ybar, J xdot> = <J^T ybar, xdot> for random tangents of q0, qd0, every tau and
+    the link masses, to round-off -- no finite-difference truncation."""
+    work = wl.config(cfg, B=2) if cfg != 1 else wl.config(1, B=1)
+    om = _om(work)
+    q0, qd0, _ = _state(work, om, seed=5)
+    gen = torch.Generator().manual_seed(11)
+    tau = torch.randn(T, om.B, om.nv, generator=gen)
+    wq = torch.randn(om.B, om.nq, generator=gen)
+    wqd = torch.randn(om.B, om.nv, generator=gen)
+    m0 = om.mass.clone()
+    dq = torch.randn(q0.shape, generator=gen)
+    dqd = torch.randn(qd0.shape, generator=gen)
+    dtau = torch.randn(tau.shape, generator=gen)
+    dm = 0.1 * torch.randn(m0.shape, generator=gen)
+
+    def final_state(q, qd, ta, m):
+        qT, qdT, _ = rollout(om, q, qd, ta, integrator, mass=m, keep=False)
+        return qT, qdT
+
+    _, (tq, tqd) = torch.func.jvp(final_state, (q0, qd0, tau, m0), (dq, dqd, dtau, dm))
+    lhs = (wq * tq).sum() + (wqd * tqd).sum()
+    gq0, gqd0, gtau, gm = rollout_backward(om, q0, qd0, tau, wq, wqd, integrator=integrator)
+    rhs = (gq0 * dq).sum() + (gqd0 * dqd).sum() + (gtau * dtau).sum() + (gm * dm).sum()
+    assert abs(lhs - rhs) <= 1e-10 * max(1.0, abs(rhs)), (lhs.item(), rhs.item())
