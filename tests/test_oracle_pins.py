@@ -370,3 +370,34 @@ def test_adjoint_dot_product_with_forward_mode(cfg, T, integrator):
     gq0, gqd0, gtau, gm = rollout_backward(om, q0, qd0, tau, wq, wqd, integrator=integrator)
     rhs = (gq0 * dq).sum() + (gqd0 * dqd).sum() + (gtau * dtau).sum() + (gm * dm).sum()
     assert abs(lhs - rhs) <= 1e-10 * max(1.0, abs(rhs)), (lhs.item(), rhs.item())
+
+
+def test_double_pendulum_gradient_by_brute_force():
+    """The small-case configuration (one double pendulum, Phi = sum q_T^2, T = 1000):
+    the oracle's gradient with respect to every one of its 2 + 2 + 2000 inputs
+    (q0, qd0, every torque) against central differences, all 4008 perturbed rollouts
+    run as the systems of one batched oracle rollout."""
+    T, h = 1000, 1e-5
+    base = wl.config(1, B=1, T=T)
+    q0 = torch.tensor(base.q0[:, 0])
+    qd0 = torch.tensor(base.qd0[:, 0])
+    tau = base.tau(T=T)[:, :, 0]
+    n_in = 4 + 2 * T
+    B = 2 * n_in
+    work = wl.config(1, B=B, T=T)
+    assert np.array_equal(work.model.mass, np.tile(base.model.mass, B))   # one model, B copies
+    om = OracleModel(work.model, range(B))
+    x = torch.cat([q0, qd0, tau.reshape(-1)]).repeat(B, 1)
+    i = torch.arange(n_in)
+    x[2 * i, i] += h
+    x[2 * i + 1, i] -= h
+    qT, _, _ = rollout(om, x[:, :2], x[:, 2:4], x[:, 4:].reshape(B, T, 2).permute(1, 0, 2).contiguous(),
+                       keep=False)
+    phi = (qT ** 2).sum(1)
+    fd = (phi[0::2] - phi[1::2]) / (2 * h)
+    om1 = OracleModel(base.model, [0])
+    qT1, qdT1, _ = rollout(om1, q0[None], qd0[None], tau[:, None, :], keep=False)
+    gq0, gqd0, gtau, _ = rollout_backward(om1, q0[None], qd0[None], tau[:, None, :], 2 * qT1,
+                                          torch.zeros_like(qdT1))
+    an = torch.cat([gq0[0], gqd0[0], gtau[:, 0, :].reshape(-1)])
+    assert float((fd - an).abs().max() / an.abs().max()) < 1e-7
