@@ -49,7 +49,11 @@ extern "C" {
 #define SIM_ECUDA (-2)       /* a CUDA runtime call failed */
 #define SIM_ENOMEM (-3)      /* device allocation or caller workspace too small */
 #define SIM_ENONFINITE (-4)  /* sim_status: some system produced NaN/Inf */
-#define SIM_EUNSUPPORTED (-6)
+/* -5 is reserved for a timed-out wait; no call has one: the kernels never spin on
+ * a flag (the two-warp kernels hand data over through hardware named barriers that
+ * both warps reach the same number of times). */
+#define SIM_EUNSUPPORTED (-6) /* a valid request this build or model cannot run (the
+                               * message says which) */
 
 enum sim_precision { SIM_FP64 = 0, SIM_FP32 = 1, SIM_FP32_D64 = 2 };
 enum sim_integrator { SIM_SEMI_IMPLICIT_EULER = 0, SIM_EXPLICIT_EULER = 1 };
