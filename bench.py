@@ -150,6 +150,8 @@ def run_ours(args):
     sim = Simulator(m, precision=args.precision)
     sim.set_tape_space(args.tape)
     sim.set_replay(args.replay)
+    if args.state_accumulation != "fp32":
+        sim.set_state_accumulation(args.state_accumulation)
     if args.autotune:
         tuned = sim.autotune(torch.tensor(work.q0, dtype=sim.dtype, device=sim.device),
                              torch.tensor(work.qd0, dtype=sim.dtype, device=sim.device))
@@ -253,7 +255,7 @@ def run_ours(args):
                    "precision": args.precision, "l2": "flushed between steps (256 MB write)",
                    "parallelism": f"replicas x{ws}" if ws > 1 else "single GPU",
                    "block": sim.launch[0], "schedule": "persistent" if sim.launch[1] else "grid",
-                   "tape": args.tape, "replay": args.replay, "storage": {"rollout": storage[0], "adjoint": storage[1]},
+                   "tape": args.tape, "replay": args.replay, "state_accumulation": args.state_accumulation, "storage": {"rollout": storage[0], "adjoint": storage[1]},
                    "cuda_graph": bool(args.graph), "contacts": bool(args.contacts),
                    "joint_limits": bool(args.limits)},
         "fwd_env_steps_per_s": B * T / (float(np.mean(fwd_ms)) / 1e3),
@@ -294,6 +296,8 @@ def plain_per_system(work, args, k, n_sys=64):
     sims, bufs = [], []
     for b in range(min(n_sys, m.n_systems)):
         sim = Simulator(m.subset([b]), precision=args.precision)
+        if args.state_accumulation != "fp32":
+            sim.set_state_accumulation(args.state_accumulation)
         dev, dt = sim.device, sim.dtype
         q0 = torch.tensor(work.q0[:, b:b + 1], dtype=dt, device=dev).contiguous()
         qd0 = torch.tensor(work.qd0[:, b:b + 1], dtype=dt, device=dev).contiguous()
@@ -575,7 +579,9 @@ def main():
     ap.add_argument("--block", type=int, default=0)
     ap.add_argument("--persistent", action="store_true")
     ap.add_argument("--autotune", action="store_true")
-    ap.add_argument("--tape", default="auto", choices=["auto", "global", "shared", "pipelined"])
+    ap.add_argument("--tape", default="auto", choices=["auto", "global", "shared", "pipelined", "one_warp"])
+    ap.add_argument("--state-accumulation", default="fp32", choices=["fp32", "fp64"],
+                    help="running-state sums of the fp32_d64 precision (fp64: summed in FP64, stored FP32)")
     ap.add_argument("--replay", default="segment", choices=["segment", "quadratic"])
     ap.add_argument("--no-cpu-baseline", dest="cpu_baseline", action="store_false")
     ap.add_argument("--no-plain", dest="plain", action="store_false")
