@@ -152,7 +152,12 @@ size_t sim_ckpt_bytes(const sim_handle* h, int64_t T, int32_t k);
 size_t sim_work_bytes(const sim_handle* h, int32_t k);
 
 /* Replace every link mass from a device array [n_links_total] of the handle's
- * scalar type, COM and rotational inertia held fixed.  Stream ordered. */
+ * scalar type, COM and rotational inertia held fixed.  Stream ordered.  The masses
+ * are the model parameters the adjoint differentiates besides the controls (Sec. 3.1:
+ * after Eq. 4 the paper notes that the gradients of other parameters follow the
+ * same way as those of u^k; here I(m) = [Ic + m cx cx^T, m cx; m cx^T, m 1] with
+ * c and Ic fixed), so a caller can set them, roll out, and read dPhi/dm from
+ * sim_backward_rollout. */
 int sim_set_masses(sim_handle* h, const void* mass, void* stream);
 
 /* One step x -> x' for every system (Sec. 3.1: kinematics, the three ABA passes,
@@ -163,28 +168,37 @@ int sim_step_batch(sim_handle* h, const void* q, const void* qd, const void* tau
 /* Size of the library's static step scratch used by sim_step_batch_static. */
 #define SIM_STATIC_SCRATCH_BYTES (16u << 20)
 
-/* One step x -> x' like sim_step_batch, for callers that must not allocate
- * device memory: code running while a stream is captured in global mode (where
- * cudaMalloc is refused), or a component inside a host application that owns
- * every device allocation and hands it only a handle and state buffers.  The
- * paper has no counterpart; this is a deployment convenience.
+/* One step x -> x' like sim_step_batch, for callers that cannot allocate device
+ * memory.  Examples: a plug-in inside a host application (a physics or game
+ * engine, robotics middleware, a serving process) that owns every device
+ * allocation through its own pool and only hands the plug-in a handle and state
+ * buffers, so that its memory budget stays exact; or a real-time control loop in
+ * which cudaMalloc's implicit synchronisation and unbounded latency are not
+ * allowed.  The paper has no counterpart; this is a deployment convenience.
  * Allocates nothing: the per-link tape is a file-scope device array of
  * SIM_STATIC_SCRATCH_BYTES (16 MiB) that every GPU loading the library holds
- * until exit; batches whose tape (links x 119 scalars x systems) exceeds it are
- * rejected with SIM_ENOMEM.  The first call on each device looks up the array's
- * device address with that device current; make that first call before any
- * stream capture.  The array is shared by all calls and keeps the last call's
+ * until the process exits; batches whose tape (links x 119 scalars x systems x
+ * scalar size) exceeds it are rejected with SIM_ENOMEM and a message.  The first
+ * call on each device looks up the array's device address (once, with that
+ * device current); make that first call before any stream capture.  The device
+ * current at the call must be the handle's (the one current at sim_create), else
+ * SIM_EINVAL.  The array is shared by all calls and keeps the last call's
  * contents (every word a step reads is written earlier in the same step, so
- * nothing needs clearing); calls whose kernels overlap on the GPU race on it,
- * so serialize them (one stream, or events).  For a model with contact spheres
- * or joint limits the constraint solver's per-system scratch is the handle's,
- * allocated once by sim_create.  Same layouts, ownership and error codes as sim_step_batch. */
+ * nothing needs clearing); calls whose kernels overlap on the GPU race on it, so
+ * serialize them (one stream, or events).  For a model with contact spheres or
+ * joint limits the constraint solver's per-system scratch is the handle's,
+ * allocated once by sim_create.  Same layouts, ownership and error codes as
+ * sim_step_batch. */
 int sim_step_batch_static(sim_handle* h, const void* q, const void* qd, const void* tau,
                           void* q_out, void* qd_out, void* stream);
 
-/* T steps from (q0, qd0) under tau [T][nv_max][B].  Writes x^T to (qT, qdT),
- * the checkpoints x^0, x^k, ... to ckpt (if non-NULL; sim_ckpt_bytes(T, k)
- * bytes) and every state to traj (if non-NULL).  T == 0 copies the input. */
+/* T steps from (q0, qd0) under tau [T][nv_max][B] (Sec. 2: x^{k+1} from x^k and
+ * u^k; each step as sim_step_batch).  Writes x^T to (qT, qdT), the checkpoints
+ * x^0, x^k, ... to ckpt (if non-NULL; sim_ckpt_bytes(T, k) bytes) and every state
+ * to traj (if non-NULL).  Only these step-initial states are kept, never a
+ * step's intermediates (Sec. 3.2, Fig. 2: the checkpoint of step k is its initial
+ * state; k > 1 is the sparser interval of the supplement's Sec. B).  T == 0
+ * copies the input. */
 int sim_rollout(sim_handle* h, const void* q0, const void* qd0, const void* tau, int64_t T,
                 int32_t k, void* ckpt, void* qT, void* qdT, void* traj, void* stream);
 
@@ -271,10 +285,13 @@ int sim_set_replay(sim_handle* h, int32_t mode);
  * allocates here, (nq_max + nv_max) * n_systems doubles) and accumulates the
  * integrator's sums there; every step's dynamics read the FP32 rounding of that
  * state, and the checkpoints, trajectory and final state are stored as FP32.
- * fp64 = 0 (default): the state is FP32 throughout.  The backward's segment
- * replay (k > 1) and sim_step_batch start from FP32 states and sum in FP32; with
- * k = 1 the adjoint recomputes every step from exactly the FP32 state the
- * rollout evaluated.  Rollouts then use the one-warp kernels.  Returns
+ * fp64 = 0 (default): the state is FP32 throughout.  With the flag on,
+ * sim_step_batch (a one-step sim_rollout) also sums in FP64, starting from the
+ * FP64 widening of its FP32 input, and returns the FP32 rounding.  The
+ * backward's segment replay (k > 1) sums in FP32, so its replayed states can
+ * differ from the rollout's by FP32 rounding; with k = 1 the adjoint recomputes
+ * every step from exactly the FP32 state the rollout evaluated.  Rollouts then
+ * use the one-warp kernels.  Returns
  * SIM_EUNSUPPORTED for the other precisions and SIM_ECUDA if the buffer cannot
  * be allocated.  Not thread-safe with a rollout in flight on the handle. */
 int sim_set_state_accumulation(sim_handle* h, int32_t fp64);

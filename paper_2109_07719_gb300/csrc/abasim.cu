@@ -227,12 +227,15 @@ constexpr int kMaxDevices = 64;
 std::mutex g_static_mu;
 void* g_static_ptr[kMaxDevices] = {};
 
-// Device address of g_static_tape on the current device, looked up once per
-// device (the symbol's name in host code is only a host-side stand-in).
+// Device address of g_static_tape on the handle's device, which must be current,
+// looked up once per device (the symbol's name in host code is only a host-side
+// stand-in, never a device address).
 int static_tape(sim_handle* h, void** out) {
   int dev = 0;
   cudaError_t e = cudaGetDevice(&dev);
   if (e != cudaSuccess) return cuda_fail(h, e, "static scratch: cudaGetDevice");
+  if (dev != h->device)
+    return fail(h, SIM_EINVAL, "static scratch: make the handle's device (current at sim_create) current");
   if (dev < 0 || dev >= kMaxDevices) return fail(h, SIM_EUNSUPPORTED, "static scratch: device index too large");
   std::lock_guard<std::mutex> lock(g_static_mu);
   if (!g_static_ptr[dev]) {

@@ -25,3 +25,15 @@ def pytest_collection_modifyitems(config, items):
     for it in items:
         if "gpu" in it.keywords:
             it.add_marker(skip)
+
+
+@pytest.fixture(autouse=True)
+def _default_dtype_guard(request):
+    """A GPU test must start with torch's stock float32 default dtype: a module
+    that changes the default for its own tests restores it, and this guard makes
+    a leak fail loudly at the first GPU test it would reach."""
+    if "gpu" in request.keywords:
+        import torch
+        assert torch.get_default_dtype() == torch.float32, (
+            f"torch default dtype leaked into a GPU test: {torch.get_default_dtype()}")
+    yield

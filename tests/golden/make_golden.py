@@ -21,7 +21,6 @@ from oracle.contact import contact_points                  # noqa: E402
 from oracle.dynamics import OracleModel                    # noqa: E402
 from oracle.rollout import rollout, rollout_backward       # noqa: E402
 
-torch.set_default_dtype(torch.float64)
 HERE = os.path.dirname(os.path.abspath(__file__))
 
 
@@ -55,6 +54,7 @@ def case(name, cite, work, q0, qd0, tau, gq_of_qT, gqd_of_qdT):
 
 
 def main():
+    torch.set_default_dtype(torch.float64)   # the oracle's precision; only when run as a script
     out = []
     # 1. the double pendulum: Phi = sum q_T^2, gradients w.r.t. q0, qd0, every torque (Sec. 2 Eq. 1-2,
     #    Sec. 3.1 Eq. 3-4, Sec. 3.2 Eq. 7)

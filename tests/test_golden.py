@@ -40,7 +40,8 @@ def test_oracle_reproduces_golden(name):
     t = torch.tensor(g["tau"], dtype=torch.float64)[:, None, :]
     with torch.no_grad():
         qT, qdT, _ = rollout(om, q, qd, t, keep=False)
-    r = rollout_backward(om, q, qd, t, torch.tensor([g["gqT"]]), torch.tensor([g["gqdT"]]))
+    r = rollout_backward(om, q, qd, t, torch.tensor([g["gqT"]], dtype=torch.float64),
+                         torch.tensor([g["gqdT"]], dtype=torch.float64))
     for key, val in (("qT", qT[0]), ("qdT", qdT[0]), ("gq0", r[0][0]), ("gqd0", r[1][0]),
                      ("gtau", r[2][:, 0]), ("gmass", r[3][0])):
         assert _rel(val.numpy(), g[key]) < 1e-12, key

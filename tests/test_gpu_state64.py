@@ -30,12 +30,12 @@ def test_fp64_sums_keep_increments_below_fp32_resolution():
     B, T = 8, 1000
     sim = Simulator(_free_body(B), precision="fp32_d64")
     dev = sim.device
-    q0 = torch.zeros(7, B, device=dev)
+    q0 = torch.zeros(7, B, dtype=torch.float32, device=dev)
     q0[0] = 1000.0
     q0[6] = 1.0                                    # identity quaternion (x y z w)
-    qd0 = torch.zeros(6, B, device=dev)
+    qd0 = torch.zeros(6, B, dtype=torch.float32, device=dev)
     qd0[3] = 0.01                                  # body-frame linear velocity along x
-    tau = torch.zeros(T, 6, B, device=dev)
+    tau = torch.zeros(T, 6, B, dtype=torch.float32, device=dev)
     qT32, qdT32, _, _ = sim.rollout(q0, qd0, tau)
     sim.set_state_accumulation("fp64")
     qT64, qdT64, ck, _ = sim.rollout(q0, qd0, tau)

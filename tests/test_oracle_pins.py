@@ -18,8 +18,17 @@ import workloads as wl
 from oracle.dynamics import OracleModel
 from oracle.rollout import step, rollout, rollout_backward
 
-torch.set_default_dtype(torch.float64)
 torch.set_num_threads(1)
+
+
+@pytest.fixture(autouse=True)
+def _fp64_default_dtype():
+    """FP64 as torch's default dtype for this module's tests only (restored after
+    each test, so GPU tests collected later see the usual float32 default)."""
+    prev = torch.get_default_dtype()
+    torch.set_default_dtype(torch.float64)
+    yield
+    torch.set_default_dtype(prev)
 G = 9.81
 
 

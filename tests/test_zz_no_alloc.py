@@ -1,13 +1,15 @@
 """sim_step_batch_static: the one-step entry point that allocates nothing.
 
-It serves callers that may not allocate device memory (code running while a
-stream is captured in global mode, where cudaMalloc is refused, or a component
-whose host application owns every device allocation).  Its per-link scratch is
-a fixed 16 MiB static device array inside the library instead of the handle's
-tape.  Here it is compared, over two calls in a row, with sim_step_batch on the
-same inputs, at the single-step tolerance of the parity tests (1e-12 relative
-for FP64, 1e-6 for FP32).  This file is collected last so that a failure here
-stops a first-failure run only after every other test has run.
+It serves callers that cannot allocate device memory: a plug-in whose host
+application owns every device allocation through its own pool and hands it only
+a handle and state buffers, or a real-time loop where cudaMalloc's implicit
+synchronisation and latency are not allowed.  Its per-link scratch is a fixed
+16 MiB static device array inside the library instead of the handle's tape.
+Here it is called through the C ABI (the ctypes binding) and compared, over two
+calls in a row, with sim_step_batch on the same inputs, at the single-step
+tolerance of the parity tests (1e-12 relative for FP64, 1e-6 for FP32).  This
+file is collected last so that a failure here stops a first-failure run only
+after every other test has run; it also passes alone in a fresh process.
 """
 import numpy as np
 import pytest
