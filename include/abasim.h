@@ -261,12 +261,26 @@ int sim_set_launch(sim_handle* h, int32_t threads, int32_t schedule);
 #define SIM_TAPE_SHARED 2
 #define SIM_TAPE_PIPELINED 3
 #define SIM_TAPE_ONE_WARP 4  /* as SIM_TAPE_AUTO, without the pipelined kernels */
+/* SIM_TAPE_ALIGNED runs models whose joints are all revolute, with no contact
+ * spheres or limits, on the kernels of the world-aligned step: the same ABA step
+ * and adjoint (Sec. 3.1) written in link frames that keep the world's
+ * orientation with their origin at the joint, so that the inward recursion on
+ * the articulated inertias translates them from child to parent instead of
+ * rotating and translating them (each body's inertia is rotated into world axes
+ * once per step, off that serial chain).  Tape and adjoint record in shared
+ * memory when a block's tiles fit, else in the handle's global scratch.  AUTO
+ * picks these kernels for such models; forcing them on another model fails with
+ * SIM_EUNSUPPORTED.  The FP64 state accumulation of SIM_FP32_D64 rollouts is not
+ * available on them (AUTO then takes the one-warp kernels). */
+#define SIM_TAPE_ALIGNED 5
 int sim_set_tape_space(sim_handle* h, int32_t space);
 
 /* The storage mode the last sim_rollout (or step) and sim_backward_rollout
  * launches of this handle ran with: 0 tape in global memory, 1 tape global with
  * state and input streams on chip, 2 tape on chip, 3 the pipelined two-warp
- * adjoint.  Either pointer may be NULL.  No device work. */
+ * kernels, 4 the world-aligned kernels with the tape on chip, 5 the world-aligned
+ * kernels with the tape in global memory.  Either pointer may be NULL.  No device
+ * work. */
 int sim_last_storage(const sim_handle* h, int32_t* rollout_mode, int32_t* backward_mode);
 
 /* How sim_backward_rollout rebuilds the states inside a checkpoint segment when

@@ -198,17 +198,20 @@ class Simulator:
         self.launch = (int(threads) or 32, bool(persistent))
 
     def set_tape_space(self, space: str = "auto"):
-        """'auto' (the pipelined kernels or shared memory when they fit), 'global',
-        'shared' (one warp per tile, tape on chip), 'pipelined' (two warps per tile)
-        or 'one_warp' (as 'auto' without the pipelined kernels)."""
-        code = {"auto": 0, "global": 1, "shared": 2, "pipelined": 3, "one_warp": 4}[space]
+        """'auto' (the world-aligned kernels for revolute models without contacts
+        or limits; otherwise the pipelined kernels or shared memory when they fit),
+        'global', 'shared' (one warp per tile, tape on chip), 'pipelined' (two warps
+        per tile), 'one_warp' (as 'auto' without the pipelined and world-aligned
+        kernels) or 'aligned' (the world-aligned kernels)."""
+        code = {"auto": 0, "global": 1, "shared": 2, "pipelined": 3, "one_warp": 4, "aligned": 5}[space]
         self._check(lib.sim_set_tape_space(self._h, code), "sim_set_tape_space")
 
-    STORAGE = ("global", "hybrid", "shared", "pipelined")
+    STORAGE = ("global", "hybrid", "shared", "pipelined", "aligned_shared", "aligned_global")
 
     def last_storage(self):
         """(rollout, backward) storage modes of the last launches: 'global', 'hybrid',
-        'shared' or 'pipelined'."""
+        'shared', 'pipelined', or the world-aligned kernels' 'aligned_shared' /
+        'aligned_global'."""
         f, b = ctypes.c_int32(), ctypes.c_int32()
         self._check(lib.sim_last_storage(self._h, ctypes.byref(f), ctypes.byref(b)), "sim_last_storage")
         return self.STORAGE[f.value], self.STORAGE[b.value]

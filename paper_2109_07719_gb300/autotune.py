@@ -1,23 +1,27 @@
 """Launch-shape autotuner for the batched rollout kernels.
 
-Times a short forward + adjoint rollout for each candidate — lanes per system
-(one warp per 32-system tile, or the pipelined kernels' two wherever they
-apply), threads per block (systems per block with one lane) and grid or
-persistent schedule — and keeps the fastest.  A two-lane candidate is dropped
-when neither direction ran pipelined (the model is not a batch of short serial
-chains, or the checkpoint interval is above 1).  Results are cached in a JSON file keyed by the batch signature
-(systems, padded sizes, links, precision, link-count histogram) and the GPU
-name, so a model is tuned once per device type.
+Times a short forward + adjoint rollout for each candidate -- the kernel family
+(the link-frame one-warp kernels, one lane per system; the link-frame pipelined
+kernels, two warps per 32-system tile, for short serial chains; the
+world-aligned kernels, one lane per system, for revolute models without
+contacts or limits), threads per block (systems per block) and grid or
+persistent schedule -- and keeps the fastest.  A candidate whose kernels the
+model cannot run (the library refuses the launch, or the pipelined space ran
+nothing pipelined) is dropped.  Results are cached in a JSON file keyed by the
+batch signature (systems, padded sizes, links, precision, link-count histogram)
+and the GPU name, so a model is tuned once per device type.
 """
 from __future__ import annotations
 
 import json
 import os
 
-# (threads per block, persistent schedule, lanes per system)
+# (threads per block, persistent schedule, kernel family): 1 the link-frame
+# one-warp kernels, 2 the pipelined kernels (two lanes per system), 3 the
+# world-aligned kernels
 CANDIDATES = [(32, False, 1), (64, False, 1), (128, False, 1), (32, True, 1), (64, True, 1), (128, True, 1),
-              (32, False, 2), (32, True, 2)]
-TAPE_SPACE = {1: "one_warp", 2: "auto"}
+              (32, False, 2), (32, True, 2), (32, False, 3), (64, False, 3), (32, True, 3), (64, True, 3)]
+TAPE_SPACE = {1: "one_warp", 2: "pipelined", 3: "aligned"}
 
 
 def cache_path() -> str:
@@ -76,25 +80,29 @@ def autotune(sim, q0, qd0, T_probe: int = 16, reps: int = 3, k: int = 1, use_cac
     table = load_cache() if use_cache else {}
     if key in table:
         e = table[key]
-        best = (e["threads"], e["persistent"], e.get("lanes", 1))
+        best = (e["threads"], e["persistent"], e.get("kernels", e.get("lanes", 1)))
         apply(sim, best)
         return best
     if timer is None:
         timer = _gpu_timer(q0, qd0, T_probe, reps, k)
+    from . import SimError
     times = {}
     for cand in CANDIDATES:
-        if cand[2] == 1 and cand[0] > 32 and cand[0] // 2 >= sim.B:
+        if cand[2] != 2 and cand[0] > 32 and cand[0] // 2 >= sim.B:
             continue
-        apply(sim, cand)
-        t = timer(sim, cand)
+        try:
+            apply(sim, cand)
+            t = timer(sim, cand)
+        except SimError:
+            continue                                   # the model cannot run on these kernels
         if cand[2] == 2 and "pipelined" not in sim.last_storage():
-            continue                                   # ran as one lane: a repeat of another candidate
+            continue                                   # ran one-lane in a direction: not this candidate
         times[cand] = t
     best = choose(times)
     apply(sim, best)
     if use_cache:
-        table[key] = {"threads": best[0], "persistent": best[1], "lanes": best[2],
-                      "seconds": {f"{c[0]}/{'persistent' if c[1] else 'grid'}/{c[2]} lane(s)": t
+        table[key] = {"threads": best[0], "persistent": best[1], "kernels": best[2],
+                      "seconds": {f"{c[0]}/{'persistent' if c[1] else 'grid'}/{TAPE_SPACE[c[2]]}": t
                                   for c, t in times.items()}}
         save_cache(table)
     return best

@@ -355,6 +355,9 @@ int sim_create(const sim_model_desc* d, sim_handle** out) {
   }
   cudaDeviceGetAttribute(&h->sms, cudaDevAttrMultiProcessorCount, h->device);
   h->all_chains = !any_contact;
+  h->all_revolute = !any_contact;
+  for (int i = 0; i < h->L_total && h->all_revolute; ++i)
+    if (d->joint_type[i] != SIM_REVOLUTE) h->all_revolute = false;
   for (int b = 0; b < B && h->all_chains; ++b)
     for (int l = 0; l < nl_sys[b]; ++l) {
       const int i = d->sys_link_offset[b] + l;
@@ -550,7 +553,7 @@ int sim_set_launch(sim_handle* h, int32_t threads, int32_t schedule) {
 int sim_set_tape_space(sim_handle* h, int32_t space) {
   if (!h) return SIM_EINVAL;
   if (space != SIM_TAPE_AUTO && space != SIM_TAPE_GLOBAL && space != SIM_TAPE_SHARED &&
-      space != SIM_TAPE_PIPELINED && space != SIM_TAPE_ONE_WARP)
+      space != SIM_TAPE_PIPELINED && space != SIM_TAPE_ONE_WARP && space != SIM_TAPE_ALIGNED)
     return fail(h, SIM_EINVAL, "unknown tape space");
   h->tape_space = space;
   return SIM_OK;

@@ -45,6 +45,7 @@ struct sim_handle {
   int last_storage = 0, last_storage_bwd = 0;
   int sms = 0;
   bool all_chains = false;   // every system a serial chain of revolute joints (the pipelined adjoint)
+  bool all_revolute = false; // every joint revolute and no contact spheres or limits (the world-aligned kernels)
   bool state64 = false;      // sim_rollout accumulates the state in FP64 (SIM_FP32_D64 only)
   void* x64 = nullptr;       // [nq_max + nv_max][B] double: that state
   std::vector<int> h_sys_of_slot;

@@ -437,6 +437,14 @@ __global__ void k_backward(DevModel<T> m, const T* __restrict__ ckpt, const T* _
                                               gtau, gm_acc, ring))
 }
 
+}  // namespace host
+}  // namespace abasim
+
+#include "wkernels.cuh"
+
+namespace abasim {
+namespace host {
+
 // ------------------------------------------------------------------ pipelined adjoint
 // Two warps per 32-system tile, for batches of serial revolute chains with a
 // checkpoint every step: the producer warp recomputes step t's forward
@@ -751,6 +759,12 @@ template <class T, class DT>
 BackwardKernel<T> backward_contact_kernel();
 template <class T, class DT>
 BackwardKernel<T> backward_pipe_kernel();
+// The world-aligned kernels (tape on chip or in global memory), instantiated in
+// their own units.
+template <class T, class DT>
+RolloutKernel<T> wrollout_kernel(bool onchip);
+template <class T, class DT>
+BackwardKernel<T> wbackward_kernel(bool onchip);
 
 // One step with tangents: the state, torque and tape are dual numbers staged in
 // the caller's workspace [tile][...][lane]; model constants stay plain.
@@ -878,9 +892,103 @@ int choose_storage(sim_handle* h, K0 k_global, K1 k_hybrid, K2 k_smem, bool bwd,
   return SIM_OK;
 }
 
+// Storage of a world-aligned launch: the tape on chip when a block's tiles fit the
+// per-block opt-in limit and that adds no wave of blocks over the global-tape
+// kernel (whose blocks still keep their state and input streams on chip).
+template <class T, class K>
+int choose_w(sim_handle* h, K k_on, K k_off, bool bwd, bool* onchip, size_t* bytes) {
+  int limit = 0;
+  cudaError_t e = cudaDeviceGetAttribute(&limit, cudaDevAttrMaxSharedMemoryPerBlockOptin, h->device);
+  if (e != cudaSuccess) return cuda_fail(h, e, "shared-memory limit query");
+  const int tiles = h->block / LANES;
+  const int nx = h->nq_max + h->nv_max;
+  const size_t need_on = (size_t)tiles * w_smem_per_tile(h->maxL, nx, h->nv_max, bwd, true) * LANES * sizeof(T);
+  const size_t need_off = (size_t)tiles * w_smem_per_tile(h->maxL, nx, h->nv_max, bwd, false) * LANES * sizeof(T);
+  if (need_off > (size_t)limit) return fail(h, SIM_EUNSUPPORTED, "state and input streams do not fit in shared memory");
+  e = cudaFuncSetAttribute((const void*)k_off, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)need_off);
+  if (e != cudaSuccess) return cuda_fail(h, e, "shared-memory opt-in");
+  *onchip = false;
+  *bytes = need_off;
+  if (need_on > (size_t)limit) return SIM_OK;
+  e = cudaFuncSetAttribute((const void*)k_on, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)need_on);
+  if (e != cudaSuccess) return cuda_fail(h, e, "shared-memory opt-in");
+  int per_on = 0, per_off = 0;
+  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_on, k_on, h->block, need_on);
+  if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_off, k_off, h->block, need_off);
+  if (e != cudaSuccess) return cuda_fail(h, e, "occupancy query");
+  const long long units = (h->B + h->block - 1) / h->block;
+  const long long sms = std::max(1, h->sms);
+  auto waves = [&](int per_sm) { return per_sm > 0 ? (units + sms * per_sm - 1) / (sms * per_sm) : 1LL << 40; };
+  if (waves(per_on) <= waves(per_off)) {
+    *onchip = true;
+    *bytes = need_on;
+  }
+  return SIM_OK;
+}
+
+// The world-aligned path applies to models of revolute joints without contact
+// spheres or limits, under SIM_TAPE_AUTO or SIM_TAPE_ALIGNED.
+inline bool use_aligned(const sim_handle* h, bool rollout) {
+  if (!h->all_revolute || (rollout && h->state64)) return false;
+  return h->tape_space == SIM_TAPE_AUTO || h->tape_space == SIM_TAPE_ALIGNED;
+}
+
+template <class T, class DT>
+int launch_wrollout(sim_handle* h, const void* q0, const void* qd0, const void* tau, int64_t T_, int k, void* ckpt,
+                    void* qT, void* qdT, void* traj, void* stream) {
+  DevModel<T> m = dev_model<T>(h);
+  const RolloutKernel<T> k_on = wrollout_kernel<T, DT>(true), k_off = wrollout_kernel<T, DT>(false);
+  bool onchip = false;
+  size_t shm = 0;
+  int rc = choose_w<T>(h, k_on, k_off, false, &onchip, &shm);
+  if (rc != SIM_OK) return rc;
+  const RolloutKernel<T> kern = onchip ? k_on : k_off;
+  h->last_storage = onchip ? 4 : 5;
+  int grid = 0;
+  rc = launch_shape(h, kern, &grid, &m.persistent, shm, stream);
+  if (rc != SIM_OK) return rc;
+  kern<<<grid, h->block, shm, S(stream)>>>(m, (const T*)q0, (const T*)qd0, (const T*)tau, (long long)T_, k,
+                                           (T*)ckpt, (T*)qT, (T*)qdT, (T*)traj);
+  cudaError_t e = cudaGetLastError();
+  return e == cudaSuccess ? SIM_OK : cuda_fail(h, e, "rollout launch");
+}
+
+template <class T, class DT>
+int launch_wbackward(sim_handle* h, const void* ckpt, const void* tau, int64_t T_, int k, const void* gqT,
+                     const void* gqdT, const void* gtraj, void* gq0, void* gqd0, void* gtau, void* gmass, void* work,
+                     void* stream) {
+  DevModel<T> m = dev_model<T>(h);
+  const BackwardKernel<T> k_on = wbackward_kernel<T, DT>(true), k_off = wbackward_kernel<T, DT>(false);
+  bool onchip = false;
+  size_t shm = 0;
+  int rc = choose_w<T>(h, k_on, k_off, true, &onchip, &shm);
+  if (rc != SIM_OK) return rc;
+  const BackwardKernel<T> kern = onchip ? k_on : k_off;
+  h->last_storage_bwd = onchip ? 4 : 5;
+  int grid = 0;
+  rc = launch_shape(h, kern, &grid, &m.persistent, shm, stream);
+  if (rc != SIM_OK) return rc;
+  kern<<<grid, h->block, shm, S(stream)>>>(m, (const T*)ckpt, (const T*)tau, (long long)T_, k, (const T*)gqT,
+                                           (const T*)gqdT, (const T*)gtraj, (T*)gq0, (T*)gqd0, (T*)gtau,
+                                           (T*)h->gm_acc, (T*)work);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return cuda_fail(h, e, "backward launch");
+  if (gmass) {
+    k_gather_mass_grad<T><<<(h->L_total + 255) / 256, 256, 0, S(stream)>>>((const T*)h->gm_acc, h->link_slot,
+                                                                          h->L_total, (T*)gmass);
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return cuda_fail(h, e, "mass-gradient launch");
+  }
+  return SIM_OK;
+}
+
 template <class T, class DT>
 int launch_rollout(sim_handle* h, const void* q0, const void* qd0, const void* tau, int64_t T_,
                    int k, void* ckpt, void* qT, void* qdT, void* traj, void* stream) {
+  if (use_aligned(h, true)) return launch_wrollout<T, DT>(h, q0, qd0, tau, T_, k, ckpt, qT, qdT, traj, stream);
+  if (h->tape_space == SIM_TAPE_ALIGNED)
+    return fail(h, SIM_EUNSUPPORTED,
+                "the world-aligned kernels need revolute joints only, no contact spheres or limits, and FP32 state sums");
   DevModel<T> m = dev_model<T>(h);
   size_t shm = 0;
   int st = ST_GLOBAL;
@@ -935,6 +1043,10 @@ template <class T, class DT>
 int launch_backward(sim_handle* h, const void* ckpt, const void* tau, int64_t T_, int k,
                     const void* gqT, const void* gqdT, const void* gtraj, void* gq0, void* gqd0,
                     void* gtau, void* gmass, void* work, void* stream) {
+  if (use_aligned(h, false))
+    return launch_wbackward<T, DT>(h, ckpt, tau, T_, k, gqT, gqdT, gtraj, gq0, gqd0, gtau, gmass, work, stream);
+  if (h->tape_space == SIM_TAPE_ALIGNED)
+    return fail(h, SIM_EUNSUPPORTED, "the world-aligned kernels need revolute joints only and no contact spheres or limits");
   DevModel<T> m = dev_model<T>(h);
   size_t shm = 0;
   int st = ST_GLOBAL;
