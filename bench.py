@@ -1,13 +1,15 @@
 """Throughput of batched forward + adjoint rollouts on one GPU.
 
-One step = one forward rollout of T steps with a checkpoint every step, plus the
-adjoint rollout (recompute + hand-derived adjoint) that returns gradients with
-respect to the initial state, every joint torque and every link mass, for a
-batch of B independent articulated systems.  Default workload: 4096 serial
-7-DOF revolute chains, dt 1e-3, T = 1000, FP32.
+One step = one forward rollout of T steps with a checkpoint every k steps, plus
+the adjoint rollout (recompute + hand-derived adjoint) that returns gradients
+with respect to the initial state, every joint torque and every link mass, for
+a batch of B independent articulated systems.  Default workload: the largest
+single-GPU configuration, 16384 uneven revolute trees with DOF ~ U{2..64}
+(branch factors 1..3), dt 1e-3, T = 5000, FP32, k = 1.
 
 Prints one JSON line.  `--impl reference` times the CPU FP64 oracle on a bounded
-sample of the same workload instead.
+sample of the same workload instead.  `--gpus N` without a launcher starts N
+ranks itself (one process per GPU, each on its own batch).
 """
 from __future__ import annotations
 
@@ -38,7 +40,9 @@ def _flop_table():
 
 
 def flops_per_system_step(model, kind):
-    """kind: 'fwd' (forward step) or 'adj' (adjoint step without its recompute)."""
+    """kind: 'fwd' / 'adj' (link-frame step: forward, adjoint without its recompute)
+    or 'wfwd' / 'wrec' / 'wadj' (world-aligned step: the rollout's step, the
+    adjoint's recompute, the adjoint step; revolute joints only)."""
     import numpy as np
     tab = _flop_table()[kind]
     jt = np.asarray(model.joint_type)
@@ -46,7 +50,22 @@ def flops_per_system_step(model, kind):
     n_free = int((jt == 1).sum())
     n_rev_root = int(((jt == 0) & (par < 0)).sum())
     n_rev = int(((jt == 0) & (par >= 0)).sum())
-    return (tab["rev"] * n_rev + tab["rev_root"] * n_rev_root + tab["free_root"] * n_free) / model.n_systems
+    if n_free and "free_root" not in tab:
+        raise ValueError(f"{kind}: no FLOP count for free joints")
+    return (tab["rev"] * n_rev + tab["rev_root"] * n_rev_root + tab.get("free_root", 0) * n_free) / model.n_systems
+
+
+def kernel_flops(model, storage):
+    """(rollout kernel, its FLOPs per system-step, adjoint kernel, its FLOPs per
+    system-step) for the storage modes the last launches reported."""
+    fwd_aligned = storage[0].startswith("aligned")
+    bwd_aligned = storage[1].startswith("aligned")
+    kf = "k_wrollout" if fwd_aligned else ("k_rollout_pipe" if storage[0] == "pipelined" else "k_rollout")
+    kb = "k_wbackward" if bwd_aligned else ("k_backward_pipe" if storage[1] == "pipelined" else "k_backward")
+    ff = flops_per_system_step(model, "wfwd" if fwd_aligned else "fwd")
+    fb = (flops_per_system_step(model, "wrec") + flops_per_system_step(model, "wadj")) if bwd_aligned else \
+        (flops_per_system_step(model, "fwd") + flops_per_system_step(model, "adj"))
+    return kf, ff, kb, fb
 
 
 def source_digest() -> str:
@@ -144,17 +163,21 @@ def run_ours(args):
     torch.cuda.set_device(local)
     if ws > 1:
         dist.init_process_group("nccl")
+        ws = dist.get_world_size()                 # the ranks that joined the process group
+    peak = fp_peak(args.precision) if rank == 0 else None   # before any timing: the probe fills the GPU
     work = workload(args.config, args.precision, args.batch, args.horizon, rank, args.contacts, args.limits)
     m = work.model
     T, k = work.T, args.k
+    free0 = torch.cuda.mem_get_info()[0]
     sim = Simulator(m, precision=args.precision)
+    handle_bytes = free0 - torch.cuda.mem_get_info()[0]
     sim.set_tape_space(args.tape)
     sim.set_replay(args.replay)
     if args.state_accumulation != "fp32":
         sim.set_state_accumulation(args.state_accumulation)
     if args.autotune:
-        tuned = sim.autotune(torch.tensor(work.q0, dtype=sim.dtype, device=sim.device),
-                             torch.tensor(work.qd0, dtype=sim.dtype, device=sim.device))
+        sim.autotune(torch.tensor(work.q0, dtype=sim.dtype, device=sim.device),
+                     torch.tensor(work.qd0, dtype=sim.dtype, device=sim.device))
     elif args.block or args.persistent:
         sim.set_launch(args.block, args.persistent)
     dev, dt = sim.device, sim.dtype
@@ -175,13 +198,13 @@ def run_ours(args):
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
     stream = torch.cuda.current_stream()
 
-    def step(evs=None):
+    def step(evs=None, kk=k, ckb=ck, wbuf=work_buf):
         if evs:
             evs[0].record(stream)
-        sim.rollout(q0, qd0, tau, k=k, out=(qT, qdT, ck, None))
+        sim.rollout(q0, qd0, tau, k=kk, out=(qT, qdT, ckb, None))
         if evs:
             evs[1].record(stream)
-        sim.backward(ck, tau, gqT, gqdT, k=k, work=work_buf, out=(gq0, gqd0, gtau, gm))
+        sim.backward(ckb, tau, gqT, gqdT, k=kk, work=wbuf, out=(gq0, gqd0, gtau, gm))
         if evs:
             evs[2].record(stream)
 
@@ -203,6 +226,7 @@ def run_ours(args):
     th.start()
     time.sleep(0.3)
     events = [[torch.cuda.Event(enable_timing=True) for _ in range(3)] for _ in range(args.steps)]
+    torch.cuda.reset_peak_memory_stats()
     if ws > 1:
         dist.barrier()
     torch.cuda.synchronize()
@@ -214,6 +238,7 @@ def run_ours(args):
         dist.barrier()
     stop.set()
     th.join()
+    peak_torch = torch.cuda.max_memory_allocated()
     fwd_ms = [e[0].elapsed_time(e[1]) for e in events]
     adj_ms = [e[1].elapsed_time(e[2]) for e in events]
     graph_ms = None
@@ -226,25 +251,30 @@ def run_ours(args):
             gev[i][1].record(stream)
         torch.cuda.synchronize()
         graph_ms = float(np.mean([a.elapsed_time(b) for a, b in gev]))
+        del graph
     step_ms = float(np.sum(fwd_ms) + np.sum(adj_ms)) / args.steps
     step_ms, units = aggregate(step_ms, B * T, dev)
     flags = sim.status()
     value = units / (step_ms / 1e3)
-    # end to end through the public API with host buffers
+    storage = sim.last_storage()
+    k_sweep = None
+    if args.k_sweep and rank == 0:
+        k_sweep = checkpoint_sweep(sim, step, T, B, flush, [int(x) for x in args.k_sweep.split(",")])
+    grad_err = None
+    if args.grad_check and rank == 0:
+        grad_err = precision_error(sim, work, args, (qT, qdT, gq0, gqd0, gtau, gm), ck, tau)
+    del ck, work_buf, gtau
     e2e = None
     if args.e2e:
+        torch.cuda.empty_cache()
         e2e = run_e2e(sim, work, k, args.steps, tau.cpu().pin_memory(), q0.cpu().pin_memory(),
                       qd0.cpu().pin_memory())
     if rank != 0:
         return None
-    storage = sim.last_storage()
-    kname = "k_backward_pipe" if storage[1] == "pipelined" else "k_backward"
-    f_fwd = flops_per_system_step(m, "fwd")
-    f_adj = flops_per_system_step(m, "adj")
-    adj_flops = B * T * (f_fwd + f_adj)
+    kf, f_fwd, kb, f_bwd = kernel_flops(m, storage)
+    adj_flops = B * T * f_bwd
     adj_s = float(np.mean(adj_ms)) / 1e3
     clocks = _clocks_summary(samples)
-    peak = fp_peak(args.precision)
     achieved = adj_flops / adj_s / 1e12
     line = {
         "metric": METRIC, "value": value, "unit": "env-steps/s", "n_gpus": ws, "steps": args.steps,
@@ -255,25 +285,37 @@ def run_ours(args):
                    "precision": args.precision, "l2": "flushed between steps (256 MB write)",
                    "parallelism": f"replicas x{ws}" if ws > 1 else "single GPU",
                    "block": sim.launch[0], "schedule": "persistent" if sim.launch[1] else "grid",
-                   "tape": args.tape, "replay": args.replay, "state_accumulation": args.state_accumulation, "storage": {"rollout": storage[0], "adjoint": storage[1]},
+                   "tape": args.tape, "replay": args.replay, "state_accumulation": args.state_accumulation,
+                   "storage": {"rollout": storage[0], "adjoint": storage[1]},
                    "cuda_graph": bool(args.graph), "contacts": bool(args.contacts),
                    "joint_limits": bool(args.limits)},
         "fwd_env_steps_per_s": B * T / (float(np.mean(fwd_ms)) / 1e3),
         "ms_fwd": float(np.mean(fwd_ms)), "ms_adj": float(np.mean(adj_ms)),
         "ms_per_step_cuda_graph": graph_ms,
-        "roofline": {"bound": "alu", "kernel": kname, "achieved": achieved, "peak": peak["tflops"],
+        "roofline": {"bound": "alu", "kernel": kb, "achieved": achieved, "peak": peak["tflops"],
                      "unit": "TFLOP/s", "frac": achieved / peak["tflops"],
-                     "traffic": measured_traffic(kname, m.name, B, T, args.precision, k),
-                     "flops_per_system_step": {"fwd": f_fwd, "adj": f_adj}, "peak_note": peak["note"]
-                     + ("; the FLOP count covers the ABA step only, not the constraint solve"
-                        if args.contacts or args.limits else "")},
+                     "traffic": measured_traffic(kb, m.name, B, T, args.precision, k),
+                     "flops_per_system_step": {kf: f_fwd, kb: f_bwd},
+                     "peak_note": peak["note"] + ("; the FLOP count covers the ABA step only, not the constraint "
+                                                  "solve" if args.contacts or args.limits else ""),
+                     "peaks_measured": {x: (peak.get("probe") or {}).get(x) for x in ("fp32_tflops", "fp64_tflops")},
+                     "rollout": {"kernel": kf, "achieved": B * T * f_fwd / (float(np.mean(fwd_ms)) / 1e3) / 1e12,
+                                 "frac": B * T * f_fwd / (float(np.mean(fwd_ms)) / 1e3) / 1e12 / peak["tflops"]}},
+        "peak_mem_bytes": {"device_total": int(peak_torch + handle_bytes), "torch_allocator": int(peak_torch),
+                           "handle": int(handle_bytes),
+                           "note": "peak of the timed steps: inputs, checkpoints, outputs, the 256 MB L2-flush "
+                                   "buffer (torch's allocator) and the handle's own buffers (model constants, "
+                                   "tape scratch)"},
+        "grad_rel_err": grad_err,
+        "k_sweep": k_sweep,
         "e2e": e2e,
         "gpu_launches": args.steps * 3,
         "clocks": clocks,
         "nonfinite_systems": int((flags != 0).sum()),
+        "nonfinite_ids": [int(i) for i in np.flatnonzero(np.asarray(flags) != 0)[:16]],
     }
     if args.plain:
-        pl = plain_per_system(work, args, k)
+        pl = plain_per_system(work, args, k, n_sys=args.plain_systems)
         line["plain_per_system"] = pl
         line["vs_plain_per_system"] = value / pl["value"]
     if args.cpu_baseline:
@@ -281,6 +323,100 @@ def run_ours(args):
         one = cpu_baseline(args, budget_s=8.0, threads=1)
         line["cpu_baseline"]["one_core"] = {"value": one["value"], "unit": one["unit"], "cores": 1}
     return line
+
+
+def checkpoint_sweep(sim, step, T, B, flush, ks):
+    """Time per bench step with a checkpoint every k steps (Sec. 3.2 Eq. 7 and the
+    supplement's Sec. B): one warm-up and one timed step per k, own checkpoint and
+    workspace buffers; the checkpoint memory is ceil(T/k) states."""
+    import torch
+    out = {}
+    for kk in ks:
+        ckb = sim.empty((T + kk - 1) // kk, sim.nx, B)
+        wbuf = torch.empty(max(sim.work_bytes(kk), 1), dtype=torch.uint8, device=sim.device)
+        step(kk=kk, ckb=ckb, wbuf=wbuf)
+        torch.cuda.synchronize()
+        flush.fill_(1.0)
+        ev = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
+        step(ev, kk=kk, ckb=ckb, wbuf=wbuf)
+        torch.cuda.synchronize()
+        out[str(kk)] = {"ms_fwd": ev[0].elapsed_time(ev[1]), "ms_adj": ev[1].elapsed_time(ev[2]),
+                        "env_steps_per_s": B * T / (ev[0].elapsed_time(ev[2]) / 1e3),
+                        "ckpt_bytes": int(sim.ckpt_bytes(T, kk)), "work_bytes": int(sim.work_bytes(kk))}
+        del ckb, wbuf
+    return out
+
+
+def _rel(a, b, floor=1e-12):
+    """max |a - b| / max(max |b|, floor): the per-output relative error."""
+    import numpy as np
+    a = np.asarray(a, np.float64)
+    b = np.asarray(b, np.float64)
+    if not np.all(np.isfinite(a)):
+        return float("inf")
+    return float(np.abs(a - b).max() / max(np.abs(b).max(), floor))
+
+
+def precision_error(sim, work, args, outs, ck, tau_dev, n_sample=8):
+    """Per-output relative error of the timed run against the library's FP64 path
+    (whose parity with the CPU FP64 oracle, states 1e-8 and gradients 1e-6, the GPU
+    tests check), computed after the timed region on sampled systems -- the
+    smallest, the largest and others spread over the link counts -- at the full
+    horizon: a handle of just those systems rolls them out and differentiates
+    them in FP64 from the same inputs and seeds.  Also the state error at a few
+    horizons (from the checkpoints), and the FP64 run's own sensitivity there
+    (the same run with q0 perturbed by 1e-12 relative), which says how much of
+    the error the dynamics themselves amplify over the horizon."""
+    import numpy as np
+    import torch
+    from paper_2109_07719_gb300 import Simulator
+    m = work.model
+    T, k = work.T, args.k
+    nv = m.nv_per_system()
+    order = np.argsort(nv, kind="stable")
+    pick = np.unique(np.round(np.linspace(0, len(order) - 1, n_sample)).astype(int))
+    sel = sorted({int(order[i]) for i in pick})
+    sub = m.subset(sel)
+    ref = Simulator(sub, precision="fp64")
+    dev = ref.device
+    nqs, nvs = ref.nq_max, ref.nv_max
+    # the timed run's inputs for these systems, widened to FP64
+    q0 = torch.tensor(np.ascontiguousarray(work.q0[:nqs, sel]), dtype=torch.float64, device=dev).contiguous()
+    qd0 = torch.tensor(np.ascontiguousarray(work.qd0[:nvs, sel]), dtype=torch.float64, device=dev).contiguous()
+    if sim.dtype != torch.float64:
+        q0, qd0 = q0.float().double().contiguous(), qd0.float().double().contiguous()
+    tau = tau_dev[:, :nvs][:, :, torch.tensor(sel, device=tau_dev.device)].double().to(dev).contiguous()
+    qT, qdT, ck64, _ = ref.rollout(q0, qd0, tau, k=1)
+    g = ref.backward(ck64, tau, torch.ones_like(qT), torch.zeros_like(qdT), k=1)
+    eps = 1e-12
+    qTp, _, ckp, _ = ref.rollout(q0 * (1 + eps), qd0, tau, k=1)
+    torch.cuda.synchronize()
+    qT32, qdT32, gq0, gqd0, gtau, gm = outs
+    cols = torch.tensor(sel, device=qT32.device)
+    per = {"qT": _rel(qT32[:nqs, cols].cpu(), qT.cpu()), "qdT": _rel(qdT32[:nvs, cols].cpu(), qdT.cpu()),
+           "gq0": _rel(gq0[:nqs, cols].cpu(), g[0].cpu()), "gqd0": _rel(gqd0[:nvs, cols].cpu(), g[1].cpu()),
+           "gtau": _rel(gtau[:, :nvs][:, :, cols].cpu(), g[2].cpu())}
+    lo = m.sys_link_offset
+    gmm = np.concatenate([gm.cpu().numpy()[lo[s]:lo[s + 1]] for s in sel])
+    per["gmass"] = _rel(gmm, g[3].cpu().numpy())
+    vs_step = {}
+    if ck is not None and k == 1:
+        for t in sorted({T // 10, T // 4, T // 2, T - 1}):
+            if t <= 0:
+                continue
+            x32 = ck[t][:, cols].double().cpu()
+            x64 = ck64[t].cpu()
+            xs = ckp[t].cpu()
+            a = torch.cat([x32[:nqs], x32[sim.nq_max:sim.nq_max + nvs]])
+            vs_step[str(t)] = {"state": _rel(a, x64), "fp64_self_sensitivity": _rel(xs, x64)}
+    tol = (1e-8, 1e-6) if args.precision == "fp64" else (1e-3, 1e-2)
+    del ref
+    return {"per_output": per, "reference": "the library's FP64 path (oracle parity checked in the GPU tests)",
+            "horizon": T, "systems": sel, "dof": [int(nv[s]) for s in sel],
+            "state_error_vs_step": vs_step, "perturbation": eps,
+            "tolerance": {"states": tol[0], "gradients": tol[1]},
+            "within_tolerance": bool(max(per["qT"], per["qdT"]) <= tol[0] and
+                                     max(per["gq0"], per["gqd0"], per["gtau"], per["gmass"]) <= tol[1])}
 
 
 def plain_per_system(work, args, k, n_sys=64):
@@ -339,12 +475,50 @@ def aggregate(step_ms: float, units: int, device="cpu"):
     return float(t.item()), int(u.item())
 
 
+_PEAKS = {}
+
+
+def measure_fma_peaks():
+    """FP32 and FP64 FMA throughput of this GPU from the library's probe
+    (paper_2109_07719_gb300/_lib/fma_peak, built with the library), with the SM
+    clock sampled while it runs; None if the probe is missing or fails."""
+    if "probe" in _PEAKS:
+        return _PEAKS["probe"]
+    from paper_2109_07719_gb300 import build as b
+    res = None
+    if os.path.exists(b.FMA_PEAK):
+        stop, samples = threading.Event(), []
+        th = threading.Thread(target=_clock_sampler, args=(stop, samples), daemon=True)
+        th.start()
+        try:
+            r = subprocess.run([b.FMA_PEAK], capture_output=True, text=True, timeout=120)
+            if r.returncode == 0:
+                res = json.loads(r.stdout.strip().splitlines()[-1])
+        except (subprocess.TimeoutExpired, ValueError, IndexError):
+            res = None
+        stop.set()
+        th.join()
+        if res is not None:
+            res["clocks"] = _clocks_summary(samples)
+    _PEAKS["probe"] = res
+    return res
+
+
 def fp_peak(precision):
-    """Plain-ALU peak from unit counts and the maximum SM clock: 152 SMs x 128 FP32
-    lanes x 2 FLOP per FMA x 2.07 GHz (FP64: the nominal 1.25 TFLOP/s)."""
+    """The roofline denominator: the FMA throughput measured on this GPU by the
+    probe (FP32 for the FP32 storage modes, FP64 for the FP64 one); if the probe
+    is unavailable, the nominal unit counts x the maximum clock (152 SMs x 128
+    FP32 lanes x 2 FLOP x 2.07 GHz; FP64 the nominal 1.25 TFLOP/s), said so."""
+    p = measure_fma_peaks()
+    key = "fp64_tflops" if precision == "fp64" else "fp32_tflops"
+    if p is not None and p.get(key):
+        clk = p.get("clocks", {})
+        return {"tflops": p[key], "note": f"measured: FMA-chain probe on this GPU ({key}; median SM clock "
+                                          f"{clk.get('sm_mhz')} MHz during the probe)", "probe": p}
     if precision == "fp64":
-        return {"tflops": 1.25, "note": "nominal FP64 vector rate of GB300 (1.25 TFLOP/s)"}
-    return {"tflops": 152 * 128 * 2 * 2.07e9 / 1e12, "note": "152 SM x 128 FP32 lanes x 2 x 2.07 GHz"}
+        return {"tflops": 1.25, "note": "nominal FP64 vector rate of GB300 (1.25 TFLOP/s): probe unavailable"}
+    return {"tflops": 152 * 128 * 2 * 2.07e9 / 1e12,
+            "note": "nominal: 152 SM x 128 FP32 lanes x 2 x 2.07 GHz (probe unavailable)"}
 
 
 def run_e2e(sim, work, k, steps, tau_h, q0_h, qd0_h):
@@ -414,28 +588,45 @@ def run_e2e(sim, work, k, steps, tau_h, q0_h, qd0_h):
             "copies": "per step, on a second stream overlapped with the neighbouring steps' compute"}
 
 
-ORACLE_SAMPLE = (16, 20)  # systems, steps of one oracle rollout of the CPU baseline
+ORACLE_SAMPLE = {4: (4, 5)}   # systems, steps of one oracle rollout of the CPU baseline (default 16, 20)
+
+
+def _oracle_sample_size(config):
+    return ORACLE_SAMPLE.get(config, (16, 20))
 
 
 def _oracle_sample(config, precision, contacts, limits):
-    """The CPU baseline's unit of work: forward + adjoint of 16 systems of the
-    workload over 20 steps through the FP64 oracle (CRBA + RNEA forward, per-step
-    recompute + reverse-mode step adjoint)."""
+    """The CPU baseline's unit of work: forward + adjoint of a few systems of the
+    workload over a few steps through the FP64 oracle (CRBA + RNEA forward,
+    per-step recompute + reverse-mode step adjoint), one oracle batch per
+    topology.  For the uneven trees the systems are spread over the link counts
+    (the oracle's cost grows with them)."""
+    import numpy as np
     import torch
     from oracle.dynamics import OracleModel
     from oracle.rollout import rollout_backward
-    nsys, T = ORACLE_SAMPLE
-    work = workload(config, precision, nsys, T, contacts=contacts, limits=limits)
+    nsys, T = _oracle_sample_size(config)
+    work = workload(config, precision, None if config == 4 else nsys, T, contacts=contacts, limits=limits)
     m = work.model
-    sys_ = list(range(min(nsys, m.n_systems)))
+    if config == 4:
+        order = np.argsort(m.nv_per_system(), kind="stable")
+        sys_ = sorted(int(order[i]) for i in np.round(np.linspace(0, len(order) - 1, nsys)).astype(int))
+    else:
+        sys_ = list(range(min(nsys, m.n_systems)))
     tau = work.tau(T=T)
+    groups = {}
+    off = m.sys_link_offset
+    for s in sys_:
+        key = (tuple(m.parent[off[s]:off[s + 1]]), tuple(m.joint_type[off[s]:off[s + 1]]))
+        groups.setdefault(key, []).append(s)
 
     def once():
-        om = OracleModel(m, sys_)
-        q0 = torch.tensor(work.q0[:om.nq, sys_].T)
-        qd0 = torch.tensor(work.qd0[:om.nv, sys_].T)
-        ot = tau[:, :om.nv, sys_].permute(0, 2, 1).contiguous()
-        rollout_backward(om, q0, qd0, ot, torch.ones_like(q0), torch.zeros_like(qd0))
+        for grp in groups.values():
+            om = OracleModel(m, grp)
+            q0 = torch.tensor(work.q0[:om.nq, grp].T)
+            qd0 = torch.tensor(work.qd0[:om.nv, grp].T)
+            ot = tau[:, :om.nv, grp].permute(0, 2, 1).contiguous()
+            rollout_backward(om, q0, qd0, ot, torch.ones_like(q0), torch.zeros_like(qd0))
         return len(sys_) * T
 
     return once
@@ -461,7 +652,7 @@ def cpu_baseline(args, budget_s: float = 15.0, threads: int | None = None):
     small tensors, which intra-op threads barely speed up).  The process pool is
     started with spawn (this process may already hold a CUDA context)."""
     contacts, limits = getattr(args, "contacts", False), getattr(args, "limits", False)
-    nsys, T = ORACLE_SAMPLE
+    nsys, T = _oracle_sample_size(args.config)
     what = (f"{nsys} systems x {T} steps of the same workload, repeated for {budget_s:.0f} s "
             f"(FP64 CRBA+RNEA forward, per-step recompute + reverse-mode step adjoint)")
     if threads == 1:
@@ -565,27 +756,70 @@ def memory_sweep(args):
                           "bytes_per_step_per_system": slope / a["n_systems"]}))
 
 
+def launch_ranks(n: int, fn, fn_args=(), backend_env=None, port=None):
+    """Run fn(*fn_args) in n spawned processes, one per rank, with the
+    torch.distributed environment a launcher would give them (RANK, LOCAL_RANK,
+    WORLD_SIZE, MASTER_ADDR = 127.0.0.1, MASTER_PORT).  Returns the exit codes.
+    Spawn, never fork: a parent that touched CUDA cannot fork children that use it."""
+    import multiprocessing as mp
+    import socket
+    if port is None:
+        with socket.socket() as sk:
+            sk.bind(("127.0.0.1", 0))
+            port = sk.getsockname()[1]
+    ctx = mp.get_context("spawn")
+    procs = []
+    for r in range(n):
+        env = {"RANK": str(r), "LOCAL_RANK": str(r), "WORLD_SIZE": str(n), "LOCAL_WORLD_SIZE": str(n),
+               "MASTER_ADDR": "127.0.0.1", "MASTER_PORT": str(port), **(backend_env or {})}
+        p = ctx.Process(target=_rank_entry, args=(env, fn, fn_args))
+        p.start()
+        procs.append(p)
+    for p in procs:
+        p.join()
+    return [p.exitcode for p in procs]
+
+
+def _rank_entry(env, fn, fn_args):
+    os.environ.update(env)
+    fn(*fn_args)
+
+
+def _rank_bench(args):
+    line = run_ours(args)
+    if line is not None:
+        print(json.dumps(line), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--config", type=int, default=2)
+    ap.add_argument("--config", type=int, default=4,
+                    help="workload 1..5 (default 4: 16384 uneven trees, T = 5000, the largest single-GPU one)")
     ap.add_argument("--precision", default="fp32", choices=["fp64", "fp32", "fp32_d64"])
     ap.add_argument("--batch", type=int, default=None)
     ap.add_argument("--horizon", type=int, default=None)
     ap.add_argument("--k", type=int, default=1)
+    ap.add_argument("--k-sweep", default=None,
+                    help="also time one step at each of these checkpoint intervals (default 10,100 for --config 4)")
     ap.add_argument("--block", type=int, default=0)
     ap.add_argument("--persistent", action="store_true")
     ap.add_argument("--autotune", action="store_true")
-    ap.add_argument("--tape", default="auto", choices=["auto", "global", "shared", "pipelined", "one_warp"])
+    ap.add_argument("--tape", default="auto",
+                    choices=["auto", "global", "shared", "pipelined", "one_warp", "aligned"])
     ap.add_argument("--state-accumulation", default="fp32", choices=["fp32", "fp64"],
                     help="running-state sums of the fp32_d64 precision (fp64: summed in FP64, stored FP32)")
     ap.add_argument("--replay", default="segment", choices=["segment", "quadratic"])
     ap.add_argument("--no-cpu-baseline", dest="cpu_baseline", action="store_false")
     ap.add_argument("--no-plain", dest="plain", action="store_false")
+    ap.add_argument("--plain-systems", type=int, default=8,
+                    help="systems timed one per launch for the per-system comparison")
     ap.add_argument("--no-e2e", dest="e2e", action="store_false")
+    ap.add_argument("--no-grad-check", dest="grad_check", action="store_false",
+                    help="skip the per-output error against the FP64 path on sampled systems")
     ap.add_argument("--graph", action="store_true", help="replay the step as one CUDA graph")
     ap.add_argument("--contacts", action=argparse.BooleanOptionalAction, default=None,
                     help="quadruped with foot contact spheres, the contact solve running every step "
@@ -596,9 +830,19 @@ def main():
     args = ap.parse_args()
     if args.contacts is None:
         args.contacts = args.config == 3
+    if args.k_sweep is None:
+        args.k_sweep = "10,100" if args.config == 4 and args.k == 1 else ""
     args.warmup = max(args.warmup, 3)
     if args.memory_sweep:
         memory_sweep(args)
+        return
+    if args.impl == "ours" and args.gpus > 1 and "WORLD_SIZE" not in os.environ:
+        import torch
+        if torch.cuda.device_count() < args.gpus:
+            raise SystemExit(f"--gpus {args.gpus}: only {torch.cuda.device_count()} CUDA device(s) visible")
+        codes = launch_ranks(args.gpus, _rank_bench, (args,))
+        if any(codes):
+            raise SystemExit(f"a rank failed: exit codes {codes}")
         return
     line = run_reference(args) if args.impl == "reference" else run_ours(args)
     if line is not None:

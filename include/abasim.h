@@ -268,8 +268,11 @@ int sim_set_launch(sim_handle* h, int32_t threads, int32_t schedule);
  * the articulated inertias translates them from child to parent instead of
  * rotating and translating them (each body's inertia is rotated into world axes
  * once per step, off that serial chain).  Tape and adjoint record in shared
- * memory when a block's tiles fit, else in the handle's global scratch.  AUTO
- * picks these kernels for such models; forcing them on another model fails with
+ * memory when a block's tiles fit, else in the handle's global scratch (whose
+ * lines each pass prefetches two links ahead).  AUTO picks these kernels for such
+ * models, except where the pipelined kernels apply (serial chains short enough
+ * for their on-chip tapes) and where a system's state and input streams exceed a
+ * block's shared memory; forcing them on another model fails with
  * SIM_EUNSUPPORTED.  The FP64 state accumulation of SIM_FP32_D64 rollouts is not
  * available on them (AUTO then takes the one-warp kernels). */
 #define SIM_TAPE_ALIGNED 5

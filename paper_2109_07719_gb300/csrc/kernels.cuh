@@ -927,10 +927,24 @@ int choose_w(sim_handle* h, K k_on, K k_off, bool bwd, bool* onchip, size_t* byt
 }
 
 // The world-aligned path applies to models of revolute joints without contact
-// spheres or limits, under SIM_TAPE_AUTO or SIM_TAPE_ALIGNED.
-inline bool use_aligned(const sim_handle* h, bool rollout) {
+// spheres or limits whose state and input streams fit a block's shared memory,
+// under SIM_TAPE_ALIGNED, or under SIM_TAPE_AUTO unless the pipelined two-warp
+// kernels apply (serial chains short enough for their on-chip tapes, where they
+// run faster).
+template <class T>
+bool use_aligned(const sim_handle* h, bool rollout, int k) {
   if (!h->all_revolute || (rollout && h->state64)) return false;
-  return h->tape_space == SIM_TAPE_AUTO || h->tape_space == SIM_TAPE_ALIGNED;
+  if (h->tape_space != SIM_TAPE_AUTO && h->tape_space != SIM_TAPE_ALIGNED) return false;
+  int limit = 0;
+  if (cudaDeviceGetAttribute(&limit, cudaDevAttrMaxSharedMemoryPerBlockOptin, h->device) != cudaSuccess) return false;
+  const int nx = h->nq_max + h->nv_max;
+  const size_t streams = (size_t)(h->block / LANES) * w_smem_per_tile(h->maxL, nx, h->nv_max, !rollout, false) * LANES *
+                         sizeof(T);
+  if (streams > (size_t)limit) return false;
+  if (h->tape_space == SIM_TAPE_ALIGNED || !h->all_chains) return true;
+  if (rollout) return !(h->maxL <= PIPE_MAX_LINKS);
+  return !(sizeof(T) == 4 && k == 1 &&
+           (size_t)pipe_smem_per_tile(h->maxL, nx, h->nv_max) * LANES * sizeof(T) <= (size_t)limit);
 }
 
 template <class T, class DT>
@@ -985,10 +999,11 @@ int launch_wbackward(sim_handle* h, const void* ckpt, const void* tau, int64_t T
 template <class T, class DT>
 int launch_rollout(sim_handle* h, const void* q0, const void* qd0, const void* tau, int64_t T_,
                    int k, void* ckpt, void* qT, void* qdT, void* traj, void* stream) {
-  if (use_aligned(h, true)) return launch_wrollout<T, DT>(h, q0, qd0, tau, T_, k, ckpt, qT, qdT, traj, stream);
+  if (use_aligned<T>(h, true, k)) return launch_wrollout<T, DT>(h, q0, qd0, tau, T_, k, ckpt, qT, qdT, traj, stream);
   if (h->tape_space == SIM_TAPE_ALIGNED)
     return fail(h, SIM_EUNSUPPORTED,
-                "the world-aligned kernels need revolute joints only, no contact spheres or limits, and FP32 state sums");
+                "the world-aligned kernels need revolute joints only, no contact spheres or limits, FP32 state sums "
+                "and a state that fits a block's shared memory");
   DevModel<T> m = dev_model<T>(h);
   size_t shm = 0;
   int st = ST_GLOBAL;
@@ -1043,10 +1058,11 @@ template <class T, class DT>
 int launch_backward(sim_handle* h, const void* ckpt, const void* tau, int64_t T_, int k,
                     const void* gqT, const void* gqdT, const void* gtraj, void* gq0, void* gqd0,
                     void* gtau, void* gmass, void* work, void* stream) {
-  if (use_aligned(h, false))
+  if (use_aligned<T>(h, false, k))
     return launch_wbackward<T, DT>(h, ckpt, tau, T_, k, gqT, gqdT, gtraj, gq0, gqd0, gtau, gmass, work, stream);
   if (h->tape_space == SIM_TAPE_ALIGNED)
-    return fail(h, SIM_EUNSUPPORTED, "the world-aligned kernels need revolute joints only and no contact spheres or limits");
+    return fail(h, SIM_EUNSUPPORTED, "the world-aligned kernels need revolute joints only, no contact spheres or "
+                                     "limits, and a state that fits a block's shared memory");
   DevModel<T> m = dev_model<T>(h);
   size_t shm = 0;
   int st = ST_GLOBAL;

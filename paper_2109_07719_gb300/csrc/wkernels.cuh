@@ -77,7 +77,7 @@ __device__ __forceinline__ WSys<T> wsys_of(const DevModel<T>& m, int slot) {
     return WSys<T>{sp, t.meta, (T*)t.tape, (T*)t.adj, nl, MS, NPRM_W};
   }
   return WSys<T>{gprm, gmeta, m.tape + tile * L * NWT * LANES + lane, m.adj + tile * L * NWA * LANES + lane, nl, 1,
-                 NPRM};
+                 NPRM, true};
 }
 
 template <class T, class DT, bool ONCHIP>

@@ -42,10 +42,10 @@ namespace abasim {
 // velocity v, velocity-product term c, U, 1/D (hi/lo pair), u, the articulated
 // inertia and bias force after the children's contributions (I^A, p^A; for a link
 // with a child other than link l + 1 also the accumulator of those
-// contributions), a' and qdd, and the joint's sin/cos.
+// contributions), a' and qdd, the joint's sin/cos, and the joint offset d.
 enum : int {
   W_R = 0, W_V = 9, W_C = 15, W_U = 21, W_DI = 27, W_u = 29, W_IA = 30, W_PA = 51, W_AP = 57, W_QDD = 63,
-  W_SC = 64, NWT = 66
+  W_SC = 64, W_D = 66, NWT = 69
 };
 // Per-link adjoint record, [link][field][lane]: from the acceleration pass's
 // adjoint, the adjoints of U, D, u and c; the adjoints of s and d (completed by
@@ -70,11 +70,29 @@ template <class T> struct WSys {
   int nl;
   int mstride = 1;
   int pstride = NPRM;
+  bool gmem = false;  // prm, meta, tape and adj live in global memory: prefetch them
   SD T P(int l, int f) const { return prm[(l * pstride + f) * LANES]; }
   SD int M(int l) const { return meta[l * LANES * mstride]; }
   SD T& tp(int l, int f) const { return tape[(l * NWT + f) * LANES]; }
   SD T& ad(int l, int f) const { return adj[(l * NWA + f) * LANES]; }
 };
+
+// Prefetch into L1 of the cache lines holding fields [f0, f0 + n) of link l of a
+// [link][stride][LANES] global array (a warp's 32 lanes share each line).  The
+// passes run one thread per system through its links in a fixed order and
+// touch the same fields of every link, so they ask for link l +- 2's lines while
+// link l computes: with a global tape, a warp then waits for memory once per pass
+// instead of once per link.
+SD void pf_line(const void* p) {
+#ifdef __CUDA_ARCH__
+  asm volatile("prefetch.global.L1 [%0];" ::"l"(p));
+#endif
+}
+template <class T> SD void pf_fields(const T* base, int stride, int l, int f0, int n) {
+  for (int i = 0; i < n; ++i) pf_line(base + (l * stride + f0 + i) * LANES);
+}
+constexpr int W_PF = 2;  // prefetch distance in links
+template <class T> SD void pf_meta(const WSys<T>& s, int l) { pf_line(s.meta + l * LANES * s.mstride); }
 
 template <class T> SD V3<T> wv3(T* base, int stride, int l, int f) {
   const T* p = base + (l * stride + f) * LANES;
@@ -214,6 +232,10 @@ SD void wstep_forward(const WSys<T>& s, Col<const T> q, Col<const T> qd, Col<con
   M3<T> R_prev = eye3<T>();
   SV<T> v_prev = zeroSV<T>();
   for (int l = 0; l < nl; ++l) {
+    if (s.gmem && l + W_PF < nl) {
+      pf_meta(s, l + W_PF);
+      pf_fields(s.prm, s.pstride, l + W_PF, P_E, 12);
+    }
     const int m = s.M(l);
     const int par = meta_parent(m);
     T sn, cs;
@@ -233,6 +255,7 @@ SD void wstep_forward(const WSys<T>& s, Col<const T> q, Col<const T> qd, Col<con
       const V3<T> d = mul(Rp, V3<T>{s.P(l, P_R), s.P(l, P_R + 1), s.P(l, P_R + 2)});
       R = mmT(Rp, E);
       v = SV<T>{vp.w + vl * col2(R), vp.v - cross(d, vp.w)};
+      wv3(tp, NWT, l, W_D, d);
     }
     wm3(tp, NWT, l, W_R, R);
     wsv(tp, NWT, l, W_V, v);
@@ -252,6 +275,11 @@ SD void wstep_forward(const WSys<T>& s, Col<const T> q, Col<const T> qd, Col<con
   SV<T> cp = zeroSV<T>();
   bool carry = false;
   for (int l = nl - 1; l >= 0; --l) {
+    if (s.gmem && l - W_PF >= 0) {
+      pf_fields(tp, NWT, l - W_PF, W_R, 15);
+      pf_fields(tp, NWT, l - W_PF, W_D, 3);
+      pf_fields(s.prm, s.pstride, l - W_PF, P_M, NPRM_W - P_M);
+    }
     const int m = s.M(l);
     const int par = meta_parent(m), vo = meta_voff(m);
     const M3<T> R = wm3(tp, NWT, l, W_R);
@@ -296,8 +324,7 @@ SD void wstep_forward(const WSys<T>& s, Col<const T> q, Col<const T> qd, Col<con
     if (par >= 0) {
       const SI<T> Ia = minus_scaled_outer<T, DT>(IA, Di, U);
       const SV<T> pa = pA + mul(Ia, c) + (T)((DT)u * Di) * U;
-      const M3<T> Rp = wm3(tp, NWT, par, W_R);
-      const V3<T> d = mul(Rp, V3<T>{s.P(l, P_R), s.P(l, P_R + 1), s.P(l, P_R + 2)});
+      const V3<T> d = wv3(tp, NWT, l, W_D);
       const SI<T> Y = shift(Ia, d);
       const SV<T> pn{pa.w + cross(d, pa.v), pa.v};
       if (par == l - 1) {
@@ -313,8 +340,12 @@ SD void wstep_forward(const WSys<T>& s, Col<const T> q, Col<const T> qd, Col<con
   // outward: accelerations (and the integrator)
   const SV<T> a0{zero3<T>(), -grav};
   SV<T> a_prev = a0;
-  M3<T> Rp_prev = eye3<T>();
   for (int l = 0; l < nl; ++l) {
+    if (s.gmem && l + W_PF < nl) {
+      pf_fields(tp, NWT, l + W_PF, W_R, 9);
+      pf_fields(tp, NWT, l + W_PF, W_C, W_IA - W_C);
+      pf_fields(tp, NWT, l + W_PF, W_D, 3);
+    }
     const int m = s.M(l);
     const int par = meta_parent(m);
     const M3<T> R = wm3(tp, NWT, l, W_R);
@@ -327,16 +358,13 @@ SD void wstep_forward(const WSys<T>& s, Col<const T> q, Col<const T> qd, Col<con
       ap = a0 + c;
     } else {
       SV<T> apar;
-      M3<T> Rp;
       if (par == l - 1) {
         apar = a_prev;
-        Rp = Rp_prev;
       } else {
-        Rp = wm3(tp, NWT, par, W_R);
         apar = wsv(tp, NWT, par, W_AP);
-        apar.w += s.tp(par, W_QDD) * col2(Rp);
+        apar.w += s.tp(par, W_QDD) * col2(wm3(tp, NWT, par, W_R));
       }
-      const V3<T> d = mul(Rp, V3<T>{s.P(l, P_R), s.P(l, P_R + 1), s.P(l, P_R + 2)});
+      const V3<T> d = wv3(tp, NWT, l, W_D);
       ap = SV<T>{apar.w + c.w, apar.v - cross(d, apar.w) + c.v};
     }
     const T qdd = (T)(((DT)u - (DT)dot(U, ap)) * Di);
@@ -354,7 +382,6 @@ SD void wstep_forward(const WSys<T>& s, Col<const T> q, Col<const T> qd, Col<con
       qo[qi] = q1;
     }
     a_prev = a;
-    Rp_prev = R;
   }
 }
 
@@ -379,6 +406,12 @@ SD void wstep_adjoint(const WSys<T>& s, Col<const T> q, Col<const T> qd, Col<T> 
     SV<T> cab = zeroSV<T>();
     bool carry = false;
     for (int l = nl - 1; l >= 0; --l) {
+      if (s.gmem && l - W_PF >= 0) {
+        pf_fields(tp, NWT, l - W_PF, W_R, 9);
+        pf_fields(tp, NWT, l - W_PF, W_U, W_u - W_U);
+        pf_fields(tp, NWT, l - W_PF, W_AP, W_SC - W_AP);
+        pf_fields(tp, NWT, l - W_PF, W_D, 3);
+      }
       const int m = s.M(l);
       const int par = meta_parent(m), qi = meta_qoff(m), vi = meta_voff(m);
       T qddb;
@@ -411,10 +444,9 @@ SD void wstep_adjoint(const WSys<T>& s, Col<const T> q, Col<const T> qd, Col<T> 
       wv3(ad, NWA, l, WA_S, qdd * ab.w);
       V3<T> db = zero3<T>();
       if (par >= 0) {
-        const M3<T> Rp = wm3(tp, NWT, par, W_R);
-        const V3<T> d = mul(Rp, V3<T>{s.P(l, P_R), s.P(l, P_R + 1), s.P(l, P_R + 2)});
+        const V3<T> d = wv3(tp, NWT, l, W_D);
         SV<T> apar = wsv(tp, NWT, par, W_AP);
-        apar.w += s.tp(par, W_QDD) * col2(Rp);
+        apar.w += s.tp(par, W_QDD) * col2(wm3(tp, NWT, par, W_R));
         const SV<T> aparb{apb.w + cross(d, apb.v), apb.v};
         db = cross(apb.v, apar.w);
         if (par == l - 1) {
@@ -433,6 +465,12 @@ SD void wstep_adjoint(const WSys<T>& s, Col<const T> q, Col<const T> qd, Col<T> 
     SI<T> cIAb = zeroSI<T>();
     SV<T> cpAb = zeroSV<T>();
     for (int l = 0; l < nl; ++l) {
+      if (s.gmem && l + W_PF < nl) {
+        pf_fields(tp, NWT, l + W_PF, W_R, W_AP - W_R);
+        pf_fields(tp, NWT, l + W_PF, W_D, 3);
+        pf_fields(ad, NWA, l + W_PF, WA_U, WA_ACC - WA_U);
+        pf_fields(s.prm, s.pstride, l + W_PF, P_M, NPRM_W - P_M);
+      }
       const int m = s.M(l);
       const int par = meta_parent(m), vi = meta_voff(m);
       const bool tc = meta_treechild(m);
@@ -458,8 +496,7 @@ SD void wstep_adjoint(const WSys<T>& s, Col<const T> q, Col<const T> qd, Col<T> 
         const SV<T> pAbp = par == l - 1 ? cpAb : wsv(ad, NWA, par, WA_PAB);
         const SI<T> Ia = minus_scaled_outer<T, DT>(IA, Di, U);
         const SV<T> pa = pA + mul(Ia, c) + (T)((DT)u * Di) * U;
-        const M3<T> Rp = wm3(tp, NWT, par, W_R);
-        const V3<T> d = mul(Rp, V3<T>{s.P(l, P_R), s.P(l, P_R + 1), s.P(l, P_R + 2)});
+        const V3<T> d = wv3(tp, NWT, l, W_D);
         SI<T> Iab = zeroSI<T>();
         shift_adj(Ia, d, IAbp, Iab, db);
         const SV<T> pab{pAbp.w, pAbp.v + cross(pAbp.w, d)};
@@ -539,6 +576,13 @@ SD void wstep_adjoint(const WSys<T>& s, Col<const T> q, Col<const T> qd, Col<T> 
     M3<T> cRb = zeroM3<T>();
     bool carry = false;
     for (int l = nl - 1; l >= 0; --l) {
+      if (s.gmem && l - W_PF >= 0) {
+        pf_fields(tp, NWT, l - W_PF, W_R, 15);
+        pf_fields(tp, NWT, l - W_PF, W_IA, 15);
+        pf_fields(tp, NWT, l - W_PF, W_SC, 5);
+        pf_fields(ad, NWA, l - W_PF, WA_S, 6);
+        pf_fields(s.prm, s.pstride, l - W_PF, P_E, 12);
+      }
       const int m = s.M(l);
       const int par = meta_parent(m), qi = meta_qoff(m), vi = meta_voff(m);
       SV<T> vb = wsv(tp, NWT, l, W_IA);
@@ -571,7 +615,7 @@ SD void wstep_adjoint(const WSys<T>& s, Col<const T> q, Col<const T> qd, Col<T> 
         const M3<T> Rp = wm3(tp, NWT, par, W_R);
         const SV<T> vp = wsv(tp, NWT, par, W_V);
         const V3<T> rt{s.P(l, P_R), s.P(l, P_R + 1), s.P(l, P_R + 2)};
-        const V3<T> d = mul(Rp, rt);
+        const V3<T> d = wv3(tp, NWT, l, W_D);
         const SV<T> vpb{vb.w + cross(d, vb.v), vb.v};
         db += cross(vb.v, vp.w);
         // R = R_p E^T, d = R_p r

@@ -54,3 +54,18 @@ def test_two_rank_aggregation_and_disjoint_batches():
 def test_single_process_aggregation_is_identity():
     import bench
     assert bench.aggregate(3.5, 42) == (3.5, 42)
+
+
+def test_bench_launches_its_own_ranks(tmp_path):
+    """bench.py --gpus N without an external launcher starts N spawned ranks with
+    the launcher's environment (here two gloo ranks on the CPU): every rank joins
+    the process group, sees its own RANK / LOCAL_RANK and the loopback master."""
+    import json
+    import bench
+    from tests._rank_probe import gloo_rank
+    codes = bench.launch_ranks(2, gloo_rank, (str(tmp_path),))
+    assert codes == [0, 0]
+    seen = [json.load(open(tmp_path / f"rank{r}.json")) for r in range(2)]
+    for r, d in enumerate(seen):
+        assert d == {"rank": r, "world": 2, "sum": 3.0, "env_rank": str(r), "local_rank": str(r),
+                     "master": "127.0.0.1"}
