@@ -169,7 +169,7 @@ def run_ours(args):
     m = work.model
     T, k = work.T, args.k
     free0 = torch.cuda.mem_get_info()[0]
-    sim = Simulator(m, precision=args.precision)
+    sim = Simulator(m, precision=args.precision, keep_order=args.keep_order)
     handle_bytes = free0 - torch.cuda.mem_get_info()[0]
     sim.set_tape_space(args.tape)
     sim.set_replay(args.replay)
@@ -285,6 +285,7 @@ def run_ours(args):
                    "precision": args.precision, "l2": "flushed between steps (256 MB write)",
                    "parallelism": f"replicas x{ws}" if ws > 1 else "single GPU",
                    "block": sim.launch[0], "schedule": "persistent" if sim.launch[1] else "grid",
+                   "slot_order": "system" if args.keep_order else "link count",
                    "tape": args.tape, "replay": args.replay, "state_accumulation": args.state_accumulation,
                    "storage": {"rollout": storage[0], "adjoint": storage[1]},
                    "cuda_graph": bool(args.graph), "contacts": bool(args.contacts),
@@ -315,7 +316,7 @@ def run_ours(args):
         "nonfinite_ids": [int(i) for i in np.flatnonzero(np.asarray(flags) != 0)[:16]],
     }
     if args.plain:
-        pl = plain_per_system(work, args, k, n_sys=args.plain_systems)
+        pl = plain_per_system(work, args, k, n_sys=args.plain_systems, tau_dev=tau)
         line["plain_per_system"] = pl
         line["vs_plain_per_system"] = value / pl["value"]
     if args.cpu_baseline:
@@ -419,7 +420,7 @@ def precision_error(sim, work, args, outs, ck, tau_dev, n_sample=8):
                                      max(per["gq0"], per["gqd0"], per["gtau"], per["gmass"]) <= tol[1])}
 
 
-def plain_per_system(work, args, k, n_sys=64):
+def plain_per_system(work, args, k, n_sys=64, tau_dev=None):
     """The same kernels with one system per launch (a 1-system handle each), systems
     run one after another: the per-system GPU version the batched path is compared
     with.  n_sys systems are timed and the rate is per env-step (extrapolation to the
@@ -429,19 +430,19 @@ def plain_per_system(work, args, k, n_sys=64):
     from paper_2109_07719_gb300 import Simulator
     m = work.model
     T = work.T
-    sims, bufs = [], []
+    sims, bufs, taus = [], [], []
+    if tau_dev is None:
+        tau_dev = work.tau(device="cuda", dtype=torch.float64 if args.precision == "fp64" else torch.float32)
     for b in range(min(n_sys, m.n_systems)):
         sim = Simulator(m.subset([b]), precision=args.precision)
         if args.state_accumulation != "fp32":
             sim.set_state_accumulation(args.state_accumulation)
         dev, dt = sim.device, sim.dtype
-        q0 = torch.tensor(work.q0[:, b:b + 1], dtype=dt, device=dev).contiguous()
-        qd0 = torch.tensor(work.qd0[:, b:b + 1], dtype=dt, device=dev).contiguous()
+        q0 = torch.tensor(np.ascontiguousarray(work.q0[:sim.nq_max, b:b + 1]), dtype=dt, device=dev).contiguous()
+        qd0 = torch.tensor(np.ascontiguousarray(work.qd0[:sim.nv_max, b:b + 1]), dtype=dt, device=dev).contiguous()
         sims.append(sim)
         bufs.append((q0, qd0))
-    tau_all = work.tau(device=sims[0].device, dtype=sims[0].dtype)
-    taus = [tau_all[:, :, b:b + 1].contiguous() for b in range(len(sims))]
-    del tau_all
+        taus.append(tau_dev[:, :sim.nv_max, b:b + 1].to(dt).contiguous())
 
     def run_all():
         for sim, (q0, qd0), tau in zip(sims, bufs, taus):
@@ -807,6 +808,8 @@ def main():
                     help="also time one step at each of these checkpoint intervals (default 10,100 for --config 4)")
     ap.add_argument("--block", type=int, default=0)
     ap.add_argument("--persistent", action="store_true")
+    ap.add_argument("--keep-order", action="store_true",
+                    help="pack systems in their own order (coalesced streams) instead of by link count")
     ap.add_argument("--autotune", action="store_true")
     ap.add_argument("--tape", default="auto",
                     choices=["auto", "global", "shared", "pipelined", "one_warp", "aligned"])

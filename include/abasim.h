@@ -101,6 +101,14 @@ enum sim_joint { SIM_REVOLUTE = 0, SIM_FREE = 1 };
  * differentiates the solver's iterations exactly (the active set is held fixed).
  * sim_step_jvp returns SIM_EUNSUPPORTED for models with contact spheres or
  * limits. */
+/* Slot packing (how systems are assigned to the kernels' threads).  By default
+ * systems are sorted by link count, longest first, so a warp's 32 systems walk
+ * equally many links.  With SIM_KEEP_SYSTEM_ORDER in flags they keep their own
+ * order: a warp then holds 32 consecutive systems, so the per-step state,
+ * torque, checkpoint and gradient streams (indexed by system) are read and
+ * written as whole cache lines, at the price of warps whose systems walk
+ * different numbers of links.  Results do not depend on the packing. */
+#define SIM_KEEP_SYSTEM_ORDER 1
 #define SIM_MAX_CONTACTS 4
 #define SIM_MAX_LIMITS 12
 #define SIM_MAX_PGS_ITERATIONS 64
@@ -108,7 +116,7 @@ typedef struct sim_model_desc {
   int32_t n_systems;
   int32_t precision;   /* enum sim_precision */
   int32_t integrator;  /* enum sim_integrator */
-  int32_t reserved;
+  int32_t flags;       /* 0 or SIM_KEEP_SYSTEM_ORDER */
   double dt;
   double gravity[3];
   const int32_t* sys_link_offset;

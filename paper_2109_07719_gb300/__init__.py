@@ -37,7 +37,7 @@ class SimError(RuntimeError):
 
 class _Desc(ctypes.Structure):
     _fields_ = [("n_systems", ctypes.c_int32), ("precision", ctypes.c_int32),
-                ("integrator", ctypes.c_int32), ("reserved", ctypes.c_int32),
+                ("integrator", ctypes.c_int32), ("flags", ctypes.c_int32),
                 ("dt", ctypes.c_double), ("gravity", ctypes.c_double * 3),
                 ("sys_link_offset", ctypes.c_void_p), ("parent", ctypes.c_void_p),
                 ("joint_type", ctypes.c_void_p), ("axis", ctypes.c_void_p),
@@ -106,7 +106,7 @@ class Simulator:
     documented in ``include/abasim.h``.
     """
 
-    def __init__(self, model, precision: str = "fp64", integrator: str = "semi"):
+    def __init__(self, model, precision: str = "fp64", integrator: str = "semi", keep_order: bool = False):
         if not torch.cuda.is_available():
             raise SimError("no CUDA device: the simulator runs only on the GPU")
         self.precision = precision
@@ -134,6 +134,7 @@ class Simulator:
         d.n_systems = len(keep["sys_link_offset"]) - 1
         d.precision = PRECISIONS[precision]
         d.integrator = INTEGRATORS[integrator]
+        d.flags = 1 if keep_order else 0          # SIM_KEEP_SYSTEM_ORDER: no sort by link count
         d.dt = float(model.dt)
         for i in range(3):
             d.gravity[i] = float(model.gravity[i])

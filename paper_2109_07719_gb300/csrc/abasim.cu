@@ -96,6 +96,7 @@ int validate(const sim_model_desc* d, std::string& why) {
   if (d->precision < SIM_FP64 || d->precision > SIM_FP32_D64) return bad("unknown precision");
   if (d->integrator != SIM_SEMI_IMPLICIT_EULER && d->integrator != SIM_EXPLICIT_EULER)
     return bad("unknown integrator");
+  if (d->flags & ~SIM_KEEP_SYSTEM_ORDER) return bad("unknown flag bits");
   if (!(d->dt > 0) || !std::isfinite(d->dt)) return bad("dt must be finite and > 0");
   for (int i = 0; i < 3; ++i)
     if (!std::isfinite(d->gravity[i])) return bad("gravity must be finite");
@@ -287,7 +288,8 @@ int sim_create(const sim_model_desc* d, sim_handle** out) {
   // threads walk equally long link loops and the longest work starts first
   std::vector<int> order(B);
   for (int b = 0; b < B; ++b) order[b] = b;
-  std::stable_sort(order.begin(), order.end(), [&](int x, int y) { return nl_sys[x] > nl_sys[y]; });
+  if (!(d->flags & SIM_KEEP_SYSTEM_ORDER))
+    std::stable_sort(order.begin(), order.end(), [&](int x, int y) { return nl_sys[x] > nl_sys[y]; });
   h->h_sys_of_slot = order;
   const int maxL = h->maxL;
   const size_t Bpad = (size_t)((B + LANES - 1) / LANES) * LANES;
@@ -363,6 +365,9 @@ int sim_create(const sim_model_desc* d, sim_handle** out) {
       const int i = d->sys_link_offset[b] + l;
       if (d->joint_type[i] != SIM_REVOLUTE || d->parent[i] != l - 1) h->all_chains = false;
     }
+  // the pipelined kernels take a tile's first slot as its longest system
+  for (int b = 1; b < B && h->all_chains; ++b)
+    if (nl_sys[order[b]] > nl_sys[order[(b / LANES) * LANES]]) h->all_chains = false;
   int rc = h->precision == SIM_FP64 ? upload<double>(h, prm) : upload<float>(h, prm);
   auto alloc = [&](void** p, size_t bytes, const char* what) -> int {
     cudaError_t e = cudaMalloc(p, bytes);

@@ -904,9 +904,21 @@ int choose_w(sim_handle* h, K k_on, K k_off, bool bwd, bool* onchip, size_t* byt
   const int nx = h->nq_max + h->nv_max;
   const size_t need_on = (size_t)tiles * w_smem_per_tile(h->maxL, nx, h->nv_max, bwd, true) * LANES * sizeof(T);
   const size_t need_off = (size_t)tiles * w_smem_per_tile(h->maxL, nx, h->nv_max, bwd, false) * LANES * sizeof(T);
-  if (need_off > (size_t)limit) return fail(h, SIM_EUNSUPPORTED, "state and input streams do not fit in shared memory");
+  if (need_off > (size_t)limit) return fail(h, SIM_EUNSUPPORTED, "the working state does not fit in shared memory");
   e = cudaFuncSetAttribute((const void*)k_off, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)need_off);
   if (e != cudaSuccess) return cuda_fail(h, e, "shared-memory opt-in");
+  {  // the global-tape kernel: shared memory for the blocks an SM holds at once, the rest of the SM's
+     // unified L1 / shared storage as L1 for the tape lines the passes prefetch
+    const long long units = (h->B + h->block - 1) / h->block;
+    const long long per_sm = (units + std::max(1, h->sms) - 1) / std::max(1, h->sms) + 1;
+    int sm_smem = 0;
+    e = cudaDeviceGetAttribute(&sm_smem, cudaDevAttrMaxSharedMemoryPerMultiprocessor, h->device);
+    if (e != cudaSuccess) return cuda_fail(h, e, "shared-memory size query");
+    const long long want = per_sm * ((long long)need_off + 1024);
+    const int pct = (int)std::min(100LL, std::max(1LL, (100 * want + sm_smem - 1) / std::max(1, sm_smem)));
+    e = cudaFuncSetAttribute((const void*)k_off, cudaFuncAttributePreferredSharedMemoryCarveout, pct);
+    if (e != cudaSuccess) return cuda_fail(h, e, "shared-memory carve-out");
+  }
   *onchip = false;
   *bytes = need_off;
   if (need_on > (size_t)limit) return SIM_OK;

@@ -11,16 +11,18 @@
 namespace abasim {
 namespace host {
 
-// Scalars per 32-system tile a world-aligned kernel keeps in shared memory: with
-// ONCHIP the tape (and, for the adjoint, the adjoint record and the per-link
-// mass-gradient sums), the model constants and meta words; always the working
-// state (x for the rollout, the state adjoint for the backward pass) and a double
-// buffer for the per-step inputs (tau, plus x^t for the adjoint) fetched one
-// step ahead.
+// Scalars per 32-system tile a world-aligned kernel keeps in shared memory: the
+// working state (x for the rollout, the state adjoint and the per-link
+// mass-gradient sums for the backward pass); with ONCHIP also the tape (and, for
+// the adjoint, the adjoint record), the model constants and meta words, and a
+// double buffer for the per-step inputs (tau, plus x^t for the adjoint) fetched
+// one step ahead.  Without ONCHIP the inputs are read from global memory with
+// their lines prefetched a step ahead, and the small shared-memory footprint
+// leaves most of the SM's L1 to the prefetched tape lines.
 __host__ __device__ __forceinline__ long long w_smem_per_tile(int maxL, int nx, int nv, bool bwd, bool onchip) {
-  const long long streams = nx + 2LL * (nv + (bwd ? nx : 0)) + (bwd ? maxL : 0);
-  if (!onchip) return streams;
-  return (long long)maxL * (NWT + (bwd ? NWA : 0) + NPRM_W + 1) + streams;
+  const long long state = nx + (bwd ? maxL : 0);
+  if (!onchip) return state;
+  return (long long)maxL * (NWT + (bwd ? NWA : 0) + NPRM_W + 1) + state + 2LL * (nv + (bwd ? nx : 0));
 }
 
 struct WTile {
@@ -91,10 +93,13 @@ __device__ __forceinline__ void wrollout_one(const DevModel<T>& m, int slot, con
   const WSys<T> s = wsys_of<T, false, ONCHIP>(m, slot);
   const WTile st = w_tile<T, false, ONCHIP>(m.maxL, NX, nvm, slot % LANES);
   const Col<T> q{(T*)st.state, LANES}, qd{(T*)st.state + nqm * LANES, LANES};
-  T* sbuf = (T*)st.stream;  // [2][nvm][LANES]: tau, one step ahead
-  if (Tn > 0)
-    for (int d = 0; d < nvm; ++d) cp_async(sbuf + d * LANES, tau + (long long)d * B + b);
-  cp_commit();
+  const int nv = m.nqv[slot] >> 16;
+  T* sbuf = (T*)st.stream;  // ONCHIP: [2][nvm][LANES], tau one step ahead
+  if (ONCHIP) {
+    if (Tn > 0)
+      for (int d = 0; d < nvm; ++d) cp_async(sbuf + d * LANES, tau + (long long)d * B + b);
+    cp_commit();
+  }
   for (int d = 0; d < nqm; ++d) q[d] = q0[d * B + b];
   for (int d = 0; d < nvm; ++d) qd[d] = qd0[d * B + b];
   if (traj) {
@@ -107,13 +112,18 @@ __device__ __forceinline__ void wrollout_one(const DevModel<T>& m, int slot, con
       for (int d = 0; d < nqm; ++d) c[d * B] = q[d];
       for (int d = 0; d < nvm; ++d) c[(nqm + d) * B] = qd[d];
     }
-    if (t + 1 < Tn) {
-      T* nb = sbuf + ((t + 1) & 1) * nvm * LANES;
-      for (int d = 0; d < nvm; ++d) cp_async(nb + d * LANES, tau + ((t + 1) * nvm + d) * B + b);
+    Col<const T> tau_t{tau + t * nvm * B + b, B};
+    if (ONCHIP) {
+      if (t + 1 < Tn) {
+        T* nb = sbuf + ((t + 1) & 1) * nvm * LANES;
+        for (int d = 0; d < nvm; ++d) cp_async(nb + d * LANES, tau + ((t + 1) * nvm + d) * B + b);
+      }
+      cp_commit();
+      cp_wait_all_but_newest();
+      tau_t = Col<const T>{sbuf + (t & 1) * nvm * LANES, LANES};
+    } else if (t + 1 < Tn) {
+      for (int d = 0; d < nv; ++d) pf_line(tau + ((t + 1) * nvm + d) * B + b);
     }
-    cp_commit();
-    cp_wait_all_but_newest();
-    const Col<const T> tau_t{sbuf + (t & 1) * nvm * LANES, LANES};
     wstep_forward<T, DT, false, true>(s, Col<const T>{q.p, LANES}, Col<const T>{qd.p, LANES}, tau_t, g, m.dt,
                                       m.integ, q, qd);
     if (traj) {
@@ -122,7 +132,7 @@ __device__ __forceinline__ void wrollout_one(const DevModel<T>& m, int slot, con
       for (int d = 0; d < nvm; ++d) c[(nqm + d) * B] = qd[d];
     }
   }
-  cp_wait_all();
+  if (ONCHIP) cp_wait_all();
   bool ok = true;
   for (int d = 0; d < nqm; ++d) ok &= finite_t(q[d]);
   for (int d = 0; d < nvm; ++d) ok &= finite_t(qd[d]);
@@ -168,7 +178,7 @@ __device__ __forceinline__ void wbackward_one(const DevModel<T>& m, int slot, co
       for (int d = 0; d < nv; ++d) gqd[d] += gx[(nqm + d) * B];
     }
   };
-  if (k == 1) {
+  if (k == 1 && ONCHIP) {
     const int W = NX + nvm;
     auto fetch = [&](long long t, int buf) {
       T* dst = sbuf + buf * W * LANES;
@@ -186,6 +196,17 @@ __device__ __forceinline__ void wbackward_one(const DevModel<T>& m, int slot, co
                 Col<const T>{xb + NX * LANES, LANES});
     }
     cp_wait_all();
+  } else if (k == 1) {  // inputs straight from global memory, the previous step's lines prefetched
+    for (long long t = Tn - 1; t >= 0; --t) {
+      if (t > 0) {
+        const T* xn = ckpt + (t - 1) * NX * B + b;
+        for (int d = 0; d < nq; ++d) pf_line(xn + d * B);
+        for (int d = 0; d < nv; ++d) pf_line(xn + (nqm + d) * B);
+        for (int d = 0; d < nv; ++d) pf_line(tau + ((t - 1) * nvm + d) * B + b);
+      }
+      const T* x = ckpt + t * NX * B + b;
+      step_back(t, Col<const T>{x, B}, Col<const T>{x + nqm * B, B}, Col<const T>{tau + t * nvm * B + b, B});
+    }
   } else {
     const long long nseg = (Tn + k - 1) / k;
     for (long long seg = nseg - 1; seg >= 0; --seg) {

@@ -52,6 +52,7 @@ def _desc(model, precision=0, integrator=0, **override):
     d.friction = override.get("friction", 0.8)
     d.erp = override.get("erp", 0.2)
     d.pgs_iterations = override.get("pgs_iterations", 20)
+    d.flags = override.get("flags", 0)
     for i in range(3):
         d.gravity[i] = model.gravity[i]
     for k, v in arrs.items():
@@ -145,3 +146,13 @@ def test_null_arguments():
     assert p.lib.sim_set_state_accumulation(None, 1) == -1
     assert p.lib.sim_set_tape_space(None, 4) == -1
     assert p.lib.sim_set_replay(None, 0) == -1
+
+
+def test_unknown_creation_flags_rejected():
+    m = wl.config(4, B=3, T=1).model
+    d, _keep = _desc(m, flags=2)
+    rc, msg = _create(d)
+    assert rc == -1 and "flag" in msg, msg
+    d, _keep = _desc(m, flags=1)          # SIM_KEEP_SYSTEM_ORDER: valid
+    rc, msg = _create(d)
+    assert rc in (0, -2, -3), (rc, msg)

@@ -140,3 +140,19 @@ def test_aligned_refuses_other_models():
         sim.backward(ck, tau, gqT, gqdT)
         torch.cuda.synchronize()
         assert not any(m.startswith("aligned") for m in sim.last_storage())
+
+
+@pytest.mark.parametrize("space", ["aligned", "one_warp"])
+def test_keeping_the_system_order_gives_the_same_results(space):
+    """SIM_KEEP_SYSTEM_ORDER packs 32 consecutive systems per warp (lanes walking
+    different numbers of links) instead of sorting by link count."""
+    from paper_2109_07719_gb300 import Simulator
+    work = wl.config(4, B=150, T=25, dof_hi=30, precision="fp32")
+    a_sim, *x = _setup(work, "fp32")
+    a = _run(a_sim, space, *x)
+    b_sim = Simulator(work.model, precision="fp32", keep_order=True)
+    assert list(b_sim.slot_order()) == list(range(150))
+    b = _run(b_sim, space, *x)
+    for name, u, v in zip(NAMES, a, b):
+        check(name, v.cpu().numpy(), u.cpu().numpy(), 1e-6)
+    assert b_sim.status().sum() == 0
