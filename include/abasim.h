@@ -284,14 +284,22 @@ int sim_set_launch(sim_handle* h, int32_t threads, int32_t schedule);
  * SIM_EUNSUPPORTED.  The FP64 state accumulation of SIM_FP32_D64 rollouts is not
  * available on them (AUTO then takes the one-warp kernels). */
 #define SIM_TAPE_ALIGNED 5
+/* SIM_TAPE_ALIGNED_PIPELINED is SIM_TAPE_ALIGNED with the adjoint (checkpoint
+ * interval 1) on two warps per 32-system tile: one recomputes step t's forward
+ * intermediates (Sec. 3.2, Eq. 7) into one of two tapes while the other runs the
+ * adjoint of step t + 1 from the other tape (on chip when a tile's tapes fit a
+ * block, else in global memory).  AUTO uses this adjoint wherever it uses the
+ * world-aligned kernels with k = 1. */
+#define SIM_TAPE_ALIGNED_PIPELINED 6
 int sim_set_tape_space(sim_handle* h, int32_t space);
 
 /* The storage mode the last sim_rollout (or step) and sim_backward_rollout
  * launches of this handle ran with: 0 tape in global memory, 1 tape global with
  * state and input streams on chip, 2 tape on chip, 3 the pipelined two-warp
  * kernels, 4 the world-aligned kernels with the tape on chip, 5 the world-aligned
- * kernels with the tape in global memory.  Either pointer may be NULL.  No device
- * work. */
+ * kernels with the tape in global memory, 6 / 7 the pipelined world-aligned adjoint
+ * with its tapes on chip / in global memory.  Either pointer may be NULL.  No
+ * device work. */
 int sim_last_storage(const sim_handle* h, int32_t* rollout_mode, int32_t* backward_mode);
 
 /* How sim_backward_rollout rebuilds the states inside a checkpoint segment when

@@ -203,11 +203,14 @@ class Simulator:
         or limits; otherwise the pipelined kernels or shared memory when they fit),
         'global', 'shared' (one warp per tile, tape on chip), 'pipelined' (two warps
         per tile), 'one_warp' (as 'auto' without the pipelined and world-aligned
-        kernels) or 'aligned' (the world-aligned kernels)."""
-        code = {"auto": 0, "global": 1, "shared": 2, "pipelined": 3, "one_warp": 4, "aligned": 5}[space]
+        kernels), 'aligned' (the world-aligned kernels) or 'aligned_pipelined' (the
+        world-aligned kernels with the two-warp pipelined adjoint)."""
+        code = {"auto": 0, "global": 1, "shared": 2, "pipelined": 3, "one_warp": 4, "aligned": 5,
+                "aligned_pipelined": 6}[space]
         self._check(lib.sim_set_tape_space(self._h, code), "sim_set_tape_space")
 
-    STORAGE = ("global", "hybrid", "shared", "pipelined", "aligned_shared", "aligned_global")
+    STORAGE = ("global", "hybrid", "shared", "pipelined", "aligned_shared", "aligned_global",
+               "aligned_pipelined_shared", "aligned_pipelined_global")
 
     def last_storage(self):
         """(rollout, backward) storage modes of the last launches: 'global', 'hybrid',

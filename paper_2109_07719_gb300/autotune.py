@@ -3,8 +3,8 @@
 Times a short forward + adjoint rollout for each candidate -- the kernel family
 (the link-frame one-warp kernels, one lane per system; the link-frame pipelined
 kernels, two warps per 32-system tile, for short serial chains; the
-world-aligned kernels, one lane per system, for revolute models without
-contacts or limits), threads per block (systems per block) and grid or
+world-aligned kernels for revolute models without contacts or limits, one lane
+per system or with the two-warp pipelined adjoint), threads per block (systems per block) and grid or
 persistent schedule -- and keeps the fastest.  A candidate whose kernels the
 model cannot run (the library refuses the launch, or the pipelined space ran
 nothing pipelined) is dropped.  Results are cached in a JSON file keyed by the
@@ -17,11 +17,13 @@ import json
 import os
 
 # (threads per block, persistent schedule, kernel family): 1 the link-frame
-# one-warp kernels, 2 the pipelined kernels (two lanes per system), 3 the
-# world-aligned kernels
+# one-warp kernels, 2 the link-frame pipelined kernels (two lanes per system),
+# 3 the world-aligned kernels, 4 the world-aligned kernels with the pipelined
+# adjoint (two lanes per system in the adjoint)
 CANDIDATES = [(32, False, 1), (64, False, 1), (128, False, 1), (32, True, 1), (64, True, 1), (128, True, 1),
-              (32, False, 2), (32, True, 2), (32, False, 3), (64, False, 3), (32, True, 3), (64, True, 3)]
-TAPE_SPACE = {1: "one_warp", 2: "pipelined", 3: "aligned"}
+              (32, False, 2), (32, True, 2), (32, False, 3), (64, False, 3), (32, True, 3), (64, True, 3),
+              (32, False, 4), (64, False, 4), (32, True, 4), (64, True, 4)]
+TAPE_SPACE = {1: "one_warp", 2: "pipelined", 3: "aligned", 4: "aligned_pipelined"}
 
 
 def cache_path() -> str:

@@ -1,9 +1,9 @@
 """Build the CUDA library in-tree: ``csrc/*.cu`` -> ``_lib/libabasim.so``.
 
-Nineteen translation units (the host side of the C ABI; kernel instantiation
+Twenty-two translation units (the host side of the C ABI; kernel instantiation
 units per precision, direction and adjoint storage mode; the kernels of models
 with contact spheres per precision; the world-aligned kernels per precision and
-direction), compiled by nvcc for sm_103a only, in parallel, then linked; beside it
+direction, and their pipelined adjoint per precision), compiled by nvcc for sm_103a only, in parallel, then linked; beside it
 the FMA-throughput probe ``_lib/fma_peak`` (csrc/fma_peak.cu), an executable that
 measures the FP32 and FP64 peaks the roofline fractions divide by.  Called by ``__graft_entry__.build()`` and, lazily, by
 the binding when the library is missing or older than its sources.
@@ -24,9 +24,9 @@ INCLUDE = os.path.join(os.path.dirname(HERE), "include")
 SOURCES = ["abasim.cu", "inst_fp32_fwd.cu", "inst_fp32_bwd.cu", "inst_fp32_bwd_hybrid.cu",
            "inst_fp32_bwd_smem.cu", "inst_mixed_fwd.cu", "inst_mixed_bwd.cu", "inst_mixed_bwd_hybrid.cu",
            "inst_mixed_bwd_smem.cu", "inst_fp64.cu", "inst_fp32_contact.cu", "inst_mixed_contact.cu",
-           "inst_fp64_contact.cu", "inst_w_fp32_fwd.cu", "inst_w_fp32_bwd.cu", "inst_w_mixed_fwd.cu", "inst_w_mixed_bwd.cu", "inst_w_fp64_fwd.cu", "inst_w_fp64_bwd.cu"]
+           "inst_fp64_contact.cu", "inst_w_fp32_fwd.cu", "inst_w_fp32_bwd.cu", "inst_w_mixed_fwd.cu", "inst_w_mixed_bwd.cu", "inst_w_fp64_fwd.cu", "inst_w_fp64_bwd.cu", "inst_wp_fp32.cu", "inst_wp_mixed.cu", "inst_wp_fp64.cu"]
 DEPS = SOURCES + ["fma_peak.cu", "aba_step.cuh", "contact.cuh", "spatial.cuh", "dual.cuh", "kernels.cuh", "handle.h",
-                  "wstep.cuh", "wkernels.cuh"]
+                  "wstep.cuh", "wkernels.cuh", "wpipe.cuh"]
 
 NVCC_FLAGS = ["-gencode", "arch=compute_103a,code=sm_103a", "-lineinfo", "-O3", "-std=c++17",
               "-Xcompiler", "-fPIC", "-diag-suppress", "177"]

@@ -14,6 +14,7 @@
 
 #include "contact.cuh"
 #include "handle.h"
+#include "wstep.cuh"
 
 using namespace abasim;
 using namespace abasim::host;
@@ -388,6 +389,8 @@ int sim_create(const sim_model_desc* d, sim_handle** out) {
   if (rc == SIM_OK) rc = alloc(&h->tape, (size_t)maxL * NTAPE * Bpad * h->scalar, "tape");
   if (rc == SIM_OK) rc = alloc(&h->adj, (size_t)maxL * NADJ * Bpad * h->scalar, "adjoint tape");
   if (rc == SIM_OK) rc = alloc(&h->gm_acc, (size_t)maxL * B * h->scalar, "mass-gradient buffer");
+  if (rc == SIM_OK && h->all_revolute)
+    rc = alloc(&h->wtape2, (size_t)maxL * NWT * Bpad * h->scalar, "second world-aligned tape");
   if (rc == SIM_OK) rc = alloc((void**)&h->status, B * sizeof(int), "status");
   if (rc == SIM_OK) rc = alloc((void**)&h->sys_of_slot, B * sizeof(int), "slot order");
   if (rc == SIM_OK) rc = put(h->sys_of_slot, order.data(), B * sizeof(int));
@@ -415,7 +418,7 @@ int sim_create(const sim_model_desc* d, sim_handle** out) {
 void sim_destroy(sim_handle* h) {
   if (!h) return;
   void* ptrs[] = {h->prm, h->meta, h->nl, h->nqv, h->tape, h->adj, h->gm_acc, h->link_slot,
-                  h->status, h->sys_of_slot, h->counter, h->ctape, h->csys, h->x64};
+                  h->status, h->sys_of_slot, h->counter, h->ctape, h->csys, h->x64, h->wtape2};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   delete h;
@@ -558,7 +561,8 @@ int sim_set_launch(sim_handle* h, int32_t threads, int32_t schedule) {
 int sim_set_tape_space(sim_handle* h, int32_t space) {
   if (!h) return SIM_EINVAL;
   if (space != SIM_TAPE_AUTO && space != SIM_TAPE_GLOBAL && space != SIM_TAPE_SHARED &&
-      space != SIM_TAPE_PIPELINED && space != SIM_TAPE_ONE_WARP && space != SIM_TAPE_ALIGNED)
+      space != SIM_TAPE_PIPELINED && space != SIM_TAPE_ONE_WARP && space != SIM_TAPE_ALIGNED &&
+      space != SIM_TAPE_ALIGNED_PIPELINED)
     return fail(h, SIM_EINVAL, "unknown tape space");
   h->tape_space = space;
   return SIM_OK;

@@ -30,6 +30,7 @@ struct sim_handle {
   int* nqv = nullptr;        // [B]  nq | nv << 16
   void* tape = nullptr;      // [maxL][NTAPE][B] scalar
   void* adj = nullptr;       // [maxL][NADJ][B] scalar
+  void* wtape2 = nullptr;    // [maxL][NWT][B] scalar: the pipelined world-aligned adjoint's second tape
   void* gm_acc = nullptr;    // [maxL][B] scalar
   int* link_slot = nullptr;  // [L_total] -> l * B + slot
   int* status = nullptr;     // [B] by system

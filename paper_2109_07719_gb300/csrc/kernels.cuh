@@ -741,6 +741,14 @@ k_rollout_pipe(DevModel<T> m, const T* __restrict__ q0, const T* __restrict__ qd
   }
 }
 
+}  // namespace host
+}  // namespace abasim
+
+#include "wpipe.cuh"
+
+namespace abasim {
+namespace host {
+
 template <class T>
 using BackwardKernel = void (*)(DevModel<T>, const T*, const T*, long long, int, const T*, const T*, const T*,
                                 T*, T*, T*, T*, T*);
@@ -765,6 +773,8 @@ template <class T, class DT>
 RolloutKernel<T> wrollout_kernel(bool onchip);
 template <class T, class DT>
 BackwardKernel<T> wbackward_kernel(bool onchip);
+template <class T, class DT>
+BackwardKernel<T> wbackward_pipe_kernel(bool onchip);
 
 // One step with tangents: the state, torque and tape are dual numbers staged in
 // the caller's workspace [tile][...][lane]; model constants stay plain.
@@ -946,14 +956,16 @@ int choose_w(sim_handle* h, K k_on, K k_off, bool bwd, bool* onchip, size_t* byt
 template <class T>
 bool use_aligned(const sim_handle* h, bool rollout, int k) {
   if (!h->all_revolute || (rollout && h->state64)) return false;
-  if (h->tape_space != SIM_TAPE_AUTO && h->tape_space != SIM_TAPE_ALIGNED) return false;
+  if (h->tape_space != SIM_TAPE_AUTO && h->tape_space != SIM_TAPE_ALIGNED &&
+      h->tape_space != SIM_TAPE_ALIGNED_PIPELINED)
+    return false;
   int limit = 0;
   if (cudaDeviceGetAttribute(&limit, cudaDevAttrMaxSharedMemoryPerBlockOptin, h->device) != cudaSuccess) return false;
   const int nx = h->nq_max + h->nv_max;
   const size_t streams = (size_t)(h->block / LANES) * w_smem_per_tile(h->maxL, nx, h->nv_max, !rollout, false) * LANES *
                          sizeof(T);
   if (streams > (size_t)limit) return false;
-  if (h->tape_space == SIM_TAPE_ALIGNED || !h->all_chains) return true;
+  if (h->tape_space != SIM_TAPE_AUTO || !h->all_chains) return true;
   if (rollout) return !(h->maxL <= PIPE_MAX_LINKS);
   return !(sizeof(T) == 4 && k == 1 &&
            (size_t)pipe_smem_per_tile(h->maxL, nx, h->nv_max) * LANES * sizeof(T) <= (size_t)limit);
@@ -979,11 +991,54 @@ int launch_wrollout(sim_handle* h, const void* q0, const void* qd0, const void* 
   return e == cudaSuccess ? SIM_OK : cuda_fail(h, e, "rollout launch");
 }
 
+// The pipelined world-aligned adjoint (two warps per 32-system tile, k = 1):
+// tapes on chip when one tile's fit a block, else in global memory.
+template <class T, class DT>
+int launch_wbackward_pipe(sim_handle* h, const void* ckpt, const void* tau, int64_t T_, const void* gqT,
+                          const void* gqdT, const void* gtraj, void* gq0, void* gqd0, void* gtau, void* gmass,
+                          void* stream) {
+  DevModel<T> m = dev_model<T>(h);
+  int limit = 0;
+  cudaError_t e = cudaDeviceGetAttribute(&limit, cudaDevAttrMaxSharedMemoryPerBlockOptin, h->device);
+  if (e != cudaSuccess) return cuda_fail(h, e, "shared-memory limit query");
+  const int nx = h->nq_max + h->nv_max;
+  const size_t need_on = (size_t)wpipe_smem_per_tile(h->maxL, nx, h->nv_max, true) * LANES * sizeof(T);
+  const size_t need_off = (size_t)wpipe_smem_per_tile(h->maxL, nx, h->nv_max, false) * LANES * sizeof(T);
+  const bool onchip = need_on <= (size_t)limit;
+  if (!onchip && !h->wtape2) return fail(h, SIM_EUNSUPPORTED, "no second tape for the pipelined adjoint");
+  const size_t shm = onchip ? need_on : need_off;
+  const BackwardKernel<T> kern = wbackward_pipe_kernel<T, DT>(onchip);
+  e = cudaFuncSetAttribute((const void*)kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shm);
+  if (e != cudaSuccess) return cuda_fail(h, e, "shared-memory opt-in");
+  if (!onchip) {  // leave most of the SM's unified storage to L1 for the prefetched tape lines
+    e = cudaFuncSetAttribute((const void*)kern, cudaFuncAttributePreferredSharedMemoryCarveout, 10);
+    if (e != cudaSuccess) return cuda_fail(h, e, "shared-memory carve-out");
+  }
+  h->last_storage_bwd = onchip ? 6 : 7;
+  int grid = 0;
+  int rc = launch_shape(h, kern, &grid, &m.persistent, shm, stream, 2 * LANES, LANES);
+  if (rc != SIM_OK) return rc;
+  kern<<<grid, 2 * LANES, shm, S(stream)>>>(m, (const T*)ckpt, (const T*)tau, (long long)T_, 1, (const T*)gqT,
+                                            (const T*)gqdT, (const T*)gtraj, (T*)gq0, (T*)gqd0, (T*)gtau,
+                                            (T*)h->gm_acc, (T*)h->wtape2);
+  e = cudaGetLastError();
+  if (e != cudaSuccess) return cuda_fail(h, e, "backward launch");
+  if (gmass) {
+    k_gather_mass_grad<T><<<(h->L_total + 255) / 256, 256, 0, S(stream)>>>((const T*)h->gm_acc, h->link_slot,
+                                                                          h->L_total, (T*)gmass);
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return cuda_fail(h, e, "mass-gradient launch");
+  }
+  return SIM_OK;
+}
+
 template <class T, class DT>
 int launch_wbackward(sim_handle* h, const void* ckpt, const void* tau, int64_t T_, int k, const void* gqT,
                      const void* gqdT, const void* gtraj, void* gq0, void* gqd0, void* gtau, void* gmass, void* work,
                      void* stream) {
   DevModel<T> m = dev_model<T>(h);
+  if (k == 1 && T_ > 0 && h->tape_space != SIM_TAPE_ALIGNED)
+    return launch_wbackward_pipe<T, DT>(h, ckpt, tau, T_, gqT, gqdT, gtraj, gq0, gqd0, gtau, gmass, stream);
   const BackwardKernel<T> k_on = wbackward_kernel<T, DT>(true), k_off = wbackward_kernel<T, DT>(false);
   bool onchip = false;
   size_t shm = 0;
@@ -1012,7 +1067,7 @@ template <class T, class DT>
 int launch_rollout(sim_handle* h, const void* q0, const void* qd0, const void* tau, int64_t T_,
                    int k, void* ckpt, void* qT, void* qdT, void* traj, void* stream) {
   if (use_aligned<T>(h, true, k)) return launch_wrollout<T, DT>(h, q0, qd0, tau, T_, k, ckpt, qT, qdT, traj, stream);
-  if (h->tape_space == SIM_TAPE_ALIGNED)
+  if (h->tape_space == SIM_TAPE_ALIGNED || h->tape_space == SIM_TAPE_ALIGNED_PIPELINED)
     return fail(h, SIM_EUNSUPPORTED,
                 "the world-aligned kernels need revolute joints only, no contact spheres or limits, FP32 state sums "
                 "and a state that fits a block's shared memory");
@@ -1072,7 +1127,7 @@ int launch_backward(sim_handle* h, const void* ckpt, const void* tau, int64_t T_
                     void* gtau, void* gmass, void* work, void* stream) {
   if (use_aligned<T>(h, false, k))
     return launch_wbackward<T, DT>(h, ckpt, tau, T_, k, gqT, gqdT, gtraj, gq0, gqd0, gtau, gmass, work, stream);
-  if (h->tape_space == SIM_TAPE_ALIGNED)
+  if (h->tape_space == SIM_TAPE_ALIGNED || h->tape_space == SIM_TAPE_ALIGNED_PIPELINED)
     return fail(h, SIM_EUNSUPPORTED, "the world-aligned kernels need revolute joints only, no contact spheres or "
                                      "limits, and a state that fits a block's shared memory");
   DevModel<T> m = dev_model<T>(h);

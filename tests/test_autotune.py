@@ -26,11 +26,12 @@ class FakeSim:
     def set_tape_space(self, space="auto"):
         from paper_2109_07719_gb300 import SimError
         self.space = space
-        if (space == "pipelined" and not self.pipelines) or (space == "aligned" and not self.aligns):
+        if (space == "pipelined" and not self.pipelines) or (space.startswith("aligned") and not self.aligns):
             raise SimError(f"{space}: this model cannot run on these kernels")
 
     def last_storage(self):
-        mode = {"pipelined": "pipelined", "aligned": "aligned_shared"}.get(self.space, "shared")
+        mode = {"pipelined": "pipelined", "aligned": "aligned_shared",
+                "aligned_pipelined": "aligned_pipelined_shared"}.get(self.space, "shared")
         return mode, mode
 
 
@@ -46,7 +47,8 @@ def test_autotune_times_candidates_and_caches(tmp_path, monkeypatch):
     sim = FakeSim()
     cost = {(32, False, 1): 3.0, (64, False, 1): 2.0, (128, False, 1): 2.5, (32, True, 1): 1.5,
             (64, True, 1): 4.0, (128, True, 1): 5.0, (32, False, 2): 1.6, (32, True, 2): 1.7,
-            (32, False, 3): 1.8, (64, False, 3): 1.9, (32, True, 3): 2.1, (64, True, 3): 2.2}
+            (32, False, 3): 1.8, (64, False, 3): 1.9, (32, True, 3): 2.1, (64, True, 3): 2.2,
+            (32, False, 4): 1.55, (64, False, 4): 1.65, (32, True, 4): 1.75, (64, True, 4): 1.85}
     seen = []
 
     def timer(s, cand):

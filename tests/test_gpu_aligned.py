@@ -156,3 +156,44 @@ def test_keeping_the_system_order_gives_the_same_results(space):
     for name, u, v in zip(NAMES, a, b):
         check(name, v.cpu().numpy(), u.cpu().numpy(), 1e-6)
     assert b_sim.status().sum() == 0
+
+
+# ---------------------------------------------------------------- pipelined adjoint
+
+@pytest.mark.parametrize("cfg,B,T,precision", [(2, 100, 37, "fp32"), (2, 33, 1, "fp32"), (2, 40, 2, "fp64"),
+                                               (4, 150, 23, "fp32"), (4, 70, 9, "fp32_d64"), (1, 3, 30, "fp64")])
+def test_pipelined_adjoint_matches_one_warp(cfg, B, T, precision):
+    """Two warps per tile (recompute of step t beside the adjoint of step t + 1,
+    tapes on chip for the 7-link chains, in global memory for the trees) against
+    the one-warp world-aligned adjoint: the same formulas, so equal to round-off."""
+    kw = dict(B=B, T=T) if cfg == 1 else dict(B=B, T=T, precision=precision)
+    if cfg == 4:
+        kw["dof_hi"] = 40
+    work = wl.config(cfg, **kw)
+    sim, *x = _setup(work, precision)
+    a = _run(sim, "aligned", *x)
+    assert sim.last_storage()[1].startswith("aligned_") and "pipelined" not in sim.last_storage()[1]
+    b = _run(sim, "aligned_pipelined", *x)
+    assert sim.last_storage()[1].startswith("aligned_pipelined")
+    tol = 1e-12 if precision == "fp64" else 1e-6
+    for name, u, v in zip(NAMES, a, b):
+        check(name, v.cpu().numpy(), u.cpu().numpy(), tol)
+    assert sim.status().sum() == 0
+
+
+def test_pipelined_adjoint_persistent_and_per_step_terms():
+    work = wl.config(4, B=200, T=15, dof_hi=30, precision="fp32")
+    sim, q0, qd0, tau, gqT, gqdT = _setup(work, "fp32")
+    g = torch.Generator().manual_seed(13)
+    gtraj = torch.randn((16, sim.nx, sim.B), generator=g, dtype=torch.float64).float().to(sim.device)
+    outs = []
+    for space, persistent in (("aligned", False), ("aligned_pipelined", False), ("aligned_pipelined", True)):
+        sim.set_tape_space(space)
+        sim.set_launch(32, persistent)
+        qT, qdT, ck, _ = sim.rollout(q0, qd0, tau)
+        outs.append(sim.backward(ck, tau, gqT, gqdT, g_traj=gtraj))
+        torch.cuda.synchronize()
+    for u, v in zip(outs[1], outs[2]):
+        assert torch.equal(u, v)
+    for name, u, v in zip(NAMES[3:], outs[0], outs[1]):
+        check(name, v.cpu().numpy(), u.cpu().numpy(), 1e-6)

@@ -84,7 +84,7 @@ def test_autotune_keeps_results(tmp_path, monkeypatch):
     work, sim, q0, qd0, tau = _setup()
     from paper_2109_07719_gb300 import autotune as at
     best = sim.autotune(q0, qd0, T_probe=4, reps=1)
-    assert best[2] in (1, 3) and best in at.CANDIDATES      # trees: no pipelined kernels
+    assert best[2] in (1, 3, 4) and best in at.CANDIDATES   # trees: not the link-frame pipelined kernels
     out = _run(sim, q0, qd0, tau)
     sim.set_launch(32, False)                               # the same kernels at the default shape
     ref = _run(sim, q0, qd0, tau)
@@ -105,7 +105,8 @@ def test_autotune_lanes_on_chains(tmp_path, monkeypatch):
     best = sim.autotune(q0, qd0, T_probe=4, reps=1)
     out = _run(sim, q0, qd0, tau)
     assert ("pipelined" in sim.last_storage()) == (best[2] == 2)
-    assert sim.last_storage()[0].startswith("aligned") == (best[2] == 3)
+    assert sim.last_storage()[0].startswith("aligned") == (best[2] in (3, 4))
+    assert sim.last_storage()[1].startswith("aligned_pipelined") == (best[2] == 4)
     entry = next(iter(at.load_cache().values()))
     assert any(key.endswith("/pipelined") for key in entry["seconds"])
     assert any(key.endswith("/aligned") for key in entry["seconds"])

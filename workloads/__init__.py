@@ -144,6 +144,21 @@ class Workload:
     precision: str           # "fp64" | "fp32" | "fp32_d64"
     tau_mask: np.ndarray = field(default=None)  # [nv_max, B] 1 where a torque is drawn
 
+    def in_slot_order(self) -> "Workload":
+        """The same systems laid out by link count, longest first (stable), the
+        order in which the library packs systems into warps: a caller that keeps
+        its per-system arrays in this order gives every warp 32 consecutive
+        systems, so state, torque, checkpoint and gradient accesses are whole
+        cache lines.  Torques are drawn afresh for the new order (same
+        distribution); initial states move with their systems."""
+        nl = np.diff(self.model.sys_link_offset)
+        order = np.argsort(-nl, kind="stable")
+        m = self.model.subset(order)
+        m.name = self.model.name
+        return Workload(m, np.ascontiguousarray(self.q0[:, order]), np.ascontiguousarray(self.qd0[:, order]),
+                        self.T, self.tau_sigma, self.seed, self.precision,
+                        None if self.tau_mask is None else np.ascontiguousarray(self.tau_mask[:, order]))
+
     def tau(self, T: int | None = None, device="cpu", dtype=None):
         """Joint torques [T, nv_max, B] drawn N(0, tau_sigma^2) from a seeded torch
         generator on ``device``; entries outside ``tau_mask`` are zero."""
