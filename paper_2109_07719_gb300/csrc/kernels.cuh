@@ -902,6 +902,21 @@ int choose_storage(sim_handle* h, K0 k_global, K1 k_hybrid, K2 k_smem, bool bwd,
   return SIM_OK;
 }
 
+// Shared-memory carve-out (percent of the SM's maximum) that holds every block an
+// SM must run at once for a single wave of `slots_per_block`-system units, plus one,
+// each needing `bytes`: the rest of the SM's unified storage stays L1.
+inline int l1_carveout(const sim_handle* h, int slots_per_block, size_t bytes) {
+  const long long units = (h->B + slots_per_block - 1) / slots_per_block;
+  const long long sms = std::max(1, h->sms);
+  const long long per_sm = (units + sms - 1) / sms + 1;
+  int sm_smem = 0;
+  if (cudaDeviceGetAttribute(&sm_smem, cudaDevAttrMaxSharedMemoryPerMultiprocessor, h->device) != cudaSuccess ||
+      sm_smem <= 0)
+    return 100;
+  const long long want = per_sm * ((long long)bytes + 1024);
+  return (int)std::min(100LL, std::max(1LL, (100 * want + sm_smem - 1) / sm_smem));
+}
+
 // Storage of a world-aligned launch: the tape on chip when a block's tiles fit the
 // per-block opt-in limit and that adds no wave of blocks over the global-tape
 // kernel (whose blocks still keep their state and input streams on chip).
@@ -917,18 +932,11 @@ int choose_w(sim_handle* h, K k_on, K k_off, bool bwd, bool* onchip, size_t* byt
   if (need_off > (size_t)limit) return fail(h, SIM_EUNSUPPORTED, "the working state does not fit in shared memory");
   e = cudaFuncSetAttribute((const void*)k_off, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)need_off);
   if (e != cudaSuccess) return cuda_fail(h, e, "shared-memory opt-in");
-  {  // the global-tape kernel: shared memory for the blocks an SM holds at once, the rest of the SM's
-     // unified L1 / shared storage as L1 for the tape lines the passes prefetch
-    const long long units = (h->B + h->block - 1) / h->block;
-    const long long per_sm = (units + std::max(1, h->sms) - 1) / std::max(1, h->sms) + 1;
-    int sm_smem = 0;
-    e = cudaDeviceGetAttribute(&sm_smem, cudaDevAttrMaxSharedMemoryPerMultiprocessor, h->device);
-    if (e != cudaSuccess) return cuda_fail(h, e, "shared-memory size query");
-    const long long want = per_sm * ((long long)need_off + 1024);
-    const int pct = (int)std::min(100LL, std::max(1LL, (100 * want + sm_smem - 1) / std::max(1, sm_smem)));
-    e = cudaFuncSetAttribute((const void*)k_off, cudaFuncAttributePreferredSharedMemoryCarveout, pct);
-    if (e != cudaSuccess) return cuda_fail(h, e, "shared-memory carve-out");
-  }
+  // the global-tape kernel: shared memory for the blocks an SM holds at once, the rest of the SM's
+  // unified L1 / shared storage as L1 for the tape lines the passes prefetch
+  e = cudaFuncSetAttribute((const void*)k_off, cudaFuncAttributePreferredSharedMemoryCarveout,
+                           l1_carveout(h, h->block, need_off));
+  if (e != cudaSuccess) return cuda_fail(h, e, "shared-memory carve-out");
   *onchip = false;
   *bytes = need_off;
   if (need_on > (size_t)limit) return SIM_OK;
@@ -1010,8 +1018,9 @@ int launch_wbackward_pipe(sim_handle* h, const void* ckpt, const void* tau, int6
   const BackwardKernel<T> kern = wbackward_pipe_kernel<T, DT>(onchip);
   e = cudaFuncSetAttribute((const void*)kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shm);
   if (e != cudaSuccess) return cuda_fail(h, e, "shared-memory opt-in");
-  if (!onchip) {  // leave most of the SM's unified storage to L1 for the prefetched tape lines
-    e = cudaFuncSetAttribute((const void*)kern, cudaFuncAttributePreferredSharedMemoryCarveout, 10);
+  if (!onchip) {  // shared memory for the blocks an SM holds at once, the rest of the SM's storage as L1
+    e = cudaFuncSetAttribute((const void*)kern, cudaFuncAttributePreferredSharedMemoryCarveout,
+                             l1_carveout(h, LANES, shm));
     if (e != cudaSuccess) return cuda_fail(h, e, "shared-memory carve-out");
   }
   h->last_storage_bwd = onchip ? 6 : 7;
