@@ -177,6 +177,8 @@ def run_ours(args):
     handle_bytes = free0 - torch.cuda.mem_get_info()[0]
     sim.set_tape_space(args.tape)
     sim.set_replay(args.replay)
+    if args.prefetch is not None:
+        sim.set_prefetch(args.prefetch)
     if args.state_accumulation != "fp32":
         sim.set_state_accumulation(args.state_accumulation)
     if args.autotune:
@@ -291,7 +293,7 @@ def run_ours(args):
                    "block": sim.launch[0], "schedule": "persistent" if sim.launch[1] else "grid",
                    "slot_order": "system" if args.keep_order else "link count",
                    "batch_layout": "by link count (the packing order)" if args.slot_layout else "as generated",
-                   "tape": args.tape, "replay": args.replay, "state_accumulation": args.state_accumulation,
+                   "tape": args.tape, "replay": args.replay, "prefetch": args.prefetch, "state_accumulation": args.state_accumulation,
                    "storage": {"rollout": storage[0], "adjoint": storage[1]},
                    "cuda_graph": bool(args.graph), "contacts": bool(args.contacts),
                    "joint_limits": bool(args.limits)},
@@ -838,7 +840,9 @@ def main():
                          "streams are whole cache lines (default: on for the uneven trees, --config 4)")
     ap.add_argument("--autotune", action="store_true")
     ap.add_argument("--tape", default="auto",
-                    choices=["auto", "global", "shared", "pipelined", "one_warp", "aligned"])
+                    choices=["auto", "global", "shared", "pipelined", "one_warp", "aligned", "aligned_pipelined"])
+    ap.add_argument("--prefetch", type=int, default=None,
+                    help="links ahead the world-aligned global-tape passes prefetch (library default 2; 0: off)")
     ap.add_argument("--state-accumulation", default="fp32", choices=["fp32", "fp64"],
                     help="running-state sums of the fp32_d64 precision (fp64: summed in FP64, stored FP32)")
     ap.add_argument("--replay", default="segment", choices=["segment", "quadratic"])

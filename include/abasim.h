@@ -302,6 +302,14 @@ int sim_set_tape_space(sim_handle* h, int32_t space);
  * device work. */
 int sim_last_storage(const sim_handle* h, int32_t* rollout_mode, int32_t* backward_mode);
 
+/* Prefetch distance of the world-aligned kernels when their tape is in global
+ * memory: while link l computes, each pass asks for the cache lines of the link
+ * links_ahead further along its walk (and the next step's input lines), so a
+ * warp's tape reads find L1 instead of waiting on L2 / HBM once per link.
+ * 0 switches prefetching off; default 2; at most 16.  A tuning control (the
+ * autotuner may set it); results do not depend on it. */
+int sim_set_prefetch(sim_handle* h, int32_t links_ahead);
+
 /* How sim_backward_rollout rebuilds the states inside a checkpoint segment when
  * k > 1.  SIM_REPLAY_SEGMENT (default): replay the segment once into the caller
  * workspace, then differentiate it backwards (≈ one extra forward step per step).

@@ -68,6 +68,7 @@ _SIGS = {
     "sim_slot_order": (ctypes.c_int, [_P, _P]),
     "sim_set_tape_space": (ctypes.c_int, [_P, ctypes.c_int32]),
     "sim_set_replay": (ctypes.c_int, [_P, ctypes.c_int32]),
+    "sim_set_prefetch": (ctypes.c_int, [_P, ctypes.c_int32]),
     "sim_set_state_accumulation": (ctypes.c_int, [_P, ctypes.c_int32]),
     "sim_jvp_work_bytes": (ctypes.c_size_t, [_P]),
     "sim_step_jvp": (ctypes.c_int, [_P] * 11 + [_P, ctypes.c_size_t, _P]),
@@ -219,6 +220,10 @@ class Simulator:
         f, b = ctypes.c_int32(), ctypes.c_int32()
         self._check(lib.sim_last_storage(self._h, ctypes.byref(f), ctypes.byref(b)), "sim_last_storage")
         return self.STORAGE[f.value], self.STORAGE[b.value]
+
+    def set_prefetch(self, links_ahead: int = 2):
+        """How many links ahead the world-aligned global-tape passes prefetch (0: off)."""
+        self._check(lib.sim_set_prefetch(self._h, int(links_ahead)), "sim_set_prefetch")
 
     def set_replay(self, mode: str = "segment"):
         """k > 1 state rebuild: 'segment' (replay once) or 'quadratic' (from the checkpoint)."""

@@ -575,6 +575,13 @@ int sim_last_storage(const sim_handle* h, int32_t* rollout_mode, int32_t* backwa
   return SIM_OK;
 }
 
+int sim_set_prefetch(sim_handle* h, int32_t links_ahead) {
+  if (!h) return SIM_EINVAL;
+  if (links_ahead < 0 || links_ahead > 16) return fail(h, SIM_EINVAL, "prefetch distance must be in [0, 16]");
+  h->prefetch = links_ahead;
+  return SIM_OK;
+}
+
 int sim_set_replay(sim_handle* h, int32_t mode) {
   if (!h) return SIM_EINVAL;
   if (mode != SIM_REPLAY_SEGMENT && mode != SIM_REPLAY_QUADRATIC) return fail(h, SIM_EINVAL, "unknown replay mode");

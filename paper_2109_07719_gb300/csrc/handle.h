@@ -43,6 +43,7 @@ struct sim_handle {
   int schedule = SIM_SCHED_GRID;
   int tape_space = SIM_TAPE_AUTO;
   int replay = SIM_REPLAY_SEGMENT;
+  int prefetch = 2;          // links ahead the world-aligned global-tape passes prefetch
   int last_storage = 0, last_storage_bwd = 0;
   int sms = 0;
   bool all_chains = false;   // every system a serial chain of revolute joints (the pipelined adjoint)

@@ -38,6 +38,7 @@ template <class T> struct DevModel {
   ContactParams<T> cp;
   double dt64;   // the time step in FP64
   double* x64;   // FP64 running state [nq_max + nv_max][B] of the rollout (null: off; FP32 + FP64 D only)
+  int pf;        // world-aligned kernels with a global tape: prefetch distance in links (0: none)
 };
 
 template <class T> DevModel<T> dev_model(const sim_handle* h) {
@@ -46,7 +47,7 @@ template <class T> DevModel<T> dev_model(const sim_handle* h) {
                      (T)h->g[0], (T)h->g[1], (T)h->g[2], h->integrator, 0, 0,
                      h->replay == SIM_REPLAY_QUADRATIC, (T*)h->ctape, (T*)h->csys,
                      ContactParams<T>{(T)h->friction, (T)h->erp, h->pgs_iterations}, h->dt,
-                     h->state64 ? (double*)h->x64 : nullptr};
+                     h->state64 ? (double*)h->x64 : nullptr, h->prefetch};
 }
 
 extern __shared__ __align__(16) unsigned char g_smem[];

@@ -79,7 +79,7 @@ __device__ __forceinline__ WSys<T> wsys_of(const DevModel<T>& m, int slot) {
     return WSys<T>{sp, t.meta, (T*)t.tape, (T*)t.adj, nl, MS, NPRM_W};
   }
   return WSys<T>{gprm, gmeta, m.tape + tile * L * NWT * LANES + lane, m.adj + tile * L * NWA * LANES + lane, nl, 1,
-                 NPRM, true};
+                 NPRM, m.pf};
 }
 
 template <class T, class DT, bool ONCHIP>
@@ -121,7 +121,7 @@ __device__ __forceinline__ void wrollout_one(const DevModel<T>& m, int slot, con
       cp_commit();
       cp_wait_all_but_newest();
       tau_t = Col<const T>{sbuf + (t & 1) * nvm * LANES, LANES};
-    } else if (t + 1 < Tn) {
+    } else if (t + 1 < Tn && m.pf > 0) {
       for (int d = 0; d < nv; ++d) pf_line(tau + ((t + 1) * nvm + d) * B + b);
     }
     wstep_forward<T, DT, false, true>(s, Col<const T>{q.p, LANES}, Col<const T>{qd.p, LANES}, tau_t, g, m.dt,
@@ -198,7 +198,7 @@ __device__ __forceinline__ void wbackward_one(const DevModel<T>& m, int slot, co
     cp_wait_all();
   } else if (k == 1) {  // inputs straight from global memory, the previous step's lines prefetched
     for (long long t = Tn - 1; t >= 0; --t) {
-      if (t > 0) {
+      if (t > 0 && m.pf > 0) {
         const T* xn = ckpt + (t - 1) * NX * B + b;
         for (int d = 0; d < nq; ++d) pf_line(xn + d * B);
         for (int d = 0; d < nv; ++d) pf_line(xn + (nqm + d) * B);

@@ -80,8 +80,8 @@ k_wbackward_pipe(DevModel<T> m, const T* __restrict__ ckpt, const T* __restrict_
       return (buf ? tape2 : m.tape) + (long long)unit * L * NWT * LANES + lane;
     };
     auto sys_of_buf = [&](int buf) -> WSys<T> {
-      if (ONCHIP) return WSys<T>{s_prm + lane, meta_l, tape_of(buf), s_adj + lane, nl, MS, NPRM_W, false};
-      return WSys<T>{gprm, gmeta, tape_of(buf), m.adj + (long long)unit * L * NWA * LANES + lane, nl, 1, NPRM, true};
+      if (ONCHIP) return WSys<T>{s_prm + lane, meta_l, tape_of(buf), s_adj + lane, nl, MS, NPRM_W, 0};
+      return WSys<T>{gprm, gmeta, tape_of(buf), m.adj + (long long)unit * L * NWA * LANES + lane, nl, 1, NPRM, m.pf};
     };
     // the producer's inputs of step t: x^t and tau^t, fetched one step ahead
     auto fetch = [&](long long t, int buf) {
@@ -114,7 +114,7 @@ k_wbackward_pipe(DevModel<T> m, const T* __restrict__ ckpt, const T* __restrict_
           if (act && t > 0) fetch(t - 1, (int)((t - 1) & 1));
           cp_commit();
           cp_wait_all_but_newest();
-        } else if (act && t > 0) {
+        } else if (act && t > 0 && m.pf > 0) {
           const T* xn = ckpt + (t - 1) * NX * B + b;
           for (int d = 0; d < nq; ++d) pf_line(xn + d * B);
           for (int d = 0; d < nv; ++d) pf_line(xn + (nqm + d) * B);

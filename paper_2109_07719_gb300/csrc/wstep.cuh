@@ -70,7 +70,7 @@ template <class T> struct WSys {
   int nl;
   int mstride = 1;
   int pstride = NPRM;
-  bool gmem = false;  // prm, meta, tape and adj live in global memory: prefetch them
+  int pf = 0;  // prm, meta, tape and adj in global memory: prefetch this many links ahead (0: none)
   SD T P(int l, int f) const { return prm[(l * pstride + f) * LANES]; }
   SD int M(int l) const { return meta[l * LANES * mstride]; }
   SD T& tp(int l, int f) const { return tape[(l * NWT + f) * LANES]; }
@@ -80,9 +80,9 @@ template <class T> struct WSys {
 // Prefetch into L1 of the cache lines holding fields [f0, f0 + n) of link l of a
 // [link][stride][LANES] global array (a warp's 32 lanes share each line).  The
 // passes run one thread per system through its links in a fixed order and
-// touch the same fields of every link, so they ask for link l +- 2's lines while
-// link l computes: with a global tape, a warp then waits for memory once per pass
-// instead of once per link.
+// touch the same fields of every link, so they ask for link l +- pf's lines while
+// link l computes (pf from sim_set_prefetch, 2 by default): with a global tape, a
+// warp then waits for memory once per pass instead of once per link.
 SD void pf_line(const void* p) {
 #ifdef __CUDA_ARCH__
   asm volatile("prefetch.global.L1 [%0];" ::"l"(p));
@@ -91,7 +91,6 @@ SD void pf_line(const void* p) {
 template <class T> SD void pf_fields(const T* base, int stride, int l, int f0, int n) {
   for (int i = 0; i < n; ++i) pf_line(base + (l * stride + f0 + i) * LANES);
 }
-constexpr int W_PF = 2;  // prefetch distance in links
 template <class T> SD void pf_meta(const WSys<T>& s, int l) { pf_line(s.meta + l * LANES * s.mstride); }
 
 template <class T> SD V3<T> wv3(T* base, int stride, int l, int f) {
@@ -232,9 +231,9 @@ SD void wstep_forward(const WSys<T>& s, Col<const T> q, Col<const T> qd, Col<con
   M3<T> R_prev = eye3<T>();
   SV<T> v_prev = zeroSV<T>();
   for (int l = 0; l < nl; ++l) {
-    if (s.gmem && l + W_PF < nl) {
-      pf_meta(s, l + W_PF);
-      pf_fields(s.prm, s.pstride, l + W_PF, P_E, 12);
+    if (s.pf > 0 && l + s.pf < nl) {
+      pf_meta(s, l + s.pf);
+      pf_fields(s.prm, s.pstride, l + s.pf, P_E, 12);
     }
     const int m = s.M(l);
     const int par = meta_parent(m);
@@ -275,10 +274,10 @@ SD void wstep_forward(const WSys<T>& s, Col<const T> q, Col<const T> qd, Col<con
   SV<T> cp = zeroSV<T>();
   bool carry = false;
   for (int l = nl - 1; l >= 0; --l) {
-    if (s.gmem && l - W_PF >= 0) {
-      pf_fields(tp, NWT, l - W_PF, W_R, 15);
-      pf_fields(tp, NWT, l - W_PF, W_D, 3);
-      pf_fields(s.prm, s.pstride, l - W_PF, P_M, NPRM_W - P_M);
+    if (s.pf > 0 && l - s.pf >= 0) {
+      pf_fields(tp, NWT, l - s.pf, W_R, 15);
+      pf_fields(tp, NWT, l - s.pf, W_D, 3);
+      pf_fields(s.prm, s.pstride, l - s.pf, P_M, NPRM_W - P_M);
     }
     const int m = s.M(l);
     const int par = meta_parent(m), vo = meta_voff(m);
@@ -341,10 +340,10 @@ SD void wstep_forward(const WSys<T>& s, Col<const T> q, Col<const T> qd, Col<con
   const SV<T> a0{zero3<T>(), -grav};
   SV<T> a_prev = a0;
   for (int l = 0; l < nl; ++l) {
-    if (s.gmem && l + W_PF < nl) {
-      pf_fields(tp, NWT, l + W_PF, W_R, 9);
-      pf_fields(tp, NWT, l + W_PF, W_C, W_IA - W_C);
-      pf_fields(tp, NWT, l + W_PF, W_D, 3);
+    if (s.pf > 0 && l + s.pf < nl) {
+      pf_fields(tp, NWT, l + s.pf, W_R, 9);
+      pf_fields(tp, NWT, l + s.pf, W_C, W_IA - W_C);
+      pf_fields(tp, NWT, l + s.pf, W_D, 3);
     }
     const int m = s.M(l);
     const int par = meta_parent(m);
@@ -406,11 +405,11 @@ SD void wstep_adjoint(const WSys<T>& s, Col<const T> q, Col<const T> qd, Col<T> 
     SV<T> cab = zeroSV<T>();
     bool carry = false;
     for (int l = nl - 1; l >= 0; --l) {
-      if (s.gmem && l - W_PF >= 0) {
-        pf_fields(tp, NWT, l - W_PF, W_R, 9);
-        pf_fields(tp, NWT, l - W_PF, W_U, W_u - W_U);
-        pf_fields(tp, NWT, l - W_PF, W_AP, W_SC - W_AP);
-        pf_fields(tp, NWT, l - W_PF, W_D, 3);
+      if (s.pf > 0 && l - s.pf >= 0) {
+        pf_fields(tp, NWT, l - s.pf, W_R, 9);
+        pf_fields(tp, NWT, l - s.pf, W_U, W_u - W_U);
+        pf_fields(tp, NWT, l - s.pf, W_AP, W_SC - W_AP);
+        pf_fields(tp, NWT, l - s.pf, W_D, 3);
       }
       const int m = s.M(l);
       const int par = meta_parent(m), qi = meta_qoff(m), vi = meta_voff(m);
@@ -465,11 +464,11 @@ SD void wstep_adjoint(const WSys<T>& s, Col<const T> q, Col<const T> qd, Col<T> 
     SI<T> cIAb = zeroSI<T>();
     SV<T> cpAb = zeroSV<T>();
     for (int l = 0; l < nl; ++l) {
-      if (s.gmem && l + W_PF < nl) {
-        pf_fields(tp, NWT, l + W_PF, W_R, W_AP - W_R);
-        pf_fields(tp, NWT, l + W_PF, W_D, 3);
-        pf_fields(ad, NWA, l + W_PF, WA_U, WA_ACC - WA_U);
-        pf_fields(s.prm, s.pstride, l + W_PF, P_M, NPRM_W - P_M);
+      if (s.pf > 0 && l + s.pf < nl) {
+        pf_fields(tp, NWT, l + s.pf, W_R, W_AP - W_R);
+        pf_fields(tp, NWT, l + s.pf, W_D, 3);
+        pf_fields(ad, NWA, l + s.pf, WA_U, WA_ACC - WA_U);
+        pf_fields(s.prm, s.pstride, l + s.pf, P_M, NPRM_W - P_M);
       }
       const int m = s.M(l);
       const int par = meta_parent(m), vi = meta_voff(m);
@@ -576,12 +575,12 @@ SD void wstep_adjoint(const WSys<T>& s, Col<const T> q, Col<const T> qd, Col<T> 
     M3<T> cRb = zeroM3<T>();
     bool carry = false;
     for (int l = nl - 1; l >= 0; --l) {
-      if (s.gmem && l - W_PF >= 0) {
-        pf_fields(tp, NWT, l - W_PF, W_R, 15);
-        pf_fields(tp, NWT, l - W_PF, W_IA, 15);
-        pf_fields(tp, NWT, l - W_PF, W_SC, 5);
-        pf_fields(ad, NWA, l - W_PF, WA_S, 6);
-        pf_fields(s.prm, s.pstride, l - W_PF, P_E, 12);
+      if (s.pf > 0 && l - s.pf >= 0) {
+        pf_fields(tp, NWT, l - s.pf, W_R, 15);
+        pf_fields(tp, NWT, l - s.pf, W_IA, 15);
+        pf_fields(tp, NWT, l - s.pf, W_SC, 5);
+        pf_fields(ad, NWA, l - s.pf, WA_S, 6);
+        pf_fields(s.prm, s.pstride, l - s.pf, P_E, 12);
       }
       const int m = s.M(l);
       const int par = meta_parent(m), qi = meta_qoff(m), vi = meta_voff(m);

@@ -146,6 +146,7 @@ def test_null_arguments():
     assert p.lib.sim_set_state_accumulation(None, 1) == -1
     assert p.lib.sim_set_tape_space(None, 4) == -1
     assert p.lib.sim_set_replay(None, 0) == -1
+    assert p.lib.sim_set_prefetch(None, 2) == -1
 
 
 def test_unknown_creation_flags_rejected():
