@@ -81,17 +81,27 @@ def source_digest() -> str:
 
 
 def measured_traffic(kernel: str, workload_name: str, B: int, T: int, precision: str, k: int):
-    """DRAM bytes per launch from the committed ncu launch list, when it was taken on
-    this workload with the current sources; else None."""
-    path = os.path.join(ROOT, "profiles", "traffic_serial_chains_7dof_b4096_t1000.json")
-    if not (workload_name == "serial_chains_7dof" and B == 4096 and T == 1000 and precision == "fp32"
-            and k == 1 and os.path.exists(path)):
-        return None
-    with open(path) as f:
-        rec = json.load(f)
-    if rec.get("source_sha256_16") != source_digest():
-        return None
-    return rec["kernels"].get(kernel, {}).get("traffic_bytes_per_launch")
+    """DRAM bytes per launch of `kernel` from a committed ncu capture taken on this
+    workload with the current sources (profiles/traffic_*.json), else None.  A
+    record either holds per-launch bytes at one horizon or, for captures taken at
+    a short horizon, bytes per step, scaled here to T steps (the kernels stream the
+    same per-step traffic at every step)."""
+    import glob
+    for path in sorted(glob.glob(os.path.join(ROOT, "profiles", "traffic_*.json"))):
+        with open(path) as f:
+            rec = json.load(f)
+        match = rec.get("match", {})
+        if not (match.get("workload") == workload_name and match.get("n_systems") == B and
+                match.get("precision") == precision and match.get("k") == k and
+                match.get("horizon") in (None, T)):
+            continue
+        if rec.get("source_sha256_16") != source_digest():
+            return None
+        kr = rec["kernels"].get(kernel, {})
+        if "traffic_bytes_per_step" in kr:
+            return kr["traffic_bytes_per_step"] * T
+        return kr.get("traffic_bytes_per_launch")
+    return None
 
 
 def _clock_sampler(stop, out):
@@ -249,8 +259,9 @@ def run_ours(args):
     adj_ms = [e[1].elapsed_time(e[2]) for e in events]
     graph_ms = None
     if graph is not None:   # the same step replayed as one CUDA graph
-        gev = [[torch.cuda.Event(enable_timing=True) for _ in range(2)] for _ in range(args.steps)]
-        for i in range(args.steps):
+        n_rep = min(args.steps, 2)
+        gev = [[torch.cuda.Event(enable_timing=True) for _ in range(2)] for _ in range(n_rep)]
+        for i in range(n_rep):
             flush.fill_(float(i))
             gev[i][0].record(stream)
             graph.replay()
@@ -853,7 +864,8 @@ def main():
     ap.add_argument("--no-e2e", dest="e2e", action="store_false")
     ap.add_argument("--no-grad-check", dest="grad_check", action="store_false",
                     help="skip the per-output error against the FP64 path on sampled systems")
-    ap.add_argument("--graph", action="store_true", help="replay the step as one CUDA graph")
+    ap.add_argument("--graph", action=argparse.BooleanOptionalAction, default=True,
+                    help="also time the step captured as one CUDA graph (two replays after the timed steps)")
     ap.add_argument("--contacts", action=argparse.BooleanOptionalAction, default=None,
                     help="quadruped with foot contact spheres, the contact solve running every step "
                          "(default: on for --config 3, whose specification includes foot contacts)")
