@@ -4,7 +4,8 @@ Times a short forward + adjoint rollout for each candidate -- the kernel family
 (the link-frame one-warp kernels, one lane per system; the link-frame pipelined
 kernels, two warps per 32-system tile, for short serial chains; the
 world-aligned kernels for revolute models without contacts or limits, one lane
-per system or with the two-warp pipelined adjoint), threads per block (systems per block) and grid or
+per system or with the two-warp pipelined adjoint; the library's automatic
+choice per direction), threads per block (systems per block) and grid or
 persistent schedule -- and keeps the fastest.  A candidate whose kernels the
 model cannot run (the library refuses the launch, or the pipelined space ran
 nothing pipelined) is dropped.  Results are cached in a JSON file keyed by the
@@ -19,11 +20,13 @@ import os
 # (threads per block, persistent schedule, kernel family): 1 the link-frame
 # one-warp kernels, 2 the link-frame pipelined kernels (two lanes per system),
 # 3 the world-aligned kernels, 4 the world-aligned kernels with the pipelined
-# adjoint (two lanes per system in the adjoint)
+# adjoint (two lanes per system in the adjoint), 5 the library's automatic choice
+# in each direction (which may mix families, e.g. the link-frame pipelined rollout
+# with the world-aligned pipelined adjoint)
 CANDIDATES = [(32, False, 1), (64, False, 1), (128, False, 1), (32, True, 1), (64, True, 1), (128, True, 1),
               (32, False, 2), (32, True, 2), (32, False, 3), (64, False, 3), (32, True, 3), (64, True, 3),
-              (32, False, 4), (64, False, 4), (32, True, 4), (64, True, 4)]
-TAPE_SPACE = {1: "one_warp", 2: "pipelined", 3: "aligned", 4: "aligned_pipelined"}
+              (32, False, 4), (64, False, 4), (32, True, 4), (64, True, 4), (32, False, 5), (32, True, 5)]
+TAPE_SPACE = {1: "one_warp", 2: "pipelined", 3: "aligned", 4: "aligned_pipelined", 5: "auto"}
 
 
 def cache_path() -> str:
@@ -99,6 +102,8 @@ def autotune(sim, q0, qd0, T_probe: int = 16, reps: int = 3, k: int = 1, use_cac
             continue                                   # the model cannot run on these kernels
         if cand[2] == 2 and "pipelined" not in sim.last_storage():
             continue                                   # ran one-lane in a direction: not this candidate
+        if cand[2] == 5 and not any(s.startswith(("pipelined", "aligned")) for s in sim.last_storage()):
+            continue                                   # the automatic choice was the one-warp family
         times[cand] = t
     best = choose(times)
     apply(sim, best)

@@ -959,10 +959,13 @@ int choose_w(sim_handle* h, K k_on, K k_off, bool bwd, bool* onchip, size_t* byt
 
 // The world-aligned path applies to models of revolute joints without contact
 // spheres or limits whose state and input streams fit a block's shared memory,
-// under SIM_TAPE_ALIGNED, or under SIM_TAPE_AUTO unless the pipelined two-warp
-// kernels apply (serial chains short enough for their on-chip tapes, where they
-// run faster).
-template <class T>
+// under SIM_TAPE_ALIGNED, or under SIM_TAPE_AUTO unless the link-frame two-warp
+// kernels apply and run faster: the pipelined rollout of serial chains short
+// enough for its on-chip tapes, and the link-frame pipelined adjoint of such
+// chains when the world-aligned one's two tapes do not fit a block or the
+// pivots are FP64 (7-DOF chains, FP32, per 1000-step rollout: world-aligned
+// adjoint 10.8 ms against 13.1; with FP64 pivots 40.3 against 34.5).
+template <class T, class DT>
 bool use_aligned(const sim_handle* h, bool rollout, int k) {
   if (!h->all_revolute || (rollout && h->state64)) return false;
   if (h->tape_space != SIM_TAPE_AUTO && h->tape_space != SIM_TAPE_ALIGNED &&
@@ -976,8 +979,11 @@ bool use_aligned(const sim_handle* h, bool rollout, int k) {
   if (streams > (size_t)limit) return false;
   if (h->tape_space != SIM_TAPE_AUTO || !h->all_chains) return true;
   if (rollout) return !(h->maxL <= PIPE_MAX_LINKS);
-  return !(sizeof(T) == 4 && k == 1 &&
-           (size_t)pipe_smem_per_tile(h->maxL, nx, h->nv_max) * LANES * sizeof(T) <= (size_t)limit);
+  const bool link_pipe = sizeof(T) == 4 && k == 1 &&
+                         (size_t)pipe_smem_per_tile(h->maxL, nx, h->nv_max) * LANES * sizeof(T) <= (size_t)limit;
+  if (!link_pipe) return true;
+  return sizeof(DT) == sizeof(T) &&
+         (size_t)wpipe_smem_per_tile(h->maxL, nx, h->nv_max, true) * LANES * sizeof(T) <= (size_t)limit;
 }
 
 template <class T, class DT>
@@ -1076,7 +1082,7 @@ int launch_wbackward(sim_handle* h, const void* ckpt, const void* tau, int64_t T
 template <class T, class DT>
 int launch_rollout(sim_handle* h, const void* q0, const void* qd0, const void* tau, int64_t T_,
                    int k, void* ckpt, void* qT, void* qdT, void* traj, void* stream) {
-  if (use_aligned<T>(h, true, k)) return launch_wrollout<T, DT>(h, q0, qd0, tau, T_, k, ckpt, qT, qdT, traj, stream);
+  if (use_aligned<T, DT>(h, true, k)) return launch_wrollout<T, DT>(h, q0, qd0, tau, T_, k, ckpt, qT, qdT, traj, stream);
   if (h->tape_space == SIM_TAPE_ALIGNED || h->tape_space == SIM_TAPE_ALIGNED_PIPELINED)
     return fail(h, SIM_EUNSUPPORTED,
                 "the world-aligned kernels need revolute joints only, no contact spheres or limits, FP32 state sums "
@@ -1135,7 +1141,7 @@ template <class T, class DT>
 int launch_backward(sim_handle* h, const void* ckpt, const void* tau, int64_t T_, int k,
                     const void* gqT, const void* gqdT, const void* gtraj, void* gq0, void* gqd0,
                     void* gtau, void* gmass, void* work, void* stream) {
-  if (use_aligned<T>(h, false, k))
+  if (use_aligned<T, DT>(h, false, k))
     return launch_wbackward<T, DT>(h, ckpt, tau, T_, k, gqT, gqdT, gtraj, gq0, gqd0, gtau, gmass, work, stream);
   if (h->tape_space == SIM_TAPE_ALIGNED || h->tape_space == SIM_TAPE_ALIGNED_PIPELINED)
     return fail(h, SIM_EUNSUPPORTED, "the world-aligned kernels need revolute joints only, no contact spheres or "

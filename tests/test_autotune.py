@@ -48,7 +48,8 @@ def test_autotune_times_candidates_and_caches(tmp_path, monkeypatch):
     cost = {(32, False, 1): 3.0, (64, False, 1): 2.0, (128, False, 1): 2.5, (32, True, 1): 1.5,
             (64, True, 1): 4.0, (128, True, 1): 5.0, (32, False, 2): 1.6, (32, True, 2): 1.7,
             (32, False, 3): 1.8, (64, False, 3): 1.9, (32, True, 3): 2.1, (64, True, 3): 2.2,
-            (32, False, 4): 1.55, (64, False, 4): 1.65, (32, True, 4): 1.75, (64, True, 4): 1.85}
+            (32, False, 4): 1.55, (64, False, 4): 1.65, (32, True, 4): 1.75, (64, True, 4): 1.85,
+            (32, False, 5): 1.52, (32, True, 5): 1.51}
     seen = []
 
     def timer(s, cand):
@@ -103,14 +104,17 @@ def test_world_aligned_kernels_are_a_candidate(tmp_path, monkeypatch):
 
 def test_candidates_the_model_cannot_run_are_dropped(tmp_path, monkeypatch):
     """A model neither the pipelined nor the world-aligned kernels can run (the
-    library refuses those tape spaces): only the one-warp kernels are timed."""
+    library refuses those tape spaces): only the one-warp kernels are kept."""
     monkeypatch.setenv("ABASIM_TUNE_CACHE", str(tmp_path / "tune.json"))
     sim = FakeSim(pipelines=False, aligns=False)
     seen = []
     best = at.autotune(sim, None, None, timer=lambda s, c: seen.append(c) or (1.0 if c[2] != 1 else 2.0),
                        device_name="x")
     assert best[2] == 1 and sim.space == "one_warp"
-    assert all(c[2] == 1 for c in seen)
+    # the automatic choice is timed too, and dropped: it ran the one-warp kernels
+    assert all(c[2] in (1, 5) for c in seen)
+    kept = json.load(open(tmp_path / "tune.json")).popitem()[1]["seconds"]
+    assert kept and all(key.endswith("/one_warp") for key in kept)
 
 
 def test_old_cache_entries(tmp_path, monkeypatch):

@@ -104,9 +104,9 @@ def test_autotune_lanes_on_chains(tmp_path, monkeypatch):
     assert "pipelined" not in sim.last_storage()
     best = sim.autotune(q0, qd0, T_probe=4, reps=1)
     out = _run(sim, q0, qd0, tau)
-    assert ("pipelined" in sim.last_storage()) == (best[2] == 2)
+    assert (sim.last_storage()[0] == "pipelined") == (best[2] in (2, 5))
     assert sim.last_storage()[0].startswith("aligned") == (best[2] in (3, 4))
-    assert sim.last_storage()[1].startswith("aligned_pipelined") == (best[2] == 4)
+    assert sim.last_storage()[1].startswith("aligned_pipelined") == (best[2] in (4, 5))
     entry = next(iter(at.load_cache().values()))
     assert any(key.endswith("/pipelined") for key in entry["seconds"])
     assert any(key.endswith("/aligned") for key in entry["seconds"])

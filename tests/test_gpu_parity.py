@@ -134,7 +134,8 @@ def test_oblique_joint_axes(precision):
 
 def test_headline_configuration_full_size_sampled():
     """The chain configuration at full size -- 4096 serial 7-DOF chains,
-    T = 1000, FP32, k = 1, automatic kernel choice (the pipelined rollout and adjoint) --
+    T = 1000, FP32, k = 1, automatic kernel choice (the link-frame pipelined rollout and the
+    world-aligned pipelined adjoint) --
     against the FP64 oracle on sampled systems: the final state of every 64th system
     and the last, and the gradients of the first, a middle and the last system (first
     tile, a middle tile, the ragged end of the slot order)."""
@@ -153,7 +154,7 @@ def test_headline_configuration_full_size_sampled():
     qT, qdT, ck, _ = sim.rollout(q0.to(dev), qd0.to(dev), tau.to(dev), k=1)
     gq0, gqd0, gtau, gm = sim.backward(ck, tau.to(dev), gqT.to(dev), gqdT.to(dev), k=1)
     torch.cuda.synchronize()
-    assert sim.last_storage() == ("pipelined", "pipelined")
+    assert sim.last_storage() == ("pipelined", "aligned_pipelined_shared")
     assert sim.status().sum() == 0
     h = [x.double().numpy() for x in (q0, qd0, tau, gqT, gqdT)]
     ts, tg = TOL["fp32"]

@@ -55,3 +55,26 @@ def test_static_step_rejects_batches_beyond_the_static_scratch():
     qd = torch.zeros(sim.nv_max, sim.B, dtype=sim.dtype, device=sim.device)
     with pytest.raises(SimError, match="static"):
         sim.step_static(q, qd, qd)
+
+
+def test_static_step_leaves_device_memory_unchanged():
+    """After the first call (which looks up the static array's address), further
+    calls into caller-owned outputs change neither the device's free memory
+    (cudaMemGetInfo) nor the memory torch has handed out."""
+    from paper_2109_07719_gb300 import Simulator
+    work = wl.config(2, B=512, T=1, precision="fp32")
+    sim = Simulator(work.model, precision="fp32")
+    dev, dt = sim.device, sim.dtype
+    q = torch.tensor(work.q0, dtype=dt, device=dev)
+    qd = torch.zeros(sim.nv_max, sim.B, dtype=dt, device=dev)
+    tau = torch.zeros(sim.nv_max, sim.B, dtype=dt, device=dev)
+    q_out, qd_out = torch.empty_like(q), torch.empty_like(qd)
+    sim.step_static(q, qd, tau, q_out, qd_out)
+    torch.cuda.synchronize()
+    free0, alloc0 = torch.cuda.mem_get_info(dev)[0], torch.cuda.memory_allocated(dev)
+    for _ in range(3):
+        sim.step_static(q, qd, tau, q_out, qd_out)
+    torch.cuda.synchronize()
+    assert torch.cuda.mem_get_info(dev)[0] == free0
+    assert torch.cuda.memory_allocated(dev) == alloc0
+    assert torch.isfinite(q_out).all() and torch.isfinite(qd_out).all()
