@@ -26,7 +26,7 @@ SOURCES = ["abasim.cu", "inst_fp32_fwd.cu", "inst_fp32_bwd.cu", "inst_fp32_bwd_h
            "inst_mixed_bwd_smem.cu", "inst_fp64.cu", "inst_fp32_contact.cu", "inst_mixed_contact.cu",
            "inst_fp64_contact.cu", "inst_w_fp32_fwd.cu", "inst_w_fp32_bwd.cu", "inst_w_mixed_fwd.cu", "inst_w_mixed_bwd.cu", "inst_w_fp64_fwd.cu", "inst_w_fp64_bwd.cu", "inst_wp_fp32.cu", "inst_wp_mixed.cu", "inst_wp_fp64.cu"]
 DEPS = SOURCES + ["fma_peak.cu", "aba_step.cuh", "contact.cuh", "spatial.cuh", "dual.cuh", "kernels.cuh", "handle.h",
-                  "wstep.cuh", "wkernels.cuh", "wpipe.cuh"]
+                  "wstep.cuh", "wkernels.cuh", "wpipe.cuh", "tree_order.h"]
 
 NVCC_FLAGS = ["-gencode", "arch=compute_103a,code=sm_103a", "-lineinfo", "-O3", "-std=c++17",
               "-Xcompiler", "-fPIC", "-diag-suppress", "177"]

@@ -67,15 +67,22 @@ enum : int {
 };
 
 // meta word per link: parent+1 (8 bits) | joint type (1) | "has a child other than
-// link l+1" (1) | q offset (10) | v offset (10).  Chains never set the flag: their
-// parent/child values are carried in registers from one loop iteration to the next.
+// link l+1" (1) | q offset (10) | v offset (10) | "last of several children" (1).
+// Chains never set the flags: their parent/child values are carried in registers
+// from one loop iteration to the next.  Links are numbered in depth-first preorder
+// (children in ascending order of the model's numbering), so a link with children
+// has link l+1 as its first child, and the flags say when a world-aligned pass
+// pushes or pops its stack of parent values: a link with a child other than l+1
+// pushes (or, in the passes that run leaves -> root, pops) one entry, and the last
+// child of such a link, which is never link parent+1, pops it (or pushes it).
 SD int meta_parent(int m) { return (m & 0xff) - 1; }
 SD int meta_jtype(int m) { return (m >> 8) & 0x1; }
 SD bool meta_treechild(int m) { return (m >> 9) & 0x1; }
 SD int meta_qoff(int m) { return (m >> 10) & 0x3ff; }
 SD int meta_voff(int m) { return (m >> 20) & 0x3ff; }
-SD int make_meta(int parent, int jt, bool treechild, int qo, int vo) {
-  return (parent + 1) | (jt << 8) | ((treechild ? 1 : 0) << 9) | (qo << 10) | (vo << 20);
+SD bool meta_lastsib(int m) { return (m >> 30) & 0x1; }
+SD int make_meta(int parent, int jt, bool treechild, int qo, int vo, bool lastsib = false) {
+  return (parent + 1) | (jt << 8) | ((treechild ? 1 : 0) << 9) | (qo << 10) | (vo << 20) | ((lastsib ? 1 : 0) << 30);
 }
 
 template <class T> SD void sincos_t(T x, T* s, T* c);

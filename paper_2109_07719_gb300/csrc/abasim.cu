@@ -14,6 +14,7 @@
 
 #include "contact.cuh"
 #include "handle.h"
+#include "tree_order.h"
 #include "wstep.cuh"
 
 using namespace abasim;
@@ -310,9 +311,22 @@ int sim_create(const sim_model_desc* d, sim_handle** out) {
   for (int sl = 0; sl < B; ++sl) {
     const int b = order[sl];
     nl[sl] = nl_sys[b];
+    const int n = nl[sl], o = d->sys_link_offset[b];
+    // coordinates keep the model's numbering; the links are stored in depth-first
+    // preorder (perm: stored position -> model link), children in model order
+    std::vector<int> qoff(n), voff(n);
     int qo = 0, vo = 0;
-    for (int l = 0; l < nl[sl]; ++l) {
-      const int i = d->sys_link_offset[b] + l;
+    for (int l = 0; l < n; ++l) {
+      qoff[l] = qo;
+      voff[l] = vo;
+      qo += d->joint_type[o + l] == SIM_FREE ? 7 : 1;
+      vo += d->joint_type[o + l] == SIM_FREE ? 6 : 1;
+    }
+    const TreeOrder to = tree_order(d->parent + o, n);
+    const std::vector<int>& perm = to.perm;
+    h->wdepth = std::max(h->wdepth, to.depth);
+    for (int l = 0; l < n; ++l) {
+      const int i = o + perm[l];
       const int jt = d->joint_type[i];
       const size_t tile = sl / LANES, lane = sl % LANES;
       auto P = [&](int f) -> double& { return prm[((tile * maxL + l) * NPRM + f) * LANES + lane]; };
@@ -344,13 +358,9 @@ int sim_create(const sim_model_desc* d, sim_handle** out) {
       P(P_LO) = lim ? d->limits[2 * i] : -INFINITY;
       P(P_HI) = lim ? d->limits[2 * i + 1] : INFINITY;
       if (lim && (std::isfinite(d->limits[2 * i]) || std::isfinite(d->limits[2 * i + 1]))) any_contact = true;
-      bool treechild = false;  // a child other than link l + 1
-      for (int c = l + 2; c < nl[sl]; ++c)
-        if (d->parent[d->sys_link_offset[b] + c] == l) treechild = true;
-      meta[(tile * maxL + l) * LANES + lane] = make_meta(d->parent[i], jt, treechild, qo, vo);
+      meta[(tile * maxL + l) * LANES + lane] =
+          make_meta(to.parent[l], jt, to.branch[l], qoff[perm[l]], voff[perm[l]], to.lastsib[l]);
       slot[i] = l * B + sl;
-      qo += jt == SIM_FREE ? 7 : 1;
-      vo += jt == SIM_FREE ? 6 : 1;
     }
     nqv[sl] = qo | (vo << 16);
     h->nq_max = std::max(h->nq_max, qo);
@@ -391,6 +401,8 @@ int sim_create(const sim_model_desc* d, sim_handle** out) {
   if (rc == SIM_OK) rc = alloc(&h->gm_acc, (size_t)maxL * B * h->scalar, "mass-gradient buffer");
   if (rc == SIM_OK && h->all_revolute)
     rc = alloc(&h->wtape2, (size_t)maxL * NWT * Bpad * h->scalar, "second world-aligned tape");
+  if (rc == SIM_OK && h->all_revolute && h->wdepth > 0)
+    rc = alloc(&h->wstk, (size_t)2 * h->wdepth * WSW * Bpad * h->scalar, "world-aligned stacks");
   if (rc == SIM_OK) rc = alloc((void**)&h->status, B * sizeof(int), "status");
   if (rc == SIM_OK) rc = alloc((void**)&h->sys_of_slot, B * sizeof(int), "slot order");
   if (rc == SIM_OK) rc = put(h->sys_of_slot, order.data(), B * sizeof(int));
@@ -418,7 +430,7 @@ int sim_create(const sim_model_desc* d, sim_handle** out) {
 void sim_destroy(sim_handle* h) {
   if (!h) return;
   void* ptrs[] = {h->prm, h->meta, h->nl, h->nqv, h->tape, h->adj, h->gm_acc, h->link_slot,
-                  h->status, h->sys_of_slot, h->counter, h->ctape, h->csys, h->x64, h->wtape2};
+                  h->status, h->sys_of_slot, h->counter, h->ctape, h->csys, h->x64, h->wtape2, h->wstk};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   delete h;

@@ -31,6 +31,8 @@ struct sim_handle {
   void* tape = nullptr;      // [maxL][NTAPE][B] scalar
   void* adj = nullptr;       // [maxL][NADJ][B] scalar
   void* wtape2 = nullptr;    // [maxL][NWT][B] scalar: the pipelined world-aligned adjoint's second tape
+  void* wstk = nullptr;      // [2][wdepth][WSW][B] scalar: the world-aligned passes' stacks of parent values
+  int wdepth = 0;            // entries a system's stack holds at most (depth-first nesting of its branchings)
   void* gm_acc = nullptr;    // [maxL][B] scalar
   int* link_slot = nullptr;  // [L_total] -> l * B + slot
   int* status = nullptr;     // [B] by system

@@ -39,6 +39,8 @@ template <class T> struct DevModel {
   double dt64;   // the time step in FP64
   double* x64;   // FP64 running state [nq_max + nv_max][B] of the rollout (null: off; FP32 + FP64 D only)
   int pf;        // world-aligned kernels with a global tape: prefetch distance in links (0: none)
+  T* stk;        // world-aligned kernels: two stacks of parent values [2][tiles][wdepth][WSW][lane] (null: none)
+  int wdepth;    // entries per stack
 };
 
 template <class T> DevModel<T> dev_model(const sim_handle* h) {
@@ -47,7 +49,7 @@ template <class T> DevModel<T> dev_model(const sim_handle* h) {
                      (T)h->g[0], (T)h->g[1], (T)h->g[2], h->integrator, 0, 0,
                      h->replay == SIM_REPLAY_QUADRATIC, (T*)h->ctape, (T*)h->csys,
                      ContactParams<T>{(T)h->friction, (T)h->erp, h->pgs_iterations}, h->dt,
-                     h->state64 ? (double*)h->x64 : nullptr, h->prefetch};
+                     h->state64 ? (double*)h->x64 : nullptr, h->prefetch, (T*)h->wstk, h->wdepth};
 }
 
 extern __shared__ __align__(16) unsigned char g_smem[];
@@ -928,8 +930,8 @@ int choose_w(sim_handle* h, K k_on, K k_off, bool bwd, bool* onchip, size_t* byt
   if (e != cudaSuccess) return cuda_fail(h, e, "shared-memory limit query");
   const int tiles = h->block / LANES;
   const int nx = h->nq_max + h->nv_max;
-  const size_t need_on = (size_t)tiles * w_smem_per_tile(h->maxL, nx, h->nv_max, bwd, true) * LANES * sizeof(T);
-  const size_t need_off = (size_t)tiles * w_smem_per_tile(h->maxL, nx, h->nv_max, bwd, false) * LANES * sizeof(T);
+  const size_t need_on = (size_t)tiles * w_smem_per_tile(h->maxL, nx, h->nv_max, bwd, true, h->wdepth * WSW) * LANES * sizeof(T);
+  const size_t need_off = (size_t)tiles * w_smem_per_tile(h->maxL, nx, h->nv_max, bwd, false, 0) * LANES * sizeof(T);
   if (need_off > (size_t)limit) return fail(h, SIM_EUNSUPPORTED, "the working state does not fit in shared memory");
   e = cudaFuncSetAttribute((const void*)k_off, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)need_off);
   if (e != cudaSuccess) return cuda_fail(h, e, "shared-memory opt-in");
@@ -974,7 +976,7 @@ bool use_aligned(const sim_handle* h, bool rollout, int k) {
   int limit = 0;
   if (cudaDeviceGetAttribute(&limit, cudaDevAttrMaxSharedMemoryPerBlockOptin, h->device) != cudaSuccess) return false;
   const int nx = h->nq_max + h->nv_max;
-  const size_t streams = (size_t)(h->block / LANES) * w_smem_per_tile(h->maxL, nx, h->nv_max, !rollout, false) * LANES *
+  const size_t streams = (size_t)(h->block / LANES) * w_smem_per_tile(h->maxL, nx, h->nv_max, !rollout, false, 0) * LANES *
                          sizeof(T);
   if (streams > (size_t)limit) return false;
   if (h->tape_space != SIM_TAPE_AUTO || !h->all_chains) return true;
@@ -983,7 +985,7 @@ bool use_aligned(const sim_handle* h, bool rollout, int k) {
                          (size_t)pipe_smem_per_tile(h->maxL, nx, h->nv_max) * LANES * sizeof(T) <= (size_t)limit;
   if (!link_pipe) return true;
   return sizeof(DT) == sizeof(T) &&
-         (size_t)wpipe_smem_per_tile(h->maxL, nx, h->nv_max, true) * LANES * sizeof(T) <= (size_t)limit;
+         (size_t)wpipe_smem_per_tile(h->maxL, nx, h->nv_max, true, h->wdepth * WSW) * LANES * sizeof(T) <= (size_t)limit;
 }
 
 template <class T, class DT>
@@ -1017,8 +1019,8 @@ int launch_wbackward_pipe(sim_handle* h, const void* ckpt, const void* tau, int6
   cudaError_t e = cudaDeviceGetAttribute(&limit, cudaDevAttrMaxSharedMemoryPerBlockOptin, h->device);
   if (e != cudaSuccess) return cuda_fail(h, e, "shared-memory limit query");
   const int nx = h->nq_max + h->nv_max;
-  const size_t need_on = (size_t)wpipe_smem_per_tile(h->maxL, nx, h->nv_max, true) * LANES * sizeof(T);
-  const size_t need_off = (size_t)wpipe_smem_per_tile(h->maxL, nx, h->nv_max, false) * LANES * sizeof(T);
+  const size_t need_on = (size_t)wpipe_smem_per_tile(h->maxL, nx, h->nv_max, true, h->wdepth * WSW) * LANES * sizeof(T);
+  const size_t need_off = (size_t)wpipe_smem_per_tile(h->maxL, nx, h->nv_max, false, 0) * LANES * sizeof(T);
   const bool onchip = need_on <= (size_t)limit;
   if (!onchip && !h->wtape2) return fail(h, SIM_EUNSUPPORTED, "no second tape for the pipelined adjoint");
   const size_t shm = onchip ? need_on : need_off;

@@ -14,15 +14,26 @@ namespace host {
 // Scalars per 32-system tile a world-aligned kernel keeps in shared memory: the
 // working state (x for the rollout, the state adjoint and the per-link
 // mass-gradient sums for the backward pass); with ONCHIP also the tape (and, for
-// the adjoint, the adjoint record), the model constants and meta words, and a
-// double buffer for the per-step inputs (tau, plus x^t for the adjoint) fetched
-// one step ahead.  Without ONCHIP the inputs are read from global memory with
-// their lines prefetched a step ahead, and the small shared-memory footprint
-// leaves most of the SM's L1 to the prefetched tape lines.
-__host__ __device__ __forceinline__ long long w_smem_per_tile(int maxL, int nx, int nv, bool bwd, bool onchip) {
+// the adjoint, the adjoint record), the model constants and meta words, the stack
+// of parent values (sd scalars per system) and a double buffer for the per-step
+// inputs (tau, plus x^t for the adjoint) fetched one step ahead.  Without ONCHIP
+// the stack is in the handle's global scratch and the inputs are read from global
+// memory with their lines prefetched a step ahead, and the small shared-memory
+// footprint leaves most of the SM's L1 to the prefetched tape lines.
+__host__ __device__ __forceinline__ long long w_smem_per_tile(int maxL, int nx, int nv, bool bwd, bool onchip,
+                                                              int sd) {
   const long long state = nx + (bwd ? maxL : 0);
   if (!onchip) return state;
-  return (long long)maxL * (NWT + (bwd ? NWA : 0) + NPRM_W + 1) + state + 2LL * (nv + (bwd ? nx : 0));
+  return (long long)maxL * (NWT + (bwd ? NWA : 0) + NPRM_W + 1) + sd + state + 2LL * (nv + (bwd ? nx : 0));
+}
+
+// Stack `which` (0, or 1 for the second warp of the pipelined adjoint) of a tile's
+// system at `lane` in the handle's global scratch (null when no system branches).
+template <class T>
+__device__ __forceinline__ T* w_stack(const DevModel<T>& m, int which, long long tile, long long lane) {
+  if (!m.stk) return nullptr;
+  const long long tiles = (m.B + LANES - 1) / LANES;
+  return m.stk + ((long long)which * tiles + tile) * m.wdepth * WSW * LANES + lane;
 }
 
 struct WTile {
@@ -30,16 +41,18 @@ struct WTile {
   void* adj;
   void* prm;
   int* meta;
+  void* stk;
   void* state;
   void* gm;
   void* stream;
 };
 
 template <class T, bool BWD, bool ONCHIP>
-__device__ __forceinline__ WTile w_tile(int maxL, int nx, int nv, int lane) {
+__device__ __forceinline__ WTile w_tile(int maxL, int nx, int nv, int sd, int lane) {
   const int tb = threadIdx.x / LANES;
   const long long L = maxL;
-  T* base = reinterpret_cast<T*>(g_smem) + (long long)tb * w_smem_per_tile(maxL, nx, nv, BWD, ONCHIP) * LANES + lane;
+  T* base =
+      reinterpret_cast<T*>(g_smem) + (long long)tb * w_smem_per_tile(maxL, nx, nv, BWD, ONCHIP, sd) * LANES + lane;
   WTile t{};
   if (ONCHIP) {
     t.tape = base;
@@ -50,6 +63,8 @@ __device__ __forceinline__ WTile w_tile(int maxL, int nx, int nv, int lane) {
     base += L * NPRM_W * LANES;
     t.meta = reinterpret_cast<int*>(base);
     base += L * LANES;
+    t.stk = base;
+    base += (long long)sd * LANES;
   }
   t.state = base;
   base += (long long)nx * LANES;
@@ -69,17 +84,17 @@ __device__ __forceinline__ WSys<T> wsys_of(const DevModel<T>& m, int slot) {
   const int* gmeta = m.meta + tile * L * LANES + lane;
   const int nl = m.nl[slot];
   if (ONCHIP) {
-    const WTile t = w_tile<T, BWD, ONCHIP>(m.maxL, m.nq_max + m.nv_max, m.nv_max, (int)lane);
+    const WTile t = w_tile<T, BWD, ONCHIP>(m.maxL, m.nq_max + m.nv_max, m.nv_max, m.wdepth * WSW, (int)lane);
     T* sp = (T*)t.prm;
     constexpr int MS = (int)(sizeof(T) / sizeof(int));
     for (int l = 0; l < nl; ++l) {
       for (int f = 0; f < NPRM_W; ++f) sp[(l * NPRM_W + f) * LANES] = gprm[(l * NPRM + f) * LANES];
       t.meta[l * LANES * MS] = gmeta[l * LANES];
     }
-    return WSys<T>{sp, t.meta, (T*)t.tape, (T*)t.adj, nl, MS, NPRM_W};
+    return WSys<T>{sp, t.meta, (T*)t.tape, (T*)t.adj, nl, MS, NPRM_W, 0, (T*)t.stk};
   }
   return WSys<T>{gprm, gmeta, m.tape + tile * L * NWT * LANES + lane, m.adj + tile * L * NWA * LANES + lane, nl, 1,
-                 NPRM, m.pf};
+                 NPRM, m.pf, w_stack(m, 0, tile, lane)};
 }
 
 template <class T, class DT, bool ONCHIP>
@@ -91,7 +106,7 @@ __device__ __forceinline__ void wrollout_one(const DevModel<T>& m, int slot, con
   const int nqm = m.nq_max, nvm = m.nv_max, NX = nqm + nvm;
   const V3<T> g{m.g0, m.g1, m.g2};
   const WSys<T> s = wsys_of<T, false, ONCHIP>(m, slot);
-  const WTile st = w_tile<T, false, ONCHIP>(m.maxL, NX, nvm, slot % LANES);
+  const WTile st = w_tile<T, false, ONCHIP>(m.maxL, NX, nvm, m.wdepth * WSW, slot % LANES);
   const Col<T> q{(T*)st.state, LANES}, qd{(T*)st.state + nqm * LANES, LANES};
   const int nv = m.nqv[slot] >> 16;
   T* sbuf = (T*)st.stream;  // ONCHIP: [2][nvm][LANES], tau one step ahead
@@ -153,7 +168,7 @@ __device__ __forceinline__ void wbackward_one(const DevModel<T>& m, int slot, co
   const int nq = m.nqv[slot] & 0xffff, nv = m.nqv[slot] >> 16;
   const V3<T> g{m.g0, m.g1, m.g2};
   const WSys<T> s = wsys_of<T, true, ONCHIP>(m, slot);
-  const WTile st = w_tile<T, true, ONCHIP>(m.maxL, NX, nvm, slot % LANES);
+  const WTile st = w_tile<T, true, ONCHIP>(m.maxL, NX, nvm, m.wdepth * WSW, slot % LANES);
   const Col<T> gq{(T*)st.state, LANES}, gqd{(T*)st.state + nqm * LANES, LANES}, gm{(T*)st.gm, LANES};
   T* sbuf = (T*)st.stream;  // [2][NX + nvm][LANES]: x^t and tau^t, one step ahead (k = 1)
   for (int d = 0; d < nqm; ++d) {

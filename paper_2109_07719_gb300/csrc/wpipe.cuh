@@ -20,11 +20,12 @@ namespace host {
 
 // Scalars per tile: the state adjoint and per-link mass-gradient sums; with
 // ONCHIP also both tapes, the adjoint record, model constants and meta words, the
-// consumer's copy of x^t and the producer's double-buffered (x^t, tau^t).
-__host__ __device__ __forceinline__ long long wpipe_smem_per_tile(int maxL, int nx, int nv, bool onchip) {
+// two warps' stacks of parent values (sd scalars per system each), the consumer's
+// copy of x^t and the producer's double-buffered (x^t, tau^t).
+__host__ __device__ __forceinline__ long long wpipe_smem_per_tile(int maxL, int nx, int nv, bool onchip, int sd) {
   const long long state = nx + maxL;
   if (!onchip) return state;
-  return (long long)maxL * (2 * NWT + NWA + NPRM_W + 1) + state + nx + 2LL * (nx + nv);
+  return (long long)maxL * (2 * NWT + NWA + NPRM_W + 1) + 2LL * sd + state + nx + 2LL * (nx + nv);
 }
 
 template <class T, class DT, bool ONCHIP>
@@ -41,6 +42,8 @@ k_wbackward_pipe(DevModel<T> m, const T* __restrict__ ckpt, const T* __restrict_
   constexpr int MS = (int)(sizeof(T) / sizeof(int));
   T* base = reinterpret_cast<T*>(g_smem);
   T *s_tape = nullptr, *s_adj = nullptr, *s_prm = nullptr, *s_meta = nullptr, *s_x = nullptr, *s_in = nullptr;
+  T* s_stk = nullptr;
+  const long long sdw = (long long)m.wdepth * WSW;  // stack scalars per system
   if (ONCHIP) {
     s_tape = base;  // [2][L][NWT][LANES]
     base += 2 * L * NWT * LANES;
@@ -50,6 +53,8 @@ k_wbackward_pipe(DevModel<T> m, const T* __restrict__ ckpt, const T* __restrict_
     base += L * NPRM_W * LANES;
     s_meta = base;
     base += L * LANES;
+    s_stk = base;  // [2][sdw][LANES]: the producer's stack, then the consumer's
+    base += 2 * sdw * LANES;
   }
   T* s_state = base;
   T* s_gm = s_state + (long long)NX * LANES;
@@ -79,9 +84,13 @@ k_wbackward_pipe(DevModel<T> m, const T* __restrict__ ckpt, const T* __restrict_
       if (ONCHIP) return s_tape + buf * L * NWT * LANES + lane;
       return (buf ? tape2 : m.tape) + (long long)unit * L * NWT * LANES + lane;
     };
+    const int who = consumer ? 1 : 0;  // each warp walks its own stack
     auto sys_of_buf = [&](int buf) -> WSys<T> {
-      if (ONCHIP) return WSys<T>{s_prm + lane, meta_l, tape_of(buf), s_adj + lane, nl, MS, NPRM_W, 0};
-      return WSys<T>{gprm, gmeta, tape_of(buf), m.adj + (long long)unit * L * NWA * LANES + lane, nl, 1, NPRM, m.pf};
+      if (ONCHIP)
+        return WSys<T>{s_prm + lane, meta_l, tape_of(buf), s_adj + lane, nl, MS, NPRM_W, 0,
+                       s_stk + who * sdw * LANES + lane};
+      return WSys<T>{gprm, gmeta, tape_of(buf), m.adj + (long long)unit * L * NWA * LANES + lane, nl, 1, NPRM, m.pf,
+                     w_stack(m, who, unit, lane)};
     };
     // the producer's inputs of step t: x^t and tau^t, fetched one step ahead
     auto fetch = [&](long long t, int buf) {

@@ -32,6 +32,14 @@
 //   outward: a' = [a_p.w; a_p.v - d x a_p.w] + c   (a_world = [0; -g])
 //            qdd = (u - U.a') / D,  a = a' + [s qdd; 0]
 // shift(I, d) = X^T I X with X = (1, d): the congruence by a pure translation.
+//
+// Tree data flow.  Links are numbered in depth-first preorder, so a link's first
+// child is link l + 1 and its values pass to it in registers; the values a link
+// with several children hands to its later children (outward passes), or collects
+// from them (leaves -> root passes), live on a per-system stack whose depth is the
+// nesting of branchings, not the link count: a branching link pushes, its later
+// children read (or add to) the top, and its last child pops (mirrored in the
+// passes that run leaves -> root).  No pass reads another link's tape words.
 #pragma once
 
 #include "aba_step.cuh"
@@ -49,14 +57,13 @@ enum : int {
 };
 // Per-link adjoint record, [link][field][lane]: from the acceleration pass's
 // adjoint, the adjoints of U, D, u and c; the adjoints of s and d (completed by
-// the later passes); the accumulator of a's adjoint from children other than
-// link l + 1 (later reused for v's); that of R's; and a parent's final adjoints
-// of I^A and p^A handed to such children.  The inward adjoint pass leaves each
-// link's v and R adjoints in its (by then dead) tape words W_IA..W_IA+14.
-enum : int {
-  WA_U = 0, WA_D = 6, WA_u = 7, WA_C = 8, WA_S = 14, WA_DD = 17, WA_ACC = 20, WA_RACC = 26, WA_IAB = 35,
-  WA_PAB = 56, NWA = 62
-};
+// the later passes).  The inward adjoint pass leaves each link's v and R adjoints
+// in its (by then dead) tape words W_IA..W_IA+14.
+enum : int { WA_U = 0, WA_D = 6, WA_u = 7, WA_C = 8, WA_S = 14, WA_DD = 17, NWA = 20 };
+// One entry of the stack of parent values, [entry][field][lane]: (R, v) or a in
+// the outward passes, (shift(I^a, d), p^a) in the inward one; in the adjoint the
+// adjoints of a, (I^A, p^A) and (v, R).
+constexpr int WSW = 27;
 // model constants a world-aligned kernel reads: fields [0, NPRM_W) of the
 // link's record (E_tree, r_tree, the axis slot, mass, COM, I_com, damping)
 constexpr int NPRM_W = P_DAMP + 1;
@@ -71,6 +78,7 @@ template <class T> struct WSys {
   int mstride = 1;
   int pstride = NPRM;
   int pf = 0;  // prm, meta, tape and adj in global memory: prefetch this many links ahead (0: none)
+  T* stk = nullptr;  // [entry][WSW][LANES]: the stack of parent values (see the tree data flow above)
   SD T P(int l, int f) const { return prm[(l * pstride + f) * LANES]; }
   SD int M(int l) const { return meta[l * LANES * mstride]; }
   SD T& tp(int l, int f) const { return tape[(l * NWT + f) * LANES]; }
@@ -230,6 +238,7 @@ SD void wstep_forward(const WSys<T>& s, Col<const T> q, Col<const T> qd, Col<con
   // outward: orientation, joint offset, axis, velocity
   M3<T> R_prev = eye3<T>();
   SV<T> v_prev = zeroSV<T>();
+  int sp = 0;  // entries on the stack
   for (int l = 0; l < nl; ++l) {
     if (s.pf > 0 && l + s.pf < nl) {
       pf_meta(s, l + s.pf);
@@ -249,8 +258,13 @@ SD void wstep_forward(const WSys<T>& s, Col<const T> q, Col<const T> qd, Col<con
       R = transpose(E);
       v = SV<T>{vl * col2(R), zero3<T>()};
     } else {
-      const M3<T> Rp = par == l - 1 ? R_prev : wm3(tp, NWT, par, W_R);
-      const SV<T> vp = par == l - 1 ? v_prev : wsv(tp, NWT, par, W_V);
+      M3<T> Rp = R_prev;
+      SV<T> vp = v_prev;
+      if (par != l - 1) {  // a later child of a branching link: its values on the stack top
+        Rp = wm3(s.stk, WSW, sp - 1, 0);
+        vp = wsv(s.stk, WSW, sp - 1, 9);
+        if (meta_lastsib(m)) --sp;
+      }
       const V3<T> d = mul(Rp, V3<T>{s.P(l, P_R), s.P(l, P_R + 1), s.P(l, P_R + 2)});
       R = mmT(Rp, E);
       v = SV<T>{vp.w + vl * col2(R), vp.v - cross(d, vp.w)};
@@ -263,8 +277,9 @@ SD void wstep_forward(const WSys<T>& s, Col<const T> q, Col<const T> qd, Col<con
       s.tp(l, W_SC + 1) = cs;
     }
     if (meta_treechild(m)) {
-      wsi(tp, NWT, l, W_IA, zeroSI<T>());
-      wsv(tp, NWT, l, W_PA, zeroSV<T>());
+      wm3(s.stk, WSW, sp, 0, R);
+      wsv(s.stk, WSW, sp, 9, v);
+      ++sp;
     }
     R_prev = R;
     v_prev = v;
@@ -300,9 +315,10 @@ SD void wstep_forward(const WSys<T>& s, Col<const T> q, Col<const T> qd, Col<con
       IA += cI;
       pA += cp;
     }
-    if (meta_treechild(m)) {
-      IA += wsi(tp, NWT, l, W_IA);
-      pA += wsv(tp, NWT, l, W_PA);
+    if (meta_treechild(m)) {  // the contributions of the children after link l + 1
+      --sp;
+      IA += wsi(s.stk, WSW, sp, 0);
+      pA += wsv(s.stk, WSW, sp, 21);
     }
     carry = false;
     const SV<T> U{mul(IA.A, sx), mulT(IA.B, sx)};
@@ -330,9 +346,13 @@ SD void wstep_forward(const WSys<T>& s, Col<const T> q, Col<const T> qd, Col<con
         cI = Y;
         cp = pn;
         carry = true;
+      } else if (meta_lastsib(m)) {
+        wsi(s.stk, WSW, sp, 0, Y);
+        wsv(s.stk, WSW, sp, 21, pn);
+        ++sp;
       } else {
-        wsi(tp, NWT, par, W_IA, wsi(tp, NWT, par, W_IA) + Y);
-        wsv(tp, NWT, par, W_PA, wsv(tp, NWT, par, W_PA) + pn);
+        wsi(s.stk, WSW, sp - 1, 0, wsi(s.stk, WSW, sp - 1, 0) + Y);
+        wsv(s.stk, WSW, sp - 1, 21, wsv(s.stk, WSW, sp - 1, 21) + pn);
       }
     }
   }
@@ -356,21 +376,23 @@ SD void wstep_forward(const WSys<T>& s, Col<const T> q, Col<const T> qd, Col<con
     if (par < 0) {
       ap = a0 + c;
     } else {
-      SV<T> apar;
-      if (par == l - 1) {
-        apar = a_prev;
-      } else {
-        apar = wsv(tp, NWT, par, W_AP);
-        apar.w += s.tp(par, W_QDD) * col2(wm3(tp, NWT, par, W_R));
+      SV<T> apar = a_prev;
+      if (par != l - 1) {
+        apar = wsv(s.stk, WSW, sp - 1, 0);
+        if (meta_lastsib(m)) --sp;
       }
       const V3<T> d = wv3(tp, NWT, l, W_D);
       ap = SV<T>{apar.w + c.w, apar.v - cross(d, apar.w) + c.v};
     }
     const T qdd = (T)(((DT)u - (DT)dot(U, ap)) * Di);
     const SV<T> a{ap.w + qdd * col2(R), ap.v};
-    if (ADJ || meta_treechild(m)) {
+    if (ADJ) {
       wsv(tp, NWT, l, W_AP, ap);
       s.tp(l, W_QDD) = qdd;
+    }
+    if (meta_treechild(m)) {
+      wsv(s.stk, WSW, sp, 0, a);
+      ++sp;
     }
     if (INTEG) {
       const int qi = meta_qoff(m), vi = meta_voff(m);
@@ -398,15 +420,15 @@ SD void wstep_adjoint(const WSys<T>& s, Col<const T> q, Col<const T> qd, Col<T> 
   T* ad = s.adj;
   const int nl = s.nl;
   const T half = T(0.5);
-  for (int l = 0; l < nl; ++l)
-    if (meta_treechild(s.M(l))) wsv(ad, NWA, l, WA_ACC, zeroSV<T>());
   // integrator + acceleration pass adjoint (leaves -> root)
   {
     SV<T> cab = zeroSV<T>();
     bool carry = false;
+    int sp = 0;
     for (int l = nl - 1; l >= 0; --l) {
       if (s.pf > 0 && l - s.pf >= 0) {
         pf_fields(tp, NWT, l - s.pf, W_R, 9);
+        pf_fields(tp, NWT, l - s.pf, W_C, 3);
         pf_fields(tp, NWT, l - s.pf, W_U, W_u - W_U);
         pf_fields(tp, NWT, l - s.pf, W_AP, W_SC - W_AP);
         pf_fields(tp, NWT, l - s.pf, W_D, 3);
@@ -425,9 +447,12 @@ SD void wstep_adjoint(const WSys<T>& s, Col<const T> q, Col<const T> qd, Col<T> 
           qddb = dt * vb;
         }
       }
-      SV<T> ab = meta_treechild(m) ? wsv(ad, NWA, l, WA_ACC) : zeroSV<T>();
-      if (carry) ab += cab;
+      SV<T> ab = carry ? cab : zeroSV<T>();
       carry = false;
+      if (meta_treechild(m)) {
+        --sp;
+        ab += wsv(s.stk, WSW, sp, 0);
+      }
       const V3<T> sx = col2(wm3(tp, NWT, l, W_R));
       const T qdd = s.tp(l, W_QDD);
       const SV<T> ap = wsv(tp, NWT, l, W_AP);
@@ -444,15 +469,17 @@ SD void wstep_adjoint(const WSys<T>& s, Col<const T> q, Col<const T> qd, Col<T> 
       V3<T> db = zero3<T>();
       if (par >= 0) {
         const V3<T> d = wv3(tp, NWT, l, W_D);
-        SV<T> apar = wsv(tp, NWT, par, W_AP);
-        apar.w += s.tp(par, W_QDD) * col2(wm3(tp, NWT, par, W_R));
+        const V3<T> apw = ap.w - wv3(tp, NWT, l, W_C);  // the parent's angular acceleration: a'.w = a_p.w + c.w
         const SV<T> aparb{apb.w + cross(d, apb.v), apb.v};
-        db = cross(apb.v, apar.w);
+        db = cross(apb.v, apw);
         if (par == l - 1) {
           cab = aparb;
           carry = true;
+        } else if (meta_lastsib(m)) {
+          wsv(s.stk, WSW, sp, 0, aparb);
+          ++sp;
         } else {
-          wsv(ad, NWA, par, WA_ACC, wsv(ad, NWA, par, WA_ACC) + aparb);
+          wsv(s.stk, WSW, sp - 1, 0, wsv(s.stk, WSW, sp - 1, 0) + aparb);
         }
       }
       wv3(ad, NWA, l, WA_DD, db);
@@ -463,11 +490,12 @@ SD void wstep_adjoint(const WSys<T>& s, Col<const T> q, Col<const T> qd, Col<T> 
   {
     SI<T> cIAb = zeroSI<T>();
     SV<T> cpAb = zeroSV<T>();
+    int sp = 0;
     for (int l = 0; l < nl; ++l) {
       if (s.pf > 0 && l + s.pf < nl) {
         pf_fields(tp, NWT, l + s.pf, W_R, W_AP - W_R);
         pf_fields(tp, NWT, l + s.pf, W_D, 3);
-        pf_fields(ad, NWA, l + s.pf, WA_U, WA_ACC - WA_U);
+        pf_fields(ad, NWA, l + s.pf, WA_U, NWA - WA_U);
         pf_fields(s.prm, s.pstride, l + s.pf, P_M, NPRM_W - P_M);
       }
       const int m = s.M(l);
@@ -491,8 +519,13 @@ SD void wstep_adjoint(const WSys<T>& s, Col<const T> q, Col<const T> qd, Col<T> 
       SI<T> IAb = zeroSI<T>();
       SV<T> pAb = zeroSV<T>();
       if (par >= 0) {
-        const SI<T> IAbp = par == l - 1 ? cIAb : wsi(ad, NWA, par, WA_IAB);
-        const SV<T> pAbp = par == l - 1 ? cpAb : wsv(ad, NWA, par, WA_PAB);
+        SI<T> IAbp = cIAb;
+        SV<T> pAbp = cpAb;
+        if (par != l - 1) {
+          IAbp = wsi(s.stk, WSW, sp - 1, 0);
+          pAbp = wsv(s.stk, WSW, sp - 1, 21);
+          if (meta_lastsib(m)) --sp;
+        }
         const SI<T> Ia = minus_scaled_outer<T, DT>(IA, Di, U);
         const SV<T> pa = pA + mul(Ia, c) + (T)((DT)u * Di) * U;
         const V3<T> d = wv3(tp, NWT, l, W_D);
@@ -525,10 +558,9 @@ SD void wstep_adjoint(const WSys<T>& s, Col<const T> q, Col<const T> qd, Col<T> 
       IAb.B += scale(half, outer(sx, Ub.v));
       sb += mul(IA.A, Ub.w) + mul(IA.B, Ub.v);
       if (tc) {
-        wsi(ad, NWA, l, WA_IAB, IAb);
-        wsv(ad, NWA, l, WA_PAB, pAb);
-        wsv(ad, NWA, l, WA_ACC, zeroSV<T>());
-        wm3(ad, NWA, l, WA_RACC, zeroM3<T>());
+        wsi(s.stk, WSW, sp, 0, IAb);
+        wsv(s.stk, WSW, sp, 21, pAb);
+        ++sp;
       }
       cIAb = IAb;
       cpAb = pAb;
@@ -574,6 +606,7 @@ SD void wstep_adjoint(const WSys<T>& s, Col<const T> q, Col<const T> qd, Col<T> 
     SV<T> cvb = zeroSV<T>();
     M3<T> cRb = zeroM3<T>();
     bool carry = false;
+    int sp = 0;
     for (int l = nl - 1; l >= 0; --l) {
       if (s.pf > 0 && l - s.pf >= 0) {
         pf_fields(tp, NWT, l - s.pf, W_R, 15);
@@ -588,19 +621,21 @@ SD void wstep_adjoint(const WSys<T>& s, Col<const T> q, Col<const T> qd, Col<T> 
       M3<T> Rb = wm3(tp, NWT, l, W_IA + 6);
       V3<T> sb = wv3(ad, NWA, l, WA_S);
       V3<T> db = wv3(ad, NWA, l, WA_DD);
-      if (meta_treechild(m)) {
-        vb += wsv(ad, NWA, l, WA_ACC);
-        Rb += wm3(ad, NWA, l, WA_RACC);
-      }
       if (carry) {
         vb += cvb;
         Rb += cRb;
       }
       carry = false;
+      if (meta_treechild(m)) {
+        --sp;
+        vb += wsv(s.stk, WSW, sp, 0);
+        Rb += wm3(s.stk, WSW, sp, 6);
+      }
       const M3<T> R = wm3(tp, NWT, l, W_R);
       const V3<T> sx = col2(R);
+      const T vl = qd[vi];
       // v = [v_p.w + s qd; v_p.v - d x v_p.w]
-      sb += qd[vi] * vb.w;
+      sb += vl * vb.w;
       gqd[vi] += dot(sx, vb.w);
       // s = R e_z
       Rb.a[2] += sb.x;
@@ -611,14 +646,15 @@ SD void wstep_adjoint(const WSys<T>& s, Col<const T> q, Col<const T> qd, Col<T> 
       for (int i = 0; i < 9; ++i) Et.a[i] = s.P(l, P_E + i);
       M3<T> Eb;
       if (par >= 0) {
-        const M3<T> Rp = wm3(tp, NWT, par, W_R);
-        const SV<T> vp = wsv(tp, NWT, par, W_V);
+        // R = R_p E^T, d = R_p r; the parent's orientation and angular velocity
+        // from the link's own: R_p = R E, v_p.w = v.w - s qd
+        const M3<T> E = rotz_T_mm(sn, cs, Et);
+        const M3<T> Rp = mm(R, E);
+        const V3<T> vpw = wv3(tp, NWT, l, W_V) - vl * sx;
         const V3<T> rt{s.P(l, P_R), s.P(l, P_R + 1), s.P(l, P_R + 2)};
         const V3<T> d = wv3(tp, NWT, l, W_D);
         const SV<T> vpb{vb.w + cross(d, vb.v), vb.v};
-        db += cross(vb.v, vp.w);
-        // R = R_p E^T, d = R_p r
-        const M3<T> E = rotz_T_mm(sn, cs, Et);
+        db += cross(vb.v, vpw);
         M3<T> Rpb = mm(Rb, E);
         Rpb += outer(db, rt);
         Eb = mTm(Rb, Rp);
@@ -626,9 +662,13 @@ SD void wstep_adjoint(const WSys<T>& s, Col<const T> q, Col<const T> qd, Col<T> 
           cvb = vpb;
           cRb = Rpb;
           carry = true;
+        } else if (meta_lastsib(m)) {
+          wsv(s.stk, WSW, sp, 0, vpb);
+          wm3(s.stk, WSW, sp, 6, Rpb);
+          ++sp;
         } else {
-          wsv(ad, NWA, par, WA_ACC, wsv(ad, NWA, par, WA_ACC) + vpb);
-          wm3(ad, NWA, par, WA_RACC, wm3(ad, NWA, par, WA_RACC) + Rpb);
+          wsv(s.stk, WSW, sp - 1, 0, wsv(s.stk, WSW, sp - 1, 0) + vpb);
+          wm3(s.stk, WSW, sp - 1, 6, wm3(s.stk, WSW, sp - 1, 6) + Rpb);
         }
       } else {
         Eb = transpose(Rb);

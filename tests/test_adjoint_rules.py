@@ -111,9 +111,13 @@ def test_world_aligned_step(tmp_path):
     """The world-aligned formulation of the step (host build, FP64): its joint
     accelerations equal the link-frame step's to rounding, and its adjoint matches
     central differences of its own forward step in q, qd, tau and the masses along
-    random directions and along each block alone (chains, branched trees,
-    damping, both integrators).  A 0.1 % error planted in one adjoint term shows
-    as 5e-7 to 6e-5 here."""
+    random directions and along each block alone (chains, branched trees, random
+    trees, a forest, a star, a caterpillar whose stack of parent values is 8 deep,
+    damping, both integrators).  The models are stored in the library's
+    depth-first order with a stack exactly as deep as that order says, followed by
+    NaN guard entries that must stay untouched; the order's own invariants are
+    checked on random trees and forests.  A 0.1 % error planted in one
+    adjoint term shows as 5e-7 to 6e-5 here."""
     cxx = shutil.which("g++")
     if cxx is None:
         pytest.skip("no host C++ compiler")
@@ -121,8 +125,16 @@ def test_world_aligned_step(tmp_path):
     subprocess.run([cxx, "-O1", "-std=c++17", "-o", str(exe), os.path.join(HERE, "wstep_check.cpp")], check=True)
     out = subprocess.run([str(exe)], check=True, capture_output=True, text=True).stdout
     res = {line.split()[0]: float(line.split()[1]) for line in out.strip().splitlines()}
-    cases = {"chain", "damped_chain", "branched_tree", "tree_explicit", "single_link"}
-    assert set(res) == {f"{k}_{c}" for k in ("forward", "adjoint") for c in cases}
+    cases = {"chain", "damped_chain", "branched_tree", "tree_explicit", "single_link", "two_roots",
+             "random_tree_bf2", "random_tree_bf3", "star", "caterpillar"}
+    assert set(res) == {f"{k}_{c}" for k in ("forward", "adjoint", "depth", "guards") for c in cases} | {
+        "order_invariants"}
+    assert res["order_invariants"] == 1
     for c in cases:
         assert res[f"forward_{c}"] < 1e-13, (c, res[f"forward_{c}"])
         assert res[f"adjoint_{c}"] < 1e-7, (c, res[f"adjoint_{c}"])
+        assert res[f"guards_{c}"] == 1, c
+    depth = {"chain": 0, "damped_chain": 0, "single_link": 0, "branched_tree": 2, "star": 1, "two_roots": 1,
+             "caterpillar": 8}
+    for c, d in depth.items():
+        assert res[f"depth_{c}"] == d, (c, res[f"depth_{c}"])

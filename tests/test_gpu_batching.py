@@ -84,7 +84,7 @@ def test_autotune_keeps_results(tmp_path, monkeypatch):
     work, sim, q0, qd0, tau = _setup()
     from paper_2109_07719_gb300 import autotune as at
     best = sim.autotune(q0, qd0, T_probe=4, reps=1)
-    assert best[2] in (1, 3, 4) and best in at.CANDIDATES   # trees: not the link-frame pipelined kernels
+    assert best[2] in (1, 3, 4, 5) and best in at.CANDIDATES   # trees: not the link-frame pipelined kernels
     out = _run(sim, q0, qd0, tau)
     sim.set_launch(32, False)                               # the same kernels at the default shape
     ref = _run(sim, q0, qd0, tau)

@@ -5,6 +5,10 @@
 // (2) its adjoint (wstep_adjoint) against central differences of its own
 //     forward step (with the integrator) in q, qd, tau and the link masses,
 //     for serial chains, branched trees, damping and both integrators.
+// Models are stored as the library stores them: links in depth-first preorder
+// (csrc/tree_order.h), the branching flags in the meta words and a stack of
+// parent values exactly as deep as the order needs, with NaN guard entries after
+// it (a pass that overran the stack would read them back).
 // Prints: case name, max relative error.
 #include <cmath>
 #include <cstdio>
@@ -12,6 +16,7 @@
 #include <random>
 #include <vector>
 
+#include "../paper_2109_07719_gb300/csrc/tree_order.h"
 #include "../paper_2109_07719_gb300/csrc/wstep.cuh"
 
 using namespace abasim;
@@ -20,19 +25,23 @@ using D = double;
 static std::mt19937_64 rng(2109077191);
 static D U(D lo = -1, D hi = 1) { return std::uniform_real_distribution<D>(lo, hi)(rng); }
 
-constexpr int MAXL = 12;
+constexpr int MAXL = 40;
 static D prm[MAXL * NPRM * LANES], tape[MAXL * NTAPE * LANES], adjw[MAXL * NADJ * LANES];
 static D wtape[MAXL * NWT * LANES], wadj[MAXL * NWA * LANES];
 static int meta[MAXL * LANES];
+static std::vector<D> wstk;  // depth + 2 guard entries, [entry][WSW][LANES]
 
 struct Model {
-  int n = 0, integ = I_SEMI_IMPLICIT;
-  std::vector<int> parent;
+  int n = 0, integ = I_SEMI_IMPLICIT, depth = 0;
+  std::vector<int> parent;  // in stored (preorder) numbering
 };
 
-static void build(Model& md, const std::vector<int>& parent, bool damping) {
-  md.parent = parent;
-  md.n = (int)parent.size();
+static void build(Model& md, const std::vector<int>& model_parent, bool damping) {
+  const TreeOrder to = tree_order(model_parent.data(), (int)model_parent.size());
+  md.parent = to.parent;
+  md.n = (int)model_parent.size();
+  md.depth = to.depth;
+  wstk.assign((size_t)(md.depth + 2) * WSW * LANES, std::nan(""));
   std::memset(prm, 0, sizeof prm);
   for (int l = 0; l < md.n; ++l) {
     auto P = [&](int f) -> D& { return prm[(l * NPRM + f) * LANES]; };
@@ -50,17 +59,25 @@ static void build(Model& md, const std::vector<int>& parent, bool damping) {
     const D ic[6] = {U(0.05, 0.15), U(0.05, 0.15), U(0.05, 0.15), U(-0.01, 0.01), U(-0.01, 0.01), U(-0.01, 0.01)};
     for (int i = 0; i < 6; ++i) P(P_IC + i) = ic[i];
     P(P_DAMP) = damping ? U(0.0, 0.5) : 0.0;
-    bool treechild = false;
-    for (int c = l + 2; c < md.n; ++c)
-      if (parent[c] == l) treechild = true;
-    meta[l * LANES] = make_meta(parent[l], J_REVOLUTE, treechild, l, l);
+    meta[l * LANES] = make_meta(to.parent[l], J_REVOLUTE, to.branch[l], l, l, to.lastsib[l]);
   }
+}
+
+// the stack guard entries still NaN: no pass went past the depth the order gives
+static bool guards_intact(const Model& md) {
+  for (size_t i = (size_t)md.depth * WSW * LANES; i < wstk.size(); ++i)
+    if (!std::isnan(wstk[i])) return false;
+  return true;
 }
 
 static const V3<D> kGrav{0, 0, -9.81};
 static const D kDt = 1e-3;
 
-static WSys<D> wsys(const Model& md) { return WSys<D>{prm, meta, wtape, wadj, md.n}; }
+static WSys<D> wsys(const Model& md) {
+  WSys<D> s{prm, meta, wtape, wadj, md.n};
+  s.stk = wstk.data();
+  return s;
+}
 
 // (1) joint accelerations of both formulations from random states
 static D forward_agreement(const Model& md, int trials = 8) {
@@ -150,14 +167,94 @@ static D adjoint_check(const Model& md, int trials = 12) {
   return worst;
 }
 
+// a random tree: each new link attaches to a uniformly drawn earlier link that has
+// fewer than bf children
+static std::vector<int> random_tree(int n, int bf) {
+  std::vector<int> parent{-1}, kids(n, 0), open{0};
+  for (int i = 1; i < n; ++i) {
+    const int j = std::min((int)(U(0, 1) * open.size()), (int)open.size() - 1);
+    const int p = open[j];
+    parent.push_back(p);
+    if (++kids[p] >= bf) open.erase(open.begin() + j);
+    open.push_back(i);
+  }
+  return parent;
+}
+
+// the order's invariants on random trees and forests of 1..64 links: parents
+// before children, contiguous subtrees, a link's first child at l + 1, and stack
+// traffic that never pops an empty stack nor reads a missing top, ends empty and
+// peaks at the depth the order reports, in both directions
+static bool order_invariants() {
+  for (int trial = 0; trial < 300; ++trial) {
+    const int n = 1 + trial % 64, bf = 1 + trial % 3;
+    std::vector<int> parent = random_tree(n, bf);
+    if (trial % 7 == 0)
+      for (int l = 1; l < n; l += 5) parent[l] = -1;  // a forest
+    const TreeOrder t = tree_order(parent.data(), n);
+    std::vector<int> seen(n, 0), size(n, 1);
+    for (int l = 0; l < n; ++l) {
+      if (t.pos[t.perm[l]] != l || seen[t.perm[l]]++) return false;
+      const int p = t.parent[l];
+      if (p >= l || (p >= 0 && parent[t.perm[l]] != t.perm[p]) || (p < 0 && parent[t.perm[l]] >= 0)) return false;
+    }
+    for (int l = n - 1; l > 0; --l)
+      if (t.parent[l] >= 0) size[t.parent[l]] += size[l];
+    for (int l = 0; l < n; ++l) {
+      int kids = 0;
+      for (int c = l + 1; c < n; ++c) {
+        const bool inside = c < l + size[l];
+        int a = c;
+        while (a > l) a = t.parent[a];
+        if ((a == l) != inside) return false;  // the subtree of l is exactly [l, l + size)
+        if (t.parent[c] == l) {
+          if (kids++ == 0 && c != l + 1) return false;
+        }
+      }
+      if ((kids > 1) != (bool)t.branch[l]) return false;
+    }
+    int sp = 0, peak = 0;
+    for (int l = 0; l < n; ++l) {  // outward: read (and on the last child pop) the top, then push
+      const int p = t.parent[l];
+      if (p >= 0 && p != l - 1 && sp == 0) return false;
+      if (t.lastsib[l]) --sp;
+      if (t.branch[l]) peak = std::max(peak, ++sp);
+    }
+    if (sp != 0 || peak != t.depth) return false;
+    peak = 0;
+    for (int l = n - 1; l >= 0; --l) {  // inward: pop the own entry, then push or add for the parent
+      if (t.branch[l] && sp-- == 0) return false;
+      const int p = t.parent[l];
+      if (p >= 0 && p != l - 1) {
+        if (t.lastsib[l]) peak = std::max(peak, ++sp);
+        else if (sp == 0) return false;
+      }
+    }
+    if (sp != 0 || peak != t.depth) return false;
+  }
+  return true;
+}
+
 int main() {
+  std::printf("order_invariants %d\n", order_invariants() ? 1 : 0);
   struct Case { const char* name; std::vector<int> parent; bool damping; int integ; };
+  // a caterpillar: spine links 0..8, then a leaf on each; a spine link's first
+  // child continues the spine and its leaf comes later, so the stack grows with
+  // the spine (depth 8)
+  std::vector<int> cat{-1};
+  for (int i = 1; i < 9; ++i) cat.push_back(i - 1);
+  for (int i = 0; i < 9; ++i) cat.push_back(i);
   const Case cases[] = {
       {"chain", {-1, 0, 1, 2, 3, 4, 5}, false, I_SEMI_IMPLICIT},
       {"damped_chain", {-1, 0, 1, 2, 3}, true, I_SEMI_IMPLICIT},
       {"branched_tree", {-1, 0, 1, 0, 3, 3, 1, 6, 2}, false, I_SEMI_IMPLICIT},
       {"tree_explicit", {-1, 0, 0, 1, 1, 2, 2}, true, I_EXPLICIT},
       {"single_link", {-1}, true, I_SEMI_IMPLICIT},
+      {"two_roots", {-1, 0, -1, 2, 2, 0}, true, I_SEMI_IMPLICIT},
+      {"random_tree_bf2", random_tree(24, 2), false, I_SEMI_IMPLICIT},
+      {"random_tree_bf3", random_tree(32, 3), true, I_SEMI_IMPLICIT},
+      {"star", {-1, 0, 0, 0, 0, 0, 0}, false, I_EXPLICIT},
+      {"caterpillar", cat, true, I_SEMI_IMPLICIT},
   };
   for (const Case& c : cases) {
     Model md;
@@ -165,6 +262,8 @@ int main() {
     md.integ = c.integ;
     std::printf("forward_%s %.3e\n", c.name, forward_agreement(md));
     std::printf("adjoint_%s %.3e\n", c.name, adjoint_check(md));
+    std::printf("depth_%s %d\n", c.name, md.depth);
+    std::printf("guards_%s %d\n", c.name, guards_intact(md) ? 1 : 0);
   }
   return 0;
 }
