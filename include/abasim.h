@@ -277,7 +277,11 @@ int sim_set_launch(sim_handle* h, int32_t threads, int32_t schedule);
  * rotating and translating them (each body's inertia is rotated into world axes
  * once per step, off that serial chain).  Tape and adjoint record in shared
  * memory when a block's tiles fit, else in the handle's global scratch (whose
- * lines each pass prefetches two links ahead).  AUTO picks these kernels for such
+ * lines each pass prefetches sim_set_prefetch links ahead).  Links are stored in
+ * depth-first preorder; the values a branching link hands to or collects from
+ * its later children live on a per-system stack (in shared memory with an
+ * on-chip tape, else in a handle buffer) as deep as the nesting of branchings.
+ * AUTO picks these kernels for such
  * models, except where the pipelined kernels apply (serial chains short enough
  * for their on-chip tapes) and where a system's state and input streams exceed a
  * block's shared memory; forcing them on another model fails with

@@ -19,7 +19,8 @@ namespace host {
 // inputs (tau, plus x^t for the adjoint) fetched one step ahead.  Without ONCHIP
 // the stack is in the handle's global scratch and the inputs are read from global
 // memory with their lines prefetched a step ahead, and the small shared-memory
-// footprint leaves most of the SM's L1 to the prefetched tape lines.
+// footprint leaves most of the SM's L1 to the prefetched tape lines (staging the
+// inputs on chip instead cost more in L1 than it saved in misses).
 __host__ __device__ __forceinline__ long long w_smem_per_tile(int maxL, int nx, int nv, bool bwd, bool onchip,
                                                               int sd) {
   const long long state = nx + (bwd ? maxL : 0);
@@ -185,7 +186,7 @@ __device__ __forceinline__ void wbackward_one(const DevModel<T>& m, int slot, co
   auto step_back = [&](long long t, Col<const T> q, Col<const T> qd, Col<const T> tau_t) {
     wstep_forward<T, DT, true, false>(s, q, qd, tau_t, g, m.dt, m.integ, Col<T>{nullptr, 0}, Col<T>{nullptr, 0});
     T* gt = gtau + t * nvm * B + b;
-    wstep_adjoint<T, DT>(s, q, qd, gq, gqd, Col<T>{gt, B}, gm, m.dt, m.integ);
+    wstep_adjoint<T, DT>(s, gq, gqd, Col<T>{gt, B}, gm, m.dt, m.integ);
     for (int d = nv; d < nvm; ++d) gt[d * B] = T(0);
     if (gtraj) {
       const T* gx = gtraj + t * NX * B + b;

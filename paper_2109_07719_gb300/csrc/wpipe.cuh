@@ -20,12 +20,13 @@ namespace host {
 
 // Scalars per tile: the state adjoint and per-link mass-gradient sums; with
 // ONCHIP also both tapes, the adjoint record, model constants and meta words, the
-// two warps' stacks of parent values (sd scalars per system each), the consumer's
-// copy of x^t and the producer's double-buffered (x^t, tau^t).
+// two warps' stacks of parent values (sd scalars per system each) and the
+// producer's double-buffered inputs (x^t, tau^t).  Without ONCHIP the producer
+// reads its inputs from global memory, their lines prefetched a step ahead.
 __host__ __device__ __forceinline__ long long wpipe_smem_per_tile(int maxL, int nx, int nv, bool onchip, int sd) {
   const long long state = nx + maxL;
   if (!onchip) return state;
-  return (long long)maxL * (2 * NWT + NWA + NPRM_W + 1) + 2LL * sd + state + nx + 2LL * (nx + nv);
+  return (long long)maxL * (2 * NWT + NWA + NPRM_W + 1) + 2LL * sd + state + 2LL * (nx + nv);
 }
 
 template <class T, class DT, bool ONCHIP>
@@ -41,7 +42,7 @@ k_wbackward_pipe(DevModel<T> m, const T* __restrict__ ckpt, const T* __restrict_
   const V3<T> g{m.g0, m.g1, m.g2};
   constexpr int MS = (int)(sizeof(T) / sizeof(int));
   T* base = reinterpret_cast<T*>(g_smem);
-  T *s_tape = nullptr, *s_adj = nullptr, *s_prm = nullptr, *s_meta = nullptr, *s_x = nullptr, *s_in = nullptr;
+  T *s_tape = nullptr, *s_adj = nullptr, *s_prm = nullptr, *s_meta = nullptr, *s_in = nullptr;
   T* s_stk = nullptr;
   const long long sdw = (long long)m.wdepth * WSW;  // stack scalars per system
   if (ONCHIP) {
@@ -58,10 +59,7 @@ k_wbackward_pipe(DevModel<T> m, const T* __restrict__ ckpt, const T* __restrict_
   }
   T* s_state = base;
   T* s_gm = s_state + (long long)NX * LANES;
-  if (ONCHIP) {
-    s_x = s_gm + L * LANES;
-    s_in = s_x + (long long)NX * LANES;  // [2][NX + nvm][LANES]
-  }
+  if (ONCHIP) s_in = s_gm + L * LANES;  // [2][NX + nvm][LANES]
   const int W = NX + nvm;
   int unit = m.persistent ? next_unit(m.counter) : (int)blockIdx.x;
   while ((long long)unit * LANES < B) {
@@ -92,11 +90,12 @@ k_wbackward_pipe(DevModel<T> m, const T* __restrict__ ckpt, const T* __restrict_
       return WSys<T>{gprm, gmeta, tape_of(buf), m.adj + (long long)unit * L * NWA * LANES + lane, nl, 1, NPRM, m.pf,
                      w_stack(m, who, unit, lane)};
     };
-    // the producer's inputs of step t: x^t and tau^t, fetched one step ahead
+    // the producer's inputs of step t: x^t and tau^t (the system's own coordinates)
     auto fetch = [&](long long t, int buf) {
       T* dst = s_in + buf * W * LANES + lane;
-      for (int d = 0; d < NX; ++d) cp_async(dst + d * LANES, ckpt + (t * NX + d) * B + b);
-      for (int d = 0; d < nvm; ++d) cp_async(dst + (NX + d) * LANES, tau + (t * nvm + d) * B + b);
+      for (int d = 0; d < nq; ++d) cp_async(dst + d * LANES, ckpt + (t * NX + d) * B + b);
+      for (int d = 0; d < nv; ++d) cp_async(dst + (nqm + d) * LANES, ckpt + (t * NX + nqm + d) * B + b);
+      for (int d = 0; d < nv; ++d) cp_async(dst + (NX + d) * LANES, tau + (t * nvm + d) * B + b);
     };
     if (ONCHIP && !consumer) {
       if (act && Tn > 0) fetch(Tn - 1, (int)((Tn - 1) & 1));
@@ -149,20 +148,12 @@ k_wbackward_pipe(DevModel<T> m, const T* __restrict__ ckpt, const T* __restrict_
         __syncwarp();
         pair_arrive_full(buf);
       } else {  // consumer: the adjoint of step t from tape t & 1
-        if (ONCHIP) {
-          if (act)
-            for (int d = 0; d < NX; ++d) cp_async(s_x + d * LANES + lane, ckpt + (t * NX + d) * B + b);
-          cp_commit();
-        }
         __syncwarp();
         pair_sync_full(buf);
-        if (ONCHIP) cp_wait_all();
         if (act) {
           const WSys<T> sc = sys_of_buf(buf);
-          const Col<const T> qd = ONCHIP ? Col<const T>{s_x + nqm * LANES + lane, LANES}
-                                         : Col<const T>{ckpt + (t * NX + nqm) * B + b, B};
           T* gt = gtau + t * nvm * B + b;
-          wstep_adjoint<T, DT>(sc, Col<const T>{nullptr, 0}, qd, gq, gqd, Col<T>{gt, B}, gm, m.dt, m.integ);
+          wstep_adjoint<T, DT>(sc, gq, gqd, Col<T>{gt, B}, gm, m.dt, m.integ);
           for (int d = nv; d < nvm; ++d) gt[d * B] = T(0);
           if (gtraj) {
             const T* gx = gtraj + t * NX * B + b;

@@ -48,12 +48,12 @@ namespace abasim {
 
 // Per-link tape of the world-aligned step, [link][field][lane]: orientation R,
 // velocity v, velocity-product term c, U, 1/D (hi/lo pair), u, the articulated
-// inertia and bias force after the children's contributions (I^A, p^A; for a link
-// with a child other than link l + 1 also the accumulator of those
-// contributions), a' and qdd, the joint's sin/cos, and the joint offset d.
+// inertia and bias force after the children's contributions (I^A, p^A), a' and
+// qdd, the joint's sin/cos, the joint offset d and the joint rate qd (so that the
+// adjoint reads every per-link value from its own tape words).
 enum : int {
   W_R = 0, W_V = 9, W_C = 15, W_U = 21, W_DI = 27, W_u = 29, W_IA = 30, W_PA = 51, W_AP = 57, W_QDD = 63,
-  W_SC = 64, W_D = 66, NWT = 69
+  W_SC = 64, W_D = 66, W_QD = 69, NWT = 70
 };
 // Per-link adjoint record, [link][field][lane]: from the acceleration pass's
 // adjoint, the adjoints of U, D, u and c; the adjoints of s and d (completed by
@@ -275,6 +275,7 @@ SD void wstep_forward(const WSys<T>& s, Col<const T> q, Col<const T> qd, Col<con
     if (ADJ) {
       s.tp(l, W_SC) = sn;
       s.tp(l, W_SC + 1) = cs;
+      s.tp(l, W_QD) = vl;
     }
     if (meta_treechild(m)) {
       wm3(s.stk, WSW, sp, 0, R);
@@ -414,7 +415,7 @@ SD void wstep_forward(const WSys<T>& s, Col<const T> q, Col<const T> qd, Col<con
 // adjoint with the per-link inertia and velocity-product adjoints (root -> leaves),
 // the velocity and orientation adjoint and the joint angles' (leaves -> root).
 template <class T, class DT>
-SD void wstep_adjoint(const WSys<T>& s, Col<const T> q, Col<const T> qd, Col<T> gq, Col<T> gqd, Col<T> gtau,
+SD void wstep_adjoint(const WSys<T>& s, Col<T> gq, Col<T> gqd, Col<T> gtau,
                       Col<T> gm, T dt, int integ) {
   T* tp = s.tape;
   T* ad = s.adj;
@@ -486,21 +487,33 @@ SD void wstep_adjoint(const WSys<T>& s, Col<const T> q, Col<const T> qd, Col<T> 
     }
   }
   // articulated-inertia adjoint (root -> leaves) with each link's inertia,
-  // bias-force and velocity-product adjoints
+  // bias-force and velocity-product adjoints.  Each link's work has a part on the
+  // chain (from its parent's adjoints of I^A and p^A to its own, which its children
+  // need) and a per-link part that nothing downstream in this pass waits for; the
+  // loop runs link l's chain part beside link l - 1's per-link part, so that one
+  // thread has two independent instruction streams (the same arithmetic in the
+  // same order per link as running the two parts back to back).
   {
     SI<T> cIAb = zeroSI<T>();
     SV<T> cpAb = zeroSV<T>();
     int sp = 0;
-    for (int l = 0; l < nl; ++l) {
+    struct Chain {  // a link's state between its two parts
+      SI<T> IAb;
+      SV<T> pAb, cb, v;
+      V3<T> sb, db;
+      M3<T> R;
+      int vi;
+      bool tc;
+    };
+    auto chain_part = [&](int l) -> Chain {
       if (s.pf > 0 && l + s.pf < nl) {
         pf_fields(tp, NWT, l + s.pf, W_R, W_AP - W_R);
-        pf_fields(tp, NWT, l + s.pf, W_D, 3);
+        pf_fields(tp, NWT, l + s.pf, W_D, 4);
         pf_fields(ad, NWA, l + s.pf, WA_U, NWA - WA_U);
         pf_fields(s.prm, s.pstride, l + s.pf, P_M, NPRM_W - P_M);
       }
       const int m = s.M(l);
       const int par = meta_parent(m), vi = meta_voff(m);
-      const bool tc = meta_treechild(m);
       const SI<T> IA = wsi(tp, NWT, l, W_IA);
       const SV<T> pA = wsv(tp, NWT, l, W_PA);
       const SV<T> U = wsv(tp, NWT, l, W_U);
@@ -516,37 +529,39 @@ SD void wstep_adjoint(const WSys<T>& s, Col<const T> q, Col<const T> qd, Col<T> 
       SV<T> cb = wsv(ad, NWA, l, WA_C);
       V3<T> sb = wv3(ad, NWA, l, WA_S);
       V3<T> db = wv3(ad, NWA, l, WA_DD);
-      SI<T> IAb = zeroSI<T>();
-      SV<T> pAb = zeroSV<T>();
-      if (par >= 0) {
-        SI<T> IAbp = cIAb;
-        SV<T> pAbp = cpAb;
-        if (par != l - 1) {
-          IAbp = wsi(s.stk, WSW, sp - 1, 0);
-          pAbp = wsv(s.stk, WSW, sp - 1, 21);
-          if (meta_lastsib(m)) --sp;
-        }
-        const SI<T> Ia = minus_scaled_outer<T, DT>(IA, Di, U);
-        const SV<T> pa = pA + mul(Ia, c) + (T)((DT)u * Di) * U;
-        const V3<T> d = wv3(tp, NWT, l, W_D);
-        SI<T> Iab = zeroSI<T>();
-        shift_adj(Ia, d, IAbp, Iab, db);
-        const SV<T> pab{pAbp.w, pAbp.v + cross(pAbp.w, d)};
-        db += cross(pa.v, pAbp.w);
-        // p^a = p^A + I^a c + U u / D
-        pAb += pab;
-        Iab += sym_outer(pab, c);
-        cb += mul(Ia, pab);
-        Ub += (T)((DT)u * Di) * pab;
-        const T gb = dot(U, pab);
-        ub += (T)((DT)gb * Di);
-        Db -= (T)((DT)gb * (DT)u * Di * Di);
-        // I^a = I^A - U U^T / D
-        IAb += Iab;
-        const SV<T> IbU = mul(Iab, U);
-        Ub -= (T)(DT(2) * Di) * IbU;
-        Db += (T)(Di * Di * (DT)dot(U, IbU));
+      // the parent's adjoints (zero for a root, whose terms below then add zeros)
+      SI<T> IAbp = cIAb;
+      SV<T> pAbp = cpAb;
+      if (par >= 0 && par != l - 1) {
+        IAbp = wsi(s.stk, WSW, sp - 1, 0);
+        pAbp = wsv(s.stk, WSW, sp - 1, 21);
+        if (meta_lastsib(m)) --sp;
       }
+      V3<T> d = wv3(tp, NWT, l, W_D);
+      if (par < 0) {
+        IAbp = zeroSI<T>();
+        pAbp = zeroSV<T>();
+        d = zero3<T>();
+      }
+      const SI<T> Ia = minus_scaled_outer<T, DT>(IA, Di, U);
+      const SV<T> pa = pA + mul(Ia, c) + (T)((DT)u * Di) * U;
+      SI<T> Iab = zeroSI<T>();
+      shift_adj(Ia, d, IAbp, Iab, db);
+      const SV<T> pab{pAbp.w, pAbp.v + cross(pAbp.w, d)};
+      db += cross(pa.v, pAbp.w);
+      // p^a = p^A + I^a c + U u / D
+      SV<T> pAb = pab;
+      Iab += sym_outer(pab, c);
+      cb += mul(Ia, pab);
+      Ub += (T)((DT)u * Di) * pab;
+      const T gb = dot(U, pab);
+      ub += (T)((DT)gb * Di);
+      Db -= (T)((DT)gb * (DT)u * Di * Di);
+      // I^a = I^A - U U^T / D
+      SI<T> IAb = Iab;
+      const SV<T> IbU = mul(Iab, U);
+      Ub -= (T)(DT(2) * Di) * IbU;
+      Db += (T)(Di * Di * (DT)dot(U, IbU));
       // u = tau - b qd - s.p^A_w,  D = s.U_w,  U = [A s; B^T s]
       gtau[vi] = ub;
       gqd[vi] -= s.P(l, P_DAMP) * ub;
@@ -557,13 +572,23 @@ SD void wstep_adjoint(const WSys<T>& s, Col<const T> q, Col<const T> qd, Col<T> 
       IAb.A += sym_outer(Ub.w, sx);
       IAb.B += scale(half, outer(sx, Ub.v));
       sb += mul(IA.A, Ub.w) + mul(IA.B, Ub.v);
-      if (tc) {
-        wsi(s.stk, WSW, sp, 0, IAb);
-        wsv(s.stk, WSW, sp, 21, pAb);
-        ++sp;
-      }
       cIAb = IAb;
       cpAb = pAb;
+      return Chain{IAb, pAb, cb, v, sb, db, R, vi, meta_treechild(m)};
+    };
+    auto push = [&](const Chain& k) {  // hand a branching link's adjoints to its later children
+      if (k.tc) {
+        wsi(s.stk, WSW, sp, 0, k.IAb);
+        wsv(s.stk, WSW, sp, 21, k.pAb);
+        ++sp;
+      }
+    };
+    auto per_link_part = [&](int l, const Chain& k) {
+      SV<T> cb = k.cb;
+      V3<T> sb = k.sb;
+      const M3<T>& R = k.R;
+      const SV<T>& v = k.v;
+      const V3<T> sx = col2(R);
       // p^A0 = v x* h, h = I^W v: I^W enters I^A additively, p^A0 enters p^A
       const T mass = s.P(l, P_M);
       const V3<T> com{s.P(l, P_C), s.P(l, P_C + 1), s.P(l, P_C + 2)};
@@ -575,8 +600,8 @@ SD void wstep_adjoint(const WSys<T>& s, Col<const T> q, Col<const T> qd, Col<T> 
       const V3<T> g = mass * rw;
       const SV<T> h = mul_iw(AW, g, mass, v);
       SV<T> vb = zeroSV<T>(), hb = zeroSV<T>();
-      crossf_adj(v, h, pAb, vb, hb);
-      SI<T> IWb = IAb;
+      crossf_adj(v, h, k.pAb, vb, hb);
+      SI<T> IWb = k.IAb;
       IWb += sym_outer(hb, v);
       vb += mul_iw(AW, g, mass, hb);
       const V3<T> gb = T(2) * unskew_grad(IWb.B);
@@ -588,17 +613,28 @@ SD void wstep_adjoint(const WSys<T>& s, Col<const T> q, Col<const T> qd, Col<T> 
       mb += dot(com, com) * trace(AWb) - dot(rw, mul(AWb, rw)) + dot(rw, gb);
       gm[l] += mb;
       // c = [v_w x s qd; v_v x s qd]
-      const T vl = qd[vi];
+      const T vl = s.tp(l, W_QD);
       const V3<T> sq = vl * sx;
       vb.w += cross(sq, cb.w);
       vb.v += cross(sq, cb.v);
       const V3<T> sqb = cross(cb.w, v.w) + cross(cb.v, v.v);
       sb += vl * sqb;
-      gqd[vi] += dot(sx, sqb);
+      gqd[k.vi] += dot(sx, sqb);
       wv3(ad, NWA, l, WA_S, sb);
-      wv3(ad, NWA, l, WA_DD, db);
-      wsv(tp, NWT, l, W_IA, vb);        // the tape's I^A words are dead from here on
+      wv3(ad, NWA, l, WA_DD, k.db);
+      wsv(tp, NWT, l, W_IA, vb);  // the tape's I^A words are dead from here on
       wm3(tp, NWT, l, W_IA + 6, Rb);
+    };
+    if (nl > 0) {
+      Chain prev = chain_part(0);
+      push(prev);
+      for (int l = 1; l < nl; ++l) {
+        const Chain cur = chain_part(l);
+        per_link_part(l - 1, prev);
+        push(cur);
+        prev = cur;
+      }
+      per_link_part(nl - 1, prev);
     }
   }
   // velocity, orientation and joint-angle adjoint (leaves -> root)
@@ -611,7 +647,7 @@ SD void wstep_adjoint(const WSys<T>& s, Col<const T> q, Col<const T> qd, Col<T> 
       if (s.pf > 0 && l - s.pf >= 0) {
         pf_fields(tp, NWT, l - s.pf, W_R, 15);
         pf_fields(tp, NWT, l - s.pf, W_IA, 15);
-        pf_fields(tp, NWT, l - s.pf, W_SC, 5);
+        pf_fields(tp, NWT, l - s.pf, W_SC, 6);
         pf_fields(ad, NWA, l - s.pf, WA_S, 6);
         pf_fields(s.prm, s.pstride, l - s.pf, P_E, 12);
       }
@@ -633,7 +669,7 @@ SD void wstep_adjoint(const WSys<T>& s, Col<const T> q, Col<const T> qd, Col<T> 
       }
       const M3<T> R = wm3(tp, NWT, l, W_R);
       const V3<T> sx = col2(R);
-      const T vl = qd[vi];
+      const T vl = s.tp(l, W_QD);
       // v = [v_p.w + s qd; v_p.v - d x v_p.w]
       sb += vl * vb.w;
       gqd[vi] += dot(sx, vb.w);

@@ -104,7 +104,7 @@ static WCounts wcount(int n) {
                                    I_SEMI_IMPLICIT, Col<F>{q2, B}, Col<F>{qd2, B});
   c.rec = g_flops;
   g_flops = 0;
-  wstep_adjoint<F, F>(s, Col<const F>{q, B}, Col<const F>{qd, B}, Col<F>{gq, B}, Col<F>{gqd, B}, Col<F>{gtau, B},
+  wstep_adjoint<F, F>(s, Col<F>{gq, B}, Col<F>{gqd, B}, Col<F>{gtau, B},
                       Col<F>{gm, B}, F(1e-3), I_SEMI_IMPLICIT);
   c.adj = g_flops;
   return c;

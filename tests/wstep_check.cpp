@@ -128,7 +128,7 @@ static std::vector<D> gradient(const Model& md, const std::vector<D>& x, const s
   wstep_forward<D, D, true, false>(wsys(md), Col<const D>{q.data(), 1}, Col<const D>{qd.data(), 1},
                                    Col<const D>{tau, 1}, kGrav, kDt, md.integ, Col<D>{q2.data(), 1},
                                    Col<D>{qd2.data(), 1});
-  wstep_adjoint<D, D>(wsys(md), Col<const D>{q.data(), 1}, Col<const D>{qd.data(), 1}, Col<D>{gq.data(), 1},
+  wstep_adjoint<D, D>(wsys(md), Col<D>{gq.data(), 1},
                       Col<D>{gqd.data(), 1}, Col<D>{gtau.data(), 1}, Col<D>{gm.data(), 1}, kDt, md.integ);
   std::vector<D> g = gq;
   g.insert(g.end(), gqd.begin(), gqd.end());
