@@ -61,7 +61,8 @@ def kernel_flops(model, storage):
     fwd_aligned = storage[0].startswith("aligned")
     bwd_aligned = storage[1].startswith("aligned")
     kf = "k_wrollout" if fwd_aligned else ("k_rollout_pipe" if storage[0] == "pipelined" else "k_rollout")
-    kb = "k_wbackward" if bwd_aligned else ("k_backward_pipe" if storage[1] == "pipelined" else "k_backward")
+    kb = ("k_wbackward_pipe" if storage[1].startswith("aligned_pipelined") else "k_wbackward") if bwd_aligned else \
+        ("k_backward_pipe" if storage[1] == "pipelined" else "k_backward")
     ff = flops_per_system_step(model, "wfwd" if fwd_aligned else "fwd")
     fb = (flops_per_system_step(model, "wrec") + flops_per_system_step(model, "wadj")) if bwd_aligned else \
         (flops_per_system_step(model, "fwd") + flops_per_system_step(model, "adj"))

@@ -186,7 +186,7 @@ __device__ __forceinline__ void wbackward_one(const DevModel<T>& m, int slot, co
   auto step_back = [&](long long t, Col<const T> q, Col<const T> qd, Col<const T> tau_t) {
     wstep_forward<T, DT, true, false>(s, q, qd, tau_t, g, m.dt, m.integ, Col<T>{nullptr, 0}, Col<T>{nullptr, 0});
     T* gt = gtau + t * nvm * B + b;
-    wstep_adjoint<T, DT>(s, gq, gqd, Col<T>{gt, B}, gm, m.dt, m.integ);
+    wstep_adjoint<T, DT, !ONCHIP && sizeof(T) == 4>(s, gq, gqd, Col<T>{gt, B}, gm, m.dt, m.integ);
     for (int d = nv; d < nvm; ++d) gt[d * B] = T(0);
     if (gtraj) {
       const T* gx = gtraj + t * NX * B + b;

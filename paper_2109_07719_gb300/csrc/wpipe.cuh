@@ -153,7 +153,7 @@ k_wbackward_pipe(DevModel<T> m, const T* __restrict__ ckpt, const T* __restrict_
         if (act) {
           const WSys<T> sc = sys_of_buf(buf);
           T* gt = gtau + t * nvm * B + b;
-          wstep_adjoint<T, DT>(sc, gq, gqd, Col<T>{gt, B}, gm, m.dt, m.integ);
+          wstep_adjoint<T, DT, !ONCHIP && sizeof(T) == 4>(sc, gq, gqd, Col<T>{gt, B}, gm, m.dt, m.integ);
           for (int d = nv; d < nvm; ++d) gt[d * B] = T(0);
           if (gtraj) {
             const T* gx = gtraj + t * NX * B + b;

@@ -235,68 +235,82 @@ SD void wstep_forward(const WSys<T>& s, Col<const T> q, Col<const T> qd, Col<con
                       int integ, Col<T> qo, Col<T> qdo) {
   T* tp = s.tape;
   const int nl = s.nl;
-  // outward: orientation, joint offset, axis, velocity
-  M3<T> R_prev = eye3<T>();
-  SV<T> v_prev = zeroSV<T>();
-  int sp = 0;  // entries on the stack
-  for (int l = 0; l < nl; ++l) {
-    if (s.pf > 0 && l + s.pf < nl) {
-      pf_meta(s, l + s.pf);
-      pf_fields(s.prm, s.pstride, l + s.pf, P_E, 12);
-    }
+  // outward: orientation, joint offset, axis, velocity (a root takes R_p = 1,
+  // v_p = 0, which gives its values exactly)
+  struct OwnOut {
+    M3<T> E;
+    V3<T> r;
+    T sn, cs, vl;
+    int m;
+  };
+  auto joint_terms = [&](int l) -> OwnOut {
     const int m = s.M(l);
-    const int par = meta_parent(m);
     T sn, cs;
     sincos_t(q[meta_qoff(m)], &sn, &cs);
     M3<T> Et;
     for (int i = 0; i < 9; ++i) Et.a[i] = s.P(l, P_E + i);
-    const M3<T> E = rotz_T_mm(sn, cs, Et);
-    const T vl = qd[meta_voff(m)];
-    M3<T> R;
-    SV<T> v;
+    return OwnOut{rotz_T_mm(sn, cs, Et), V3<T>{s.P(l, P_R), s.P(l, P_R + 1), s.P(l, P_R + 2)}, sn, cs,
+                  qd[meta_voff(m)], m};
+  };
+  M3<T> R_prev = eye3<T>();
+  SV<T> v_prev = zeroSV<T>();
+  int sp = 0;  // entries on the stack
+  auto chain_step = [&](int l, const OwnOut& o, M3<T> Rp, SV<T> vp) {
+    const int par = meta_parent(o.m);
     if (par < 0) {
-      R = transpose(E);
-      v = SV<T>{vl * col2(R), zero3<T>()};
-    } else {
-      M3<T> Rp = R_prev;
-      SV<T> vp = v_prev;
-      if (par != l - 1) {  // a later child of a branching link: its values on the stack top
-        Rp = wm3(s.stk, WSW, sp - 1, 0);
-        vp = wsv(s.stk, WSW, sp - 1, 9);
-        if (meta_lastsib(m)) --sp;
-      }
-      const V3<T> d = mul(Rp, V3<T>{s.P(l, P_R), s.P(l, P_R + 1), s.P(l, P_R + 2)});
-      R = mmT(Rp, E);
-      v = SV<T>{vp.w + vl * col2(R), vp.v - cross(d, vp.w)};
-      wv3(tp, NWT, l, W_D, d);
+      Rp = eye3<T>();
+      vp = zeroSV<T>();
     }
+    const V3<T> d = mul(Rp, o.r);
+    const M3<T> R = mmT(Rp, o.E);
+    const SV<T> v{vp.w + o.vl * col2(R), vp.v - cross(d, vp.w)};
+    wv3(tp, NWT, l, W_D, d);
     wm3(tp, NWT, l, W_R, R);
     wsv(tp, NWT, l, W_V, v);
     if (ADJ) {
-      s.tp(l, W_SC) = sn;
-      s.tp(l, W_SC + 1) = cs;
-      s.tp(l, W_QD) = vl;
+      s.tp(l, W_SC) = o.sn;
+      s.tp(l, W_SC + 1) = o.cs;
+      s.tp(l, W_QD) = o.vl;
     }
-    if (meta_treechild(m)) {
+    if (meta_treechild(o.m)) {
       wm3(s.stk, WSW, sp, 0, R);
       wsv(s.stk, WSW, sp, 9, v);
       ++sp;
     }
     R_prev = R;
     v_prev = v;
-  }
-  // inward: articulated inertias and bias forces
-  SI<T> cI = zeroSI<T>();
-  SV<T> cp = zeroSV<T>();
-  bool carry = false;
-  for (int l = nl - 1; l >= 0; --l) {
-    if (s.pf > 0 && l - s.pf >= 0) {
-      pf_fields(tp, NWT, l - s.pf, W_R, 15);
-      pf_fields(tp, NWT, l - s.pf, W_D, 3);
-      pf_fields(s.prm, s.pstride, l - s.pf, P_M, NPRM_W - P_M);
+  };
+  {
+    for (int l = 0; l < nl; ++l) {
+      if (s.pf > 0 && l + s.pf < nl) {
+        pf_meta(s, l + s.pf);
+        pf_fields(s.prm, s.pstride, l + s.pf, P_E, 12);
+      }
+      const OwnOut cur = joint_terms(l);
+      const int par = meta_parent(cur.m);
+      M3<T> Rp = R_prev;
+      SV<T> vp = v_prev;
+      if (par >= 0 && par != l - 1) {
+        Rp = wm3(s.stk, WSW, sp - 1, 0);
+        vp = wsv(s.stk, WSW, sp - 1, 9);
+        if (meta_lastsib(cur.m)) --sp;
+      }
+      chain_step(l, cur, Rp, vp);
     }
+  }
+  // inward: articulated inertias and bias forces, from each link's own terms (its
+  // inertia in world axes, velocity-product and bias terms) and its children's
+  // contributions
+  struct Own {
+    SI<T> IA;
+    SV<T> pA, c;
+    V3<T> sx;
+    T tl;
+    int m;
+  };
+  auto own_terms = [&](int l) -> Own {
     const int m = s.M(l);
-    const int par = meta_parent(m), vo = meta_voff(m);
+    const int vo = meta_voff(m);
     const M3<T> R = wm3(tp, NWT, l, W_R);
     const SV<T> v = wsv(tp, NWT, l, W_V);
     const V3<T> sx = col2(R);
@@ -310,21 +324,23 @@ SD void wstep_forward(const WSys<T>& s, Col<const T> q, Col<const T> qd, Col<con
                    s.P(l, P_IC + 5)};
     const S3<T> AW = rot_sym(R, body_A(mass, com, Ic));
     const V3<T> g = mass * mul(R, com);
-    SV<T> pA = crossf(v, mul_iw(AW, g, mass, v));
-    SI<T> IA{AW, skew(g), S3<T>{mass, mass, mass, T(0), T(0), T(0)}};
-    if (carry) {
-      IA += cI;
-      pA += cp;
-    }
-    if (meta_treechild(m)) {  // the contributions of the children after link l + 1
-      --sp;
-      IA += wsi(s.stk, WSW, sp, 0);
-      pA += wsv(s.stk, WSW, sp, 21);
-    }
-    carry = false;
+    const SV<T> pA = crossf(v, mul_iw(AW, g, mass, v));
+    return Own{SI<T>{AW, skew(g), S3<T>{mass, mass, mass, T(0), T(0), T(0)}}, pA, c, sx, tl, m};
+  };
+  SI<T> cI = zeroSI<T>();  // link l + 1's contribution when l is its parent
+  SV<T> cp = zeroSV<T>();
+  bool carry = false;
+  // the recursion step of link l from its own terms o, to which its children's
+  // contributions have been added
+  auto recursion = [&](int l, const Own& o) {
+    const int m = o.m;
+    const int par = meta_parent(m);
+    const V3<T> sx = o.sx;
+    const SI<T>& IA = o.IA;
+    const SV<T>& pA = o.pA;
     const SV<T> U{mul(IA.A, sx), mulT(IA.B, sx)};
     const DT Di = DT(1) / (DT)dot(sx, U.w);
-    const T u = tl - dot(sx, pA.w);
+    const T u = o.tl - dot(sx, pA.w);
     wsv(tp, NWT, l, W_U, U);
     {
       const T hi = (T)Di;
@@ -332,29 +348,49 @@ SD void wstep_forward(const WSys<T>& s, Col<const T> q, Col<const T> qd, Col<con
       s.tp(l, W_DI + 1) = (T)(Di - (DT)hi);
     }
     s.tp(l, W_u) = u;
-    wsv(tp, NWT, l, W_C, c);
+    wsv(tp, NWT, l, W_C, o.c);
     if (ADJ) {
       wsi(tp, NWT, l, W_IA, IA);
       wsv(tp, NWT, l, W_PA, pA);
     }
-    if (par >= 0) {
-      const SI<T> Ia = minus_scaled_outer<T, DT>(IA, Di, U);
-      const SV<T> pa = pA + mul(Ia, c) + (T)((DT)u * Di) * U;
-      const V3<T> d = wv3(tp, NWT, l, W_D);
-      const SI<T> Y = shift(Ia, d);
-      const SV<T> pn{pa.w + cross(d, pa.v), pa.v};
-      if (par == l - 1) {
-        cI = Y;
-        cp = pn;
-        carry = true;
-      } else if (meta_lastsib(m)) {
-        wsi(s.stk, WSW, sp, 0, Y);
-        wsv(s.stk, WSW, sp, 21, pn);
-        ++sp;
-      } else {
-        wsi(s.stk, WSW, sp - 1, 0, wsi(s.stk, WSW, sp - 1, 0) + Y);
-        wsv(s.stk, WSW, sp - 1, 21, wsv(s.stk, WSW, sp - 1, 21) + pn);
+    // the contribution to the parent (computed for a root too, with d = 0, and dropped)
+    V3<T> d = wv3(tp, NWT, l, W_D);
+    if (par < 0) d = zero3<T>();
+    const SI<T> Ia = minus_scaled_outer<T, DT>(IA, Di, U);
+    const SV<T> pa = pA + mul(Ia, o.c) + (T)((DT)u * Di) * U;
+    const SI<T> Y = shift(Ia, d);
+    const SV<T> pn{pa.w + cross(d, pa.v), pa.v};
+    carry = par == l - 1 && par >= 0;
+    if (carry) {
+      cI = Y;
+      cp = pn;
+    } else if (par >= 0 && meta_lastsib(m)) {
+      wsi(s.stk, WSW, sp, 0, Y);
+      wsv(s.stk, WSW, sp, 21, pn);
+      ++sp;
+    } else if (par >= 0) {
+      wsi(s.stk, WSW, sp - 1, 0, wsi(s.stk, WSW, sp - 1, 0) + Y);
+      wsv(s.stk, WSW, sp - 1, 21, wsv(s.stk, WSW, sp - 1, 21) + pn);
+    }
+  };
+  {
+    for (int l = nl - 1; l >= 0; --l) {
+      if (s.pf > 0 && l - s.pf >= 0) {
+        pf_fields(tp, NWT, l - s.pf, W_R, 15);
+        pf_fields(tp, NWT, l - s.pf, W_D, 3);
+        pf_fields(s.prm, s.pstride, l - s.pf, P_M, NPRM_W - P_M);
       }
+      Own cur = own_terms(l);
+      if (carry) {
+        cur.IA += cI;
+        cur.pA += cp;
+      }
+      if (meta_treechild(cur.m)) {
+        --sp;
+        cur.IA += wsi(s.stk, WSW, sp, 0);
+        cur.pA += wsv(s.stk, WSW, sp, 21);
+      }
+      recursion(l, cur);
     }
   }
   // outward: accelerations (and the integrator)
@@ -414,7 +450,7 @@ SD void wstep_forward(const WSys<T>& s, Col<const T> q, Col<const T> qd, Col<con
 // integrator and acceleration adjoint (leaves -> root), the articulated-inertia
 // adjoint with the per-link inertia and velocity-product adjoints (root -> leaves),
 // the velocity and orientation adjoint and the joint angles' (leaves -> root).
-template <class T, class DT>
+template <class T, class DT, bool ILP = false>
 SD void wstep_adjoint(const WSys<T>& s, Col<T> gq, Col<T> gqd, Col<T> gtau,
                       Col<T> gm, T dt, int integ) {
   T* tp = s.tape;
@@ -489,10 +525,12 @@ SD void wstep_adjoint(const WSys<T>& s, Col<T> gq, Col<T> gqd, Col<T> gtau,
   // articulated-inertia adjoint (root -> leaves) with each link's inertia,
   // bias-force and velocity-product adjoints.  Each link's work has a part on the
   // chain (from its parent's adjoints of I^A and p^A to its own, which its children
-  // need) and a per-link part that nothing downstream in this pass waits for; the
-  // loop runs link l's chain part beside link l - 1's per-link part, so that one
-  // thread has two independent instruction streams (the same arithmetic in the
-  // same order per link as running the two parts back to back).
+  // need) and a per-link part that nothing downstream in this pass waits for; with
+  // ILP the loop runs link l's chain part beside link l - 1's per-link part, so
+  // that one thread has two independent instruction streams (the same arithmetic
+  // in the same order per link as running the two parts back to back).  It pays
+  // where the tape is in global memory and the registers suffice (FP32 storage);
+  // on chip the longer code costs more in instruction fetch than it gains.
   {
     SI<T> cIAb = zeroSI<T>();
     SV<T> cpAb = zeroSV<T>();
@@ -625,7 +663,13 @@ SD void wstep_adjoint(const WSys<T>& s, Col<T> gq, Col<T> gqd, Col<T> gtau,
       wsv(tp, NWT, l, W_IA, vb);  // the tape's I^A words are dead from here on
       wm3(tp, NWT, l, W_IA + 6, Rb);
     };
-    if (nl > 0) {
+    if (!ILP) {
+      for (int l = 0; l < nl; ++l) {
+        const Chain k = chain_part(l);
+        push(k);
+        per_link_part(l, k);
+      }
+    } else if (nl > 0) {
       Chain prev = chain_part(0);
       push(prev);
       for (int l = 1; l < nl; ++l) {

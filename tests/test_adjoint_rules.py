@@ -116,7 +116,9 @@ def test_world_aligned_step(tmp_path):
     damping, both integrators).  The models are stored in the library's
     depth-first order with a stack exactly as deep as that order says, followed by
     NaN guard entries that must stay untouched; the order's own invariants are
-    checked on random trees and forests.  A 0.1 % error planted in one
+    checked on random trees and forests.  Both loop orders of the adjoint run
+    (the plain one and the interleaved one of the FP32 global-tape kernels, two
+    links' independent work per loop body) and agree.  A 0.1 % error planted in one
     adjoint term shows as 5e-7 to 6e-5 here."""
     cxx = shutil.which("g++")
     if cxx is None:
@@ -127,13 +129,14 @@ def test_world_aligned_step(tmp_path):
     res = {line.split()[0]: float(line.split()[1]) for line in out.strip().splitlines()}
     cases = {"chain", "damped_chain", "branched_tree", "tree_explicit", "single_link", "two_roots",
              "random_tree_bf2", "random_tree_bf3", "star", "caterpillar"}
-    assert set(res) == {f"{k}_{c}" for k in ("forward", "adjoint", "depth", "guards") for c in cases} | {
+    assert set(res) == {f"{k}_{c}" for k in ("forward", "adjoint", "depth", "guards", "ilp") for c in cases} | {
         "order_invariants"}
     assert res["order_invariants"] == 1
     for c in cases:
         assert res[f"forward_{c}"] < 1e-13, (c, res[f"forward_{c}"])
         assert res[f"adjoint_{c}"] < 1e-7, (c, res[f"adjoint_{c}"])
         assert res[f"guards_{c}"] == 1, c
+        assert res[f"ilp_{c}"] < 1e-12, (c, res[f"ilp_{c}"])   # the two loop orders agree
     depth = {"chain": 0, "damped_chain": 0, "single_link": 0, "branched_tree": 2, "star": 1, "two_roots": 1,
              "caterpillar": 8}
     for c, d in depth.items():

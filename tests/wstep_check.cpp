@@ -72,6 +72,23 @@ static bool guards_intact(const Model& md) {
 
 static const V3<D> kGrav{0, 0, -9.81};
 static const D kDt = 1e-3;
+static V3<D> kGravD() { return kGrav; }
+static D kDtD() { return kDt; }
+
+// the adjoint's interleaved loop order (two links' independent work in one loop
+// body, the kernels' choice with an FP32 global tape) or the plain one
+static bool g_ilp = false;
+template <bool ADJ, bool INTEG>
+static void wfwd(const WSys<D>& s, const D* q, const D* qd, const D* tau, D* qo, D* qdo, int integ) {
+  wstep_forward<D, D, ADJ, INTEG>(s, Col<const D>{q, 1}, Col<const D>{qd, 1}, Col<const D>{tau, 1}, kGravD(), kDtD(),
+                                  integ, Col<D>{qo, 1}, Col<D>{qdo, 1});
+}
+static void wadjoint(const WSys<D>& s, D* gq, D* gqd, D* gtau, D* gm, int integ) {
+  if (g_ilp)
+    wstep_adjoint<D, D, true>(s, Col<D>{gq, 1}, Col<D>{gqd, 1}, Col<D>{gtau, 1}, Col<D>{gm, 1}, kDtD(), integ);
+  else
+    wstep_adjoint<D, D, false>(s, Col<D>{gq, 1}, Col<D>{gqd, 1}, Col<D>{gtau, 1}, Col<D>{gm, 1}, kDtD(), integ);
+}
 
 static WSys<D> wsys(const Model& md) {
   WSys<D> s{prm, meta, wtape, wadj, md.n};
@@ -89,9 +106,7 @@ static D forward_agreement(const Model& md, int trials = 8) {
     aba_forward<D, D, true>(s, Col<const D>{q.data(), 1}, Col<const D>{qd.data(), 1}, Col<const D>{tau.data(), 1},
                             kGrav);
     std::vector<D> q2 = q, qd2 = qd;
-    wstep_forward<D, D, true, false>(wsys(md), Col<const D>{q.data(), 1}, Col<const D>{qd.data(), 1},
-                                     Col<const D>{tau.data(), 1}, kGrav, kDt, md.integ, Col<D>{q2.data(), 1},
-                                     Col<D>{qd2.data(), 1});
+    wfwd<true, false>(wsys(md), q.data(), qd.data(), tau.data(), q2.data(), qd2.data(), md.integ);
     D mx = 0, err = 0;
     for (int l = 0; l < md.n; ++l) {
       const D a = tape[(l * NTAPE + T_QDD) * LANES], b = wtape[(l * NWT + W_QDD) * LANES];
@@ -109,9 +124,7 @@ static D loss(const Model& md, const std::vector<D>& x, const std::vector<D>& wq
   std::vector<D> q(x.begin(), x.begin() + n), qd(x.begin() + n, x.begin() + 2 * n);
   const D* tau = x.data() + 2 * n;
   for (int l = 0; l < n; ++l) prm[(l * NPRM + P_M) * LANES] = x[3 * n + l];
-  wstep_forward<D, D, false, true>(wsys(md), Col<const D>{q.data(), 1}, Col<const D>{qd.data(), 1},
-                                   Col<const D>{tau, 1}, kGrav, kDt, md.integ, Col<D>{q.data(), 1},
-                                   Col<D>{qd.data(), 1});
+  wfwd<false, true>(wsys(md), q.data(), qd.data(), tau, q.data(), qd.data(), md.integ);
   D L = 0;
   for (int i = 0; i < n; ++i) L += wq[i] * q[i] + wqd[i] * qd[i];
   return L;
@@ -125,11 +138,8 @@ static std::vector<D> gradient(const Model& md, const std::vector<D>& x, const s
   for (int l = 0; l < n; ++l) prm[(l * NPRM + P_M) * LANES] = x[3 * n + l];
   for (D& v : wadj) v = std::nan("");  // every adjoint word is written before it is read
   std::vector<D> gq = wq, gqd = wqd, gtau(n, 0.0), gm(n, 0.0), q2 = q, qd2 = qd;
-  wstep_forward<D, D, true, false>(wsys(md), Col<const D>{q.data(), 1}, Col<const D>{qd.data(), 1},
-                                   Col<const D>{tau, 1}, kGrav, kDt, md.integ, Col<D>{q2.data(), 1},
-                                   Col<D>{qd2.data(), 1});
-  wstep_adjoint<D, D>(wsys(md), Col<D>{gq.data(), 1},
-                      Col<D>{gqd.data(), 1}, Col<D>{gtau.data(), 1}, Col<D>{gm.data(), 1}, kDt, md.integ);
+  wfwd<true, false>(wsys(md), q.data(), qd.data(), tau, q2.data(), qd2.data(), md.integ);
+  wadjoint(wsys(md), gq.data(), gqd.data(), gtau.data(), gm.data(), md.integ);
   std::vector<D> g = gq;
   g.insert(g.end(), gqd.begin(), gqd.end());
   g.insert(g.end(), gtau.begin(), gtau.end());
@@ -260,8 +270,33 @@ int main() {
     Model md;
     build(md, c.parent, c.damping);
     md.integ = c.integ;
-    std::printf("forward_%s %.3e\n", c.name, forward_agreement(md));
-    std::printf("adjoint_%s %.3e\n", c.name, adjoint_check(md));
+    // both loop orders: the worse of the two against the references, and the two
+    // against each other on one gradient
+    D fw = 0, aj = 0;
+    for (int ilp = 0; ilp < 2; ++ilp) {
+      g_ilp = ilp;
+      fw = std::fmax(fw, forward_agreement(md));
+      aj = std::fmax(aj, adjoint_check(md));
+    }
+    std::printf("forward_%s %.3e\n", c.name, fw);
+    std::printf("adjoint_%s %.3e\n", c.name, aj);
+    {
+      const int n = md.n;
+      std::vector<D> x, wq(n), wqd(n);
+      for (int i = 0; i < 4 * n; ++i) x.push_back(i >= 3 * n ? U(0.5, 2.0) : U());
+      for (D& v : wq) v = U();
+      for (D& v : wqd) v = U();
+      g_ilp = false;
+      const std::vector<D> g0 = gradient(md, x, wq, wqd);
+      g_ilp = true;
+      const std::vector<D> g1 = gradient(md, x, wq, wqd);
+      D mx = 0, err = 0;
+      for (size_t i = 0; i < g0.size(); ++i) {
+        mx = std::fmax(mx, std::fabs(g0[i]));
+        err = std::fmax(err, std::fabs(g0[i] - g1[i]));
+      }
+      std::printf("ilp_%s %.3e\n", c.name, err / std::fmax(mx, 1e-300));
+    }
     std::printf("depth_%s %d\n", c.name, md.depth);
     std::printf("guards_%s %d\n", c.name, guards_intact(md) ? 1 : 0);
   }
