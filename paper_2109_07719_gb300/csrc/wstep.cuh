@@ -48,9 +48,11 @@ namespace abasim {
 
 // Per-link tape of the world-aligned step, [link][field][lane]: orientation R,
 // velocity v, velocity-product term c, U, 1/D (hi/lo pair), u, the articulated
-// inertia and bias force after the children's contributions (I^A, p^A), a' and
-// qdd, the joint's sin/cos, the joint offset d and the joint rate qd (so that the
-// adjoint reads every per-link value from its own tape words).
+// inertia I^a = I^A - U U^T / D handed to the parent, p^a's linear and p^A's
+// angular part (what the adjoint reads of the bias forces), a' and qdd, the
+// joint's sin/cos, the joint offset d and the joint rate qd (so that the adjoint
+// reads every per-link value from its own tape words and recomputes none of the
+// articulated quantities).
 enum : int {
   W_R = 0, W_V = 9, W_C = 15, W_U = 21, W_DI = 27, W_u = 29, W_IA = 30, W_PA = 51, W_AP = 57, W_QDD = 63,
   W_SC = 64, W_D = 66, W_QD = 69, NWT = 70
@@ -349,15 +351,16 @@ SD void wstep_forward(const WSys<T>& s, Col<const T> q, Col<const T> qd, Col<con
     }
     s.tp(l, W_u) = u;
     wsv(tp, NWT, l, W_C, o.c);
-    if (ADJ) {
-      wsi(tp, NWT, l, W_IA, IA);
-      wsv(tp, NWT, l, W_PA, pA);
-    }
     // the contribution to the parent (computed for a root too, with d = 0, and dropped)
     V3<T> d = wv3(tp, NWT, l, W_D);
     if (par < 0) d = zero3<T>();
     const SI<T> Ia = minus_scaled_outer<T, DT>(IA, Di, U);
     const SV<T> pa = pA + mul(Ia, o.c) + (T)((DT)u * Di) * U;
+    if (ADJ) {  // what the adjoint reads of them: I^a, p^a's linear part and p^A's angular part
+      wsi(tp, NWT, l, W_IA, Ia);
+      wv3(tp, NWT, l, W_PA, pa.v);
+      wv3(tp, NWT, l, W_PA + 3, pA.w);
+    }
     const SI<T> Y = shift(Ia, d);
     const SV<T> pn{pa.w + cross(d, pa.v), pa.v};
     carry = par == l - 1 && par >= 0;
@@ -552,8 +555,8 @@ SD void wstep_adjoint(const WSys<T>& s, Col<T> gq, Col<T> gqd, Col<T> gtau,
       }
       const int m = s.M(l);
       const int par = meta_parent(m), vi = meta_voff(m);
-      const SI<T> IA = wsi(tp, NWT, l, W_IA);
-      const SV<T> pA = wsv(tp, NWT, l, W_PA);
+      const SI<T> Ia = wsi(tp, NWT, l, W_IA);
+      const V3<T> pav = wv3(tp, NWT, l, W_PA), pAw = wv3(tp, NWT, l, W_PA + 3);
       const SV<T> U = wsv(tp, NWT, l, W_U);
       const DT Di = (DT)s.tp(l, W_DI) + (DT)s.tp(l, W_DI + 1);
       const T u = s.tp(l, W_u);
@@ -581,12 +584,10 @@ SD void wstep_adjoint(const WSys<T>& s, Col<T> gq, Col<T> gqd, Col<T> gtau,
         pAbp = zeroSV<T>();
         d = zero3<T>();
       }
-      const SI<T> Ia = minus_scaled_outer<T, DT>(IA, Di, U);
-      const SV<T> pa = pA + mul(Ia, c) + (T)((DT)u * Di) * U;
       SI<T> Iab = zeroSI<T>();
       shift_adj(Ia, d, IAbp, Iab, db);
       const SV<T> pab{pAbp.w, pAbp.v + cross(pAbp.w, d)};
-      db += cross(pa.v, pAbp.w);
+      db += cross(pav, pAbp.w);
       // p^a = p^A + I^a c + U u / D
       SV<T> pAb = pab;
       Iab += sym_outer(pab, c);
@@ -603,13 +604,14 @@ SD void wstep_adjoint(const WSys<T>& s, Col<T> gq, Col<T> gqd, Col<T> gtau,
       // u = tau - b qd - s.p^A_w,  D = s.U_w,  U = [A s; B^T s]
       gtau[vi] = ub;
       gqd[vi] -= s.P(l, P_DAMP) * ub;
-      sb -= ub * pA.w;
+      sb -= ub * pAw;
       pAb.w -= ub * sx;
       sb += Db * U.w;
       Ub.w += Db * sx;
       IAb.A += sym_outer(Ub.w, sx);
       IAb.B += scale(half, outer(sx, Ub.v));
-      sb += mul(IA.A, Ub.w) + mul(IA.B, Ub.v);
+      // the top rows of I^A Ub, with I^A = I^a + U U^T / D
+      sb += mul(Ia.A, Ub.w) + mul(Ia.B, Ub.v) + (T)(Di * (DT)dot(U, Ub)) * U.w;
       cIAb = IAb;
       cpAb = pAb;
       return Chain{IAb, pAb, cb, v, sb, db, R, vi, meta_treechild(m)};
