@@ -197,3 +197,69 @@ def test_pipelined_adjoint_persistent_and_per_step_terms():
         assert torch.equal(u, v)
     for name, u, v in zip(NAMES[3:], outs[0], outs[1]):
         check(name, v.cpu().numpy(), u.cpu().numpy(), 1e-6)
+
+
+def _nested_trees(big=True, reps=8, precision="fp64", seed=11):
+    """Trees whose stack of parent values runs deep, repeated with fresh link
+    parameters: a caterpillar (each spine link's first child continues the spine,
+    its leaf comes later, so every spine link keeps a stack entry: depth 19, or 3
+    for the small one), a star, a forest of three roots, a chain and a random tree
+    with up to three children per link."""
+    if big:
+        cat = [-1] + list(range(0, 19)) + list(range(0, 20))
+        rng0 = np.random.default_rng(seed)
+        rnd, kids, open_ = [-1], [0] * 30, [0]
+        for i in range(1, 30):
+            j = int(rng0.integers(len(open_)))
+            p = open_[j]
+            rnd.append(p)
+            kids[p] += 1
+            if kids[p] >= 3:
+                open_.pop(j)
+            open_.append(i)
+        shapes = [cat, [-1] + [0] * 8, [-1, 0, 0, -1, 3, 3, 5, -1, 7], [-1] + list(range(0, 14)), rnd]
+    else:
+        shapes = [[-1, 0, 1, 2, 0, 1, 2, 3], [-1, 0, 0, 0, 0], [-1, 0, 0, -1, 3, 3, 5, -1, 7]]
+    shapes = shapes * reps
+    counts = [len(s) for s in shapes]
+    parents = np.concatenate([np.asarray(s) for s in shapes])
+    starts = np.zeros(len(parents), bool)
+    starts[np.cumsum([0] + counts[:-1])] = True
+    rng = np.random.default_rng(seed + 1)
+    axis, r, mass, com, Ic = wl._random_tree_params(rng, parents, starts)
+    r[parents < 0] = 0.0
+    model = wl._assemble(counts, parents, np.zeros(len(parents)), axis, r, mass, com, Ic, 1e-3,
+                         (0.0, 0.0, -9.81), "nested_trees")
+    q0, qd0, mask = wl._state_arrays(model)
+    q0[:] = rng.uniform(-1, 1, q0.shape) * (np.arange(model.nq_max)[:, None] < model.nq_per_system()[None, :])
+    mask[:] = (np.arange(model.nv_max)[:, None] < model.nv_per_system()[None, :])
+    return wl.Workload(model, q0, qd0, 30, 1.0, seed, precision, mask)
+
+
+@pytest.mark.parametrize("big", [True, False])
+def test_deeply_nested_trees_fp64(big):
+    """The stack of parent values at depth 19 (and in shared memory for the small
+    trees), stars, forests: the world-aligned kernels, one-warp and pipelined,
+    against the link-frame kernels (which keep one accumulator per branching
+    link) within 1e-10 (states) and 1e-9 (gradients)."""
+    work = _nested_trees(big)
+    sim, *x = _setup(work, "fp64")
+    a = _run(sim, "one_warp", *x)
+    for space in ("aligned", "aligned_pipelined"):
+        b = _run(sim, space, *x)
+        assert sim.last_storage()[1].startswith(space)
+        for name, u, v in zip(NAMES, a, b):
+            check(name, v.cpu().numpy(), u.cpu().numpy(), 1e-10 if name in ("qT", "qdT", "traj") else 1e-9)
+    assert sim.status().sum() == 0
+
+
+def test_deeply_nested_trees_fp32_interleaved_adjoint():
+    """FP32 with the tapes in global memory, where the adjoint interleaves two
+    links' independent work: against the FP32 link-frame kernels."""
+    work = _nested_trees(True, precision="fp32")
+    sim, *x = _setup(work, "fp32")
+    a = _run(sim, "one_warp", *x)
+    b = _run(sim, "aligned_pipelined", *x)
+    assert sim.last_storage()[1] == "aligned_pipelined_global"
+    for name, u, v in zip(NAMES, a, b):
+        check(name, v.cpu().numpy(), u.cpu().numpy(), 1e-4)
