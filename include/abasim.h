@@ -139,7 +139,9 @@ typedef struct sim_model_desc {
 typedef struct sim_handle sim_handle;
 
 /* Validate and pack a model (Sec. 2: state x = [q, qd], control u = tau), upload
- * its constants to the current device and allocate the per-step tape.
+ * its constants to the current device and allocate the per-step tape.  Each
+ * system's links are stored in depth-first preorder (children in the model's
+ * order); coordinates, masses and every result keep the model's numbering.
  * Returns SIM_EINVAL with a message for an invalid tree, joint, axis, rotation or
  * inertia; SIM_ENOMEM / SIM_ECUDA for device failures.  *out is NULL on error. */
 int sim_create(const sim_model_desc* desc, sim_handle** out);
