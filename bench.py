@@ -192,9 +192,13 @@ def run_ours(args):
         sim.set_prefetch(args.prefetch)
     if args.state_accumulation != "fp32":
         sim.set_state_accumulation(args.state_accumulation)
+    tuned = None
     if args.autotune:
-        sim.autotune(torch.tensor(work.q0, dtype=sim.dtype, device=sim.device),
-                     torch.tensor(work.qd0, dtype=sim.dtype, device=sim.device))
+        from paper_2109_07719_gb300 import autotune as _at
+        best = sim.autotune(torch.tensor(work.q0, dtype=sim.dtype, device=sim.device),
+                            torch.tensor(work.qd0, dtype=sim.dtype, device=sim.device))
+        tuned = {"threads": best[0], "schedule": "persistent" if best[1] else "grid",
+                 "kernels": _at.TAPE_SPACE[best[2]]}
     elif args.block or args.persistent:
         sim.set_launch(args.block, args.persistent)
     dev, dt = sim.device, sim.dtype
@@ -305,7 +309,7 @@ def run_ours(args):
                    "block": sim.launch[0], "schedule": "persistent" if sim.launch[1] else "grid",
                    "slot_order": "system" if args.keep_order else "link count",
                    "batch_layout": "by link count (the packing order)" if args.slot_layout else "as generated",
-                   "tape": args.tape, "replay": args.replay, "prefetch": args.prefetch, "state_accumulation": args.state_accumulation,
+                   "tape": args.tape, "autotuned": tuned, "replay": args.replay, "prefetch": args.prefetch, "state_accumulation": args.state_accumulation,
                    "storage": {"rollout": storage[0], "adjoint": storage[1]},
                    "cuda_graph": bool(args.graph), "contacts": bool(args.contacts),
                    "joint_limits": bool(args.limits)},
@@ -850,7 +854,9 @@ def main():
     ap.add_argument("--slot-layout", action=argparse.BooleanOptionalAction, default=None,
                     help="lay the batch out by link count, the library's packing order, so each warp's "
                          "streams are whole cache lines (default: on for the uneven trees, --config 4)")
-    ap.add_argument("--autotune", action="store_true")
+    ap.add_argument("--autotune", action=argparse.BooleanOptionalAction, default=None,
+                    help="time the kernel families and launch shapes on a short probe and keep the fastest "
+                         "(default: on for the uneven-tree batch, whose configuration names autotuned grouping)")
     ap.add_argument("--tape", default="auto",
                     choices=["auto", "global", "shared", "pipelined", "one_warp", "aligned", "aligned_pipelined"])
     ap.add_argument("--prefetch", type=int, default=None,
@@ -878,6 +884,8 @@ def main():
         args.contacts = args.config == 3
     if args.slot_layout is None:
         args.slot_layout = args.config == 4
+    if args.autotune is None:  # a forced kernel family or launch shape is kept as given
+        args.autotune = args.config == 4 and args.tape == "auto" and not (args.block or args.persistent)
     if args.k_sweep is None:
         args.k_sweep = "10,100" if args.config == 4 and args.k == 1 else ""
     args.warmup = max(args.warmup, 3)
